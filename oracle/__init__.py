@@ -1,0 +1,278 @@
+"""FP64 CPU oracle for the discrete Radon transform (TEST INFRASTRUCTURE ONLY).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA library never touches it and it
+never touches the CUDA library: it has its own geometry defaults, its own ray
+construction and its own interpolation (``radon_oracle.c``), compiled with gcc
+in IEEE double precision.
+
+Readings of the paper that this oracle encodes (each one is also listed with its
+justification in the design notes):
+
+* geometry conventions of Sections 3.1.1 / 3.1.2 -- see ``radon_oracle.c``;
+* ``det_count`` defaults to the image size, ``det_spacing`` to 1 (Section 3.1.1);
+* fan beam: ``det_distance`` defaults to ``source_distance`` and ``det_spacing``
+  to the magnified image width over the detector count,
+  ``(S + Ddet) / S * N / D`` (Section 3.1.2; reproduces the worked value 2.0);
+* Landweber iteration ``x <- x - alpha A^T (A x - y)`` (Section 4.2) with the
+  step from a power iteration on ``A^T A`` (Section 4.2), and its reverse mode.
+
+Parity status of every function is pinned by tests in ``tests/test_oracle_*.py``
+(closed forms, exact symmetries, analytic projections, dense-matrix transposes,
+finite differences).
+"""
+
+from __future__ import annotations
+
+import contextlib
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "radon_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``radon_oracle.c`` into ``liboracle.so`` (gcc, -O2, OpenMP, no fast-math)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _CGeom(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int),
+        ("n_angles", ctypes.c_int),
+        ("angles", ctypes.POINTER(ctypes.c_double)),
+        ("det_count", ctypes.c_int),
+        ("det_spacing", ctypes.c_double),
+        ("step", ctypes.c_double),
+        ("fan", ctypes.c_int),
+        ("source_distance", ctypes.c_double),
+        ("det_distance", ctypes.c_double),
+    ]
+
+
+def _bind(lib):
+    P = ctypes.POINTER
+    lib.oracle_ray.argtypes = [P(_CGeom), ctypes.c_int, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double)]
+    lib.oracle_sample_count.argtypes = [P(_CGeom)]
+    lib.oracle_sample_count.restype = ctypes.c_int64
+    lib.oracle_ray_sample_counts.argtypes = [P(_CGeom), P(ctypes.c_int64)]
+    lib.oracle_forward.argtypes = [P(_CGeom), P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int]
+    lib.oracle_adjoint.argtypes = [P(_CGeom), P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int]
+    lib.oracle_num_threads.restype = ctypes.c_int
+    return lib
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = _bind(ctypes.CDLL(build()))
+    return _lib
+
+
+@contextlib.contextmanager
+def using_library(path: str):
+    """Test hook: run this wrapper against another build of the oracle source (planted mistakes)."""
+    global _lib
+    saved = _load()
+    _lib = _bind(ctypes.CDLL(os.path.abspath(path)))
+    try:
+        yield
+    finally:
+        _lib = saved
+
+
+@dataclass
+class Geometry:
+    """Oracle geometry.  ``kind`` is "parallel" or "fan"; ``None`` fields take the paper's defaults."""
+
+    kind: str
+    n: int
+    angles: np.ndarray
+    det_count: int | None = None
+    det_spacing: float | None = None
+    step: float = 1.0
+    source_distance: float = 0.0
+    det_distance: float | None = None
+    _c: _CGeom = field(default=None, repr=False)
+    _angles64: np.ndarray = field(default=None, repr=False)
+
+    def __post_init__(self):
+        if self.kind not in ("parallel", "fan"):
+            raise ValueError("kind must be 'parallel' or 'fan'")
+        self._angles64 = np.ascontiguousarray(np.asarray(self.angles, dtype=np.float64))
+        if self.det_count is None or self.det_count <= 0:
+            self.det_count = self.n                      # Section 3.1.1: 512 detectors for N = 512
+        if self.kind == "fan":
+            if self.source_distance <= 0:
+                raise ValueError("fan beam needs source_distance > 0")
+            if self.det_distance is None or self.det_distance <= 0:
+                self.det_distance = self.source_distance  # Section 3.1.2 default
+            if self.det_spacing is None or self.det_spacing <= 0:
+                # Section 3.1.2: smallest spacing whose bins span the magnified image width
+                self.det_spacing = (self.source_distance + self.det_distance) / self.source_distance \
+                    * self.n / self.det_count
+        else:
+            if self.det_spacing is None or self.det_spacing <= 0:
+                self.det_spacing = 1.0                   # Section 3.1.1 default
+            self.det_distance = 0.0 if self.det_distance is None else self.det_distance
+        if self.step is None or self.step <= 0:
+            self.step = 1.0
+        self._c = _CGeom(int(self.n), int(self._angles64.size),
+                         self._angles64.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                         int(self.det_count), float(self.det_spacing), float(self.step),
+                         1 if self.kind == "fan" else 0, float(self.source_distance),
+                         float(self.det_distance or 0.0))
+
+    @property
+    def n_angles(self) -> int:
+        return int(self._angles64.size)
+
+    @property
+    def sino_shape(self) -> tuple[int, int]:
+        return (self.n_angles, int(self.det_count))
+
+    @classmethod
+    def from_args(cls, args: dict) -> "Geometry":
+        a = dict(args)
+        kind = a.pop("kind")
+        return cls(kind=kind, **a)
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def ray(g: Geometry, v: int, d: int) -> tuple[np.ndarray, np.ndarray]:
+    """Origin m (closest point to the rotation centre) and unit direction u of ray (v, d)."""
+    m = np.zeros(2)
+    u = np.zeros(2)
+    _load().oracle_ray(ctypes.byref(g._c), v, d, _dp(m), _dp(u))
+    return m, u
+
+
+def sample_count(g: Geometry) -> int:
+    """Samples of all rays of one image: the throughput unit."""
+    return int(_load().oracle_sample_count(ctypes.byref(g._c)))
+
+
+def ray_sample_counts(g: Geometry) -> np.ndarray:
+    out = np.zeros(g.sino_shape, dtype=np.int64)
+    _load().oracle_ray_sample_counts(ctypes.byref(g._c), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    return out
+
+
+def forward(g: Geometry, img: np.ndarray) -> np.ndarray:
+    """A x in FP64; ``img`` is [N,N] or [B,N,N]."""
+    x = np.ascontiguousarray(np.asarray(img, dtype=np.float64))
+    single = x.ndim == 2
+    if single:
+        x = x[None]
+    if x.shape[1:] != (g.n, g.n):
+        raise ValueError("image shape %s does not match N=%d" % (x.shape, g.n))
+    out = np.zeros((x.shape[0],) + g.sino_shape)
+    if x.shape[0]:
+        _load().oracle_forward(ctypes.byref(g._c), _dp(x), _dp(out), x.shape[0])
+    return out[0] if single else out
+
+
+def adjoint(g: Geometry, sino: np.ndarray) -> np.ndarray:
+    """A^T y in FP64 (literal scatter); ``sino`` is [V,D] or [B,V,D]."""
+    y = np.ascontiguousarray(np.asarray(sino, dtype=np.float64))
+    single = y.ndim == 2
+    if single:
+        y = y[None]
+    if y.shape[1:] != g.sino_shape:
+        raise ValueError("sinogram shape %s does not match %s" % (y.shape, g.sino_shape))
+    out = np.zeros((y.shape[0], g.n, g.n))
+    if y.shape[0]:
+        _load().oracle_adjoint(ctypes.byref(g._c), _dp(y), _dp(out), y.shape[0])
+    return out[0] if single else out
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def dense_matrix(g: Geometry) -> np.ndarray:
+    """Dense A ([V*D, N*N]) by projecting every unit impulse (small N only)."""
+    npix = g.n * g.n
+    eye = np.eye(npix).reshape(npix, g.n, g.n)
+    cols = forward(g, eye).reshape(npix, -1)
+    return cols.T.copy()
+
+
+def dense_matrix_adjoint(g: Geometry) -> np.ndarray:
+    """Dense A^T ([N*N, V*D]) by back-projecting every unit sinogram impulse (small sizes only)."""
+    nsino = g.n_angles * g.det_count
+    eye = np.eye(nsino).reshape((nsino,) + g.sino_shape)
+    cols = adjoint(g, eye).reshape(nsino, -1)
+    return cols.T.copy()
+
+
+# ---------------------------------------------------------------------------
+# Landweber iteration (Section 4.2) and its reverse mode.
+# ---------------------------------------------------------------------------
+
+def power_iteration(g: Geometry, iterations: int, seed: int) -> float:
+    """Rayleigh-quotient estimate of lambda_max(A^T A) after ``iterations`` steps from a seeded N(0,1) start."""
+    z = np.random.default_rng(seed).standard_normal((g.n, g.n))
+    z /= np.linalg.norm(z)
+    lam = 0.0
+    for _ in range(iterations):
+        w = adjoint(g, forward(g, z))
+        lam = float(np.vdot(z, w))   # Rayleigh quotient, |z| = 1
+        z = w / np.linalg.norm(w)
+    return lam
+
+
+def landweber(g: Geometry, x0: np.ndarray, y: np.ndarray, alpha: float, iterations: int,
+              keep: bool = False):
+    """x_{k+1} = x_k - alpha * A^T (A x_k - y); returns x_K (and all iterates if ``keep``)."""
+    xs = [np.asarray(x0, dtype=np.float64)]
+    for _ in range(iterations):
+        x = xs[-1]
+        xs.append(x - alpha * adjoint(g, forward(g, x) - y))
+    return (xs[-1], xs) if keep else xs[-1]
+
+
+def landweber_grads(g: Geometry, x0, y, alpha: float, iterations: int, x_true):
+    """Loss L = ||x_K - x_true||^2 and its gradients w.r.t. y and alpha (hand-derived reverse mode).
+
+    With r_k = A x_k - y and x_{k+1} = x_k - alpha A^T r_k:
+      g_K = dL/dx_K = 2 (x_K - x_true);  g_k = g_{k+1} - alpha A^T A g_{k+1};
+      dL/dy     = sum_k alpha * A g_{k+1};
+      dL/dalpha = - sum_k <g_{k+1}, A^T r_k>.
+    """
+    xK, xs = landweber(g, x0, y, alpha, iterations, keep=True)
+    loss = float(np.sum((xK - x_true) ** 2))
+    gk = 2.0 * (xK - x_true)
+    dy = np.zeros_like(np.asarray(y, dtype=np.float64))
+    dalpha = 0.0
+    for k in range(iterations - 1, -1, -1):
+        r = forward(g, xs[k]) - y
+        dalpha -= float(np.vdot(gk, adjoint(g, r)))
+        Ag = forward(g, gk)
+        dy += alpha * Ag
+        gk = gk - alpha * adjoint(g, Ag)
+    return loss, dy, dalpha
+
+
+__all__ = [
+    "Geometry", "build", "ray", "sample_count", "ray_sample_counts", "forward", "adjoint",
+    "num_threads", "dense_matrix", "dense_matrix_adjoint", "power_iteration", "landweber",
+    "landweber_grads",
+]
+
