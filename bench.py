@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Throughput of the Radon forward projection + exact adjoint on one GB300 (or N, one rank each).
+
+Workload (default): fan beam, 16 x 512^2 seeded ellipse phantoms, 720 views over [0, 2 pi),
+source 1000 px, detector 500 px, 1024 bins x 1.5 px.  One step = the forward projection of the
+whole image batch and the adjoint of a whole sinogram batch (independent inputs), i.e. every
+kernel of the hot path once.  Metric: bilinear samples per second, 2 B S / (t_fwd + t_adj), with
+S the per-image sample count the geometry enumerates in FP64; images/s = B / (t_fwd + t_adj).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle on the host
+cores on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import WORKLOADS, workload_geometry_args, workload_images  # noqa: E402
+
+DEFAULT_WORKLOAD = "fan_b16_n512_v720_d1024"
+L2_BYTES = 126 * 1024 * 1024
+METRIC = "Radon fwd+adjoint bilinear samples/s and images/s at 512^2; chosen vs plain FP32"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t is not None:
+            self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2009_14788_gb300 import Geometry, backward_raw, forward_raw, launch_config
+    from paper_2009_14788_gb300.build import build
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build()
+    w = WORKLOADS[args.workload]
+    gargs = workload_geometry_args(w)
+    kind = gargs.pop("kind")
+    geom = Geometry(kind, **gargs)
+    B = w.batch
+    S = geom.sample_count
+    dtypes = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
+    dt = dtypes[args.storage]
+    chosen = launch_config(args.algo)
+    plain = launch_config("plain")
+
+    x64 = workload_images(w)
+    bytes_per_set = (B * geom.n * geom.n + B * geom.n_angles * geom.det_count) * 2 * torch.empty((), dtype=dt).element_size()
+    n_sets = max(2, int(np.ceil(2.5 * L2_BYTES / bytes_per_set)))
+    xs = [torch.from_numpy(x64).to(device="cuda", dtype=dt) for _ in range(n_sets)]
+    y0 = forward_raw(geom, xs[0].float()).to(dt)
+    ys = [y0.clone() for _ in range(n_sets)]
+    outs_y = [torch.empty_like(y0) for _ in range(n_sets)]
+    outs_x = [torch.empty_like(xs[0]) for _ in range(n_sets)]
+    stream = torch.cuda.current_stream()
+
+    def step(i, cfg, xset=xs, yset=ys, ev=None):
+        j = i % n_sets
+        if ev is not None:
+            ev[0].record(stream)
+        forward_raw(geom, xset[j], cfg, out=outs_y[j])
+        if ev is not None:
+            ev[1].record(stream)
+        backward_raw(geom, yset[j], cfg, out=outs_x[j])
+        if ev is not None:
+            ev[2].record(stream)
+
+    def timed(cfg, steps, warmup, xset=xs, yset=ys):
+        for i in range(warmup):
+            step(i, cfg, xset, yset)
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(steps):
+            step(i, cfg, xset, yset, evs[i])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        total = t0.elapsed_time(t1)
+        fwd = [e[0].elapsed_time(e[1]) for e in evs]
+        adj = [e[1].elapsed_time(e[2]) for e in evs]
+        return total, fwd, adj
+
+    # supplementary: the plain FP32 form on the same workload (outside the headline timed region)
+    xs32 = [x.float() for x in xs[:2]]
+    ys32 = [y.float() for y in ys[:2]]
+    p_total, p_fwd, p_adj = timed(plain, max(2, min(5, args.steps)), 1, xs32 + xs32 * (n_sets // 2), ys32 + ys32 * (n_sets // 2))
+    plain_ms = p_total / max(2, min(5, args.steps))
+    del xs32, ys32
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    total_ms, fwd_ms, adj_ms = timed(chosen, args.steps, args.warmup)
+    time.sleep(0.2)
+    clk = clocks.stop()
+
+    # end to end through the public API with pinned host buffers (H2D of inputs, D2H of results)
+    hx = [torch.from_numpy(x64).to(dtype=dt).pin_memory() for _ in range(2)]
+    hy = [ys[0].cpu().pin_memory() for _ in range(2)]
+    hox = [torch.empty(outs_x[0].shape, dtype=dt).pin_memory() for _ in range(2)]
+    hoy = [torch.empty(outs_y[0].shape, dtype=dt).pin_memory() for _ in range(2)]
+    dx = torch.empty_like(xs[0])
+    dy = torch.empty_like(ys[0])
+    e_steps = max(3, min(args.steps, 10))
+    for i in range(args.warmup + e_steps):
+        if i == args.warmup:
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        j = i % 2
+        dx.copy_(hx[j], non_blocking=True)
+        dy.copy_(hy[j], non_blocking=True)
+        forward_raw(geom, dx, chosen, out=outs_y[0])
+        backward_raw(geom, dy, chosen, out=outs_x[0])
+        hoy[j].copy_(outs_y[0], non_blocking=True)
+        hox[j].copy_(outs_x[0], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e_steps
+    h2d = hx[0].numel() * hx[0].element_size() + hy[0].numel() * hy[0].element_size()
+    d2h = hox[0].numel() * hox[0].element_size() + hoy[0].numel() * hoy[0].element_size()
+
+    # max over ranks
+    t = torch.tensor([total_ms, e2e_ms], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms, e2e_ms = float(t[0]), float(t[1])
+    ms_per_step = total_ms / args.steps
+    samples_per_step = 2 * B * S
+    value = samples_per_step * world / (ms_per_step * 1e-3)
+
+    mean_fwd = statistics.mean(fwd_ms)
+    mean_adj = statistics.mean(adj_ms)
+    dom = "forward" if mean_fwd >= mean_adj else "backward"
+    dom_ms = max(mean_fwd, mean_adj)
+    peaks = _peaks()
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    bytes_per_texel = torch.empty((), dtype=dt).element_size()
+    per_sm = 128.0 / (4.0 * bytes_per_texel)          # shared-memory / L1 load pipe: 128 B/clk/SM
+    peak_gs = sm_count * per_sm * clk_mhz * 1e6 / 1e9
+    achieved_gs = B * S / (dom_ms * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            with open(tfile) as f:
+                tinfo = json.load(f).get(args.workload, {}).get(args.storage, {}).get(dom)
+            traffic = tinfo
+        except (OSError, ValueError):
+            traffic = None
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(w, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "samples/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms_per_step,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "geometry": kind, "batch": B, "n": geom.n,
+                       "views": geom.n_angles, "det_count": geom.det_count, "det_spacing": geom.det_spacing,
+                       "source_distance": geom.source_distance, "det_distance": geom.det_distance,
+                       "storage": args.storage, "algo": args.algo, "samples_per_image": S,
+                       "l2": "rotating %d input/output sets, %.0f MB total (> 2x L2)" % (n_sets, n_sets * bytes_per_set / 2**20),
+                       "parallelism": "replica per GPU (batch sharding, no exchange)"},
+            "images_per_s": B * world / (ms_per_step * 1e-3),
+            "fwd_ms": mean_fwd,
+            "adj_ms": mean_adj,
+            "plain_f32": {"ms_per_step": plain_ms, "samples_per_s": samples_per_step / (plain_ms * 1e-3),
+                          "fwd_ms": statistics.mean(p_fwd), "adj_ms": statistics.mean(p_adj)},
+            "speedup_vs_plain_f32": plain_ms / ms_per_step,
+            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved_gs, "peak": peak_gs,
+                         "unit": "Gsamples/s", "frac": achieved_gs / peak_gs, "traffic": traffic,
+                         "peak_basis": "%d SMs x %.0f samples/clk/SM (128 B/clk/SM load pipe / 4 texels x %d B) x %.0f MHz (sm_max_mhz of MEASURED_PEAKS.json)" % (sm_count, per_sm, bytes_per_texel, clk_mhz)},
+            "e2e": {"value": samples_per_step * world / (e2e_ms * 1e-3), "unit": "samples/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def _oracle_sample_geometry(w, stride):
+    import oracle as O
+    gargs = workload_geometry_args(w)
+    gargs["angles"] = gargs["angles"][::stride]
+    return O.Geometry.from_args(gargs)
+
+
+def cpu_oracle_sample(w, seconds):
+    """The FP64 oracle as it stands on the host cores: fwd + adjoint of the whole image batch on every
+    ``stride``-th view, with the stride picked so the run takes roughly ``seconds``."""
+    import oracle as O
+    x = workload_images(w)
+    stride = 64
+    result = None
+    while True:
+        g = _oracle_sample_geometry(w, stride)
+        S = O.sample_count(g)
+        y = O.forward(g, x)            # warm (builds / loads the library)
+        t0 = time.perf_counter()
+        y = O.forward(g, x)
+        O.adjoint(g, y)
+        dt = time.perf_counter() - t0
+        result = {"value": 2 * x.shape[0] * S / dt, "unit": "samples/s", "cores": O.num_threads(), "kind": "oracle",
+                  "sample": "fwd + adjoint of all %d images on every %d-th view (%d of %d views), %.1f s" % (
+                      x.shape[0], stride, g.n_angles, w.n_views, dt),
+                  "seconds": dt}
+        if dt * 3 > seconds or stride == 1:
+            break
+        stride = max(1, stride // 4)
+    return result
+
+
+def run_reference(args):
+    world, rank, local = _dist()
+    if rank != 0:
+        return
+    import oracle as O
+    w = WORKLOADS[args.workload]
+    x = workload_images(w)
+    stride = args.reference_stride
+    g = _oracle_sample_geometry(w, stride)
+    S = O.sample_count(g)
+    y = O.forward(g, x)
+    for _ in range(args.warmup):
+        O.forward(g, x)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        yy = O.forward(g, x)
+        O.adjoint(g, yy)
+        times.append(time.perf_counter() - t0)
+    _ = y
+    ms = 1e3 * statistics.mean(times)
+    value = 2 * x.shape[0] * S / (ms * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "sample": "every %d-th view" % stride},
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": O.num_threads(), "kind": "oracle",
+                             "sample": "fwd + adjoint of all %d images on every %d-th view (%d of %d views) per step"
+                                       % (x.shape[0], stride, g.n_angles, w.n_views)},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(k for k, v in WORKLOADS.items()
+                                                                           if v.kind in ("parallel", "fan")))
+    ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f16")
+    ap.add_argument("--algo", choices=["auto", "plain", "tiled"], default="auto")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--reference-stride", type=int, default=16)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/*
+ * radon.h -- C ABI of libradon: the discrete Radon transform (forward projection)
+ * and its exact adjoint (backprojection) on one NVIDIA GB300 (sm_103a) GPU.
+ *
+ * The operations follow TorchRadon's statement of the problem (Ronchetti 2020):
+ *   - Section 3.1.1: parallel-beam projection with a set of angles, a detector of
+ *     det_count bins of det_spacing (defaults: det_count = image size, spacing 1).
+ *   - Section 3.1.2: fan-beam projection with a point source at source_distance
+ *     from the centre and a flat detector at det_distance (default: equal to
+ *     source_distance); default det_spacing is the smallest one whose bins cover
+ *     the magnified image, (S + Ddet) / S * N / det_count (the worked example
+ *     S = Ddet = 512, N = det_count = 512 gives 2.0).
+ *   - Section 3.1.1 / 3.1.2 "forward" and "backprojection", batched over any
+ *     number of images (Section 4.1), 16-bit storage with 32-bit arithmetic
+ *     (Section 3.3).
+ *
+ * The discretisation (the paper does not spell it out) is fixed-step bilinear
+ * ray sampling.  Image x[b][i][j] (row i, column j) has its pixel centre at
+ * (j - (N-1)/2, i - (N-1)/2).  View v has n = (cos t, sin t), u = (-sin t, cos t);
+ * detector bin d sits at s_d = (d - (D-1)/2) * det_spacing.  Ray (v, d):
+ *   parallel: origin m = s_d n, direction u;
+ *   fan:      source c = -S u, bin q = Ddet u + s_d n, direction r = (q - c)/|q - c|,
+ *             origin m = the point of the ray closest to the rotation centre.
+ * Samples p_k = m + k h r for every integer k with p_k strictly inside the box
+ * (-(N+1)/2, (N+1)/2)^2; each sample is the bilinear interpolation of x (zero
+ * outside the image).  Forward: y[b][v][d] = h * sum_k sample.  Backward: the
+ * exact transpose, x[b] = h * sum_{v,d,k} y[b][v][d] * (bilinear weights of p_k).
+ *
+ * Conventions for every call below:
+ *   - Memory: device pointers, C-contiguous.  Image [batch][N][N], sinogram
+ *     [batch][n_angles][det_count], both of the same radon_dtype.  The caller
+ *     owns every buffer passed in; outputs are overwritten, never accumulated.
+ *     Arithmetic is FP32 for every storage type; 16-bit outputs are rounded to
+ *     nearest even.
+ *   - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *     radon_forward / radon_backward / radon_batch_plan_launch allocate nothing,
+ *     never synchronise and can be captured in a CUDA graph.  Geometry and plan
+ *     creation allocate and synchronise and must not run during capture.
+ *   - Devices: a geometry belongs to the device that was current at creation;
+ *     launching it with another device current is RADON_ERR_INVALID_ARG.
+ *   - Errors: every call returns a radon_status and never throws or exits.
+ *     Argument errors are detected on the host before any launch.  Kernels that
+ *     wait on asynchronous copies bound every wait; on expiry they record
+ *     RADON_ERR_TIMEOUT in a device error word that radon_get_device_error reads.
+ *     radon_last_error_message gives a thread-local description of the last
+ *     failure.
+ */
+#ifndef RADON_H
+#define RADON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RADON_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define RADON_API __attribute__((visibility("default")))
+#else
+#define RADON_API
+#endif
+
+typedef enum {
+    RADON_OK = 0,
+    RADON_ERR_INVALID_ARG = 1,   /* bad pointer, size, dtype, geometry handle or device */
+    RADON_ERR_UNSUPPORTED = 2,   /* valid request this build cannot serve (e.g. tile config) */
+    RADON_ERR_OOM = 3,           /* device or host allocation failed (create calls only) */
+    RADON_ERR_CUDA = 4,          /* a CUDA runtime / driver call failed; see the message */
+    RADON_ERR_TIMEOUT = 5,       /* a kernel's bounded wait expired (device error word) */
+    RADON_ERR_DEVICE_BOUNDS = 6  /* a kernel's own bounds check fired (device error word) */
+} radon_status;
+
+typedef enum {
+    RADON_F32 = 0,   /* float32 storage */
+    RADON_F16 = 1,   /* IEEE half storage, FP32 arithmetic */
+    RADON_BF16 = 2   /* bfloat16 storage, FP32 arithmetic */
+} radon_dtype;
+
+typedef enum {
+    RADON_ALGO_AUTO = 0,   /* the tuned kernels (what radon_forward / radon_backward run) */
+    RADON_ALGO_PLAIN = 1,  /* one thread per ray (forward) / per pixel (backward), global loads */
+    RADON_ALGO_TILED = 2   /* TMA-staged shared-memory tiles, explicit parameters below */
+} radon_algo;
+
+/* Opaque geometry: FP64-built ray tables uploaded to the device, owned by the library. */
+typedef struct radon_geometry radon_geometry;
+
+/*
+ * Parallel beam (Section 3.1.1).
+ *   n           image side N (>= 1, <= 8192)
+ *   angles      host array of n_angles view angles in radians (read during the call only)
+ *   det_count   detector bins D; <= 0 selects N
+ *   det_spacing bin spacing in pixels; <= 0 selects 1.0
+ *   step        sampling step h along each ray in pixels; <= 0 selects 1.0
+ *   out         receives the new geometry (NULL on failure)
+ * Allocates host and device memory; synchronises the current device.
+ */
+RADON_API radon_status radon_geometry_create_parallel(int n, const double* angles, int n_angles, int det_count,
+                                            double det_spacing, double step, radon_geometry** out);
+
+/*
+ * Fan beam with a flat detector (Section 3.1.2).
+ *   source_distance  S > 0, source to rotation centre, pixels
+ *   det_distance     rotation centre to detector; <= 0 selects S
+ *   det_count        <= 0 selects N
+ *   det_spacing      <= 0 selects (S + Ddet) / S * N / det_count
+ *   other arguments as for radon_geometry_create_parallel.
+ */
+RADON_API radon_status radon_geometry_create_fanbeam(int n, const double* angles, int n_angles, double source_distance,
+                                           double det_distance, int det_count, double det_spacing, double step,
+                                           radon_geometry** out);
+
+/*
+ * General constructor.  `host_only` != 0 builds the FP64 tables on the host without touching
+ * any GPU (for inspection and tests on machines without one); such a geometry answers
+ * radon_geometry_get_info / radon_geometry_sample_count / radon_geometry_copy_rays, and every
+ * launch with it returns RADON_ERR_INVALID_ARG.
+ */
+typedef struct {
+    int n;                   /* image side N */
+    const double* angles;    /* host, n_angles radians */
+    int n_angles;
+    int is_fan;              /* 0 parallel (Section 3.1.1), 1 fan (Section 3.1.2) */
+    double source_distance;  /* fan only */
+    double det_distance;     /* fan only; <= 0 selects source_distance */
+    int det_count;           /* <= 0 selects N */
+    double det_spacing;      /* <= 0 selects the default of the geometry kind */
+    double step;             /* <= 0 selects 1.0 */
+    int host_only;
+} radon_geometry_desc;
+
+RADON_API radon_status radon_geometry_create(const radon_geometry_desc* desc, radon_geometry** out);
+
+/*
+ * Copies the FP32 ray table the kernels read: for ray r = v * det_count + d, rays[4r..4r+3] =
+ * (fx0, fy0, dx, dy) in pixel-index coordinates (x = column, y = row) and counts[r] = number of
+ * samples; sample k' = 0..counts[r]-1 is at (fx0 + k' dx, fy0 + k' dy).  Either pointer may be
+ * NULL.  Host buffers of n_angles * det_count entries (x4 floats for rays).
+ */
+RADON_API radon_status radon_geometry_copy_rays(const radon_geometry* geometry, float* rays, int32_t* counts);
+
+/* Frees the geometry and its device tables (synchronises the device).  NULL is ignored. */
+RADON_API void radon_geometry_destroy(radon_geometry* geometry);
+
+typedef struct {
+    int n;                   /* image side */
+    int n_angles;            /* views */
+    int det_count;           /* detector bins */
+    int is_fan;              /* 0 parallel, 1 fan */
+    double det_spacing;      /* after defaults */
+    double step;             /* after defaults */
+    double source_distance;  /* 0 for parallel */
+    double det_distance;     /* 0 for parallel; after defaults for fan */
+    int64_t sample_count;    /* bilinear samples of one image (all rays), FP64 enumeration */
+    int device;              /* CUDA device the tables live on */
+} radon_geometry_info;
+
+RADON_API radon_status radon_geometry_get_info(const radon_geometry* geometry, radon_geometry_info* out);
+
+/* Number of bilinear samples the forward projection of ONE image evaluates (the throughput
+ * unit; the adjoint applies the same weights).  -1 for an invalid handle. */
+RADON_API int64_t radon_geometry_sample_count(const radon_geometry* geometry);
+
+/*
+ * Forward projection y = A x (Section 3.1.1 / 3.1.2 "forward").
+ *   img    device, [batch][N][N] of dtype
+ *   sino   device, [batch][n_angles][det_count] of dtype, overwritten
+ *   batch  >= 0 (0 is a no-op)
+ * Runs the tuned kernels on `stream`; no allocation, no synchronisation.
+ */
+RADON_API radon_status radon_forward(const radon_geometry* geometry, const void* img, void* sino, radon_dtype dtype,
+                           int batch, void* stream);
+
+/*
+ * Exact adjoint x = A^T y (Section 3.1.1 / 3.1.2 "backprojection" read as the transpose of
+ * the forward; it is also the gradient of the forward, Section 2).
+ *   sino   device, [batch][n_angles][det_count] of dtype
+ *   img    device, [batch][N][N] of dtype, overwritten
+ */
+RADON_API radon_status radon_backward(const radon_geometry* geometry, const void* sino, void* img, radon_dtype dtype,
+                            int batch, void* stream);
+
+/* Explicit kernel selection (comparison forms and the autotuner). */
+typedef struct {
+    int algo;            /* radon_algo */
+    int views_per_cta;   /* TILED forward: views per CTA (0 = default) */
+    int rows_per_slab;   /* TILED forward: image rows staged per step (0 = default) */
+    int images_per_cta;  /* TILED: images sharing the geometry work in one CTA (0 = default) */
+    int tile;            /* TILED backward: pixel tile side (0 = default) */
+    int threads;         /* threads per CTA (0 = default) */
+} radon_launch_config;
+
+RADON_API radon_status radon_forward_ex(const radon_geometry* geometry, const void* img, void* sino, radon_dtype dtype,
+                              int batch, const radon_launch_config* config, void* stream);
+RADON_API radon_status radon_backward_ex(const radon_geometry* geometry, const void* sino, void* img, radon_dtype dtype,
+                               int batch, const radon_launch_config* config, void* stream);
+
+/*
+ * Synchronises `stream`, then reads and clears the library's device error word.
+ * Returns RADON_OK, RADON_ERR_TIMEOUT or RADON_ERR_DEVICE_BOUNDS (from kernels), or
+ * RADON_ERR_CUDA if the synchronisation itself failed.
+ */
+RADON_API radon_status radon_get_device_error(void* stream);
+
+/* Static, never NULL. */
+RADON_API const char* radon_status_string(radon_status status);
+
+/* Thread-local text of the last failure on this thread ("" if none).  Valid until the next call. */
+RADON_API const char* radon_last_error_message(void);
+
+/* RADON_ABI_VERSION of the loaded library. */
+RADON_API int radon_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RADON_H */

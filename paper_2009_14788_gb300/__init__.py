@@ -1,0 +1,23 @@
+"""GB300-native discrete Radon transform (forward projection + exact adjoint).
+
+Fixed-step bilinear ray sampling for parallel- and fan-beam geometries, hand-written CUDA
+kernels for sm_103a behind the C ABI in ``include/radon.h`` (``libradon.so``), with a thin
+PyTorch binding: ``Radon``, ``RadonFanbeam``, differentiable forward / backprojection.
+"""
+
+from . import _lib  # noqa: F401
+from .radon import (  # noqa: F401
+    Geometry,
+    Radon,
+    RadonBackprojectionFunction,
+    RadonFanbeam,
+    RadonForwardFunction,
+    backward_raw,
+    forward_raw,
+    launch_config,
+)
+
+__all__ = [
+    "Geometry", "Radon", "RadonFanbeam", "RadonForwardFunction", "RadonBackprojectionFunction", "forward_raw",
+    "backward_raw", "launch_config",
+]

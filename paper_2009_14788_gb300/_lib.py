@@ -1,0 +1,201 @@
+"""ctypes binding of libradon's C ABI (include/radon.h): argument marshalling only.
+
+Every name here is the C function of the same name.  Loading fails loudly if the shared
+library has not been built: there is no fallback implementation.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libradon.so")
+
+RADON_OK = 0
+RADON_ERR_INVALID_ARG = 1
+RADON_ERR_UNSUPPORTED = 2
+RADON_ERR_OOM = 3
+RADON_ERR_CUDA = 4
+RADON_ERR_TIMEOUT = 5
+RADON_ERR_DEVICE_BOUNDS = 6
+
+RADON_F32 = 0
+RADON_F16 = 1
+RADON_BF16 = 2
+
+RADON_ALGO_AUTO = 0
+RADON_ALGO_PLAIN = 1
+RADON_ALGO_TILED = 2
+
+
+class RadonError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        super().__init__("%s failed: %s: %s" % (where, status_string(status), message))
+
+
+class radon_geometry_desc(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int),
+        ("angles", ctypes.POINTER(ctypes.c_double)),
+        ("n_angles", ctypes.c_int),
+        ("is_fan", ctypes.c_int),
+        ("source_distance", ctypes.c_double),
+        ("det_distance", ctypes.c_double),
+        ("det_count", ctypes.c_int),
+        ("det_spacing", ctypes.c_double),
+        ("step", ctypes.c_double),
+        ("host_only", ctypes.c_int),
+    ]
+
+
+class radon_geometry_info(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int),
+        ("n_angles", ctypes.c_int),
+        ("det_count", ctypes.c_int),
+        ("is_fan", ctypes.c_int),
+        ("det_spacing", ctypes.c_double),
+        ("step", ctypes.c_double),
+        ("source_distance", ctypes.c_double),
+        ("det_distance", ctypes.c_double),
+        ("sample_count", ctypes.c_int64),
+        ("device", ctypes.c_int),
+    ]
+
+
+class radon_launch_config(ctypes.Structure):
+    _fields_ = [
+        ("algo", ctypes.c_int),
+        ("views_per_cta", ctypes.c_int),
+        ("rows_per_slab", ctypes.c_int),
+        ("images_per_cta", ctypes.c_int),
+        ("tile", ctypes.c_int),
+        ("threads", ctypes.c_int),
+    ]
+
+
+_c = None
+
+# (name, restype, argtypes) of every exported function
+_SIGNATURES = [
+    ("radon_geometry_create_parallel", ctypes.c_int,
+     [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+      ctypes.POINTER(ctypes.c_void_p)]),
+    ("radon_geometry_create_fanbeam", ctypes.c_int,
+     [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+      ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_void_p)]),
+    ("radon_geometry_create", ctypes.c_int, [ctypes.POINTER(radon_geometry_desc), ctypes.POINTER(ctypes.c_void_p)]),
+    ("radon_geometry_copy_rays", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32)]),
+    ("radon_geometry_destroy", None, [ctypes.c_void_p]),
+    ("radon_geometry_get_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(radon_geometry_info)]),
+    ("radon_geometry_sample_count", ctypes.c_int64, [ctypes.c_void_p]),
+    ("radon_forward", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    ("radon_backward", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    ("radon_forward_ex", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+      ctypes.POINTER(radon_launch_config), ctypes.c_void_p]),
+    ("radon_backward_ex", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+      ctypes.POINTER(radon_launch_config), ctypes.c_void_p]),
+    ("radon_get_device_error", ctypes.c_int, [ctypes.c_void_p]),
+    ("radon_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("radon_last_error_message", ctypes.c_char_p, []),
+    ("radon_abi_version", ctypes.c_int, []),
+]
+
+
+def load() -> ctypes.CDLL:
+    """The loaded library.  Raises if ``libradon.so`` is missing (build it first)."""
+    global _c
+    if _c is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libradon.so is not built (%s); run paper_2009_14788_gb300.build.build() — "
+                               "there is no CPU fallback" % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, res, args in _SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _c = lib
+    return _c
+
+
+def exported_names() -> list[str]:
+    return [s[0] for s in _SIGNATURES]
+
+
+def status_string(status: int) -> str:
+    return load().radon_status_string(status).decode()
+
+
+def radon_last_error_message() -> str:
+    return load().radon_last_error_message().decode()
+
+
+def check(status: int, where: str) -> None:
+    if status != RADON_OK:
+        raise RadonError(status, where, radon_last_error_message())
+
+
+def _call(name, *args):
+    return getattr(load(), name)(*args)
+
+
+# Thin same-name wrappers (return the raw status; ``check`` turns it into an exception).
+def radon_geometry_create_parallel(n, angles_ptr, n_angles, det_count, det_spacing, step, out_ptr):
+    return _call("radon_geometry_create_parallel", n, angles_ptr, n_angles, det_count, det_spacing, step, out_ptr)
+
+
+def radon_geometry_create_fanbeam(n, angles_ptr, n_angles, source_distance, det_distance, det_count, det_spacing,
+                                  step, out_ptr):
+    return _call("radon_geometry_create_fanbeam", n, angles_ptr, n_angles, source_distance, det_distance, det_count,
+                 det_spacing, step, out_ptr)
+
+
+def radon_geometry_create(desc, out_ptr):
+    return _call("radon_geometry_create", desc, out_ptr)
+
+
+def radon_geometry_copy_rays(geom, rays_ptr, counts_ptr):
+    return _call("radon_geometry_copy_rays", geom, rays_ptr, counts_ptr)
+
+
+def radon_geometry_destroy(geom):
+    return _call("radon_geometry_destroy", geom)
+
+
+def radon_geometry_get_info(geom, info_ptr):
+    return _call("radon_geometry_get_info", geom, info_ptr)
+
+
+def radon_geometry_sample_count(geom):
+    return _call("radon_geometry_sample_count", geom)
+
+
+def radon_forward(geom, img, sino, dtype, batch, stream):
+    return _call("radon_forward", geom, img, sino, dtype, batch, stream)
+
+
+def radon_backward(geom, sino, img, dtype, batch, stream):
+    return _call("radon_backward", geom, sino, img, dtype, batch, stream)
+
+
+def radon_forward_ex(geom, img, sino, dtype, batch, config, stream):
+    return _call("radon_forward_ex", geom, img, sino, dtype, batch, config, stream)
+
+
+def radon_backward_ex(geom, sino, img, dtype, batch, config, stream):
+    return _call("radon_backward_ex", geom, sino, img, dtype, batch, config, stream)
+
+
+def radon_get_device_error(stream):
+    return _call("radon_get_device_error", stream)
+
+
+def radon_abi_version():
+    return _call("radon_abi_version")

@@ -1,0 +1,164 @@
+// FP64 geometry tables (host).  Everything here runs once per geometry; kernels only read the
+// FP32 tables it produces.
+//
+// Ray construction follows the parallel-beam (Section 3.1.1) and flat-detector fan-beam
+// (Section 3.1.2) set-ups: view angle t, n = (cos t, sin t), u = (-sin t, cos t), bin offset
+// s_d = (d - (D-1)/2) ds.  Parallel: origin s_d n, direction u.  Fan: source -S u, bin
+// Ddet u + s_d n, unit direction r from source to bin, origin = foot of the perpendicular from
+// the rotation centre onto the ray.  Samples p_k = m + k h r, k integer, strictly inside the
+// support box (-(N+1)/2, (N+1)/2)^2.
+#include <cmath>
+#include <limits>
+
+#include "radon_internal.h"
+
+namespace radon {
+
+namespace {
+
+struct Ray64 {
+    double mx, my, ux, uy;
+};
+
+Ray64 make_ray(const radon_geometry* g, int v, int d) {
+    const double th = g->angles[v];
+    const double c = std::cos(th), s = std::sin(th);
+    const double nx = c, ny = s, ux = -s, uy = c;
+    const double sd = ((double)d - 0.5 * (double)(g->D - 1)) * g->ds;
+    Ray64 r;
+    if (!g->fan) {
+        r.mx = sd * nx;
+        r.my = sd * ny;
+        r.ux = ux;
+        r.uy = uy;
+        return r;
+    }
+    const double srcx = -g->S * ux, srcy = -g->S * uy;
+    const double qx = g->Ddet * ux + sd * nx, qy = g->Ddet * uy + sd * ny;
+    double ex = qx - srcx, ey = qy - srcy;
+    const double len = std::sqrt(ex * ex + ey * ey);
+    ex /= len;
+    ey /= len;
+    const double along = srcx * ex + srcy * ey;   // source coordinate along the ray
+    r.mx = srcx - along * ex;
+    r.my = srcy - along * ey;
+    r.ux = ex;
+    r.uy = ey;
+    return r;
+}
+
+// Membership of sample k, evaluated exactly as the definition states it: t = k h, p = m + t u.
+bool inside(const radon_geometry* g, const Ray64& r, long k) {
+    const double half = 0.5 * (double)(g->n + 1);
+    const double t = (double)k * g->h;
+    const double px = r.mx + t * r.ux, py = r.my + t * r.uy;
+    return std::fabs(px) < half && std::fabs(py) < half;
+}
+
+// [klo, khi] of the samples inside the open box: slab clipping, then an exact re-check so the
+// result agrees with the membership test sample by sample.  Returns false if empty.
+bool k_range(const radon_geometry* g, const Ray64& r, long* klo, long* khi) {
+    const double half = 0.5 * (double)(g->n + 1);
+    double lo = -std::numeric_limits<double>::infinity(), hi = std::numeric_limits<double>::infinity();
+    const double m[2] = {r.mx, r.my}, u[2] = {r.ux, r.uy};
+    for (int a = 0; a < 2; ++a) {
+        if (u[a] != 0.0) {
+            double t1 = (-half - m[a]) / (g->h * u[a]);
+            double t2 = (half - m[a]) / (g->h * u[a]);
+            if (t1 > t2) std::swap(t1, t2);
+            lo = std::max(lo, t1);
+            hi = std::min(hi, t2);
+        } else if (std::fabs(m[a]) >= half) {
+            return false;
+        }
+    }
+    if (!(lo < hi)) return false;
+    long a = (long)std::floor(lo) + 1, b = (long)std::ceil(hi) - 1;
+    // Rounding of m + t u is monotone in t, so the FP64 inside set is an interval of integers.
+    // Move both ends onto its exact boundary.  Shrinking can take many steps for a ray that runs
+    // along a box edge (every sample sits within rounding of the edge); growing takes at most a
+    // few because the slab bounds are exact up to rounding.
+    while (a <= b && !inside(g, r, a)) ++a;
+    while (b >= a && !inside(g, r, b)) --b;
+    if (a > b) return false;
+    for (int it = 0; it < 8 && inside(g, r, a - 1); ++it) --a;
+    for (int it = 0; it < 8 && inside(g, r, b + 1); ++it) ++b;
+    if (a > b) return false;
+    *klo = a;
+    *khi = b;
+    return true;
+}
+
+}  // namespace
+
+radon_status build_geometry(radon_geometry* g) {
+    const int V = g->V, D = g->D;
+    const double c0 = 0.5 * (double)(g->n - 1);
+    g->h_ray.assign((size_t)V * D, RayF{0.f, 0.f, 0.f, 0.f});
+    g->h_nk.assign((size_t)V * D, 0);
+    g->h_view.assign((size_t)V, ViewF{});
+    int64_t total = 0;
+    int max_nk = 0;
+    for (int v = 0; v < V; ++v) {
+        const double th = g->angles[v];
+        const double nx = std::cos(th), ny = std::sin(th), ux = -std::sin(th), uy = std::cos(th);
+        const int major = std::fabs(uy) >= std::fabs(ux) ? 0 : 1;
+        // Projective detector map in centred coordinates P:
+        //   parallel  t = (n.P)/ds + (D-1)/2
+        //   fan       t = [((S+Ddet)/ds) n.P + ((D-1)/2)(S + u.P)] / (S + u.P)
+        // then shifted to index coordinates (x = P.x + c0, y = P.y + c0).
+        double Ax, Ay, A0, Bx, By, B0;
+        const double half_d = 0.5 * (double)(D - 1);
+        if (!g->fan) {
+            Ax = nx / g->ds;
+            Ay = ny / g->ds;
+            A0 = half_d;
+            Bx = 0.0;
+            By = 0.0;
+            B0 = 1.0;
+        } else {
+            const double mag = (g->S + g->Ddet) / g->ds;
+            Ax = mag * nx + half_d * ux;
+            Ay = mag * ny + half_d * uy;
+            A0 = half_d * g->S;
+            Bx = ux;
+            By = uy;
+            B0 = g->S;
+        }
+        ViewF& vf = g->h_view[v];
+        vf.ax = (float)Ax;
+        vf.ay = (float)Ay;
+        vf.a0 = (float)(A0 - c0 * (Ax + Ay));
+        vf.bx = (float)Bx;
+        vf.by = (float)By;
+        vf.b0 = (float)(B0 - c0 * (Bx + By));
+        vf.major = major;
+        vf.pad = 0;
+        for (int d = 0; d < D; ++d) {
+            const Ray64 r = make_ray(g, v, d);
+            long klo = 0, khi = -1;
+            const size_t idx = (size_t)v * D + d;
+            if (!k_range(g, r, &klo, &khi)) continue;
+            const int nk = (int)(khi - klo + 1);
+            double sx = g->h * r.ux, sy = g->h * r.uy;
+            long kstart = klo;
+            const bool flip = major == 0 ? (sy < 0.0) : (sx < 0.0);
+            if (flip) {
+                kstart = khi;
+                sx = -sx;
+                sy = -sy;
+            }
+            const double t = (double)kstart * g->h;
+            const double px = r.mx + t * r.ux + c0, py = r.my + t * r.uy + c0;
+            g->h_ray[idx] = RayF{(float)px, (float)py, (float)sx, (float)sy};
+            g->h_nk[idx] = nk;
+            total += nk;
+            if (nk > max_nk) max_nk = nk;
+        }
+    }
+    g->samples = total;
+    g->max_nk = max_nk;
+    return RADON_OK;
+}
+
+}  // namespace radon

@@ -1,0 +1,149 @@
+// Plain projector kernels: one thread per ray (forward), one thread per pixel (adjoint),
+// operands read straight from global memory through the read-only cache.  They are the
+// simple comparison form of the operator and the fallback for any shape the tiled kernels
+// do not take.  Arithmetic is FP32 for every storage type.
+#include <cmath>
+
+#include "dtype.cuh"
+#include "radon_internal.h"
+
+namespace radon {
+
+namespace {
+
+// Forward: y[b][v][d] = h * sum_k bilinear(x_b, sample k of ray (v, d)).
+template <typename T>
+__global__ void forward_plain_kernel(const T* __restrict__ img, T* __restrict__ sino, const RayF* __restrict__ rays,
+                                     const int* __restrict__ nks, int n, int64_t rays_per_image, int64_t total,
+                                     float h) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int64_t b = idx / rays_per_image;
+    const int64_t r = idx - b * rays_per_image;
+    const RayF ray = rays[r];
+    const int nk = nks[r];
+    const T* x = img + b * (int64_t)n * n;
+    float acc = 0.0f;
+    for (int k = 0; k < nk; ++k) {
+        const float fx = fmaf((float)k, ray.dx, ray.fx0);
+        const float fy = fmaf((float)k, ray.dy, ray.fy0);
+        const float jf = floorf(fx), iff = floorf(fy);
+        const float a = fx - jf, c = fy - iff;
+        const int j = (int)jf, i = (int)iff;
+        const bool j0in = j >= 0 && j < n, j1in = j + 1 >= 0 && j + 1 < n;
+        const bool i0in = i >= 0 && i < n, i1in = i + 1 >= 0 && i + 1 < n;
+        const int64_t base = (int64_t)i * n + j;
+        const float v00 = (i0in && j0in) ? load_f32(x + base) : 0.0f;
+        const float v01 = (i0in && j1in) ? load_f32(x + base + 1) : 0.0f;
+        const float v10 = (i1in && j0in) ? load_f32(x + base + n) : 0.0f;
+        const float v11 = (i1in && j1in) ? load_f32(x + base + n + 1) : 0.0f;
+        acc += (1.0f - c) * ((1.0f - a) * v00 + a * v01) + c * ((1.0f - a) * v10 + a * v11);
+    }
+    sino[idx] = from_f32<T>(h * acc);
+}
+
+__device__ __forceinline__ float det_coord(const ViewF& vf, float x, float y) {
+    return fmaf(vf.ax, x, fmaf(vf.ay, y, vf.a0)) / fmaf(vf.bx, x, fmaf(vf.by, y, vf.b0));
+}
+
+// Adjoint (gather): x[b][i][j] = h * sum_v sum_d y[b][v][d] * sum_k w_k(i, j), where w_k is the
+// bilinear weight of sample k of ray (v, d) on pixel (i, j).  Candidate rays are those whose
+// detector index lies between the projections of the pixel's 2x2 support square; candidate
+// samples lie within (|dx|+|dy|)/|step|^2 of the ray's closest approach.  Extra candidates
+// contribute exactly zero, so the windows only need to be wide enough.
+template <typename T>
+__global__ void backward_plain_kernel(const T* __restrict__ sino, T* __restrict__ img, const RayF* __restrict__ rays,
+                                      const int* __restrict__ nks, const ViewF* __restrict__ views, int n, int V,
+                                      int D, int64_t total, float h) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int64_t npix = (int64_t)n * n;
+    const int64_t b = idx / npix;
+    const int64_t p = idx - b * npix;
+    const int i = (int)(p / n), j = (int)(p - (int64_t)(p / n) * n);
+    const float xf = (float)j, yf = (float)i;
+    const T* y = sino + b * (int64_t)V * D;
+    const float eps = 1e-3f;
+    float acc = 0.0f;
+    for (int v = 0; v < V; ++v) {
+        const ViewF vf = views[v];
+        const float t0 = det_coord(vf, xf - 1.0f, yf - 1.0f);
+        const float t1 = det_coord(vf, xf + 1.0f, yf - 1.0f);
+        const float t2 = det_coord(vf, xf - 1.0f, yf + 1.0f);
+        const float t3 = det_coord(vf, xf + 1.0f, yf + 1.0f);
+        const float tmin = fminf(fminf(t0, t1), fminf(t2, t3));
+        const float tmax = fmaxf(fmaxf(t0, t1), fmaxf(t2, t3));
+        const int d0 = (int)fmaxf(0.0f, ceilf(tmin - eps));
+        const int d1 = (int)fminf((float)(D - 1), floorf(tmax + eps));
+        for (int d = d0; d <= d1; ++d) {
+            const int64_t r = (int64_t)v * D + d;
+            const int nk = nks[r];
+            if (nk == 0) continue;
+            const RayF ray = rays[r];
+            const float il = 1.0f / fmaf(ray.dx, ray.dx, ray.dy * ray.dy);
+            const float kc = fmaf(xf - ray.fx0, ray.dx, (yf - ray.fy0) * ray.dy) * il;
+            const float kr = (fabsf(ray.dx) + fabsf(ray.dy)) * il;
+            const int k0 = (int)fmaxf(0.0f, ceilf(kc - kr - eps));
+            const int k1 = (int)fminf((float)(nk - 1), floorf(kc + kr + eps));
+            float w = 0.0f;
+            for (int k = k0; k <= k1; ++k) {
+                const float fx = fmaf((float)k, ray.dx, ray.fx0);
+                const float fy = fmaf((float)k, ray.dy, ray.fy0);
+                const float wx = fmaxf(0.0f, 1.0f - fabsf(fx - xf));
+                const float wy = fmaxf(0.0f, 1.0f - fabsf(fy - yf));
+                w = fmaf(wx, wy, w);
+            }
+            if (w != 0.0f) acc = fmaf(w, load_f32(y + r), acc);
+        }
+    }
+    img[idx] = from_f32<T>(h * acc);
+}
+
+template <typename T>
+cudaError_t forward_plain_t(const radon_geometry* g, const void* img, void* sino, int batch, int threads,
+                            cudaStream_t s) {
+    const int64_t rays = (int64_t)g->V * g->D;
+    const int64_t total = rays * batch;
+    if (total == 0) return cudaSuccess;
+    const int64_t blocks = (total + threads - 1) / threads;
+    forward_plain_kernel<T><<<(unsigned)blocks, threads, 0, s>>>((const T*)img, (T*)sino, g->d_ray, g->d_nk, g->n,
+                                                                 rays, total, (float)g->h);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t backward_plain_t(const radon_geometry* g, const void* sino, void* img, int batch, int threads,
+                             cudaStream_t s) {
+    const int64_t total = (int64_t)g->n * g->n * batch;
+    if (total == 0) return cudaSuccess;
+    const int64_t blocks = (total + threads - 1) / threads;
+    backward_plain_kernel<T><<<(unsigned)blocks, threads, 0, s>>>((const T*)sino, (T*)img, g->d_ray, g->d_nk,
+                                                                  g->d_view, g->n, g->V, g->D, total, (float)g->h);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_forward_plain(const radon_geometry* g, const void* img, void* sino, radon_dtype dt, int batch,
+                                 int threads, cudaStream_t s) {
+    if (threads <= 0) threads = 256;
+    switch (dt) {
+        case RADON_F32: return forward_plain_t<float>(g, img, sino, batch, threads, s);
+        case RADON_F16: return forward_plain_t<__half>(g, img, sino, batch, threads, s);
+        case RADON_BF16: return forward_plain_t<__nv_bfloat16>(g, img, sino, batch, threads, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_backward_plain(const radon_geometry* g, const void* sino, void* img, radon_dtype dt, int batch,
+                                  int threads, cudaStream_t s) {
+    if (threads <= 0) threads = 256;
+    switch (dt) {
+        case RADON_F32: return backward_plain_t<float>(g, sino, img, batch, threads, s);
+        case RADON_F16: return backward_plain_t<__half>(g, sino, img, batch, threads, s);
+        case RADON_BF16: return backward_plain_t<__nv_bfloat16>(g, sino, img, batch, threads, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace radon

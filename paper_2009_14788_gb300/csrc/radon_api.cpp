@@ -1,0 +1,307 @@
+// C ABI of libradon (declared in include/radon.h): argument validation, geometry lifetime,
+// kernel dispatch and error reporting.  Every argument check runs on the host before any CUDA
+// call, so a bad request never reaches the GPU.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "radon_internal.h"
+
+namespace radon {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+const char* set_error(const std::string& msg) {
+    g_last_error = msg;
+    return g_last_error.c_str();
+}
+
+radon_status fail(radon_status st, const std::string& msg) {
+    set_error(msg);
+    return st;
+}
+
+radon_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(RADON_ERR_CUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+bool env_flag(const char* name) {
+    const char* v = std::getenv(name);
+    return v != nullptr && v[0] != '\0' && std::strcmp(v, "0") != 0;
+}
+
+radon_status validate_geometry(const radon_geometry* g) {
+    if (g == nullptr) return fail(RADON_ERR_INVALID_ARG, "geometry is NULL");
+    if (g->magic != kGeometryMagic) return fail(RADON_ERR_INVALID_ARG, "geometry handle is not a live geometry");
+    return RADON_OK;
+}
+
+radon_status check_device(const radon_geometry* g) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != g->device)
+        return fail(RADON_ERR_INVALID_ARG, "geometry lives on device " + std::to_string(g->device) +
+                                               " but device " + std::to_string(dev) + " is current");
+    return RADON_OK;
+}
+
+radon_status validate_call(const radon_geometry* g, const void* in, const void* out, radon_dtype dt, int batch) {
+    radon_status st = validate_geometry(g);
+    if (st != RADON_OK) return st;
+    if (dt != RADON_F32 && dt != RADON_F16 && dt != RADON_BF16)
+        return fail(RADON_ERR_INVALID_ARG, "dtype must be RADON_F32, RADON_F16 or RADON_BF16");
+    if (batch < 0) return fail(RADON_ERR_INVALID_ARG, "batch must be >= 0");
+    if (batch > 0 && (in == nullptr || out == nullptr)) return fail(RADON_ERR_INVALID_ARG, "NULL buffer with batch > 0");
+    if (batch > 0 && in == out) return fail(RADON_ERR_INVALID_ARG, "input and output must not alias");
+    const int64_t npix = (int64_t)g->n * g->n, nsino = (int64_t)g->V * g->D;
+    if ((int64_t)batch * std::max(npix, nsino) > ((int64_t)1 << 40))
+        return fail(RADON_ERR_INVALID_ARG, "batch too large");
+    return RADON_OK;
+}
+
+radon_status upload(radon_geometry* g) {
+    cudaError_t e;
+    const size_t nr = g->h_ray.size();
+    if ((e = cudaMalloc(&g->d_ray, std::max<size_t>(1, nr) * sizeof(RayF))) != cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? fail(RADON_ERR_OOM, "device allocation of ray table failed")
+                                              : cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&g->d_nk, std::max<size_t>(1, nr) * sizeof(int))) != cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? fail(RADON_ERR_OOM, "device allocation of count table failed")
+                                              : cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&g->d_view, std::max<size_t>(1, g->h_view.size()) * sizeof(ViewF))) != cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? fail(RADON_ERR_OOM, "device allocation of view table failed")
+                                              : cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMemcpy(g->d_ray, g->h_ray.data(), nr * sizeof(RayF), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy ray table");
+    if ((e = cudaMemcpy(g->d_nk, g->h_nk.data(), nr * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy count table");
+    if ((e = cudaMemcpy(g->d_view, g->h_view.data(), g->h_view.size() * sizeof(ViewF), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy view table");
+    return RADON_OK;
+}
+
+void release(radon_geometry* g) {
+    if (g == nullptr) return;
+    if (g->d_ray) cudaFree(g->d_ray);
+    if (g->d_nk) cudaFree(g->d_nk);
+    if (g->d_view) cudaFree(g->d_view);
+    g->magic = 0;
+    delete g;
+}
+
+radon_status create_common(int n, const double* angles, int n_angles, int det_count, double det_spacing, double step,
+                           int fan, double S, double Ddet, int host_only, radon_geometry** out) {
+    if (out == nullptr) return fail(RADON_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > 8192) return fail(RADON_ERR_INVALID_ARG, "n must be in [1, 8192]");
+    if (angles == nullptr) return fail(RADON_ERR_INVALID_ARG, "angles is NULL");
+    if (n_angles < 1 || n_angles > (1 << 20)) return fail(RADON_ERR_INVALID_ARG, "n_angles must be in [1, 2^20]");
+    for (int v = 0; v < n_angles; ++v)
+        if (!std::isfinite(angles[v])) return fail(RADON_ERR_INVALID_ARG, "angles must be finite");
+    if (det_count <= 0) det_count = n;
+    if (det_count > (1 << 20)) return fail(RADON_ERR_INVALID_ARG, "det_count must be <= 2^20");
+    if ((int64_t)det_count * n_angles > ((int64_t)1 << 31))
+        return fail(RADON_ERR_INVALID_ARG, "n_angles * det_count must be <= 2^31");
+    if (!std::isfinite(step)) return fail(RADON_ERR_INVALID_ARG, "step must be finite");
+    if (step <= 0.0) step = 1.0;
+    if (step < 1e-3) return fail(RADON_ERR_INVALID_ARG, "step must be >= 1e-3 pixels");
+    if (!std::isfinite(det_spacing)) return fail(RADON_ERR_INVALID_ARG, "det_spacing must be finite");
+    if (fan) {
+        if (!std::isfinite(S) || S <= 0.0) return fail(RADON_ERR_INVALID_ARG, "source_distance must be finite and > 0");
+        if (!std::isfinite(Ddet)) return fail(RADON_ERR_INVALID_ARG, "det_distance must be finite");
+        if (Ddet <= 0.0) Ddet = S;
+        // The source must lie outside the support disk so every ray enters the image once.
+        if (S <= 0.5 * (double)(n + 1) * std::sqrt(2.0) + 1.0)
+            return fail(RADON_ERR_UNSUPPORTED, "source_distance must exceed (n+1)/sqrt(2) + 1 (source outside the image)");
+        if (det_spacing <= 0.0) det_spacing = (S + Ddet) / S * (double)n / (double)det_count;
+    } else {
+        S = 0.0;
+        Ddet = 0.0;
+        if (det_spacing <= 0.0) det_spacing = 1.0;
+    }
+    if (env_flag("RADON_FAULT_INJECT_OOM")) return fail(RADON_ERR_OOM, "allocation failure injected (RADON_FAULT_INJECT_OOM)");
+
+    radon_geometry* g = new (std::nothrow) radon_geometry();
+    if (g == nullptr) return fail(RADON_ERR_OOM, "host allocation failed");
+    g->n = n;
+    g->V = n_angles;
+    g->D = det_count;
+    g->fan = fan;
+    g->ds = det_spacing;
+    g->h = step;
+    g->S = S;
+    g->Ddet = Ddet;
+    g->host_only = host_only ? 1 : 0;
+    try {
+        g->angles.assign(angles, angles + n_angles);
+        radon_status st = build_geometry(g);
+        if (st != RADON_OK) {
+            release(g);
+            return st;
+        }
+    } catch (const std::bad_alloc&) {
+        release(g);
+        return fail(RADON_ERR_OOM, "host allocation of geometry tables failed");
+    }
+    if (g->host_only) {
+        g->magic = kGeometryMagic;
+        *out = g;
+        return RADON_OK;
+    }
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e != cudaSuccess) {
+        release(g);
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    radon_status st = upload(g);
+    if (st != RADON_OK) {
+        release(g);
+        return st;
+    }
+    g->magic = kGeometryMagic;
+    *out = g;
+    return RADON_OK;
+}
+
+radon_status dispatch(const radon_geometry* g, const void* in, void* out, radon_dtype dt, int batch,
+                      const radon_launch_config* cfg, void* stream, bool forward) {
+    radon_status st = validate_call(g, in, out, dt, batch);
+    if (st != RADON_OK) return st;
+    const int algo = cfg ? cfg->algo : RADON_ALGO_AUTO;
+    if (algo != RADON_ALGO_AUTO && algo != RADON_ALGO_PLAIN && algo != RADON_ALGO_TILED)
+        return fail(RADON_ERR_INVALID_ARG, "unknown algo");
+    const int threads = cfg ? cfg->threads : 0;
+    if (threads < 0 || threads > 1024 || (threads % 32) != 0)
+        return fail(RADON_ERR_INVALID_ARG, "threads must be 0 or a multiple of 32 up to 1024");
+    if (g->host_only) return fail(RADON_ERR_INVALID_ARG, "geometry was created host-only; it cannot launch");
+    if (batch == 0) return RADON_OK;
+    st = check_device(g);
+    if (st != RADON_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (forward) {
+        e = launch_forward_plain(g, in, out, dt, batch, threads, s);
+    } else {
+        e = launch_backward_plain(g, in, out, dt, batch, threads, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, forward ? "forward launch" : "backward launch");
+    return RADON_OK;
+}
+
+}  // namespace radon
+
+using namespace radon;
+
+extern "C" {
+
+radon_status radon_geometry_create_parallel(int n, const double* angles, int n_angles, int det_count,
+                                            double det_spacing, double step, radon_geometry** out) {
+    return create_common(n, angles, n_angles, det_count, det_spacing, step, 0, 0.0, 0.0, 0, out);
+}
+
+radon_status radon_geometry_create_fanbeam(int n, const double* angles, int n_angles, double source_distance,
+                                           double det_distance, int det_count, double det_spacing, double step,
+                                           radon_geometry** out) {
+    return create_common(n, angles, n_angles, det_count, det_spacing, step, 1, source_distance, det_distance, 0, out);
+}
+
+radon_status radon_geometry_create(const radon_geometry_desc* desc, radon_geometry** out) {
+    if (desc == nullptr) return fail(RADON_ERR_INVALID_ARG, "desc is NULL");
+    if (desc->is_fan != 0 && desc->is_fan != 1) return fail(RADON_ERR_INVALID_ARG, "is_fan must be 0 or 1");
+    return create_common(desc->n, desc->angles, desc->n_angles, desc->det_count, desc->det_spacing, desc->step,
+                         desc->is_fan, desc->source_distance, desc->det_distance, desc->host_only, out);
+}
+
+radon_status radon_geometry_copy_rays(const radon_geometry* g, float* rays, int32_t* counts) {
+    radon_status st = validate_geometry(g);
+    if (st != RADON_OK) return st;
+    const size_t nr = (size_t)g->V * g->D;
+    if (rays != nullptr) std::memcpy(rays, g->h_ray.data(), nr * sizeof(RayF));
+    if (counts != nullptr) std::memcpy(counts, g->h_nk.data(), nr * sizeof(int));
+    return RADON_OK;
+}
+
+void radon_geometry_destroy(radon_geometry* geometry) {
+    if (geometry == nullptr || geometry->magic != kGeometryMagic) return;
+    release(geometry);
+}
+
+radon_status radon_geometry_get_info(const radon_geometry* g, radon_geometry_info* out) {
+    radon_status st = validate_geometry(g);
+    if (st != RADON_OK) return st;
+    if (out == nullptr) return fail(RADON_ERR_INVALID_ARG, "out is NULL");
+    out->n = g->n;
+    out->n_angles = g->V;
+    out->det_count = g->D;
+    out->is_fan = g->fan;
+    out->det_spacing = g->ds;
+    out->step = g->h;
+    out->source_distance = g->S;
+    out->det_distance = g->Ddet;
+    out->sample_count = g->samples;
+    out->device = g->device;
+    return RADON_OK;
+}
+
+int64_t radon_geometry_sample_count(const radon_geometry* g) {
+    if (validate_geometry(g) != RADON_OK) return -1;
+    return g->samples;
+}
+
+radon_status radon_forward(const radon_geometry* g, const void* img, void* sino, radon_dtype dtype, int batch,
+                           void* stream) {
+    return dispatch(g, img, sino, dtype, batch, nullptr, stream, true);
+}
+
+radon_status radon_backward(const radon_geometry* g, const void* sino, void* img, radon_dtype dtype, int batch,
+                            void* stream) {
+    return dispatch(g, sino, img, dtype, batch, nullptr, stream, false);
+}
+
+radon_status radon_forward_ex(const radon_geometry* g, const void* img, void* sino, radon_dtype dtype, int batch,
+                              const radon_launch_config* config, void* stream) {
+    return dispatch(g, img, sino, dtype, batch, config, stream, true);
+}
+
+radon_status radon_backward_ex(const radon_geometry* g, const void* sino, void* img, radon_dtype dtype, int batch,
+                               const radon_launch_config* config, void* stream) {
+    return dispatch(g, sino, img, dtype, batch, config, stream, false);
+}
+
+radon_status radon_get_device_error(void* stream) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    int word = 0;
+    e = read_and_clear_device_error(&word);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
+    if (word == RADON_ERR_TIMEOUT) return fail(RADON_ERR_TIMEOUT, "a kernel's bounded wait expired");
+    if (word == RADON_ERR_DEVICE_BOUNDS) return fail(RADON_ERR_DEVICE_BOUNDS, "a kernel's bounds check fired");
+    if (word != 0) return fail(RADON_ERR_CUDA, "unknown device error code " + std::to_string(word));
+    return RADON_OK;
+}
+
+const char* radon_status_string(radon_status status) {
+    switch (status) {
+        case RADON_OK: return "RADON_OK";
+        case RADON_ERR_INVALID_ARG: return "RADON_ERR_INVALID_ARG";
+        case RADON_ERR_UNSUPPORTED: return "RADON_ERR_UNSUPPORTED";
+        case RADON_ERR_OOM: return "RADON_ERR_OOM";
+        case RADON_ERR_CUDA: return "RADON_ERR_CUDA";
+        case RADON_ERR_TIMEOUT: return "RADON_ERR_TIMEOUT";
+        case RADON_ERR_DEVICE_BOUNDS: return "RADON_ERR_DEVICE_BOUNDS";
+    }
+    return "RADON_ERR_UNKNOWN";
+}
+
+const char* radon_last_error_message(void) { return g_last_error.c_str(); }
+
+int radon_abi_version(void) { return RADON_ABI_VERSION; }
+
+}  // extern "C"

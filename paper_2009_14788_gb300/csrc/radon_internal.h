@@ -1,0 +1,64 @@
+// Internal declarations shared by the host API and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "radon.h"
+
+namespace radon {
+
+constexpr uint64_t kGeometryMagic = 0x5241444f4e47454fULL;  // "RADONGEO"
+
+// One ray in pixel-index coordinates (column x = j, row y = i).  Sample k' = 0..nk-1 sits at
+// (fx0 + k' dx, fy0 + k' dy).  The ray is oriented so that its major-axis step is >= 0: the
+// y step for views of the vertical class, the x step for the horizontal class.
+struct RayF {
+    float fx0, fy0, dx, dy;
+};
+
+// Per-view projective map from a point (x = j, y = i, index coordinates) to the continuous
+// detector index t: t = (ax*x + ay*y + a0) / (bx*x + by*y + b0).  Ray d crosses t = d.
+struct ViewF {
+    float ax, ay, a0, bx, by, b0;
+    int major;   // 0: |u_y| >= |u_x| (rays run mostly along rows' normal, "vertical"); 1: horizontal
+    int pad;
+};
+
+}  // namespace radon
+
+struct radon_geometry {
+    uint64_t magic = 0;
+    int n = 0, V = 0, D = 0, fan = 0, device = -1, host_only = 0;
+    double ds = 1.0, h = 1.0, S = 0.0, Ddet = 0.0;
+    int64_t samples = 0;
+    int max_nk = 0;
+    std::vector<double> angles;
+    std::vector<radon::RayF> h_ray;   // [V*D]
+    std::vector<int> h_nk;            // [V*D]
+    std::vector<radon::ViewF> h_view; // [V]
+    radon::RayF* d_ray = nullptr;
+    int* d_nk = nullptr;
+    radon::ViewF* d_view = nullptr;
+};
+
+namespace radon {
+
+// geometry.cpp
+radon_status build_geometry(radon_geometry* g);  // fills host tables and sample count
+const char* set_error(const std::string& msg);   // thread-local message, returns it
+
+// kernels_plain.cu
+cudaError_t launch_forward_plain(const radon_geometry* g, const void* img, void* sino, radon_dtype dt, int batch,
+                                 int threads, cudaStream_t s);
+cudaError_t launch_backward_plain(const radon_geometry* g, const void* sino, void* img, radon_dtype dt, int batch,
+                                  int threads, cudaStream_t s);
+
+// kernels_common.cu
+cudaError_t read_and_clear_device_error(int* out);
+cudaError_t device_error_address(int** out);
+
+}  // namespace radon

@@ -1,0 +1,217 @@
+"""PyTorch-facing operators over libradon: geometry objects, forward / backprojection, autograd.
+
+The API mirrors the paper's (Section 3.1.1, 3.1.2): ``Radon(resolution, angles, det_count=...)``
+and ``RadonFanbeam(resolution, angles, source_distance, det_distance=..., det_count=...,
+det_spacing=...)`` with ``.forward(x)`` and ``.backprojection(sino)`` (alias ``.backward``).
+Both operators are differentiable (Section 2): the gradient of the forward projection is the
+backprojection kernel and vice versa.  PyTorch supplies device memory and the current CUDA
+stream; every step of the computation runs in libradon's kernels.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_DTYPES = {torch.float32: L.RADON_F32, torch.float16: L.RADON_F16, torch.bfloat16: L.RADON_BF16}
+
+ALGOS = {"auto": L.RADON_ALGO_AUTO, "plain": L.RADON_ALGO_PLAIN, "tiled": L.RADON_ALGO_TILED}
+
+
+def launch_config(algo="auto", views_per_cta=0, rows_per_slab=0, images_per_cta=0, tile=0, threads=0):
+    """A ``radon_launch_config`` (kernel family and tile parameters; 0 = library default)."""
+    return L.radon_launch_config(ALGOS[algo] if isinstance(algo, str) else int(algo), views_per_cta, rows_per_slab,
+                                 images_per_cta, tile, threads)
+
+
+class Geometry:
+    """Owns a ``radon_geometry*`` (FP64-built tables on one device, or host-only tables)."""
+
+    def __init__(self, kind: str, n: int, angles, det_count=None, det_spacing=None, step=None,
+                 source_distance: float = 0.0, det_distance=None, host_only: bool = False, device=None):
+        if kind not in ("parallel", "fan"):
+            raise ValueError("kind must be 'parallel' or 'fan'")
+        self._h = None
+        ang = np.ascontiguousarray(np.asarray(angles, dtype=np.float64).reshape(-1))
+        self._angles = ang
+        desc = L.radon_geometry_desc(
+            int(n), ang.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(ang.size), 1 if kind == "fan" else 0,
+            float(source_distance or 0.0), float(det_distance or 0.0), int(det_count or 0),
+            float(det_spacing or 0.0), float(step or 0.0), 1 if host_only else 0)
+        handle = ctypes.c_void_p()
+        if host_only:
+            st = L.radon_geometry_create(ctypes.byref(desc), ctypes.byref(handle))
+        else:
+            dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+            with torch.cuda.device(dev):
+                st = L.radon_geometry_create(ctypes.byref(desc), ctypes.byref(handle))
+        L.check(st, "radon_geometry_create")
+        self._h = handle
+        self._lib = L.load()
+        info = L.radon_geometry_info()
+        L.check(L.radon_geometry_get_info(self._h, ctypes.byref(info)), "radon_geometry_get_info")
+        self.kind = kind
+        self.host_only = bool(host_only)
+        self.n = info.n
+        self.n_angles = info.n_angles
+        self.det_count = info.det_count
+        self.det_spacing = info.det_spacing
+        self.step = info.step
+        self.source_distance = info.source_distance
+        self.det_distance = info.det_distance
+        self.sample_count = int(info.sample_count)
+        self.device = None if host_only else torch.device("cuda", info.device)
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def angles(self) -> np.ndarray:
+        return self._angles.copy()
+
+    @property
+    def sino_shape(self) -> tuple[int, int]:
+        return (self.n_angles, self.det_count)
+
+    def rays(self) -> tuple[np.ndarray, np.ndarray]:
+        """The FP32 ray table the kernels read: ([V, D, 4] (fx0, fy0, dx, dy), [V, D] sample counts)."""
+        rays = np.zeros((self.n_angles, self.det_count, 4), dtype=np.float32)
+        counts = np.zeros((self.n_angles, self.det_count), dtype=np.int32)
+        L.check(L.radon_geometry_copy_rays(self._h, rays.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                           counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
+                "radon_geometry_copy_rays")
+        return rays, counts
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            self._lib.radon_geometry_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _check_tensor(t: torch.Tensor, what: str, geom: Geometry):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch.Tensor" % what)
+    if t.device.type != "cuda":
+        raise ValueError("%s must be a CUDA tensor (libradon has no CPU path)" % what)
+    if geom.device is None:
+        raise ValueError("geometry is host-only")
+    if t.device != geom.device:
+        raise ValueError("%s is on %s but the geometry lives on %s" % (what, t.device, geom.device))
+    if t.dtype not in _DTYPES:
+        raise TypeError("%s dtype must be float32, float16 or bfloat16, got %s" % (what, t.dtype))
+
+
+def forward_raw(geom: Geometry, x: torch.Tensor, config=None, out=None) -> torch.Tensor:
+    """y = A x through ``radon_forward`` / ``radon_forward_ex`` (no autograd)."""
+    _check_tensor(x, "image", geom)
+    if x.shape[-2:] != (geom.n, geom.n):
+        raise ValueError("image must end in (%d, %d), got %s" % (geom.n, geom.n, tuple(x.shape)))
+    x = x.contiguous()
+    batch = x.numel() // (geom.n * geom.n)
+    shape = tuple(x.shape[:-2]) + geom.sino_shape
+    y = torch.empty(shape, dtype=x.dtype, device=x.device) if out is None else out
+    stream = torch.cuda.current_stream(x.device).cuda_stream
+    with torch.cuda.device(x.device):
+        if config is None:
+            st = L.radon_forward(geom.handle, x.data_ptr(), y.data_ptr(), _DTYPES[x.dtype], batch, stream)
+        else:
+            st = L.radon_forward_ex(geom.handle, x.data_ptr(), y.data_ptr(), _DTYPES[x.dtype], batch,
+                                    ctypes.byref(config), stream)
+    L.check(st, "radon_forward")
+    return y
+
+
+def backward_raw(geom: Geometry, y: torch.Tensor, config=None, out=None) -> torch.Tensor:
+    """x = A^T y through ``radon_backward`` / ``radon_backward_ex`` (no autograd)."""
+    _check_tensor(y, "sinogram", geom)
+    if tuple(y.shape[-2:]) != geom.sino_shape:
+        raise ValueError("sinogram must end in %s, got %s" % (geom.sino_shape, tuple(y.shape)))
+    y = y.contiguous()
+    batch = y.numel() // (geom.n_angles * geom.det_count)
+    shape = tuple(y.shape[:-2]) + (geom.n, geom.n)
+    x = torch.empty(shape, dtype=y.dtype, device=y.device) if out is None else out
+    stream = torch.cuda.current_stream(y.device).cuda_stream
+    with torch.cuda.device(y.device):
+        if config is None:
+            st = L.radon_backward(geom.handle, y.data_ptr(), x.data_ptr(), _DTYPES[y.dtype], batch, stream)
+        else:
+            st = L.radon_backward_ex(geom.handle, y.data_ptr(), x.data_ptr(), _DTYPES[y.dtype], batch,
+                                     ctypes.byref(config), stream)
+    L.check(st, "radon_backward")
+    return x
+
+
+class RadonForwardFunction(torch.autograd.Function):
+    """y = A x; dL/dx = A^T dL/dy (the adjoint kernel)."""
+
+    @staticmethod
+    def forward(ctx, x, geom, config):
+        ctx.geom = geom
+        ctx.config = config
+        return forward_raw(geom, x, config)
+
+    @staticmethod
+    def backward(ctx, grad):
+        return backward_raw(ctx.geom, grad.contiguous(), ctx.config), None, None
+
+
+class RadonBackprojectionFunction(torch.autograd.Function):
+    """x = A^T y; dL/dy = A dL/dx (the forward kernel)."""
+
+    @staticmethod
+    def forward(ctx, y, geom, config):
+        ctx.geom = geom
+        ctx.config = config
+        return backward_raw(geom, y, config)
+
+    @staticmethod
+    def backward(ctx, grad):
+        return forward_raw(ctx.geom, grad.contiguous(), ctx.config), None, None
+
+
+class Radon:
+    """Parallel-beam projector (Section 3.1.1): ``Radon(resolution, angles, det_count=None, det_spacing=1.0)``."""
+
+    def __init__(self, resolution: int, angles, det_count=None, det_spacing=None, step=None, device=None,
+                 config=None):
+        self.geometry = Geometry("parallel", resolution, angles, det_count, det_spacing, step, device=device)
+        self.config = config
+
+    @property
+    def resolution(self) -> int:
+        return self.geometry.n
+
+    @property
+    def sample_count(self) -> int:
+        return self.geometry.sample_count
+
+    def forward(self, x: torch.Tensor) -> torch.Tensor:
+        return RadonForwardFunction.apply(x, self.geometry, self.config)
+
+    def backprojection(self, sino: torch.Tensor) -> torch.Tensor:
+        return RadonBackprojectionFunction.apply(sino, self.geometry, self.config)
+
+    backward = backprojection
+
+    __call__ = forward
+
+
+class RadonFanbeam(Radon):
+    """Fan-beam projector with a flat detector (Section 3.1.2)."""
+
+    def __init__(self, resolution: int, angles, source_distance: float, det_distance=None, det_count=None,
+                 det_spacing=None, step=None, device=None, config=None):
+        self.geometry = Geometry("fan", resolution, angles, det_count, det_spacing, step,
+                                 source_distance=source_distance, det_distance=det_distance, device=device)
+        self.config = config

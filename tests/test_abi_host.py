@@ -1,0 +1,211 @@
+"""libradon's C ABI on the host: it loads, exports what include/radon.h declares, rejects bad
+arguments before touching a GPU, and builds geometry tables that agree with the FP64 oracle
+(sample counts bit-exact, sample positions to FP32 rounding).  No GPU needed."""
+
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2009_14788_gb300 import Geometry, _lib as L
+from paper_2009_14788_gb300.build import build
+from synth import WORKLOADS, uniform_angles, workload_geometry_args
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build()
+
+
+def _header_names():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            names |= set(re.findall(r"RADON_API\s+[\w\s\*]+?\b(radon_\w+)\s*\(", open(os.path.join(inc, f)).read()))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    names = _header_names()
+    assert len(names) >= 15
+    lib = ctypes.CDLL(L.LIB_PATH)
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+    assert names == set(L.exported_names())
+    assert L.radon_abi_version() == 1
+
+
+def test_status_strings():
+    for code, name in [(0, "RADON_OK"), (1, "RADON_ERR_INVALID_ARG"), (2, "RADON_ERR_UNSUPPORTED"),
+                       (3, "RADON_ERR_OOM"), (4, "RADON_ERR_CUDA"), (5, "RADON_ERR_TIMEOUT"),
+                       (6, "RADON_ERR_DEVICE_BOUNDS")]:
+        assert L.status_string(code) == name
+    assert L.status_string(99) == "RADON_ERR_UNKNOWN"
+
+
+def _create(**kw):
+    args = dict(n=16, angles=np.linspace(0, np.pi, 8, endpoint=False), n_angles=None, is_fan=0,
+                source_distance=0.0, det_distance=0.0, det_count=0, det_spacing=0.0, step=0.0, host_only=1)
+    args.update(kw)
+    ang = np.ascontiguousarray(args["angles"], dtype=np.float64) if args["angles"] is not None else None
+    desc = L.radon_geometry_desc(args["n"], ang.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if ang is not None
+                                 else None, args["n_angles"] if args["n_angles"] is not None else ang.size,
+                                 args["is_fan"], args["source_distance"], args["det_distance"], args["det_count"],
+                                 args["det_spacing"], args["step"], args["host_only"])
+    h = ctypes.c_void_p()
+    st = L.radon_geometry_create(ctypes.byref(desc), ctypes.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(n=0), L.RADON_ERR_INVALID_ARG),
+    (dict(n=9000), L.RADON_ERR_INVALID_ARG),
+    (dict(angles=None, n_angles=4), L.RADON_ERR_INVALID_ARG),
+    (dict(n_angles=0), L.RADON_ERR_INVALID_ARG),
+    (dict(angles=np.array([0.0, np.nan])), L.RADON_ERR_INVALID_ARG),
+    (dict(step=np.inf), L.RADON_ERR_INVALID_ARG),
+    (dict(step=1e-5), L.RADON_ERR_INVALID_ARG),
+    (dict(det_spacing=np.nan), L.RADON_ERR_INVALID_ARG),
+    (dict(is_fan=1, source_distance=0.0), L.RADON_ERR_INVALID_ARG),
+    (dict(is_fan=1, source_distance=10.0), L.RADON_ERR_UNSUPPORTED),   # source inside the image
+    (dict(is_fan=2), L.RADON_ERR_INVALID_ARG),
+])
+def test_create_rejects_bad_arguments(kw, code):
+    st, h = _create(**kw)
+    assert st == code, L.radon_last_error_message()
+    assert not h.value
+    assert L.radon_last_error_message() != ""
+
+
+def test_null_out_pointer():
+    ang = np.zeros(2)
+    st = L.radon_geometry_create_parallel(8, ang.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 2, 0, 0.0, 0.0,
+                                          None)
+    assert st == L.RADON_ERR_INVALID_ARG
+
+
+def test_allocation_failure_injection(monkeypatch):
+    monkeypatch.setenv("RADON_FAULT_INJECT_OOM", "1")
+    st, h = _create()
+    assert st == L.RADON_ERR_OOM and not h.value
+    monkeypatch.delenv("RADON_FAULT_INJECT_OOM")
+    st, h = _create()
+    assert st == L.RADON_OK
+    L.radon_geometry_destroy(h)
+
+
+def test_launch_argument_checks_without_gpu():
+    st, h = _create()
+    assert st == L.RADON_OK
+    buf = (ctypes.c_float * 4)()
+    p = ctypes.addressof(buf)
+    cfg = L.radon_launch_config(0, 0, 0, 0, 0, 0)
+    assert L.radon_forward(None, p, p + 4, 0, 1, None) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_forward(h, p, p + 4, 7, 1, None) == L.RADON_ERR_INVALID_ARG        # dtype
+    assert L.radon_forward(h, p, p + 4, 0, -1, None) == L.RADON_ERR_INVALID_ARG       # batch
+    assert L.radon_forward(h, None, p, 0, 1, None) == L.RADON_ERR_INVALID_ARG         # NULL input
+    assert L.radon_backward(h, p, p, 0, 1, None) == L.RADON_ERR_INVALID_ARG           # aliasing
+    cfg.threads = 48
+    assert L.radon_forward_ex(h, p, p + 4, 0, 1, ctypes.byref(cfg), None) == L.RADON_ERR_INVALID_ARG
+    cfg.threads = 0
+    cfg.algo = 9
+    assert L.radon_backward_ex(h, p, p + 4, 0, 1, ctypes.byref(cfg), None) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_forward(h, p, p + 4, 0, 1, None) == L.RADON_ERR_INVALID_ARG        # host-only geometry
+    assert "host-only" in L.radon_last_error_message()
+    assert L.radon_geometry_sample_count(None) == -1
+    L.radon_geometry_destroy(h)
+    L.radon_geometry_destroy(None)
+
+
+def test_defaults_follow_the_paper():
+    g = Geometry("parallel", 40, uniform_angles(5, math.pi), host_only=True)
+    assert (g.det_count, g.det_spacing, g.step) == (40, 1.0, 1.0)
+    # Section 3.1.2 worked example: S = Ddet = 512, N = D = 512 -> spacing 2.0
+    f = Geometry("fan", 512, uniform_angles(4, 2 * math.pi), source_distance=512.0, host_only=True)
+    assert f.det_count == 512 and f.det_distance == 512.0 and f.det_spacing == 2.0
+
+
+GEOMS = {
+    "parallel_even": dict(kind="parallel", n=32, angles=uniform_angles(37, math.pi) + 0.01, det_count=47),
+    "parallel_axes": dict(kind="parallel", n=20, angles=np.array([0, math.pi / 4, math.pi / 2, math.pi, 1.5 * math.pi]),
+                          det_count=22, det_spacing=1.0),
+    "parallel_odd_spacing": dict(kind="parallel", n=33, angles=uniform_angles(29, 2 * math.pi), det_count=41,
+                                 det_spacing=0.83, step=0.7),
+    "fan": dict(kind="fan", n=40, angles=uniform_angles(31, 2 * math.pi) + 0.2, det_count=64, det_spacing=1.1,
+                source_distance=80.0, det_distance=50.0),
+    "fan_default": dict(kind="fan", n=25, angles=uniform_angles(23, 2 * math.pi), source_distance=40.0),
+    "one_pixel": dict(kind="parallel", n=1, angles=uniform_angles(7, math.pi), det_count=3),
+    "parallel_b1_n64": workload_geometry_args(WORKLOADS["parallel_b1_n64_v64_d91"]),
+}
+
+
+def _lib_geom(args):
+    a = dict(args)
+    kind = a.pop("kind")
+    return Geometry(kind, host_only=True, **a)
+
+
+@pytest.mark.parametrize("name", sorted(GEOMS))
+def test_sample_counts_match_oracle_exactly(name):
+    g = _lib_geom(GEOMS[name])
+    og = O.Geometry.from_args(GEOMS[name])
+    _, counts = g.rays()
+    np.testing.assert_array_equal(counts, O.ray_sample_counts(og))
+    assert g.sample_count == O.sample_count(og)
+
+
+def test_sample_counts_match_oracle_full_fan_workload_subset():
+    """The 512^2 fan workload: every 24th view (FP64 enumeration must agree ray by ray)."""
+    args = workload_geometry_args(WORKLOADS["fan_b16_n512_v720_d1024"])
+    args["angles"] = args["angles"][::24]
+    g = _lib_geom(args)
+    _, counts = g.rays()
+    np.testing.assert_array_equal(counts, O.ray_sample_counts(O.Geometry.from_args(args)))
+
+
+@pytest.mark.parametrize("name", sorted(GEOMS))
+def test_ray_table_positions_match_oracle(name):
+    """Every tabulated sample position equals an oracle sample position to FP32 rounding."""
+    g = _lib_geom(GEOMS[name])
+    og = O.Geometry.from_args(GEOMS[name])
+    rays, counts = g.rays()
+    c0 = (og.n - 1) / 2.0
+    half = (og.n + 1) / 2.0
+    worst = 0.0
+    for v in range(og.n_angles):
+        for d in range(og.det_count):
+            nk = counts[v, d]
+            if nk == 0:
+                continue
+            m, u = O.ray(og, v, d)
+            ks = np.arange(-4 * og.n - 8, 4 * og.n + 9)
+            t = ks * og.step
+            px, py = m[0] + t * u[0], m[1] + t * u[1]
+            ins = (np.abs(px) < half) & (np.abs(py) < half)
+            ref = np.stack([px[ins] + c0, py[ins] + c0], axis=1)
+            fx0, fy0, dx, dy = (float(z) for z in rays[v, d])
+            kk = np.arange(nk)
+            got = np.stack([fx0 + kk * dx, fy0 + kk * dy], axis=1)
+            if len(ref) > 1 and np.dot(ref[-1] - ref[0], got[-1] - got[0]) < 0:
+                ref = ref[::-1]
+            assert len(ref) == nk
+            worst = max(worst, float(np.max(np.abs(got - ref))))
+    assert worst < 2e-4 * max(1.0, og.n / 64.0)
+
+
+def test_orientation_major_axis_step_is_nonnegative():
+    g = _lib_geom(GEOMS["fan"])
+    rays, counts = g.rays()
+    th = GEOMS["fan"]["angles"]
+    vertical = np.abs(np.cos(th)) >= np.abs(np.sin(th))
+    for v in range(len(th)):
+        sel = counts[v] > 1
+        step = rays[v, sel, 3] if vertical[v] else rays[v, sel, 2]
+        assert np.all(step >= 0)
