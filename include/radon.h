@@ -135,10 +135,13 @@ typedef struct {
 RADON_API radon_status radon_geometry_create(const radon_geometry_desc* desc, radon_geometry** out);
 
 /*
- * Copies the FP32 ray table the kernels read: for ray r = v * det_count + d, rays[4r..4r+3] =
- * (fx0, fy0, dx, dy) in pixel-index coordinates (x = column, y = row) and counts[r] = number of
- * samples; sample k' = 0..counts[r]-1 is at (fx0 + k' dx, fy0 + k' dy).  Either pointer may be
- * NULL.  Host buffers of n_angles * det_count entries (x4 floats for rays).
+ * Copies the ray table the kernels read.  For ray r = v * det_count + d, rays[8r..8r+7] =
+ * (J0, I0, fx0, fy0, dxh, dyh, dxl, dyl) and counts[r] = number of samples; sample
+ * k' = 0..counts[r]-1 sits at x = J0 + fx0 + k' (dxh + dxl), y = I0 + fy0 + k' (dyh + dyl) in
+ * pixel-index coordinates (x = column, y = row).  J0, I0 are integers (stored exactly as floats),
+ * fx0, fy0 lie in [0, 1) and k' * dxh is exact in FP32 (split precision, so kernels can re-base
+ * positions without FP32 drift).  Either pointer may be NULL.  Host buffers of
+ * n_angles * det_count entries (x8 floats for rays).
  */
 RADON_API radon_status radon_geometry_copy_rays(const radon_geometry* geometry, float* rays, int32_t* counts);
 

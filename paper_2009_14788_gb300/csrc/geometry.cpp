@@ -7,6 +7,7 @@
 // Ddet u + s_d n, unit direction r from source to bin, origin = foot of the perpendicular from
 // the rotation centre onto the ray.  Samples p_k = m + k h r, k integer, strictly inside the
 // support box (-(N+1)/2, (N+1)/2)^2.
+#include <algorithm>
 #include <cmath>
 #include <limits>
 
@@ -89,12 +90,32 @@ bool k_range(const radon_geometry* g, const Ray64& r, long* klo, long* khi) {
     return true;
 }
 
+// Round v to `bits` significant bits (toward nearest).
+double round_bits(double v, int bits) {
+    if (v == 0.0) return 0.0;
+    int e = 0;
+    const double m = std::frexp(v, &e);   // v = m 2^e, 0.5 <= |m| < 1
+    return std::ldexp(std::nearbyint(std::ldexp(m, bits)), e - bits);
+}
+
+// Integer base and fraction in [0, 1) of a coordinate, the fraction rounded to FP32.
+void split_coord(double p, int* base, float* frac) {
+    double b = std::floor(p);
+    float f = (float)(p - b);
+    if (f >= 1.0f) {   // the FP32 rounding of a fraction just below 1
+        b += 1.0;
+        f = 0.0f;
+    }
+    *base = (int)b;
+    *frac = f;
+}
+
 }  // namespace
 
 radon_status build_geometry(radon_geometry* g) {
     const int V = g->V, D = g->D;
     const double c0 = 0.5 * (double)(g->n - 1);
-    g->h_ray.assign((size_t)V * D, RayF{0.f, 0.f, 0.f, 0.f});
+    g->h_ray.assign((size_t)V * D, RayT{0, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f});
     g->h_nk.assign((size_t)V * D, 0);
     g->h_view.assign((size_t)V, ViewF{});
     int64_t total = 0;
@@ -150,7 +171,18 @@ radon_status build_geometry(radon_geometry* g) {
             }
             const double t = (double)kstart * g->h;
             const double px = r.mx + t * r.ux + c0, py = r.my + t * r.uy + c0;
-            g->h_ray[idx] = RayF{(float)px, (float)py, (float)sx, (float)sy};
+            RayT& rt = g->h_ray[idx];
+            split_coord(px, &rt.J0, &rt.fx0);
+            split_coord(py, &rt.I0, &rt.fy0);
+            // k' * dxh exact in FP32 for k' < nk: dxh keeps 24 - bits(nk) significant bits
+            int kbits = 1;
+            while (kbits < 24 && ((long)1 << kbits) < (long)nk) ++kbits;
+            const int hbits = std::max(1, 24 - kbits);
+            const double hx = round_bits(sx, hbits), hy = round_bits(sy, hbits);
+            rt.dxh = (float)hx;
+            rt.dyh = (float)hy;
+            rt.dxl = (float)(sx - hx);
+            rt.dyl = (float)(sy - hy);
             g->h_nk[idx] = nk;
             total += nk;
             if (nk > max_nk) max_nk = nk;

@@ -11,33 +11,48 @@ namespace radon {
 
 namespace {
 
+// Samples are processed in chunks of kChunk; each chunk re-bases its start position from the
+// split-precision table (integer base + small fraction), so the FP32 position error stays at a
+// few 1e-6 pixels however far the sample lies from the image origin.
+constexpr int kChunk = 32;
+
 // Forward: y[b][v][d] = h * sum_k bilinear(x_b, sample k of ray (v, d)).
 template <typename T>
-__global__ void forward_plain_kernel(const T* __restrict__ img, T* __restrict__ sino, const RayF* __restrict__ rays,
+__global__ void forward_plain_kernel(const T* __restrict__ img, T* __restrict__ sino, const RayT* __restrict__ rays,
                                      const int* __restrict__ nks, int n, int64_t rays_per_image, int64_t total,
                                      float h) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
     const int64_t b = idx / rays_per_image;
     const int64_t r = idx - b * rays_per_image;
-    const RayF ray = rays[r];
+    const RayT ray = rays[r];
     const int nk = nks[r];
+    const float dx = ray.dxh + ray.dxl, dy = ray.dyh + ray.dyl;
     const T* x = img + b * (int64_t)n * n;
     float acc = 0.0f;
-    for (int k = 0; k < nk; ++k) {
-        const float fx = fmaf((float)k, ray.dx, ray.fx0);
-        const float fy = fmaf((float)k, ray.dy, ray.fy0);
-        const float jf = floorf(fx), iff = floorf(fy);
-        const float a = fx - jf, c = fy - iff;
-        const int j = (int)jf, i = (int)iff;
-        const bool j0in = j >= 0 && j < n, j1in = j + 1 >= 0 && j + 1 < n;
-        const bool i0in = i >= 0 && i < n, i1in = i + 1 >= 0 && i + 1 < n;
-        const int64_t base = (int64_t)i * n + j;
-        const float v00 = (i0in && j0in) ? load_f32(x + base) : 0.0f;
-        const float v01 = (i0in && j1in) ? load_f32(x + base + 1) : 0.0f;
-        const float v10 = (i1in && j0in) ? load_f32(x + base + n) : 0.0f;
-        const float v11 = (i1in && j1in) ? load_f32(x + base + n + 1) : 0.0f;
-        acc += (1.0f - c) * ((1.0f - a) * v00 + a * v01) + c * ((1.0f - a) * v10 + a * v11);
+    for (int kb = 0; kb < nk; kb += kChunk) {
+        const float kbf = (float)kb;
+        const float qx = kbf * ray.dxh, qy = kbf * ray.dyh;   // exact products
+        const float Qx = floorf(qx), Qy = floorf(qy);
+        const float sx = fmaf(kbf, ray.dxl, ray.fx0 + (qx - Qx));
+        const float sy = fmaf(kbf, ray.dyl, ray.fy0 + (qy - Qy));
+        const int jb = ray.J0 + (int)Qx, ib = ray.I0 + (int)Qy;
+        const int kend = min(nk - kb, kChunk);
+        for (int kk = 0; kk < kend; ++kk) {
+            const float lx = fmaf((float)kk, dx, sx);
+            const float ly = fmaf((float)kk, dy, sy);
+            const float flx = floorf(lx), fly = floorf(ly);
+            const float a = lx - flx, c = ly - fly;
+            const int j = jb + (int)flx, i = ib + (int)fly;
+            const bool j0in = j >= 0 && j < n, j1in = j + 1 >= 0 && j + 1 < n;
+            const bool i0in = i >= 0 && i < n, i1in = i + 1 >= 0 && i + 1 < n;
+            const int64_t base = (int64_t)i * n + j;
+            const float v00 = (i0in && j0in) ? load_f32(x + base) : 0.0f;
+            const float v01 = (i0in && j1in) ? load_f32(x + base + 1) : 0.0f;
+            const float v10 = (i1in && j0in) ? load_f32(x + base + n) : 0.0f;
+            const float v11 = (i1in && j1in) ? load_f32(x + base + n + 1) : 0.0f;
+            acc += (1.0f - c) * ((1.0f - a) * v00 + a * v01) + c * ((1.0f - a) * v10 + a * v11);
+        }
     }
     sino[idx] = from_f32<T>(h * acc);
 }
@@ -50,9 +65,10 @@ __device__ __forceinline__ float det_coord(const ViewF& vf, float x, float y) {
 // bilinear weight of sample k of ray (v, d) on pixel (i, j).  Candidate rays are those whose
 // detector index lies between the projections of the pixel's 2x2 support square; candidate
 // samples lie within (|dx|+|dy|)/|step|^2 of the ray's closest approach.  Extra candidates
-// contribute exactly zero, so the windows only need to be wide enough.
+// contribute exactly zero, so the windows only need to be wide enough.  The first candidate's
+// offset from the pixel is re-based from the split-precision table.
 template <typename T>
-__global__ void backward_plain_kernel(const T* __restrict__ sino, T* __restrict__ img, const RayF* __restrict__ rays,
+__global__ void backward_plain_kernel(const T* __restrict__ sino, T* __restrict__ img, const RayT* __restrict__ rays,
                                       const int* __restrict__ nks, const ViewF* __restrict__ views, int n, int V,
                                       int D, int64_t total, float h) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -79,19 +95,27 @@ __global__ void backward_plain_kernel(const T* __restrict__ sino, T* __restrict_
             const int64_t r = (int64_t)v * D + d;
             const int nk = nks[r];
             if (nk == 0) continue;
-            const RayF ray = rays[r];
-            const float il = 1.0f / fmaf(ray.dx, ray.dx, ray.dy * ray.dy);
-            const float kc = fmaf(xf - ray.fx0, ray.dx, (yf - ray.fy0) * ray.dy) * il;
-            const float kr = (fabsf(ray.dx) + fabsf(ray.dy)) * il;
+            const RayT ray = rays[r];
+            const float dx = ray.dxh + ray.dxl, dy = ray.dyh + ray.dyl;
+            const float ex = (float)(j - ray.J0) - ray.fx0, ey = (float)(i - ray.I0) - ray.fy0;
+            const float il = 1.0f / fmaf(dx, dx, dy * dy);
+            const float kc = fmaf(ex, dx, ey * dy) * il;
+            const float kr = (fabsf(dx) + fabsf(dy)) * il;
             const int k0 = (int)fmaxf(0.0f, ceilf(kc - kr - eps));
             const int k1 = (int)fminf((float)(nk - 1), floorf(kc + kr + eps));
+            if (k0 > k1) continue;
+            const float k0f = (float)k0;
+            const float qx = k0f * ray.dxh, qy = k0f * ray.dyh;   // exact products
+            const float Qx = floorf(qx), Qy = floorf(qy);
+            float rx = ((float)(ray.J0 - j) + Qx) + fmaf(k0f, ray.dxl, ray.fx0 + (qx - Qx));
+            float ry = ((float)(ray.I0 - i) + Qy) + fmaf(k0f, ray.dyl, ray.fy0 + (qy - Qy));
             float w = 0.0f;
             for (int k = k0; k <= k1; ++k) {
-                const float fx = fmaf((float)k, ray.dx, ray.fx0);
-                const float fy = fmaf((float)k, ray.dy, ray.fy0);
-                const float wx = fmaxf(0.0f, 1.0f - fabsf(fx - xf));
-                const float wy = fmaxf(0.0f, 1.0f - fabsf(fy - yf));
+                const float wx = fmaxf(0.0f, 1.0f - fabsf(rx));
+                const float wy = fmaxf(0.0f, 1.0f - fabsf(ry));
                 w = fmaf(wx, wy, w);
+                rx += dx;
+                ry += dy;
             }
             if (w != 0.0f) acc = fmaf(w, load_f32(y + r), acc);
         }

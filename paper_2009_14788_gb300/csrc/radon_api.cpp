@@ -68,7 +68,7 @@ radon_status validate_call(const radon_geometry* g, const void* in, const void* 
 radon_status upload(radon_geometry* g) {
     cudaError_t e;
     const size_t nr = g->h_ray.size();
-    if ((e = cudaMalloc(&g->d_ray, std::max<size_t>(1, nr) * sizeof(RayF))) != cudaSuccess)
+    if ((e = cudaMalloc(&g->d_ray, std::max<size_t>(1, nr) * sizeof(RayT))) != cudaSuccess)
         return e == cudaErrorMemoryAllocation ? fail(RADON_ERR_OOM, "device allocation of ray table failed")
                                               : cuda_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&g->d_nk, std::max<size_t>(1, nr) * sizeof(int))) != cudaSuccess)
@@ -77,7 +77,7 @@ radon_status upload(radon_geometry* g) {
     if ((e = cudaMalloc(&g->d_view, std::max<size_t>(1, g->h_view.size()) * sizeof(ViewF))) != cudaSuccess)
         return e == cudaErrorMemoryAllocation ? fail(RADON_ERR_OOM, "device allocation of view table failed")
                                               : cuda_fail(e, "cudaMalloc");
-    if ((e = cudaMemcpy(g->d_ray, g->h_ray.data(), nr * sizeof(RayF), cudaMemcpyHostToDevice)) != cudaSuccess)
+    if ((e = cudaMemcpy(g->d_ray, g->h_ray.data(), nr * sizeof(RayT), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpy ray table");
     if ((e = cudaMemcpy(g->d_nk, g->h_nk.data(), nr * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpy count table");
@@ -223,7 +223,20 @@ radon_status radon_geometry_copy_rays(const radon_geometry* g, float* rays, int3
     radon_status st = validate_geometry(g);
     if (st != RADON_OK) return st;
     const size_t nr = (size_t)g->V * g->D;
-    if (rays != nullptr) std::memcpy(rays, g->h_ray.data(), nr * sizeof(RayF));
+    if (rays != nullptr) {
+        for (size_t r = 0; r < nr; ++r) {
+            const RayT& t = g->h_ray[r];
+            float* o = rays + 8 * r;
+            o[0] = (float)t.J0;
+            o[1] = (float)t.I0;
+            o[2] = t.fx0;
+            o[3] = t.fy0;
+            o[4] = t.dxh;
+            o[5] = t.dyh;
+            o[6] = t.dxl;
+            o[7] = t.dyl;
+        }
+    }
     if (counts != nullptr) std::memcpy(counts, g->h_nk.data(), nr * sizeof(int));
     return RADON_OK;
 }

@@ -13,11 +13,17 @@ namespace radon {
 
 constexpr uint64_t kGeometryMagic = 0x5241444f4e47454fULL;  // "RADONGEO"
 
-// One ray in pixel-index coordinates (column x = j, row y = i).  Sample k' = 0..nk-1 sits at
-// (fx0 + k' dx, fy0 + k' dy).  The ray is oriented so that its major-axis step is >= 0: the
-// y step for views of the vertical class, the x step for the horizontal class.
-struct RayF {
-    float fx0, fy0, dx, dy;
+// One ray in pixel-index coordinates (column x = j, row y = i), stored in split precision so
+// kernels can re-base sample positions without FP32 drift.  Sample k' = 0..nk-1 sits at
+//     x = J0 + fx0 + k' (dxh + dxl),   y = I0 + fy0 + k' (dyh + dyl)
+// with J0, I0 integers, fx0, fy0 in [0, 1), and the step split so that k' * dxh is exact in
+// FP32 for every k' < nk (dxh carries at most 24 - ceil(log2 nk) significant bits) while dxl
+// holds the remainder.  The ray is oriented so that its major-axis step is >= 0: the y step for
+// views of the vertical class, the x step for the horizontal class.
+struct RayT {
+    int J0, I0;
+    float fx0, fy0;
+    float dxh, dyh, dxl, dyl;
 };
 
 // Per-view projective map from a point (x = j, y = i, index coordinates) to the continuous
@@ -37,10 +43,10 @@ struct radon_geometry {
     int64_t samples = 0;
     int max_nk = 0;
     std::vector<double> angles;
-    std::vector<radon::RayF> h_ray;   // [V*D]
+    std::vector<radon::RayT> h_ray;   // [V*D]
     std::vector<int> h_nk;            // [V*D]
     std::vector<radon::ViewF> h_view; // [V]
-    radon::RayF* d_ray = nullptr;
+    radon::RayT* d_ray = nullptr;
     int* d_nk = nullptr;
     radon::ViewF* d_view = nullptr;
 };

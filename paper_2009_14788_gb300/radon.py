@@ -79,8 +79,9 @@ class Geometry:
         return (self.n_angles, self.det_count)
 
     def rays(self) -> tuple[np.ndarray, np.ndarray]:
-        """The FP32 ray table the kernels read: ([V, D, 4] (fx0, fy0, dx, dy), [V, D] sample counts)."""
-        rays = np.zeros((self.n_angles, self.det_count, 4), dtype=np.float32)
+        """The split-precision ray table the kernels read: ([V, D, 8] (J0, I0, fx0, fy0, dxh, dyh, dxl, dyl),
+        [V, D] sample counts); sample k sits at (J0 + fx0 + k (dxh + dxl), I0 + fy0 + k (dyh + dyl))."""
+        rays = np.zeros((self.n_angles, self.det_count, 8), dtype=np.float32)
         counts = np.zeros((self.n_angles, self.det_count), dtype=np.int32)
         L.check(L.radon_geometry_copy_rays(self._h, rays.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                            counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
@@ -112,6 +113,17 @@ def _check_tensor(t: torch.Tensor, what: str, geom: Geometry):
         raise TypeError("%s dtype must be float32, float16 or bfloat16, got %s" % (what, t.dtype))
 
 
+def _check_out(out: torch.Tensor, like: torch.Tensor, shape) -> torch.Tensor:
+    """The library writes through raw pointers: an output buffer must match exactly."""
+    if not isinstance(out, torch.Tensor):
+        raise TypeError("out must be a torch.Tensor")
+    if out.dtype != like.dtype or out.device != like.device or tuple(out.shape) != tuple(shape) \
+            or not out.is_contiguous():
+        raise ValueError("out must be a contiguous %s tensor of shape %s on %s, got %s %s on %s"
+                         % (like.dtype, tuple(shape), like.device, out.dtype, tuple(out.shape), out.device))
+    return out
+
+
 def forward_raw(geom: Geometry, x: torch.Tensor, config=None, out=None) -> torch.Tensor:
     """y = A x through ``radon_forward`` / ``radon_forward_ex`` (no autograd)."""
     _check_tensor(x, "image", geom)
@@ -120,7 +132,7 @@ def forward_raw(geom: Geometry, x: torch.Tensor, config=None, out=None) -> torch
     x = x.contiguous()
     batch = x.numel() // (geom.n * geom.n)
     shape = tuple(x.shape[:-2]) + geom.sino_shape
-    y = torch.empty(shape, dtype=x.dtype, device=x.device) if out is None else out
+    y = torch.empty(shape, dtype=x.dtype, device=x.device) if out is None else _check_out(out, x, shape)
     stream = torch.cuda.current_stream(x.device).cuda_stream
     with torch.cuda.device(x.device):
         if config is None:
@@ -140,7 +152,7 @@ def backward_raw(geom: Geometry, y: torch.Tensor, config=None, out=None) -> torc
     y = y.contiguous()
     batch = y.numel() // (geom.n_angles * geom.det_count)
     shape = tuple(y.shape[:-2]) + (geom.n, geom.n)
-    x = torch.empty(shape, dtype=y.dtype, device=y.device) if out is None else out
+    x = torch.empty(shape, dtype=y.dtype, device=y.device) if out is None else _check_out(out, y, shape)
     stream = torch.cuda.current_stream(y.device).cuda_stream
     with torch.cuda.device(y.device):
         if config is None:
