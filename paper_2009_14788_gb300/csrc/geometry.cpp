@@ -190,7 +190,62 @@ radon_status build_geometry(radon_geometry* g) {
     }
     g->samples = total;
     g->max_nk = max_nk;
+    g->bwd_window = backward_window_width(g, 16);
     return RADON_OK;
+}
+
+namespace {
+
+double view_t(const ViewF& vf, double x, double y) {
+    return ((double)vf.ax * x + (double)vf.ay * y + (double)vf.a0) / ((double)vf.bx * x + (double)vf.by * y + (double)vf.b0);
+}
+
+// Detector window [floor(tmin - r - 0.01), floor(tmax + r)] of one tile and view, as the tiled adjoint
+// computes it (the kernel uses FP32; the caller adds slack).
+int tile_window(const radon_geometry* g, const ViewF& vf, int ti, int tj, int tile) {
+    const double x0 = tj, x1 = std::min(tj + tile - 1, g->n - 1), y0 = ti, y1 = std::min(ti + tile - 1, g->n - 1);
+    const double ts[4] = {view_t(vf, x0, y0), view_t(vf, x1, y0), view_t(vf, x0, y1), view_t(vf, x1, y1)};
+    const double tmin = std::min(std::min(ts[0], ts[1]), std::min(ts[2], ts[3]));
+    const double tmax = std::max(std::max(ts[0], ts[1]), std::max(ts[2], ts[3]));
+    double r;
+    if (vf.bx == 0.0f && vf.by == 0.0f) {
+        r = (std::fabs((double)vf.ax) + std::fabs((double)vf.ay)) / (double)vf.b0;
+    } else {
+        r = 0.0;
+        for (int c = 0; c < 4; ++c) {
+            const double cx = (c & 1) ? x1 : x0, cy = (c & 2) ? y1 : y0;
+            const double s[4] = {view_t(vf, cx - 1, cy - 1), view_t(vf, cx + 1, cy - 1), view_t(vf, cx - 1, cy + 1),
+                                 view_t(vf, cx + 1, cy + 1)};
+            const double mx = std::max(std::max(s[0], s[1]), std::max(s[2], s[3]));
+            const double mn = std::min(std::min(s[0], s[1]), std::min(s[2], s[3]));
+            r = std::max(r, 0.5 * (mx - mn));
+        }
+        r = r * 1.05 + 0.02;
+    }
+    r += 0.01;
+    const double lo = std::floor(tmin - r - 0.01), hi = std::floor(tmax + r);
+    return (int)(hi - lo) + 1;
+}
+
+}  // namespace
+
+int backward_window_width(const radon_geometry* g, int tile) {
+    const int tiles = (g->n + tile - 1) / tile;
+    const bool all = (double)tiles * tiles * g->V <= 2e7;
+    int w = 0;
+    for (int v = 0; v < g->V; ++v) {
+        const ViewF& vf = g->h_view[v];
+        for (int a = 0; a < tiles; ++a) {
+            for (int b = 0; b < tiles; ++b) {
+                // very large geometries: boundary tiles only (the projected width peaks nearest the
+                // source, i.e. on the image boundary) plus a 10% margin below
+                if (!all && a != 0 && a != tiles - 1 && b != 0 && b != tiles - 1) continue;
+                w = std::max(w, tile_window(g, vf, a * tile, b * tile, tile));
+            }
+        }
+    }
+    if (!all) w = w + w / 10 + 1;
+    return w;
 }
 
 }  // namespace radon

@@ -185,6 +185,15 @@ radon_status dispatch(const radon_geometry* g, const void* in, void* out, radon_
     st = check_device(g);
     if (st != RADON_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    const int images = cfg ? cfg->images_per_cta : 0;
+    if (!forward && algo != RADON_ALGO_PLAIN) {
+        std::string why;
+        st = launch_backward_tiled(g, in, out, dt, batch, images, s, &why);
+        if (st == RADON_OK) return RADON_OK;
+        if (st != RADON_ERR_UNSUPPORTED || algo == RADON_ALGO_TILED) return fail(st, why);
+        // AUTO: this geometry / buffer does not fit the tiled kernel; the plain kernel serves it
+    }
+    if (forward && algo == RADON_ALGO_TILED) return fail(RADON_ERR_UNSUPPORTED, "no tiled forward kernel in this build");
     cudaError_t e;
     if (forward) {
         e = launch_forward_plain(g, in, out, dt, batch, threads, s);

@@ -42,6 +42,7 @@ struct radon_geometry {
     double ds = 1.0, h = 1.0, S = 0.0, Ddet = 0.0;
     int64_t samples = 0;
     int max_nk = 0;
+    int bwd_window = 0;               // widest detector window of a 16x16 tile (tiled adjoint)
     std::vector<double> angles;
     std::vector<radon::RayT> h_ray;   // [V*D]
     std::vector<int> h_nk;            // [V*D]
@@ -55,6 +56,7 @@ namespace radon {
 
 // geometry.cpp
 radon_status build_geometry(radon_geometry* g);  // fills host tables and sample count
+int backward_window_width(const radon_geometry* g, int tile);
 const char* set_error(const std::string& msg);   // thread-local message, returns it
 
 // kernels_plain.cu
@@ -62,6 +64,10 @@ cudaError_t launch_forward_plain(const radon_geometry* g, const void* img, void*
                                  int threads, cudaStream_t s);
 cudaError_t launch_backward_plain(const radon_geometry* g, const void* sino, void* img, radon_dtype dt, int batch,
                                   int threads, cudaStream_t s);
+
+// backward_tiled.cu: RADON_ERR_UNSUPPORTED if the geometry / buffers do not fit the tiled kernel
+radon_status launch_backward_tiled(const radon_geometry* g, const void* sino, void* img, radon_dtype dt, int batch,
+                                   int images_per_cta, cudaStream_t s, std::string* why);
 
 // kernels_common.cu
 cudaError_t read_and_clear_device_error(int* out);
