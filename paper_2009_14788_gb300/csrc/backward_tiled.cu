@@ -73,7 +73,7 @@ radon_status launch_backward_tiled(const radon_geometry* g, const void* sino, vo
         *why = "sinogram pointer not 16-byte aligned";
         return RADON_ERR_UNSUPPORTED;
     }
-    const int wd = ((g->bwd_window + 2) + 3) / 4 * 4;
+    const int wd = ((g->bwd_window + 2) + align - 1) / align * align;   // box bytes stay a multiple of 16
     const int wdb = wd + align;
     if (wdb > 256) {
         *why = "detector window wider than a TMA box";
