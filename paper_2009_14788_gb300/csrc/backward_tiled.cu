@@ -96,12 +96,23 @@ radon_status launch_backward_tiled(const radon_geometry* g, const void* sino, vo
         *why = "shared memory budget exceeded";
         return RADON_ERR_UNSUPPORTED;
     }
+    // The whole sinogram batch as one 1-D tensor (element x = (b V + v) D + d): per-view windows
+    // need no row-stride alignment, so any detector count works.  A rank-2 description with a
+    // unit outer dimension is the same layout, used if the driver refuses rank 1.
     CUtensorMap map;
-    const uint64_t dims[1] = {(uint64_t)total};
-    const uint32_t box[1] = {(uint32_t)wdb};
-    if (!encode_tiled(&map, tma_dtype(dt), 1, const_cast<void*>(sino), dims, nullptr, box,
-                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B)) {
-        *why = "cuTensorMapEncodeTiled rejected the sinogram descriptor";
+    const uint64_t dims[2] = {(uint64_t)total, 1};
+    const uint64_t strides[1] = {(uint64_t)((total * esz + 15) / 16 * 16)};
+    const uint32_t box[2] = {(uint32_t)wdb, 1};
+    int rank = 1;
+    int rc = encode_tiled(&map, tma_dtype(dt), 1, const_cast<void*>(sino), dims, strides, box,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
+    if (rc != 0) {
+        rank = 2;
+        rc = encode_tiled(&map, tma_dtype(dt), 2, const_cast<void*>(sino), dims, strides, box,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
+    }
+    if (rc != 0) {
+        *why = "cuTensorMapEncodeTiled rejected the sinogram descriptor (CUresult " + std::to_string(rc) + ")";
         return RADON_ERR_UNSUPPORTED;
     }
     BwdTiledArgs a;
@@ -127,6 +138,7 @@ radon_status launch_backward_tiled(const radon_geometry* g, const void* sino, vo
     const char* stall = std::getenv("RADON_TEST_STALL_TMA");
     a.stall_test = (stall != nullptr && stall[0] == '1') ? 1 : 0;
     a.spin_limit = a.stall_test ? 4096u : kSpinLimit;
+    a.tma_rank = rank;
     dim3 grid((unsigned)(a.tiles_x * a.tiles_x), (unsigned)((batch + bg - 1) / bg));
     cudaError_t e;
     switch (dt) {

@@ -45,6 +45,7 @@ struct BwdTiledArgs {
     int* err;
     uint32_t spin_limit;
     int stall_test;    // 1: issue no copies (exercises the bounded-wait expiry path)
+    int tma_rank;      // 1: 1-D descriptor; 2: the same layout described with a unit outer dimension
 };
 
 __host__ __device__ inline int bwd_nq(int bg) { return (bg + 3) / 4; }
@@ -110,7 +111,11 @@ __device__ void bwd_issue_chunk(const CUtensorMap* tmap, const BwdTiledArgs& a, 
         const long long x = (long long)(b0 + b) * a.V * a.D + (long long)(v0 + vl) * a.D + dlo_s[slot * kBwdViews + vl];
         const long long xs = x - (((x % a.align) + a.align) % a.align);   // floor to a 16 B boundary
         off_s[(slot * kBwdViews + vl) * BG + b] = (int)(x - xs);
-        tma_load_1d(stage + ((size_t)(slot * kBwdViews + vl) * BG + b) * a.stage_stride, tmap, &mbar[slot], (int)xs);
+        unsigned char* dst = stage + ((size_t)(slot * kBwdViews + vl) * BG + b) * a.stage_stride;
+        if (a.tma_rank == 1)
+            tma_load_1d(dst, tmap, &mbar[slot], (int)xs);
+        else
+            tma_load_2d(dst, tmap, &mbar[slot], (int)xs, 0);
     }
 }
 

@@ -30,11 +30,11 @@ void resolve() {
 
 }  // namespace
 
-bool encode_tiled(CUtensorMap* map, CUtensorMapDataType dt, int rank, void* base, const uint64_t* dims,
-                  const uint64_t* strides_bytes, const uint32_t* box, CUtensorMapL2promotion l2) {
+int encode_tiled(CUtensorMap* map, CUtensorMapDataType dt, int rank, void* base, const uint64_t* dims,
+                 const uint64_t* strides_bytes, const uint32_t* box, CUtensorMapL2promotion l2) {
     std::call_once(g_once, resolve);
-    if (g_encode == nullptr) return false;
-    cuuint64_t gd[5], gs[4];
+    if (g_encode == nullptr) return -1;
+    cuuint64_t gd[5], gs[5] = {0, 0, 0, 0, 0};
     cuuint32_t bx[5], es[5];
     for (int i = 0; i < rank; ++i) {
         gd[i] = dims[i];
@@ -42,10 +42,9 @@ bool encode_tiled(CUtensorMap* map, CUtensorMapDataType dt, int rank, void* base
         es[i] = 1;
         if (i > 0) gs[i - 1] = strides_bytes[i - 1];
     }
-    CUresult r = g_encode(map, dt, (cuuint32_t)rank, base, gd, rank > 1 ? gs : nullptr, bx, es,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, l2,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
+    CUresult r = g_encode(map, dt, (cuuint32_t)rank, base, gd, gs, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, l2, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return (int)r;
 }
 
 CUtensorMapDataType tma_dtype(radon_dtype dt) {
