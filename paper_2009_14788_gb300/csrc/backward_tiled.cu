@@ -1,7 +1,6 @@
 // Host launcher and instantiations of the tiled gather adjoint (backward_tiled.cuh).
 #include <cmath>
 #include <cstdlib>
-#include <mutex>
 
 #include "backward_tiled.cuh"
 #include "tensor_map.h"
@@ -11,21 +10,6 @@ namespace radon {
 namespace {
 
 constexpr uint32_t kSpinLimit = 1u << 22;   // bounded mbarrier polls (~seconds) before giving up
-
-int* error_word() {
-    // one copy of the word per device; looked up with the launching device current
-    static std::mutex mu;
-    static int* cached[64] = {nullptr};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    std::lock_guard<std::mutex> lock(mu);
-    if (cached[dev] == nullptr) {
-        int* p = nullptr;
-        if (device_error_address(&p) != cudaSuccess) return nullptr;
-        cached[dev] = p;
-    }
-    return cached[dev];
-}
 
 template <typename T, int BG, int KW>
 cudaError_t launch_bg(const CUtensorMap& map, const BwdTiledArgs& a, dim3 grid, size_t smem, cudaStream_t s) {
@@ -130,7 +114,7 @@ radon_status launch_backward_tiled(const radon_geometry* g, const void* sino, vo
     a.align = align;
     a.stage_stride = stage_stride;
     a.tiles_x = (g->n + kBwdTile - 1) / kBwdTile;
-    a.err = error_word();
+    a.err = device_error_word();
     if (a.err == nullptr) {
         *why = "device error word unavailable";
         return RADON_ERR_CUDA;

@@ -1,0 +1,128 @@
+// Host launcher and instantiations of the tiled forward projection (forward_tiled.cuh).
+#include <algorithm>
+
+#include "forward_tiled.cuh"
+#include "tensor_map.h"
+
+namespace radon {
+
+namespace {
+
+constexpr uint32_t kSpinLimit = 1u << 22;   // bounded mbarrier polls (~seconds) before giving up
+
+template <typename T>
+cudaError_t launch_t(const CUtensorMap& mv, const CUtensorMap& mh, const FwdTiledArgs& a, dim3 grid, size_t smem,
+                     cudaStream_t s) {
+    auto kern = forward_tiled_kernel<T>;
+    static size_t attr_bytes = 0;
+    if (smem > attr_bytes) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_bytes = smem;
+    }
+    kern<<<grid, kFwdThreads, smem, s>>>(mv, mh, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+radon_status launch_forward_tiled(radon_geometry* g, const void* img, void* sino, radon_dtype dt, int batch,
+                                  const radon_launch_config* cfg, cudaStream_t s, std::string* why) {
+    const int esz = dt == RADON_F32 ? 4 : 2;
+    const int align = 16 / esz;
+    const int BG = 16 / esz;
+    if (g->n % align != 0) {
+        *why = "image side must be a multiple of 16 bytes of storage for TMA rows";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    if (((uintptr_t)img & 15) != 0) {
+        *why = "image pointer not 16-byte aligned";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    int G = cfg && cfg->views_per_cta ? cfg->views_per_cta : 4;
+    if (G != 1 && G != 2 && G != 4 && G != 8) {
+        *why = "views_per_cta must be 1, 2, 4 or 8 for the tiled forward";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    const int Dt = kFwdThreads / G;
+    const int R = cfg && cfg->rows_per_slab ? cfg->rows_per_slab : 8;
+    if (R < 2 || R > 64) {
+        *why = "rows_per_slab must be in [2, 64]";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    const int maxw = forward_band_width(g, G, Dt, R);
+    const int wbox = (maxw + 2 + align - 1 + align - 1) / align * align;
+    const int rbox_h = (R + 2 + align - 1 + align - 1) / align * align;
+    if (wbox > 256 || rbox_h > 256) {
+        *why = "working band wider than a TMA box";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    const int wc = wbox + ((2 - wbox % 8) + 8) % 8;   // row pitch = 2 (mod 8) texels spreads banks
+    const int stage_bytes = std::max(wbox * (R + 2) * 16, rbox_h * wbox * 16);
+    const size_t smem = fwd_smem_bytes(stage_bytes, R, wc);
+    if (smem > 227 * 1024) {
+        *why = "shared memory budget exceeded";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    int gi = 0;
+    while ((1 << gi) < G) ++gi;
+    const uint64_t dims[3] = {(uint64_t)g->n, (uint64_t)g->n, (uint64_t)batch};
+    const uint64_t strides[2] = {(uint64_t)g->n * esz, (uint64_t)g->n * g->n * esz};
+    const uint32_t box_v[3] = {(uint32_t)wbox, (uint32_t)(R + 2), (uint32_t)BG};
+    const uint32_t box_h[3] = {(uint32_t)rbox_h, (uint32_t)wbox, (uint32_t)BG};
+    CUtensorMap mv, mh;
+    int rc = encode_tiled(&mv, tma_dtype(dt), 3, const_cast<void*>(img), dims, strides, box_v,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
+    if (rc == 0)
+        rc = encode_tiled(&mh, tma_dtype(dt), 3, const_cast<void*>(img), dims, strides, box_h,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
+    if (rc != 0) {
+        *why = "cuTensorMapEncodeTiled rejected the image descriptor (CUresult " + std::to_string(rc) + ")";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    FwdTiledArgs a;
+    a.rays = g->d_ray;
+    a.nks = g->d_nk;
+    a.groups = g->d_groups + g->group_offset[gi];
+    a.sino = sino;
+    a.n = g->n;
+    a.V = g->V;
+    a.D = g->D;
+    a.B = batch;
+    a.h = (float)g->h;
+    a.G = G;
+    a.Dt = Dt;
+    a.n_dr = (g->D + Dt - 1) / Dt;
+    a.R = R;
+    a.n_slabs = (g->n + 3 + R - 1) / R;
+    a.wbox = wbox;
+    a.wc = wc;
+    a.rbox_h = rbox_h;
+    a.align = align;
+    a.stage_bytes = stage_bytes;
+    a.err = device_error_word();
+    if (a.err == nullptr) {
+        *why = "device error word unavailable";
+        return RADON_ERR_CUDA;
+    }
+    a.spin_limit = kSpinLimit;
+    const long long nblk = (long long)g->group_count[gi] * a.n_dr;
+    if (nblk > 0x7fffffffLL) {
+        *why = "too many CTAs";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    dim3 grid((unsigned)nblk, (unsigned)((batch + BG - 1) / BG));
+    cudaError_t e;
+    switch (dt) {
+        case RADON_F16: e = launch_t<__half>(mv, mh, a, grid, smem, s); break;
+        case RADON_BF16: e = launch_t<__nv_bfloat16>(mv, mh, a, grid, smem, s); break;
+        default: e = launch_t<float>(mv, mh, a, grid, smem, s); break;
+    }
+    if (e != cudaSuccess) {
+        *why = std::string("tiled forward launch: ") + cudaGetErrorString(e);
+        return RADON_ERR_CUDA;
+    }
+    return RADON_OK;
+}
+
+}  // namespace radon

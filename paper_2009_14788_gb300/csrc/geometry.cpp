@@ -159,8 +159,14 @@ radon_status build_geometry(radon_geometry* g) {
             const Ray64 r = make_ray(g, v, d);
             long klo = 0, khi = -1;
             const size_t idx = (size_t)v * D + d;
-            if (!k_range(g, r, &klo, &khi)) continue;
-            const int nk = (int)(khi - klo + 1);
+            // A ray that misses the image keeps its line (sample 0 = the foot point) with no samples:
+            // the tiled forward bounds its working band with the lines of its extreme rays.
+            const bool hit = k_range(g, r, &klo, &khi);
+            if (!hit) {
+                klo = 0;
+                khi = 0;
+            }
+            const int nk = hit ? (int)(khi - klo + 1) : 0;
             double sx = g->h * r.ux, sy = g->h * r.uy;
             long kstart = klo;
             const bool flip = major == 0 ? (sy < 0.0) : (sx < 0.0);
@@ -191,6 +197,22 @@ radon_status build_geometry(radon_geometry* g) {
     g->samples = total;
     g->max_nk = max_nk;
     g->bwd_window = backward_window_width(g, 16);
+    // Groups of up to G consecutive views of one orientation class (the tiled forward's CTAs):
+    // entry = (first view, count | class << 16), for G = 1, 2, 4, 8.
+    g->h_groups.clear();
+    for (int gi = 0; gi < 4; ++gi) {
+        const int G = 1 << gi;
+        g->group_offset[gi] = (int)g->h_groups.size();
+        int v = 0;
+        while (v < V) {
+            const int cls = g->h_view[v].major;
+            int cnt = 1;
+            while (cnt < G && v + cnt < V && g->h_view[v + cnt].major == cls) ++cnt;
+            g->h_groups.push_back(Int2{v, cnt | (cls << 16)});
+            v += cnt;
+        }
+        g->group_count[gi] = (int)g->h_groups.size() - g->group_offset[gi];
+    }
     return RADON_OK;
 }
 
@@ -246,6 +268,62 @@ int backward_window_width(const radon_geometry* g, int tile) {
     }
     if (!all) w = w + w / 10 + 1;
     return w;
+}
+
+}  // namespace radon
+
+namespace radon {
+
+// Widest band of the tiled forward, in compute-frame columns: for every CTA (view group x detector
+// range) and slab, the columns between the lines of the CTA's extreme rays over the slab's buffer
+// rows (+-1 row), clamped to the support, with 2 columns of margin on each side -- the formula the
+// kernel evaluates in FP32 (the launcher adds slack for the difference).
+int forward_band_width(radon_geometry* g, int G, int Dt, int R) {
+    const long long key = ((long long)G << 40) | ((long long)Dt << 20) | (long long)R;
+    std::lock_guard<std::mutex> lock(g->band_mu);
+    auto it = g->band_width.find(key);
+    if (it != g->band_width.end()) return it->second;
+    int gi = 0;
+    while ((1 << gi) < G) ++gi;
+    const int n_slabs = (g->n + 3 + R - 1) / R;
+    const int n_dr = (g->D + Dt - 1) / Dt;
+    int maxw = 0;
+    for (int q = 0; q < g->group_count[gi]; ++q) {
+        const Int2 grp = g->h_groups[g->group_offset[gi] + q];
+        const int v0 = grp.x, cnt = grp.y & 0xffff, cls = grp.y >> 16;
+        for (int dr = 0; dr < n_dr; ++dr) {
+            const int d0 = dr * Dt, d1 = std::min(d0 + Dt - 1, g->D - 1);
+            for (int s = 0; s < n_slabs; ++s) {
+                const double ylo = -2.0 + s * R - 1.0, yhi = -2.0 + s * R + R;
+                double xmin = 1e300, xmax = -1e300;
+                for (int vl = 0; vl < cnt; ++vl) {
+                    for (int e = 0; e < 2; ++e) {
+                        const RayT& r = g->h_ray[(size_t)(v0 + vl) * g->D + (e ? d1 : d0)];
+                        const double X0 = cls ? (double)r.I0 + r.fy0 : (double)r.J0 + r.fx0;
+                        const double Y0 = cls ? (double)r.J0 + r.fx0 : (double)r.I0 + r.fy0;
+                        const double dX = cls ? (double)r.dyh + r.dyl : (double)r.dxh + r.dxl;
+                        const double dY = cls ? (double)r.dxh + r.dxl : (double)r.dyh + r.dyl;
+                        if (std::fabs(dY) <= 1e-6 * std::fabs(dX)) {
+                            xmin = std::min(xmin, -3.0);
+                            xmax = std::max(xmax, g->n + 2.0);
+                        } else {
+                            const double sl = dX / dY;
+                            const double xa = X0 + (ylo - 1.0 - Y0) * sl, xb = X0 + (yhi + 1.0 - Y0) * sl;
+                            xmin = std::min(xmin, std::min(xa, xb));
+                            xmax = std::max(xmax, std::max(xa, xb));
+                        }
+                    }
+                }
+                xmin = std::max(xmin, -3.0);
+                xmax = std::min(xmax, g->n + 2.0);
+                if (xmax < xmin) continue;
+                const int w = (int)(std::ceil(xmax) + 2 - (std::floor(xmin) - 2)) + 1;
+                maxw = std::max(maxw, w);
+            }
+        }
+    }
+    g->band_width[key] = maxw;
+    return maxw;
 }
 
 }  // namespace radon

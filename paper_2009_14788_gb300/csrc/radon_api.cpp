@@ -84,6 +84,12 @@ radon_status upload(radon_geometry* g) {
     if ((e = cudaMemcpy(g->d_view, g->h_view.data(), g->h_view.size() * sizeof(ViewF), cudaMemcpyHostToDevice)) !=
         cudaSuccess)
         return cuda_fail(e, "cudaMemcpy view table");
+    if ((e = cudaMalloc(&g->d_groups, std::max<size_t>(1, g->h_groups.size()) * sizeof(Int2))) != cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? fail(RADON_ERR_OOM, "device allocation of view groups failed")
+                                              : cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMemcpy(g->d_groups, g->h_groups.data(), g->h_groups.size() * sizeof(Int2), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy view groups");
     return RADON_OK;
 }
 
@@ -92,6 +98,7 @@ void release(radon_geometry* g) {
     if (g->d_ray) cudaFree(g->d_ray);
     if (g->d_nk) cudaFree(g->d_nk);
     if (g->d_view) cudaFree(g->d_view);
+    if (g->d_groups) cudaFree(g->d_groups);
     g->magic = 0;
     delete g;
 }
@@ -193,7 +200,12 @@ radon_status dispatch(const radon_geometry* g, const void* in, void* out, radon_
         if (st != RADON_ERR_UNSUPPORTED || algo == RADON_ALGO_TILED) return fail(st, why);
         // AUTO: this geometry / buffer does not fit the tiled kernel; the plain kernel serves it
     }
-    if (forward && algo == RADON_ALGO_TILED) return fail(RADON_ERR_UNSUPPORTED, "no tiled forward kernel in this build");
+    if (forward && algo != RADON_ALGO_PLAIN) {
+        std::string why;
+        st = launch_forward_tiled(const_cast<radon_geometry*>(g), in, out, dt, batch, cfg, s, &why);
+        if (st == RADON_OK) return RADON_OK;
+        if (st != RADON_ERR_UNSUPPORTED || algo == RADON_ALGO_TILED) return fail(st, why);
+    }
     cudaError_t e;
     if (forward) {
         e = launch_forward_plain(g, in, out, dt, batch, threads, s);

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -34,6 +36,10 @@ struct ViewF {
     int pad;
 };
 
+struct Int2 {
+    int x, y;
+};
+
 }  // namespace radon
 
 struct radon_geometry {
@@ -43,6 +49,13 @@ struct radon_geometry {
     int64_t samples = 0;
     int max_nk = 0;
     int bwd_window = 0;               // widest detector window of a 16x16 tile (tiled adjoint)
+    std::vector<radon::Int2> h_groups;  // view groups for G = 1, 2, 4, 8 (concatenated)
+    int group_offset[4] = {0, 0, 0, 0};
+    int group_count[4] = {0, 0, 0, 0};
+    radon::Int2* d_groups = nullptr;
+    // widest working band of the tiled forward per (views/CTA, detectors/CTA, rows/slab)
+    std::mutex band_mu;
+    std::map<long long, int> band_width;
     std::vector<double> angles;
     std::vector<radon::RayT> h_ray;   // [V*D]
     std::vector<int> h_nk;            // [V*D]
@@ -57,6 +70,8 @@ namespace radon {
 // geometry.cpp
 radon_status build_geometry(radon_geometry* g);  // fills host tables and sample count
 int backward_window_width(const radon_geometry* g, int tile);
+// widest band (compute-frame columns, before alignment) of the tiled forward; cached per config
+int forward_band_width(radon_geometry* g, int G, int Dt, int R);
 const char* set_error(const std::string& msg);   // thread-local message, returns it
 
 // kernels_plain.cu
@@ -69,8 +84,13 @@ cudaError_t launch_backward_plain(const radon_geometry* g, const void* sino, voi
 radon_status launch_backward_tiled(const radon_geometry* g, const void* sino, void* img, radon_dtype dt, int batch,
                                    int images_per_cta, cudaStream_t s, std::string* why);
 
+// forward_tiled.cu: RADON_ERR_UNSUPPORTED if the geometry / buffers do not fit the tiled kernel
+radon_status launch_forward_tiled(radon_geometry* g, const void* img, void* sino, radon_dtype dt, int batch,
+                                  const radon_launch_config* cfg, cudaStream_t s, std::string* why);
+
 // kernels_common.cu
 cudaError_t read_and_clear_device_error(int* out);
 cudaError_t device_error_address(int** out);
+int* device_error_word();   // cached per device; NULL on failure
 
 }  // namespace radon

@@ -45,6 +45,9 @@ CASES = {
     # steep fan: wide fan angle, detector far away, rays up to ~40 degrees off the central ray
     "fan_steep": dict(kind="fan", n=64, angles=uniform_angles(11, 2 * math.pi), det_count=200, det_spacing=2.0,
                       source_distance=50.0, det_distance=300.0),
+    # a close source (magnification up to ~4 across the image) that the tiled kernels still take
+    "fan_close": dict(kind="fan", n=64, angles=uniform_angles(13, 2 * math.pi) + 0.05, det_count=160,
+                      det_spacing=1.2, source_distance=70.0, det_distance=90.0),
     # detector spacing much finer and much coarser than a pixel
     "parallel_fine": dict(kind="parallel", n=40, angles=uniform_angles(9, math.pi) + 0.1, det_count=200,
                           det_spacing=0.3, step=0.5),

@@ -224,13 +224,13 @@ def test_sample_count_is_the_throughput_unit():
 
 # ---------------------------------------------------------------- tiled kernels: explicit configurations
 
-TILED_CASES = ["parallel_n64_full", "parallel_n256_sub", "fan_n512_sub", "parallel_axes", "fan_steep",
+TILED_CASES = ["parallel_n64_full", "parallel_n256_sub", "fan_n512_sub", "parallel_axes", "fan_close",
                "parallel_fine", "parallel_coarse", "fan_ragged", "parallel_ragged", "one_ray", "one_pixel"]
 
 
 @pytest.mark.parametrize("images", [4, 8, 16])
 @pytest.mark.parametrize("batch", [1, 5, 17])
-@pytest.mark.parametrize("case", ["fan_n512_sub", "parallel_ragged", "fan_steep"])
+@pytest.mark.parametrize("case", ["fan_n512_sub", "parallel_ragged", "fan_close"])
 def test_backward_tiled_image_groups(case, batch, images):
     """Every images-per-CTA setting with full, ragged and single-image batches."""
     g, og = make(case)
@@ -254,6 +254,16 @@ def test_backward_tiled_bounds_word_stays_clear(case, dtype):
     assert rel_l2(got, O.adjoint(og, to_np(ys))) <= tol
 
 
+def test_tiled_refuses_extreme_magnification_and_auto_falls_back():
+    """Source 50 px from the centre of a 64^2 image: a 16^2 tile projects onto hundreds of detector
+    bins, more than one TMA box; TILED reports it, AUTO serves it with the plain kernel."""
+    g, og = make("fan_steep")
+    y = _rand_sino(g.sino_shape, 2, 60)
+    with pytest.raises(L.RadonError, match="TMA box"):
+        backward_raw(g, to_dev(y), launch_config("tiled"))
+    assert rel_l2(to_np(backward_raw(g, to_dev(y))), O.adjoint(og, y)) <= TOL_F32
+
+
 def test_backward_tiled_unsupported_is_reported():
     """A misaligned sinogram cannot be staged by TMA: TILED says so, AUTO serves it with the plain kernel."""
     g, og = make("parallel_n64_full")
@@ -265,3 +275,48 @@ def test_backward_tiled_unsupported_is_reported():
         backward_raw(g, view, launch_config("tiled"))
     got = to_np(backward_raw(g, view, launch_config("auto")))
     assert rel_l2(got, O.adjoint(og, y)) <= TOL_F32
+
+
+FWD_TILED_CASES = [c for c in TILED_CASES if CASES[c]["n"] % 8 == 0]
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16, torch.bfloat16])
+@pytest.mark.parametrize("case", FWD_TILED_CASES)
+def test_forward_tiled_matches_oracle(case, dtype):
+    """TMA-staged slab forward, every storage type; ragged image group (3 of 4 / 8)."""
+    g, og = make(case)
+    x = _rand_images(g.n, 3, 70)
+    xs = to_dev(x, dtype)
+    got = to_np(forward_raw(g, xs, launch_config("tiled")))
+    assert L.radon_get_device_error(torch.cuda.current_stream().cuda_stream) == L.RADON_OK
+    ref = O.forward(og, to_np(xs))
+    if dtype == torch.float32:
+        assert rel_l2(got, ref) <= TOL_F32
+        assert max_rel(got, ref) <= 2 * TOL_F32
+    else:
+        assert rel_l2(got, ref) <= TOL_16
+
+
+@pytest.mark.parametrize("rows", [3, 8, 16])
+@pytest.mark.parametrize("views", [1, 2, 4, 8])
+@pytest.mark.parametrize("case", ["fan_n512_sub", "parallel_n256_sub", "fan_close"])
+def test_forward_tiled_configs(case, views, rows):
+    g, og = make(case)
+    x = _rand_images(g.n, 9, 80)
+    cfg = launch_config("tiled", views_per_cta=views, rows_per_slab=rows)
+    got = to_np(forward_raw(g, to_dev(x), cfg))
+    assert L.radon_get_device_error(torch.cuda.current_stream().cuda_stream) == L.RADON_OK
+    ref = O.forward(og, x)
+    assert rel_l2(got, ref) <= TOL_F32
+    assert max_rel(got, ref) <= 2 * TOL_F32
+
+
+@pytest.mark.parametrize("case", ["parallel_ragged", "fan_ragged", "one_pixel"])
+def test_forward_tiled_refuses_unaligned_rows_auto_serves(case):
+    """Image rows that are not a multiple of 16 bytes cannot be described to TMA: TILED says so,
+    AUTO serves the request with the plain kernel."""
+    g, og = make(case)
+    x = _rand_images(g.n, 2, 90)
+    with pytest.raises(L.RadonError, match="16 bytes"):
+        forward_raw(g, to_dev(x), launch_config("tiled"))
+    assert rel_l2(to_np(forward_raw(g, to_dev(x))), O.forward(og, x)) <= TOL_F32
