@@ -282,6 +282,9 @@ __global__ void __launch_bounds__(kFwdThreads, 2) forward_tiled_kernel(const __g
             // every sample of this slab stays inside the band (the extreme rays' lines enclose the
             // CTA's rays); checked per ray so no access can leave the buffer
             const float ylim = (s == a.n_slabs - 1) ? 3.0e38f : (float)(a.R + 1 - IB);
+            // the ray's next sample may lie in a later slab (rays entering through a side)
+            const bool here = (sY - 0.5f) < (ylim - 0.5f);
+            if (here) {
             const float xa = (float)JB + sX;
             const float span = (s == a.n_slabs - 1 || fabsf(dY) <= 1e-6f * fabsf(dX))
                                    ? (float)(nk - 1 - k) * dX
@@ -321,6 +324,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) forward_tiled_kernel(const __g
                         acc[b] = fmaf(w00, t00[b], fmaf(w01, t01[b], fmaf(w10, t10[b], fmaf(w11, t11[b], acc[b]))));
                 }
                 k += i;
+            }
             }
         }
         __syncthreads();

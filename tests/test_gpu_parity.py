@@ -304,7 +304,12 @@ def test_forward_tiled_configs(case, views, rows):
     g, og = make(case)
     x = _rand_images(g.n, 9, 80)
     cfg = launch_config("tiled", views_per_cta=views, rows_per_slab=rows)
-    got = to_np(forward_raw(g, to_dev(x), cfg))
+    try:
+        got = to_np(forward_raw(g, to_dev(x), cfg))
+    except L.RadonError as exc:
+        # a configuration whose working band exceeds one TMA box is refused, never run
+        assert exc.status == L.RADON_ERR_UNSUPPORTED and "TMA box" in str(exc)
+        return
     assert L.radon_get_device_error(torch.cuda.current_stream().cuda_stream) == L.RADON_OK
     ref = O.forward(og, x)
     assert rel_l2(got, ref) <= TOL_F32
