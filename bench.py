@@ -305,6 +305,30 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile(args):
+    """Only the chosen form's kernels: warmup + steps launches of forward and adjoint, no timing."""
+    import torch
+
+    from paper_2009_14788_gb300 import Geometry, backward_raw, forward_raw, launch_config
+    from paper_2009_14788_gb300.build import build
+
+    build()
+    w = WORKLOADS[args.workload]
+    gargs = workload_geometry_args(w)
+    kind = gargs.pop("kind")
+    geom = Geometry(kind, **gargs)
+    dt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[args.storage]
+    cfg = launch_config(args.algo)
+    x = torch.from_numpy(workload_images(w)).to(device="cuda", dtype=dt)
+    y = forward_raw(geom, x, cfg)
+    for _ in range(args.warmup + args.steps):
+        forward_raw(geom, x, cfg, out=y)
+        backward_raw(geom, y, cfg, out=x)
+    torch.cuda.synchronize()
+    print("profile run: %s %s %s, %d launches of each operator" % (args.workload, args.storage, args.algo,
+                                                                  1 + args.warmup + args.steps))
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 
 def _oracle_sample_geometry(w, stride):
@@ -385,11 +409,15 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-stride", type=int, default=16)
+    ap.add_argument("--profile", action="store_true",
+                    help="run --warmup + --steps fwd/adjoint launches of the chosen form only (for ncu)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile:
+        run_profile(args)
     else:
         run_ours(args)
 

@@ -286,10 +286,10 @@ __global__ void __launch_bounds__(kFwdThreads, 2) forward_tiled_kernel(const __g
             const bool here = (sY - 0.5f) < (ylim - 0.5f);
             if (here) {
             const float xa = (float)JB + sX;
-            const float span = (s == a.n_slabs - 1 || fabsf(dY) <= 1e-6f * fabsf(dX))
-                                   ? (float)(nk - 1 - k) * dX
-                                   : (ylim - sY) / dY * dX;
-            const float xb = xa + span;
+            // samples this slab can take: up to the slab end or the ray's last sample, whichever first
+            float steps = (float)(nk - 1 - k);
+            if (s != a.n_slabs - 1 && fabsf(dY) > 1e-6f * fabsf(dX)) steps = fminf(steps, (ylim - sY) / dY);
+            const float xb = fmaf(steps, dX, xa);
             if (fminf(xa, xb) < 1.0f || fmaxf(xa, xb) > (float)(a.wbox - 2) || IB + sY < 0.5f) {
                 record_device_error(a.err, RADON_ERR_DEVICE_BOUNDS);
                 k = nk;
