@@ -200,23 +200,22 @@ radon_status dispatch(const radon_geometry* g, const void* in, void* out, radon_
         if (st != RADON_ERR_UNSUPPORTED || algo == RADON_ALGO_TILED) return fail(st, why);
         // AUTO: this geometry / buffer does not fit the tiled kernel; the plain kernel serves it
     }
-    if (forward && algo == RADON_ALGO_TILED) {
-        std::string why;
-        st = launch_forward_tiled(const_cast<radon_geometry*>(g), in, out, dt, batch, cfg, s, &why);
-        return st == RADON_OK ? RADON_OK : fail(st, why);
-    }
-    if (forward && algo == RADON_ALGO_AUTO) {
-        // views per CTA in order of preference; a sparse view set or a wide fan may need fewer views
-        // (or more, narrower detector ranges) for the working band to fit one TMA box
+    if (forward && algo != RADON_ALGO_PLAIN) {
+        // An explicit views-per-CTA is used as given.  Otherwise the shapes are tried in order of
+        // preference: a sparse view set or a wide fan may need fewer views (or more, narrower
+        // detector ranges) for the working band to fit one TMA box.
         static const int kViews[4] = {4, 8, 2, 1};
-        for (int i = 0; i < 4; ++i) {
-            radon_launch_config c = {RADON_ALGO_TILED, kViews[i], 0, 0, 0, 0};
-            std::string why;
+        const bool fixed = cfg != nullptr && cfg->views_per_cta != 0;
+        std::string why;
+        for (int i = 0; i < (fixed ? 1 : 4); ++i) {
+            radon_launch_config c = {RADON_ALGO_TILED, fixed ? cfg->views_per_cta : kViews[i],
+                                     cfg ? cfg->rows_per_slab : 0, 0, 0, 0};
             st = launch_forward_tiled(const_cast<radon_geometry*>(g), in, out, dt, batch, &c, s, &why);
             if (st == RADON_OK) return RADON_OK;
             if (st != RADON_ERR_UNSUPPORTED) return fail(st, why);
         }
-        // no tiled configuration fits this geometry / buffer: the plain kernel serves it
+        if (algo == RADON_ALGO_TILED) return fail(st, why);
+        // AUTO: no tiled shape fits this geometry / buffer; the plain kernel serves it
     }
     cudaError_t e;
     if (forward) {
