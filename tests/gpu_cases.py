@@ -30,6 +30,8 @@ CASES = {
     "parallel_n256_sub": _sub(workload_geometry_args(WORKLOADS["parallel_b32_n256_v256_d363"]), slice(0, None, 8)),
     # the 512^2 fan workload, every 30th view
     "fan_n512_sub": _sub(workload_geometry_args(WORKLOADS["fan_b16_n512_v720_d1024"]), slice(0, None, 30)),
+    # the 512^2 fan workload, 24 consecutive views (a contiguous block of the dense view set)
+    "fan_n512_block": _sub(workload_geometry_args(WORKLOADS["fan_b16_n512_v720_d1024"]), slice(100, 124)),
     # ragged sizes, non-unit spacing and step
     "parallel_ragged": dict(kind="parallel", n=97, angles=uniform_angles(13, math.pi) + 0.03, det_count=150,
                             det_spacing=0.83, step=0.7),

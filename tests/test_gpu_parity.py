@@ -224,7 +224,7 @@ def test_sample_count_is_the_throughput_unit():
 
 # ---------------------------------------------------------------- tiled kernels: explicit configurations
 
-TILED_CASES = ["parallel_n64_full", "parallel_n256_sub", "fan_n512_sub", "parallel_axes", "fan_close",
+TILED_CASES = ["parallel_n64_full", "parallel_n256_sub", "fan_n512_block", "parallel_axes", "fan_close",
                "parallel_fine", "parallel_coarse", "fan_ragged", "parallel_ragged", "one_ray", "one_pixel"]
 
 
@@ -299,7 +299,7 @@ def test_forward_tiled_matches_oracle(case, dtype):
 
 @pytest.mark.parametrize("rows", [3, 8, 16])
 @pytest.mark.parametrize("views", [1, 2, 4, 8])
-@pytest.mark.parametrize("case", ["fan_n512_sub", "parallel_n256_sub", "fan_close"])
+@pytest.mark.parametrize("case", ["fan_n512_block", "parallel_n256_sub", "fan_close"])
 def test_forward_tiled_configs(case, views, rows):
     g, og = make(case)
     x = _rand_images(g.n, 9, 80)
@@ -314,6 +314,16 @@ def test_forward_tiled_configs(case, views, rows):
     ref = O.forward(og, x)
     assert rel_l2(got, ref) <= TOL_F32
     assert max_rel(got, ref) <= 2 * TOL_F32
+
+
+def test_forward_tiled_refuses_sparse_wide_views_auto_serves():
+    """Every 30th view of the 512^2 fan set (15 degrees apart): no CTA shape keeps the working band
+    inside one TMA box, so TILED refuses and AUTO serves the request with the plain kernel."""
+    g, og = make("fan_n512_sub")
+    x = _rand_images(g.n, 2, 91)
+    with pytest.raises(L.RadonError, match="TMA box"):
+        forward_raw(g, to_dev(x), launch_config("tiled"))
+    assert rel_l2(to_np(forward_raw(g, to_dev(x))), O.forward(og, x)) <= TOL_F32
 
 
 @pytest.mark.parametrize("case", ["parallel_ragged", "fan_ragged", "one_pixel"])
