@@ -44,15 +44,15 @@ radon_status launch_forward_tiled(radon_geometry* g, const void* img, void* sino
         *why = "views_per_cta must be 1, 2, 4 or 8 for the tiled forward";
         return RADON_ERR_UNSUPPORTED;
     }
-    const int Dt = kFwdThreads / G;
+    const int Dt = kFwdRays / G;
     const int R = cfg && cfg->rows_per_slab ? cfg->rows_per_slab : 8;
-    if (R < 2 || R > 64) {
-        *why = "rows_per_slab must be in [2, 64]";
+    if (R < 2 || R > 64 || (R & 1)) {
+        *why = "rows_per_slab must be even and in [2, 64]";
         return RADON_ERR_UNSUPPORTED;
     }
     const int maxw = forward_band_width(g, G, Dt, R);
     const int wbox = (maxw + 2 + align - 1 + align - 1) / align * align;
-    const int rbox_h = (R + 2 + align - 1 + align - 1) / align * align;
+    const int rbox_h = (R + align + align - 1) / align * align;   // R + 2 rows at an even offset < align
     if (wbox > 256 || rbox_h > 256) {
         *why = "working band wider than a TMA box";
         return RADON_ERR_UNSUPPORTED;
@@ -94,7 +94,7 @@ radon_status launch_forward_tiled(radon_geometry* g, const void* img, void* sino
     a.Dt = Dt;
     a.n_dr = (g->D + Dt - 1) / Dt;
     a.R = R;
-    a.n_slabs = (g->n + 3 + R - 1) / R;
+    a.n_slabs = (g->n + 4 + R - 1) / R;
     a.wbox = wbox;
     a.wc = wc;
     a.rbox_h = rbox_h;

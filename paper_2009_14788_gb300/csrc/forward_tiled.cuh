@@ -1,19 +1,23 @@
 // Tiled forward projection: y[b][v][d] = h * sum_k bilinear(x_b, sample k of ray (v, d)).
 //
-// One CTA owns the rays of G views x Dt detectors (one ray per thread) for BG images and streams
-// the image through shared memory in slabs of R rows of its "compute frame": image rows for views
-// whose rays run mostly along y, image columns (a transposed frame) for the others, so every ray
-// advances monotonically through the slabs.  For each slab:
-//   * warp 0 bounds the working band (the columns crossed by the CTA's extreme rays, whose lines
-//     enclose every ray of the CTA) and issues one 3-D TMA copy of the band for all BG images
-//     into the staging buffer (bounded mbarrier wait);
-//   * all threads repack it into the compute buffer as 16-byte texels [row][col][image] (BG = 4
-//     FP32 or 8 16-bit values), transposing for the horizontal class;
-//   * each ray re-bases its next sample on the band origin from the split-precision table, then
-//     steps through the slab: one position, floor and weight computation per sample serves all
-//     BG images; four 16-byte shared loads fetch the 2x2 texels of every image.
-// The TMA copy of slab s+1 overlaps the compute of slab s.  Shared memory (128 B aligned pieces):
-//   header (mbarrier, status, band origin), staging buffer, compute buffer (R+2) x wc texels.
+// One CTA owns the rays of G views x Dt detectors (one ray per consumer thread, G * Dt = 256) for
+// BG images and streams the image through shared memory in slabs of R rows of its "compute frame":
+// image rows for views whose rays run mostly along y, image columns (a transposed frame) for the
+// others, so every ray advances monotonically through the slabs.
+//
+// Warp-specialised pipeline, no CTA-wide barrier in the slab loop:
+//   * the producer warp bounds the working band of slab s+1 (the columns crossed by the CTA's
+//     extreme rays, whose lines enclose every ray of the CTA), issues one 3-D TMA copy of it for all
+//     BG images into the staging buffer, waits for it (bounded), waits until the consumers have
+//     released the compute buffer it will fill, and repacks the band into 16-byte texels
+//     [row][col][image] (BG = 4 FP32 or 8 16-bit values; transposed for the horizontal class);
+//   * the 8 consumer warps wait for a full buffer, march their rays through the slab -- one
+//     position / floor / weight computation per sample serves all BG images, four 16-byte shared
+//     loads fetch the 2x2 texels of every image -- and release the buffer.
+// Each ray re-bases its next sample on the band origin from the split-precision table at every
+// slab.  All waits are bounded; on expiry the kernel records RADON_ERR_TIMEOUT and unwinds.
+// Shared memory: header (mbarriers, band origins, abort flag), staging buffer, two compute
+// buffers of (R+2) x wc texels.
 #pragma once
 
 #include "device_error.cuh"
@@ -23,7 +27,9 @@
 
 namespace radon {
 
-constexpr int kFwdThreads = 256;
+constexpr int kFwdConsumerWarps = 8;
+constexpr int kFwdRays = kFwdConsumerWarps * 32;          // rays per CTA
+constexpr int kFwdThreads = kFwdRays + 32;                // + one producer warp
 
 struct FwdTiledArgs {
     const RayT* rays;
@@ -32,107 +38,85 @@ struct FwdTiledArgs {
     void* sino;
     int n, V, D, B;
     float h;
-    int G, Dt;            // views and detectors per CTA (G * Dt == kFwdThreads)
+    int G, Dt;            // views and detectors per CTA (G * Dt == kFwdRays)
     int n_dr;             // detector ranges
-    int R;                // slab rows
+    int R;                // slab rows (even)
     int n_slabs;
     int wbox;             // band columns (TMA extent along the compute-frame x)
     int wc;               // compute-buffer row pitch in texels
-    int rbox_h;           // horizontal class: TMA extent along compute rows (>= R + 2 + align - 1)
+    int rbox_h;           // horizontal class: TMA extent along compute rows (>= R + 2 + align - 2)
     int align;            // elements per 16 B
     int stage_bytes;
     int* err;
     uint32_t spin_limit;
 };
 
+__host__ __device__ inline size_t fwd_comp_bytes(int R, int wc) { return (size_t)(R + 2) * wc * 16; }
+
 __host__ __device__ inline size_t fwd_smem_bytes(int stage_bytes, int R, int wc) {
-    return 128 + 128 + (size_t)(stage_bytes + 127) / 128 * 128 + (size_t)(R + 2) * wc * 16;
+    return 128 + 128 + (size_t)(stage_bytes + 127) / 128 * 128 + 2 * ((fwd_comp_bytes(R, wc) + 127) / 128 * 128);
 }
 
-// 16-byte texel -> BG floats
+// 16-byte texel: BG values of one pixel (element b = image b), accumulated with weight w.
 template <typename T>
-struct TexelCvt;
+struct Texel;
 
 template <>
-struct TexelCvt<float> {
+struct Texel<float> {
     static constexpr int BG = 4;
-    __device__ __forceinline__ static void load(const uint4& t, float* v) {
-        v[0] = __uint_as_float(t.x);
-        v[1] = __uint_as_float(t.y);
-        v[2] = __uint_as_float(t.z);
-        v[3] = __uint_as_float(t.w);
+    __device__ __forceinline__ static void fma(float* acc, float w, const uint4& t) {
+        acc[0] = fmaf(w, __uint_as_float(t.x), acc[0]);
+        acc[1] = fmaf(w, __uint_as_float(t.y), acc[1]);
+        acc[2] = fmaf(w, __uint_as_float(t.z), acc[2]);
+        acc[3] = fmaf(w, __uint_as_float(t.w), acc[3]);
     }
 };
 
 template <>
-struct TexelCvt<__half> {
+struct Texel<__half> {
     static constexpr int BG = 8;
-    __device__ __forceinline__ static void load(const uint4& t, float* v) {
-        const unsigned w[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            __half2 h2;
-            memcpy(&h2, &w[i], 4);
-            const float2 f = __half22float2(h2);
-            v[2 * i] = f.x;
-            v[2 * i + 1] = f.y;
-        }
+    __device__ __forceinline__ static void fma2(float* acc, float w, unsigned u) {
+        __half2 h2;
+        memcpy(&h2, &u, 4);
+        const float2 f = __half22float2(h2);
+        acc[0] = fmaf(w, f.x, acc[0]);
+        acc[1] = fmaf(w, f.y, acc[1]);
+    }
+    __device__ __forceinline__ static void fma(float* acc, float w, const uint4& t) {
+        fma2(acc, w, t.x);
+        fma2(acc + 2, w, t.y);
+        fma2(acc + 4, w, t.z);
+        fma2(acc + 6, w, t.w);
     }
 };
 
 template <>
-struct TexelCvt<__nv_bfloat16> {
+struct Texel<__nv_bfloat16> {
     static constexpr int BG = 8;
-    __device__ __forceinline__ static void load(const uint4& t, float* v) {
-        const unsigned w[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            v[2 * i] = __uint_as_float(w[i] << 16);
-            v[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
-        }
+    __device__ __forceinline__ static void fma2(float* acc, float w, unsigned u) {
+        acc[0] = fmaf(w, __uint_as_float(u << 16), acc[0]);
+        acc[1] = fmaf(w, __uint_as_float(u & 0xffff0000u), acc[1]);
+    }
+    __device__ __forceinline__ static void fma(float* acc, float w, const uint4& t) {
+        fma2(acc, w, t.x);
+        fma2(acc + 2, w, t.y);
+        fma2(acc + 4, w, t.z);
+        fma2(acc + 6, w, t.w);
     }
 };
-
-// Storage elements -> one 16-byte texel (element b of the texel = image b).
-template <typename T>
-__device__ __forceinline__ uint4 pack_texel(const T* e);
-
-template <>
-__device__ __forceinline__ uint4 pack_texel<float>(const float* e) {
-    return make_uint4(__float_as_uint(e[0]), __float_as_uint(e[1]), __float_as_uint(e[2]), __float_as_uint(e[3]));
-}
-
-template <typename T>
-__device__ __forceinline__ uint4 pack_texel16(const T* e) {
-    unsigned short u[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) memcpy(&u[i], &e[i], 2);
-    return make_uint4((unsigned)u[0] | ((unsigned)u[1] << 16), (unsigned)u[2] | ((unsigned)u[3] << 16),
-                      (unsigned)u[4] | ((unsigned)u[5] << 16), (unsigned)u[6] | ((unsigned)u[7] << 16));
-}
-
-template <>
-__device__ __forceinline__ uint4 pack_texel<__half>(const __half* e) {
-    return pack_texel16(e);
-}
-template <>
-__device__ __forceinline__ uint4 pack_texel<__nv_bfloat16>(const __nv_bfloat16* e) {
-    return pack_texel16(e);
-}
 
 struct FwdBand {
     int xc0;    // compute-frame column of buffer column 0
-    int yoff;   // horizontal class: staged row offset of buffer row 0
+    int xt;     // horizontal class: TMA start along compute rows (aligned); yoff = ylo - xt
     int bad;    // the band exceeded wbox (recorded; rays outside it are skipped)
 };
 
-// Warp 0: band of slab s and its TMA copy into the staging buffer.
+// Producer warp: band of slab s (all lanes return it) and, from lane 0, its TMA copy.
 template <typename T>
-__device__ void fwd_issue_slab(const CUtensorMap* map_v, const CUtensorMap* map_h, const FwdTiledArgs& a, int s,
-                               int v0, int cnt, int cls, int d0, int b0, uint64_t* mbar, FwdBand* band,
-                               unsigned char* stage) {
+__device__ FwdBand fwd_issue_slab(const CUtensorMap* map_v, const CUtensorMap* map_h, const FwdTiledArgs& a, int s,
+                                  int v0, int cnt, int cls, int d0, int b0, uint64_t* tma_bar, unsigned char* stage) {
     const int lane = threadIdx.x & 31;
-    const int ylo = -3 + s * a.R, yhi = -2 + s * a.R + a.R;
+    const int ylo = -4 + s * a.R, yhi = ylo + a.R + 1;   // buffer rows [ylo, yhi]
     float lo = 3.0e38f, hi = -3.0e38f;
     if (lane < 2 * cnt) {
         const int vl = lane >> 1;
@@ -161,51 +145,164 @@ __device__ void fwd_issue_slab(const CUtensorMap* map_v, const CUtensorMap* map_
     hi = fminf(hi, (float)a.n + 2.0f);
     if (hi < lo) hi = lo;
     const int x_lo = (int)floorf(lo) - 2, x_hi = (int)ceilf(hi) + 2;
-    const int xc0 = cls ? x_lo : x_lo - (((x_lo % a.align) + a.align) % a.align);
+    FwdBand band;
+    band.xc0 = cls ? x_lo : x_lo - (((x_lo % a.align) + a.align) % a.align);
+    band.xt = ylo - (((ylo % a.align) + a.align) % a.align);
+    band.bad = (x_hi - band.xc0 + 1 > a.wbox) ? 1 : 0;
     if (lane == 0) {
-        band->xc0 = xc0;
-        band->bad = (x_hi - xc0 + 1 > a.wbox) ? 1 : 0;
-        uint32_t bytes;
         fence_proxy_async_shared();
         if (cls == 0) {
-            band->yoff = 0;
-            bytes = (uint32_t)(a.wbox * (a.R + 2) * 16);
-            mbar_arrive_expect_tx(mbar, bytes);
-            tma_load_3d(stage, map_v, mbar, xc0, ylo, b0);
+            mbar_arrive_expect_tx(tma_bar, (uint32_t)(a.wbox * (a.R + 2) * 16));
+            tma_load_3d(stage, map_v, tma_bar, band.xc0, ylo, b0);
         } else {
-            const int xt = ylo - (((ylo % a.align) + a.align) % a.align);
-            band->yoff = ylo - xt;
-            bytes = (uint32_t)(a.rbox_h * a.wbox * (int)sizeof(T) * TexelCvt<T>::BG);
-            mbar_arrive_expect_tx(mbar, bytes);
-            tma_load_3d(stage, map_h, mbar, xt, xc0, b0);
+            mbar_arrive_expect_tx(tma_bar, (uint32_t)(a.rbox_h * a.wbox * 16));
+            tma_load_3d(stage, map_h, tma_bar, band.xt, band.xc0, b0);
         }
     }
     __syncwarp();
+    return band;
+}
+
+// Producer warp: staged band (planar per image) -> compute buffer texels [row][col][image].
+// Pairs of adjacent elements are read as one 32-bit (16-bit storage) or 64-bit (FP32) word.
+template <typename T>
+__device__ void fwd_repack(const FwdTiledArgs& a, int cls, int yoff, const unsigned char* stage, uint4* comp) {
+    const int lane = threadIdx.x & 31;
+    const int rows = a.R + 2;
+    if constexpr (sizeof(T) == 2) {
+        const unsigned short* st = reinterpret_cast<const unsigned short*>(stage);
+        if (cls == 0) {
+            const int half = a.wbox >> 1;
+            for (int e = lane; e < rows * half; e += 32) {
+                const int r = e / half, c = 2 * (e - (e / half) * half);
+                unsigned w[8];
+#pragma unroll
+                for (int b = 0; b < 8; ++b)
+                    w[b] = *reinterpret_cast<const unsigned*>(st + ((size_t)b * rows + r) * a.wbox + c);
+                comp[r * a.wc + c] = make_uint4(__byte_perm(w[0], w[1], 0x5410), __byte_perm(w[2], w[3], 0x5410),
+                                                __byte_perm(w[4], w[5], 0x5410), __byte_perm(w[6], w[7], 0x5410));
+                comp[r * a.wc + c + 1] = make_uint4(__byte_perm(w[0], w[1], 0x7632), __byte_perm(w[2], w[3], 0x7632),
+                                                    __byte_perm(w[4], w[5], 0x7632), __byte_perm(w[6], w[7], 0x7632));
+            }
+        } else {
+            const int half = rows >> 1;
+            for (int e = lane; e < a.wbox * half; e += 32) {
+                const int c = e / half, r = 2 * (e - (e / half) * half);
+                unsigned w[8];
+#pragma unroll
+                for (int b = 0; b < 8; ++b)
+                    w[b] = *reinterpret_cast<const unsigned*>(st + ((size_t)b * a.wbox + c) * a.rbox_h + yoff + r);
+                comp[r * a.wc + c] = make_uint4(__byte_perm(w[0], w[1], 0x5410), __byte_perm(w[2], w[3], 0x5410),
+                                                __byte_perm(w[4], w[5], 0x5410), __byte_perm(w[6], w[7], 0x5410));
+                comp[(r + 1) * a.wc + c] = make_uint4(__byte_perm(w[0], w[1], 0x7632), __byte_perm(w[2], w[3], 0x7632),
+                                                      __byte_perm(w[4], w[5], 0x7632), __byte_perm(w[6], w[7], 0x7632));
+            }
+        }
+    } else {
+        const float* st = reinterpret_cast<const float*>(stage);
+        if (cls == 0) {
+            const int half = a.wbox >> 1;
+            for (int e = lane; e < rows * half; e += 32) {
+                const int r = e / half, c = 2 * (e - (e / half) * half);
+                float2 w[4];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) w[b] = *reinterpret_cast<const float2*>(st + ((size_t)b * rows + r) * a.wbox + c);
+                comp[r * a.wc + c] = make_uint4(__float_as_uint(w[0].x), __float_as_uint(w[1].x), __float_as_uint(w[2].x),
+                                                __float_as_uint(w[3].x));
+                comp[r * a.wc + c + 1] = make_uint4(__float_as_uint(w[0].y), __float_as_uint(w[1].y),
+                                                    __float_as_uint(w[2].y), __float_as_uint(w[3].y));
+            }
+        } else {
+            const int half = rows >> 1;
+            for (int e = lane; e < a.wbox * half; e += 32) {
+                const int c = e / half, r = 2 * (e - (e / half) * half);
+                float2 w[4];
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    w[b] = *reinterpret_cast<const float2*>(st + ((size_t)b * a.wbox + c) * a.rbox_h + yoff + r);
+                comp[r * a.wc + c] = make_uint4(__float_as_uint(w[0].x), __float_as_uint(w[1].x), __float_as_uint(w[2].x),
+                                                __float_as_uint(w[3].x));
+                comp[(r + 1) * a.wc + c] = make_uint4(__float_as_uint(w[0].y), __float_as_uint(w[1].y),
+                                                      __float_as_uint(w[2].y), __float_as_uint(w[3].y));
+            }
+        }
+    }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kFwdThreads, 2) forward_tiled_kernel(const __grid_constant__ CUtensorMap map_v,
+__global__ void __launch_bounds__(kFwdThreads, 3) forward_tiled_kernel(const __grid_constant__ CUtensorMap map_v,
                                                                       const __grid_constant__ CUtensorMap map_h,
                                                                       const FwdTiledArgs a) {
-    constexpr int BG = TexelCvt<T>::BG;
+    constexpr int BG = Texel<T>::BG;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem);
-    int* status = reinterpret_cast<int*>(smem + 16);
-    FwdBand* band = reinterpret_cast<FwdBand*>(smem + 32);
+    uint64_t* tma_bar = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + 8);    // [2]
+    uint64_t* empty = reinterpret_cast<uint64_t*>(smem + 24);  // [2]
+    int* band_xc0 = reinterpret_cast<int*>(smem + 40);          // [2]
+    int* band_bad = reinterpret_cast<int*>(smem + 48);          // [2]
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 56);
     unsigned char* stage = smem + 128;
-    uint4* comp = reinterpret_cast<uint4*>(stage + (a.stage_bytes + 127) / 128 * 128);
+    const size_t comp_stride = (fwd_comp_bytes(a.R, a.wc) + 127) / 128 * 128;
+    unsigned char* comp_base = stage + (a.stage_bytes + 127) / 128 * 128;
 
     const int tid = threadIdx.x;
+    const int warp = tid >> 5;
     const int grp_idx = blockIdx.x / a.n_dr, dr = blockIdx.x - (blockIdx.x / a.n_dr) * a.n_dr;
     const Int2 grp = a.groups[grp_idx];
     const int v0 = grp.x, cnt = grp.y & 0xffff, cls = grp.y >> 16;
     const int d0 = dr * a.Dt;
     const int b0 = blockIdx.y * BG;
+
+    if (tid == 0) {
+        mbar_init(tma_bar, 1);
+        mbar_init(&full[0], 32);
+        mbar_init(&full[1], 32);
+        mbar_init(&empty[0], kFwdRays);
+        mbar_init(&empty[1], kFwdRays);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == kFwdConsumerWarps) {
+        // ------------------------------------------------------------------ producer warp
+        const int lane = tid & 31;
+        FwdBand band = fwd_issue_slab<T>(&map_v, &map_h, a, 0, v0, cnt, cls, d0, b0, tma_bar, stage);
+        for (int s = 0; s < a.n_slabs; ++s) {
+            const int buf = s & 1;
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait_bounded(tma_bar, (uint32_t)(s & 1), a.spin_limit);
+            if (ok && s >= 2 && lane == 0)
+                ok = mbar_wait_bounded(&empty[buf], (uint32_t)(((s >> 1) - 1) & 1), a.spin_limit);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) {
+                if (lane == 0) {
+                    record_device_error(a.err, RADON_ERR_TIMEOUT);
+                    *abort_flag = 1;
+                }
+                __syncwarp();
+                mbar_arrive(&full[buf]);   // wake the consumers so they see the abort
+                return;
+            }
+            const int ylo = -4 + s * a.R;
+            fwd_repack<T>(a, cls, ylo - band.xt, stage,
+                          reinterpret_cast<uint4*>(comp_base + (size_t)buf * comp_stride));
+            if (lane == 0) {
+                band_xc0[buf] = band.xc0;
+                band_bad[buf] = band.bad;
+            }
+            __syncwarp();
+            mbar_arrive(&full[buf]);        // every lane: its repacked texels are released
+            if (s + 1 < a.n_slabs)
+                band = fwd_issue_slab<T>(&map_v, &map_h, a, s + 1, v0, cnt, cls, d0, b0, tma_bar, stage);
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------------- consumer warps
     const int vl = tid / a.Dt, d = d0 + (tid - (tid / a.Dt) * a.Dt);
     const bool active = vl < cnt && d < a.D;
-
-    // this thread's ray, in the compute frame (x <-> y swapped for the horizontal class)
     int J0 = 0, I0 = 0, nk = 0;
     float fX0 = 0.f, fY0 = 0.f, dXh = 0.f, dYh = 0.f, dXl = 0.f, dYl = 0.f;
     if (active) {
@@ -224,54 +321,18 @@ __global__ void __launch_bounds__(kFwdThreads, 2) forward_tiled_kernel(const __g
 #pragma unroll
     for (int b = 0; b < BG; ++b) acc[b] = 0.0f;
 
-    if (tid == 0) {
-        mbar_init(mbar, 1);
-        *status = 0;
-        fence_mbar_init();
-    }
-    __syncthreads();
-    if (tid < 32) fwd_issue_slab<T>(&map_v, &map_h, a, 0, v0, cnt, cls, d0, b0, mbar, band, stage);
-
-    const int rows = a.R + 2;
     for (int s = 0; s < a.n_slabs; ++s) {
-        if (tid == 0) *status = mbar_wait_bounded(mbar, (uint32_t)(s & 1), a.spin_limit) ? 0 : 1;
-        __syncthreads();
-        if (*status) {
-            if (tid == 0) {
-                record_device_error(a.err, RADON_ERR_TIMEOUT);
-                mbar_wait_bounded(mbar, (uint32_t)(s & 1), a.spin_limit);   // the copy in flight, once more
-            }
+        const int buf = s & 1;
+        if (!mbar_wait_bounded(&full[buf], (uint32_t)((s >> 1) & 1), a.spin_limit)) {
+            record_device_error(a.err, RADON_ERR_TIMEOUT);
             return;
         }
-        const int xc0 = band->xc0, yoff = band->yoff;
-        if (tid == 0 && band->bad) record_device_error(a.err, RADON_ERR_DEVICE_BOUNDS);
-        // ---- repack the staged band into 16-byte texels [row][col][image]
-        if (cls == 0) {
-            const T* st = reinterpret_cast<const T*>(stage);
-            for (int e = tid; e < rows * a.wbox; e += kFwdThreads) {
-                const int r = e / a.wbox, c = e - (e / a.wbox) * a.wbox;
-                T v[BG];
-#pragma unroll
-                for (int b = 0; b < BG; ++b) v[b] = st[((size_t)b * rows + r) * a.wbox + c];
-                comp[r * a.wc + c] = pack_texel<T>(v);
-            }
-        } else {
-            const T* st = reinterpret_cast<const T*>(stage);
-            for (int e = tid; e < rows * a.wbox; e += kFwdThreads) {
-                const int c = e / rows, r = e - (e / rows) * rows;
-                T v[BG];
-#pragma unroll
-                for (int b = 0; b < BG; ++b) v[b] = st[((size_t)b * a.wbox + c) * a.rbox_h + yoff + r];
-                comp[r * a.wc + c] = pack_texel<T>(v);
-            }
-        }
-        __syncthreads();
-        // ---- staging buffer consumed: copy the next slab while this one is projected
-        if (tid < 32 && s + 1 < a.n_slabs)
-            fwd_issue_slab<T>(&map_v, &map_h, a, s + 1, v0, cnt, cls, d0, b0, mbar, band, stage);
-        // ---- march every ray through the slab
+        if (*abort_flag) return;
+        const int xc0 = band_xc0[buf];
+        if (tid == 0 && band_bad[buf]) record_device_error(a.err, RADON_ERR_DEVICE_BOUNDS);
+        const uint4* comp = reinterpret_cast<const uint4*>(comp_base + (size_t)buf * comp_stride);
         if (k < nk) {
-            const int ylo = -3 + s * a.R;
+            const int ylo = -4 + s * a.R;
             const float kf = (float)k;
             const float qX = kf * dXh, qY = kf * dYh;   // exact products
             const float QX = floorf(qX), QY = floorf(qY);
@@ -279,55 +340,49 @@ __global__ void __launch_bounds__(kFwdThreads, 2) forward_tiled_kernel(const __g
             const float sY = fmaf(kf, dYl, fY0 + (qY - QY));
             const int JB = J0 + (int)QX - xc0;   // band-local integer base of sample k
             const int IB = I0 + (int)QY - ylo;
-            // every sample of this slab stays inside the band (the extreme rays' lines enclose the
-            // CTA's rays); checked per ray so no access can leave the buffer
             const float ylim = (s == a.n_slabs - 1) ? 3.0e38f : (float)(a.R + 1 - IB);
             // the ray's next sample may lie in a later slab (rays entering through a side)
-            const bool here = (sY - 0.5f) < (ylim - 0.5f);
-            if (here) {
-            const float xa = (float)JB + sX;
-            // samples this slab can take: up to the slab end or the ray's last sample, whichever first
-            float steps = (float)(nk - 1 - k);
-            if (s != a.n_slabs - 1 && fabsf(dY) > 1e-6f * fabsf(dX)) steps = fminf(steps, (ylim - sY) / dY);
-            const float xb = fmaf(steps, dX, xa);
-            if (fminf(xa, xb) < 1.0f || fmaxf(xa, xb) > (float)(a.wbox - 2) || IB + sY < 0.5f) {
-                record_device_error(a.err, RADON_ERR_DEVICE_BOUNDS);
-                k = nk;
-            } else {
-                // floors by round-to-nearest of (value - 1/2) through the 1.5 * 2^23 magic constant;
-                // at exact integers either neighbour gives the same bilinear value
-                const float M = 12582912.0f;
-                const unsigned magic = 0x4B400000u;
-                const float sXm = sX - 0.5f, sYm = sY - 0.5f, ylim_m = ylim - 0.5f;
-                const unsigned base = (unsigned)(IB * a.wc + JB) - magic * (unsigned)(a.wc + 1);
-                const unsigned wcu = (unsigned)a.wc;
-                const int kleft = nk - k;
-                int i = 0;
-                float kk = 0.0f;
-                for (; i < kleft; ++i, kk += 1.0f) {
-                    const float fym = fmaf(kk, dY, sYm);
-                    if (fym >= ylim_m) break;
-                    const float fxm = fmaf(kk, dX, sXm);
-                    const float tx = fxm + M, ty = fym + M;
-                    const float ax = fxm - (tx - M), ay = fym - (ty - M);   // in [-1/2, 1/2]
-                    const unsigned idx = __float_as_uint(ty) * wcu + __float_as_uint(tx) + base;
-                    const float wx1 = 0.5f + ax, wx0 = 0.5f - ax, wy1 = 0.5f + ay, wy0 = 0.5f - ay;
-                    const float w00 = wx0 * wy0, w01 = wx1 * wy0, w10 = wx0 * wy1, w11 = wx1 * wy1;
-                    const uint4* p = comp + idx;
-                    float t00[BG], t01[BG], t10[BG], t11[BG];
-                    TexelCvt<T>::load(p[0], t00);
-                    TexelCvt<T>::load(p[1], t01);
-                    TexelCvt<T>::load(p[wcu], t10);
-                    TexelCvt<T>::load(p[wcu + 1], t11);
-#pragma unroll
-                    for (int b = 0; b < BG; ++b)
-                        acc[b] = fmaf(w00, t00[b], fmaf(w01, t01[b], fmaf(w10, t10[b], fmaf(w11, t11[b], acc[b]))));
+            if ((sY - 0.5f) < (ylim - 0.5f)) {
+                // every sample of this slab stays inside the band (the extreme rays' lines enclose
+                // the CTA's rays); checked per ray so that no access can leave the buffer
+                const float xa = (float)JB + sX;
+                float steps = (float)(nk - 1 - k);
+                if (s != a.n_slabs - 1 && fabsf(dY) > 1e-6f * fabsf(dX)) steps = fminf(steps, (ylim - sY) / dY);
+                const float xb = fmaf(steps, dX, xa);
+                if (fminf(xa, xb) < 1.0f || fmaxf(xa, xb) > (float)(a.wbox - 2) || IB + sY < 0.5f) {
+                    record_device_error(a.err, RADON_ERR_DEVICE_BOUNDS);
+                    k = nk;
+                } else {
+                    // floors by round-to-nearest of (value - 1/2) through the 1.5 * 2^23 magic
+                    // constant; at exact integers either neighbour gives the same bilinear value
+                    const float M = 12582912.0f;
+                    const unsigned magic = 0x4B400000u;
+                    const float sXm = sX - 0.5f, sYm = sY - 0.5f, ylim_m = ylim - 0.5f;
+                    const unsigned base = (unsigned)(IB * a.wc + JB) - magic * (unsigned)(a.wc + 1);
+                    const unsigned wcu = (unsigned)a.wc;
+                    const int kleft = nk - k;
+                    int i = 0;
+                    float kk = 0.0f;
+                    for (; i < kleft; ++i, kk += 1.0f) {
+                        const float fym = fmaf(kk, dY, sYm);
+                        if (fym >= ylim_m) break;
+                        const float fxm = fmaf(kk, dX, sXm);
+                        const float tx = fxm + M, ty = fym + M;
+                        const unsigned idx = __float_as_uint(ty) * wcu + __float_as_uint(tx) + base;
+                        const uint4* p = comp + idx;
+                        const uint4 q00 = p[0], q01 = p[1], q10 = p[wcu], q11 = p[wcu + 1];
+                        const float ax = fxm - (tx - M), ay = fym - (ty - M);   // in [-1/2, 1/2]
+                        const float wx1 = 0.5f + ax, wx0 = 0.5f - ax, wy1 = 0.5f + ay, wy0 = 0.5f - ay;
+                        Texel<T>::fma(acc, wx0 * wy0, q00);
+                        Texel<T>::fma(acc, wx1 * wy0, q01);
+                        Texel<T>::fma(acc, wx0 * wy1, q10);
+                        Texel<T>::fma(acc, wx1 * wy1, q11);
+                    }
+                    k += i;
                 }
-                k += i;
-            }
             }
         }
-        __syncthreads();
+        mbar_arrive(&empty[buf]);   // this thread's reads of the buffer are done
     }
     if (active) {
         T* out = reinterpret_cast<T*>(a.sino);

@@ -285,7 +285,7 @@ int forward_band_width(radon_geometry* g, int G, int Dt, int R) {
     if (it != g->band_width.end()) return it->second;
     int gi = 0;
     while ((1 << gi) < G) ++gi;
-    const int n_slabs = (g->n + 3 + R - 1) / R;
+    const int n_slabs = (g->n + 4 + R - 1) / R;
     const int n_dr = (g->D + Dt - 1) / Dt;
     int maxw = 0;
     for (int q = 0; q < g->group_count[gi]; ++q) {
@@ -294,7 +294,7 @@ int forward_band_width(radon_geometry* g, int G, int Dt, int R) {
         for (int dr = 0; dr < n_dr; ++dr) {
             const int d0 = dr * Dt, d1 = std::min(d0 + Dt - 1, g->D - 1);
             for (int s = 0; s < n_slabs; ++s) {
-                const double ylo = -2.0 + s * R - 1.0, yhi = -2.0 + s * R + R;
+                const double ylo = -4.0 + s * R, yhi = ylo + R + 1.0;
                 double xmin = 1e300, xmax = -1e300;
                 for (int vl = 0; vl < cnt; ++vl) {
                     for (int e = 0; e < 2; ++e) {

@@ -204,7 +204,7 @@ radon_status dispatch(const radon_geometry* g, const void* in, void* out, radon_
         // An explicit views-per-CTA is used as given.  Otherwise the shapes are tried in order of
         // preference: a sparse view set or a wide fan may need fewer views (or more, narrower
         // detector ranges) for the working band to fit one TMA box.
-        static const int kViews[4] = {4, 8, 2, 1};
+        static const int kViews[4] = {8, 4, 2, 1};
         const bool fixed = cfg != nullptr && cfg->views_per_cta != 0;
         std::string why;
         for (int i = 0; i < (fixed ? 1 : 4); ++i) {
