@@ -202,6 +202,24 @@ RADON_API radon_status radon_backward_ex(const radon_geometry* geometry, const v
                                int batch, const radon_launch_config* config, void* stream);
 
 /*
+ * Device workspace, in bytes, that radon_forward_ws uses for `batch` images of `dtype`: the batch
+ * packed into 16-byte texels holding 4 (FP32) or 8 (16-bit) images each, once in row order and once
+ * transposed.  Returns 0 for an invalid geometry, dtype or batch.
+ */
+RADON_API size_t radon_forward_workspace_size(const radon_geometry* geometry, radon_dtype dtype, int batch);
+
+/*
+ * Forward projection with a caller-owned device workspace (>= radon_forward_workspace_size bytes,
+ * 16-byte aligned, used in stream order on `stream`, contents overwritten).  The batch is packed
+ * once into the workspace, then every CTA copies its bands of texels straight into shared memory
+ * (the fastest path).  A NULL or too small workspace behaves exactly like radon_forward_ex.
+ * Allocates nothing; can be captured in a CUDA graph.
+ */
+RADON_API radon_status radon_forward_ws(const radon_geometry* geometry, const void* img, void* sino,
+                                        radon_dtype dtype, int batch, const radon_launch_config* config,
+                                        void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * Synchronises `stream`, then reads and clears the library's device error word.
  * Returns RADON_OK, RADON_ERR_TIMEOUT or RADON_ERR_DEVICE_BOUNDS (from kernels), or
  * RADON_ERR_CUDA if the synchronisation itself failed.

@@ -14,10 +14,11 @@ from .radon import (  # noqa: F401
     RadonForwardFunction,
     backward_raw,
     forward_raw,
+    forward_workspace_bytes,
     launch_config,
 )
 
 __all__ = [
     "Geometry", "Radon", "RadonFanbeam", "RadonForwardFunction", "RadonBackprojectionFunction", "forward_raw",
-    "backward_raw", "launch_config",
+    "backward_raw", "launch_config", "forward_workspace_bytes",
 ]

@@ -126,3 +126,116 @@ radon_status launch_forward_tiled(radon_geometry* g, const void* img, void* sino
 }
 
 }  // namespace radon
+
+namespace radon {
+
+namespace {
+
+template <typename T>
+cudaError_t launch_packed_t(const CUtensorMap& mr, const CUtensorMap& mc, const FwdTiledArgs& a, dim3 grid,
+                            size_t smem, cudaStream_t s) {
+    auto kern = forward_packed_kernel<T>;
+    static size_t attr_bytes = 0;
+    if (smem > attr_bytes) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_bytes = smem;
+    }
+    kern<<<grid, kFwdThreads, smem, s>>>(mr, mc, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+radon_status launch_forward_packed(radon_geometry* g, const void* packed, void* sino, radon_dtype dt, int batch,
+                                   const radon_launch_config* cfg, cudaStream_t s, std::string* why) {
+    const int esz = dt == RADON_F32 ? 4 : 2;
+    const int BG = 16 / esz;
+    if (((uintptr_t)packed & 15) != 0) {
+        *why = "workspace not 16-byte aligned";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    const int G = cfg && cfg->views_per_cta ? cfg->views_per_cta : 8;
+    if (G != 1 && G != 2 && G != 4 && G != 8) {
+        *why = "views_per_cta must be 1, 2, 4 or 8 for the tiled forward";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    const int Dt = kFwdRays / G;
+    const int R = cfg && cfg->rows_per_slab ? cfg->rows_per_slab : 16;
+    if (R < 2 || R > 64 || (R & 1)) {
+        *why = "rows_per_slab must be even and in [2, 64]";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    const int maxw = forward_band_width(g, G, Dt, R);
+    int wbox = maxw + 2;
+    wbox += ((2 - wbox % 8) + 8) % 8;   // row pitch = 2 (mod 8) texels spreads shared-memory banks
+    if (wbox > 256) {
+        *why = "working band wider than a TMA box";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    const size_t smem = fwd_packed_smem_bytes(R, wbox);
+    if (smem > 227 * 1024) {
+        *why = "shared memory budget exceeded";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    int gi = 0;
+    while ((1 << gi) < G) ++gi;
+    const int groups = (batch + BG - 1) / BG;
+    const uint64_t n = (uint64_t)g->n;
+    const uint64_t dims[4] = {(uint64_t)BG, n, n, (uint64_t)groups};
+    const uint64_t strides[3] = {16, n * 16, n * n * 16};
+    const uint32_t box[4] = {(uint32_t)BG, (uint32_t)wbox, (uint32_t)(R + 2), 1};
+    const unsigned char* rows = reinterpret_cast<const unsigned char*>(packed);
+    const unsigned char* cols = rows + (size_t)groups * n * n * 16;
+    CUtensorMap mr, mc;
+    int rc = encode_tiled(&mr, tma_dtype(dt), 4, const_cast<unsigned char*>(rows), dims, strides, box,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
+    if (rc == 0)
+        rc = encode_tiled(&mc, tma_dtype(dt), 4, const_cast<unsigned char*>(cols), dims, strides, box,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
+    if (rc != 0) {
+        *why = "cuTensorMapEncodeTiled rejected the packed-image descriptor (CUresult " + std::to_string(rc) + ")";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    FwdTiledArgs a;
+    a.rays = g->d_ray;
+    a.nks = g->d_nk;
+    a.groups = g->d_groups + g->group_offset[gi];
+    a.sino = sino;
+    a.n = g->n;
+    a.V = g->V;
+    a.D = g->D;
+    a.B = batch;
+    a.h = (float)g->h;
+    a.G = G;
+    a.Dt = Dt;
+    a.n_dr = (g->D + Dt - 1) / Dt;
+    a.R = R;
+    a.n_slabs = (g->n + 4 + R - 1) / R;
+    a.wbox = wbox;
+    a.wc = wbox;
+    a.rbox_h = 0;
+    a.align = 1;
+    a.stage_bytes = 0;
+    a.err = device_error_word();
+    if (a.err == nullptr) {
+        *why = "device error word unavailable";
+        return RADON_ERR_CUDA;
+    }
+    a.spin_limit = kSpinLimit;
+    const long long nblk = (long long)g->group_count[gi] * a.n_dr;
+    dim3 grid((unsigned)nblk, (unsigned)groups);
+    cudaError_t e;
+    switch (dt) {
+        case RADON_F16: e = launch_packed_t<__half>(mr, mc, a, grid, smem, s); break;
+        case RADON_BF16: e = launch_packed_t<__nv_bfloat16>(mr, mc, a, grid, smem, s); break;
+        default: e = launch_packed_t<float>(mr, mc, a, grid, smem, s); break;
+    }
+    if (e != cudaSuccess) {
+        *why = std::string("packed forward launch: ") + cudaGetErrorString(e);
+        return RADON_ERR_CUDA;
+    }
+    return RADON_OK;
+}
+
+}  // namespace radon

@@ -53,6 +53,10 @@ struct FwdTiledArgs {
 
 __host__ __device__ inline size_t fwd_comp_bytes(int R, int wc) { return (size_t)(R + 2) * wc * 16; }
 
+__host__ __device__ inline size_t fwd_packed_smem_bytes(int R, int wbox) {
+    return 128 + 128 + 2 * ((fwd_comp_bytes(R, wbox) + 127) / 128 * 128);
+}
+
 __host__ __device__ inline size_t fwd_smem_bytes(int stage_bytes, int R, int wc) {
     return 128 + 128 + (size_t)(stage_bytes + 127) / 128 * 128 + 2 * ((fwd_comp_bytes(R, wc) + 127) / 128 * 128);
 }
@@ -111,10 +115,11 @@ struct FwdBand {
     int bad;    // the band exceeded wbox (recorded; rays outside it are skipped)
 };
 
-// Producer warp: band of slab s (all lanes return it) and, from lane 0, its TMA copy.
-template <typename T>
-__device__ FwdBand fwd_issue_slab(const CUtensorMap* map_v, const CUtensorMap* map_h, const FwdTiledArgs& a, int s,
-                                  int v0, int cnt, int cls, int d0, int b0, uint64_t* tma_bar, unsigned char* stage) {
+// Producer warp: band of slab s (every lane returns it): the columns crossed by the lines of the
+// CTA's extreme rays over the slab's buffer rows (+-1 row), clamped to the support, 2 columns of
+// margin.  `align_x` aligns the start (TMA needs 16-byte aligned starts along the innermost axis).
+__device__ __forceinline__ FwdBand fwd_band(const FwdTiledArgs& a, int s, int v0, int cnt, int cls, int d0,
+                                            int align_x) {
     const int lane = threadIdx.x & 31;
     const int ylo = -4 + s * a.R, yhi = ylo + a.R + 1;   // buffer rows [ylo, yhi]
     float lo = 3.0e38f, hi = -3.0e38f;
@@ -146,9 +151,19 @@ __device__ FwdBand fwd_issue_slab(const CUtensorMap* map_v, const CUtensorMap* m
     if (hi < lo) hi = lo;
     const int x_lo = (int)floorf(lo) - 2, x_hi = (int)ceilf(hi) + 2;
     FwdBand band;
-    band.xc0 = cls ? x_lo : x_lo - (((x_lo % a.align) + a.align) % a.align);
+    band.xc0 = x_lo - (((x_lo % align_x) + align_x) % align_x);
     band.xt = ylo - (((ylo % a.align) + a.align) % a.align);
     band.bad = (x_hi - band.xc0 + 1 > a.wbox) ? 1 : 0;
+    return band;
+}
+
+// Producer warp (repacking pipeline): band of slab s and, from lane 0, its TMA copy into staging.
+template <typename T>
+__device__ FwdBand fwd_issue_slab(const CUtensorMap* map_v, const CUtensorMap* map_h, const FwdTiledArgs& a, int s,
+                                  int v0, int cnt, int cls, int d0, int b0, uint64_t* tma_bar, unsigned char* stage) {
+    const int lane = threadIdx.x & 31;
+    const int ylo = -4 + s * a.R;
+    const FwdBand band = fwd_band(a, s, v0, cnt, cls, d0, cls ? 1 : a.align);
     if (lane == 0) {
         fence_proxy_async_shared();
         if (cls == 0) {
@@ -229,6 +244,107 @@ __device__ void fwd_repack(const FwdTiledArgs& a, int cls, int yoff, const unsig
     }
 }
 
+// Consumer warps: one ray per thread, marched slab by slab through the double-buffered compute
+// buffers (texels [row][col][image], row pitch wc), released through `empty` after each slab.
+template <typename T>
+__device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int d0, int b0, uint64_t* full,
+                            uint64_t* empty, const int* band_xc0, const int* band_bad, volatile int* abort_flag,
+                            const unsigned char* comp_base, size_t comp_stride, int wc) {
+    constexpr int BG = Texel<T>::BG;
+    const int tid = threadIdx.x;
+    const int vl = tid / a.Dt, d = d0 + (tid - (tid / a.Dt) * a.Dt);
+    const bool active = vl < cnt && d < a.D;
+    int J0 = 0, I0 = 0, nk = 0;
+    float fX0 = 0.f, fY0 = 0.f, dXh = 0.f, dYh = 0.f, dXl = 0.f, dYl = 0.f;
+    if (active) {
+        const long long ridx = (long long)(v0 + vl) * a.D + d;
+        const RayT r = a.rays[ridx];
+        nk = a.nks[ridx];
+        if (cls == 0) {
+            J0 = r.J0; I0 = r.I0; fX0 = r.fx0; fY0 = r.fy0; dXh = r.dxh; dYh = r.dyh; dXl = r.dxl; dYl = r.dyl;
+        } else {
+            J0 = r.I0; I0 = r.J0; fX0 = r.fy0; fY0 = r.fx0; dXh = r.dyh; dYh = r.dxh; dXl = r.dyl; dYl = r.dxl;
+        }
+    }
+    const float dX = dXh + dXl, dY = dYh + dYl;
+    int k = 0;
+    float acc[BG];
+#pragma unroll
+    for (int b = 0; b < BG; ++b) acc[b] = 0.0f;
+
+    for (int s = 0; s < a.n_slabs; ++s) {
+        const int buf = s & 1;
+        if (!mbar_wait_bounded(&full[buf], (uint32_t)((s >> 1) & 1), a.spin_limit)) {
+            record_device_error(a.err, RADON_ERR_TIMEOUT);
+            return;
+        }
+        if (*abort_flag) return;
+        const int xc0 = band_xc0[buf];
+        if (tid == 0 && band_bad[buf]) record_device_error(a.err, RADON_ERR_DEVICE_BOUNDS);
+        const uint4* comp = reinterpret_cast<const uint4*>(comp_base + (size_t)buf * comp_stride);
+        if (k < nk) {
+            const int ylo = -4 + s * a.R;
+            const float kf = (float)k;
+            const float qX = kf * dXh, qY = kf * dYh;   // exact products
+            const float QX = floorf(qX), QY = floorf(qY);
+            const float sX = fmaf(kf, dXl, fX0 + (qX - QX));
+            const float sY = fmaf(kf, dYl, fY0 + (qY - QY));
+            const int JB = J0 + (int)QX - xc0;   // band-local integer base of sample k
+            const int IB = I0 + (int)QY - ylo;
+            const float ylim = (s == a.n_slabs - 1) ? 3.0e38f : (float)(a.R + 1 - IB);
+            // the ray's next sample may lie in a later slab (rays entering through a side)
+            if ((sY - 0.5f) < (ylim - 0.5f)) {
+                // every sample of this slab stays inside the band (the extreme rays' lines enclose
+                // the CTA's rays); checked per ray so that no access can leave the buffer
+                const float xa = (float)JB + sX;
+                float steps = (float)(nk - 1 - k);
+                if (s != a.n_slabs - 1 && fabsf(dY) > 1e-6f * fabsf(dX)) steps = fminf(steps, (ylim - sY) / dY);
+                const float xb = fmaf(steps, dX, xa);
+                if (fminf(xa, xb) < 1.0f || fmaxf(xa, xb) > (float)(a.wbox - 2) || IB + sY < 0.5f) {
+                    record_device_error(a.err, RADON_ERR_DEVICE_BOUNDS);
+                    k = nk;
+                } else {
+                    // floors by round-to-nearest of (value - 1/2) through the 1.5 * 2^23 magic
+                    // constant; at exact integers either neighbour gives the same bilinear value
+                    const float M = 12582912.0f;
+                    const unsigned magic = 0x4B400000u;
+                    const float sXm = sX - 0.5f, sYm = sY - 0.5f, ylim_m = ylim - 0.5f;
+                    const unsigned base = (unsigned)(IB * wc + JB) - magic * (unsigned)(wc + 1);
+                    const unsigned wcu = (unsigned)wc;
+                    const int kleft = nk - k;
+                    int i = 0;
+                    float kk = 0.0f;
+                    for (; i < kleft; ++i, kk += 1.0f) {
+                        const float fym = fmaf(kk, dY, sYm);
+                        if (fym >= ylim_m) break;
+                        const float fxm = fmaf(kk, dX, sXm);
+                        const float tx = fxm + M, ty = fym + M;
+                        const unsigned idx = __float_as_uint(ty) * wcu + __float_as_uint(tx) + base;
+                        const uint4* p = comp + idx;
+                        const uint4 q00 = p[0], q01 = p[1], q10 = p[wcu], q11 = p[wcu + 1];
+                        const float ax = fxm - (tx - M), ay = fym - (ty - M);   // in [-1/2, 1/2]
+                        const float wx1 = 0.5f + ax, wx0 = 0.5f - ax, wy1 = 0.5f + ay, wy0 = 0.5f - ay;
+                        Texel<T>::fma(acc, wx0 * wy0, q00);
+                        Texel<T>::fma(acc, wx1 * wy0, q01);
+                        Texel<T>::fma(acc, wx0 * wy1, q10);
+                        Texel<T>::fma(acc, wx1 * wy1, q11);
+                    }
+                    k += i;
+                }
+            }
+        }
+        mbar_arrive(&empty[buf]);   // this thread's reads of the buffer are done
+    }
+    if (active) {
+        T* out = reinterpret_cast<T*>(a.sino);
+        const long long vd = (long long)a.V * a.D;
+        const long long o = (long long)(v0 + vl) * a.D + d;
+#pragma unroll
+        for (int b = 0; b < BG; ++b)
+            if (b0 + b < a.B) out[(long long)(b0 + b) * vd + o] = from_f32<T>(a.h * acc[b]);
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kFwdThreads, 3) forward_tiled_kernel(const __grid_constant__ CUtensorMap map_v,
                                                                       const __grid_constant__ CUtensorMap map_h,
@@ -300,98 +416,75 @@ __global__ void __launch_bounds__(kFwdThreads, 3) forward_tiled_kernel(const __g
         return;
     }
 
-    // ---------------------------------------------------------------------- consumer warps
-    const int vl = tid / a.Dt, d = d0 + (tid - (tid / a.Dt) * a.Dt);
-    const bool active = vl < cnt && d < a.D;
-    int J0 = 0, I0 = 0, nk = 0;
-    float fX0 = 0.f, fY0 = 0.f, dXh = 0.f, dYh = 0.f, dXl = 0.f, dYl = 0.f;
-    if (active) {
-        const long long ridx = (long long)(v0 + vl) * a.D + d;
-        const RayT r = a.rays[ridx];
-        nk = a.nks[ridx];
-        if (cls == 0) {
-            J0 = r.J0; I0 = r.I0; fX0 = r.fx0; fY0 = r.fy0; dXh = r.dxh; dYh = r.dyh; dXl = r.dxl; dYl = r.dyl;
-        } else {
-            J0 = r.I0; I0 = r.J0; fX0 = r.fy0; fY0 = r.fx0; dXh = r.dyh; dYh = r.dxh; dXl = r.dyl; dYl = r.dxl;
-        }
-    }
-    const float dX = dXh + dXl, dY = dYh + dYl;
-    int k = 0;
-    float acc[BG];
-#pragma unroll
-    for (int b = 0; b < BG; ++b) acc[b] = 0.0f;
+    fwd_consume<T>(a, cls, v0, cnt, d0, b0, full, empty, band_xc0, band_bad, abort_flag, comp_base, comp_stride,
+                   a.wc);
+}
 
-    for (int s = 0; s < a.n_slabs; ++s) {
-        const int buf = s & 1;
-        if (!mbar_wait_bounded(&full[buf], (uint32_t)((s >> 1) & 1), a.spin_limit)) {
-            record_device_error(a.err, RADON_ERR_TIMEOUT);
-            return;
-        }
-        if (*abort_flag) return;
-        const int xc0 = band_xc0[buf];
-        if (tid == 0 && band_bad[buf]) record_device_error(a.err, RADON_ERR_DEVICE_BOUNDS);
-        const uint4* comp = reinterpret_cast<const uint4*>(comp_base + (size_t)buf * comp_stride);
-        if (k < nk) {
-            const int ylo = -4 + s * a.R;
-            const float kf = (float)k;
-            const float qX = kf * dXh, qY = kf * dYh;   // exact products
-            const float QX = floorf(qX), QY = floorf(qY);
-            const float sX = fmaf(kf, dXl, fX0 + (qX - QX));
-            const float sY = fmaf(kf, dYl, fY0 + (qY - QY));
-            const int JB = J0 + (int)QX - xc0;   // band-local integer base of sample k
-            const int IB = I0 + (int)QY - ylo;
-            const float ylim = (s == a.n_slabs - 1) ? 3.0e38f : (float)(a.R + 1 - IB);
-            // the ray's next sample may lie in a later slab (rays entering through a side)
-            if ((sY - 0.5f) < (ylim - 0.5f)) {
-                // every sample of this slab stays inside the band (the extreme rays' lines enclose
-                // the CTA's rays); checked per ray so that no access can leave the buffer
-                const float xa = (float)JB + sX;
-                float steps = (float)(nk - 1 - k);
-                if (s != a.n_slabs - 1 && fabsf(dY) > 1e-6f * fabsf(dX)) steps = fminf(steps, (ylim - sY) / dY);
-                const float xb = fmaf(steps, dX, xa);
-                if (fminf(xa, xb) < 1.0f || fmaxf(xa, xb) > (float)(a.wbox - 2) || IB + sY < 0.5f) {
-                    record_device_error(a.err, RADON_ERR_DEVICE_BOUNDS);
-                    k = nk;
+// Packed variant: the image batch was packed once into 16-byte texels (rows / cols copies, see
+// pack.cu), so the producer warp only bounds each band and copies it with one 4-D TMA load straight
+// into the compute buffer it will become (row pitch = band width); no staging, no repack.
+template <typename T>
+__global__ void __launch_bounds__(kFwdThreads, 3) forward_packed_kernel(const __grid_constant__ CUtensorMap map_rows,
+                                                                       const __grid_constant__ CUtensorMap map_cols,
+                                                                       const FwdTiledArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + 8);    // [2]: TMA completion
+    uint64_t* empty = reinterpret_cast<uint64_t*>(smem + 24);  // [2]: consumers released
+    int* band_xc0 = reinterpret_cast<int*>(smem + 40);          // [2]
+    int* band_bad = reinterpret_cast<int*>(smem + 48);          // [2]
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 56);
+    const size_t comp_stride = (fwd_comp_bytes(a.R, a.wbox) + 127) / 128 * 128;
+    unsigned char* comp_base = smem + 128;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int grp_idx = blockIdx.x / a.n_dr, dr = blockIdx.x - (blockIdx.x / a.n_dr) * a.n_dr;
+    const Int2 grp = a.groups[grp_idx];
+    const int v0 = grp.x, cnt = grp.y & 0xffff, cls = grp.y >> 16;
+    const int d0 = dr * a.Dt;
+    const int b0 = blockIdx.y * Texel<T>::BG;
+
+    if (tid == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&empty[0], kFwdRays);
+        mbar_init(&empty[1], kFwdRays);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == kFwdConsumerWarps) {
+        const int lane = tid & 31;
+        const CUtensorMap* map = cls ? &map_cols : &map_rows;
+        for (int s = 0; s < a.n_slabs; ++s) {
+            const int buf = s & 1;
+            const FwdBand band = fwd_band(a, s, v0, cnt, cls, d0, 1);
+            bool ok = true;
+            if (s >= 2 && lane == 0) ok = mbar_wait_bounded(&empty[buf], (uint32_t)(((s >> 1) - 1) & 1), a.spin_limit);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (lane == 0) {
+                if (!ok) {
+                    record_device_error(a.err, RADON_ERR_TIMEOUT);
+                    *abort_flag = 1;
+                    mbar_arrive(&full[buf]);   // completes the phase without data: consumers see the abort
                 } else {
-                    // floors by round-to-nearest of (value - 1/2) through the 1.5 * 2^23 magic
-                    // constant; at exact integers either neighbour gives the same bilinear value
-                    const float M = 12582912.0f;
-                    const unsigned magic = 0x4B400000u;
-                    const float sXm = sX - 0.5f, sYm = sY - 0.5f, ylim_m = ylim - 0.5f;
-                    const unsigned base = (unsigned)(IB * a.wc + JB) - magic * (unsigned)(a.wc + 1);
-                    const unsigned wcu = (unsigned)a.wc;
-                    const int kleft = nk - k;
-                    int i = 0;
-                    float kk = 0.0f;
-                    for (; i < kleft; ++i, kk += 1.0f) {
-                        const float fym = fmaf(kk, dY, sYm);
-                        if (fym >= ylim_m) break;
-                        const float fxm = fmaf(kk, dX, sXm);
-                        const float tx = fxm + M, ty = fym + M;
-                        const unsigned idx = __float_as_uint(ty) * wcu + __float_as_uint(tx) + base;
-                        const uint4* p = comp + idx;
-                        const uint4 q00 = p[0], q01 = p[1], q10 = p[wcu], q11 = p[wcu + 1];
-                        const float ax = fxm - (tx - M), ay = fym - (ty - M);   // in [-1/2, 1/2]
-                        const float wx1 = 0.5f + ax, wx0 = 0.5f - ax, wy1 = 0.5f + ay, wy0 = 0.5f - ay;
-                        Texel<T>::fma(acc, wx0 * wy0, q00);
-                        Texel<T>::fma(acc, wx1 * wy0, q01);
-                        Texel<T>::fma(acc, wx0 * wy1, q10);
-                        Texel<T>::fma(acc, wx1 * wy1, q11);
-                    }
-                    k += i;
+                    band_xc0[buf] = band.xc0;
+                    band_bad[buf] = band.bad;
+                    fence_proxy_async_shared();
+                    mbar_arrive_expect_tx(&full[buf], (uint32_t)(a.wbox * (a.R + 2) * 16));
+                    tma_load_4d(comp_base + (size_t)buf * comp_stride, map, &full[buf], 0, band.xc0, -4 + s * a.R,
+                                blockIdx.y);
                 }
             }
+            __syncwarp();
+            if (!ok) return;
         }
-        mbar_arrive(&empty[buf]);   // this thread's reads of the buffer are done
+        return;
     }
-    if (active) {
-        T* out = reinterpret_cast<T*>(a.sino);
-        const long long vd = (long long)a.V * a.D;
-        const long long o = (long long)(v0 + vl) * a.D + d;
-#pragma unroll
-        for (int b = 0; b < BG; ++b)
-            if (b0 + b < a.B) out[(long long)(b0 + b) * vd + o] = from_f32<T>(a.h * acc[b]);
-    }
+    fwd_consume<T>(a, cls, v0, cnt, d0, b0, full, empty, band_xc0, band_bad, abort_flag, comp_base, comp_stride,
+                   a.wbox);
 }
 
 }  // namespace radon

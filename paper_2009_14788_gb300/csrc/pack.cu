@@ -1,0 +1,105 @@
+// Batch-interleaved packing of an image batch for the packed forward projection.
+//
+// For image group g (BG consecutive images: 4 FP32 or 8 16-bit), two arrays of 16-byte texels:
+//   rows[g][i][j]  = (x[g BG + 0][i][j], ..., x[g BG + BG-1][i][j])
+//   cols[g][j][i]  = the same texel, transposed (the compute frame of horizontal-class views)
+// Images past the batch end read as zero.  One pass over the batch (HBM-bound); every CTA of the
+// forward projection then copies its bands of texels straight into shared memory with TMA.
+#include "dtype.cuh"
+#include "radon_internal.h"
+
+namespace radon {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ uint4 pack16(const T* v);
+
+template <>
+__device__ __forceinline__ uint4 pack16<float>(const float* v) {
+    return make_uint4(__float_as_uint(v[0]), __float_as_uint(v[1]), __float_as_uint(v[2]), __float_as_uint(v[3]));
+}
+
+template <typename T>
+__device__ __forceinline__ unsigned bits16(T v) {
+    unsigned short u;
+    memcpy(&u, &v, 2);
+    return u;
+}
+
+template <>
+__device__ __forceinline__ uint4 pack16<__half>(const __half* v) {
+    return make_uint4(bits16(v[0]) | (bits16(v[1]) << 16), bits16(v[2]) | (bits16(v[3]) << 16),
+                      bits16(v[4]) | (bits16(v[5]) << 16), bits16(v[6]) | (bits16(v[7]) << 16));
+}
+
+template <>
+__device__ __forceinline__ uint4 pack16<__nv_bfloat16>(const __nv_bfloat16* v) {
+    return make_uint4(bits16(v[0]) | (bits16(v[1]) << 16), bits16(v[2]) | (bits16(v[3]) << 16),
+                      bits16(v[4]) | (bits16(v[5]) << 16), bits16(v[6]) | (bits16(v[7]) << 16));
+}
+
+// 32 x 32 pixel tiles; block (32, 8); grid (tiles, tiles, groups).
+template <typename T>
+__global__ void __launch_bounds__(256) pack_interleaved_kernel(const T* __restrict__ img, uint4* __restrict__ rows,
+                                                               uint4* __restrict__ cols, int n, int B) {
+    constexpr int BG = 16 / sizeof(T);
+    __shared__ uint4 tile[32][33];
+    const int g = blockIdx.z;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const long long npix = (long long)n * n;
+    for (int jr = ty; jr < 32; jr += 8) {
+        const int r = r0 + jr, c = c0 + tx;
+        uint4 t = make_uint4(0, 0, 0, 0);
+        if (r < n && c < n) {
+            T v[BG];
+#pragma unroll
+            for (int b = 0; b < BG; ++b) {
+                const int im = g * BG + b;
+                v[b] = im < B ? img[(long long)im * npix + (long long)r * n + c] : from_f32<T>(0.0f);
+            }
+            t = pack16<T>(v);
+            rows[((long long)g * n + r) * n + c] = t;
+        }
+        tile[jr][tx] = t;
+    }
+    __syncthreads();
+    for (int jc = ty; jc < 32; jc += 8) {
+        const int c = c0 + jc, r = r0 + tx;
+        if (r < n && c < n) cols[((long long)g * n + c) * n + r] = tile[tx][jc];
+    }
+}
+
+}  // namespace
+
+size_t packed_image_bytes(int n, int batch, radon_dtype dt) {
+    const int bg = dt == RADON_F32 ? 4 : 8;
+    const long long groups = (batch + bg - 1) / bg;
+    return (size_t)(2 * groups * (long long)n * n * 16);
+}
+
+cudaError_t launch_pack_images(const void* img, void* workspace, int n, int batch, radon_dtype dt, cudaStream_t s) {
+    const int bg = dt == RADON_F32 ? 4 : 8;
+    const int groups = (batch + bg - 1) / bg;
+    if (groups == 0) return cudaSuccess;
+    uint4* rows = reinterpret_cast<uint4*>(workspace);
+    uint4* cols = rows + (size_t)groups * n * n;
+    const dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32), (unsigned)groups);
+    const dim3 block(32, 8);
+    switch (dt) {
+        case RADON_F16:
+            pack_interleaved_kernel<__half><<<grid, block, 0, s>>>((const __half*)img, rows, cols, n, batch);
+            break;
+        case RADON_BF16:
+            pack_interleaved_kernel<__nv_bfloat16><<<grid, block, 0, s>>>((const __nv_bfloat16*)img, rows, cols, n,
+                                                                          batch);
+            break;
+        default:
+            pack_interleaved_kernel<float><<<grid, block, 0, s>>>((const float*)img, rows, cols, n, batch);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace radon

@@ -178,7 +178,8 @@ radon_status create_common(int n, const double* angles, int n_angles, int det_co
 }
 
 radon_status dispatch(const radon_geometry* g, const void* in, void* out, radon_dtype dt, int batch,
-                      const radon_launch_config* cfg, void* stream, bool forward) {
+                      const radon_launch_config* cfg, void* stream, bool forward, void* ws = nullptr,
+                      size_t ws_bytes = 0) {
     radon_status st = validate_call(g, in, out, dt, batch);
     if (st != RADON_OK) return st;
     const int algo = cfg ? cfg->algo : RADON_ALGO_AUTO;
@@ -199,6 +200,27 @@ radon_status dispatch(const radon_geometry* g, const void* in, void* out, radon_
         if (st == RADON_OK) return RADON_OK;
         if (st != RADON_ERR_UNSUPPORTED || algo == RADON_ALGO_TILED) return fail(st, why);
         // AUTO: this geometry / buffer does not fit the tiled kernel; the plain kernel serves it
+    }
+    if (forward && algo != RADON_ALGO_PLAIN && ws != nullptr && ws_bytes >= packed_image_bytes(g->n, batch, dt) &&
+        (g->n * (dt == RADON_F32 ? 4 : 2)) % 16 == 0) {
+        // Packed path: pack the batch once, then copy bands of texels straight into shared memory.
+        static const int kViewsPacked[4] = {8, 4, 2, 1};
+        const bool fixed = cfg != nullptr && cfg->views_per_cta != 0;
+        std::string why;
+        bool packed_done = false;
+        for (int i = 0; i < (fixed ? 1 : 4); ++i) {
+            radon_launch_config c = {RADON_ALGO_TILED, fixed ? cfg->views_per_cta : kViewsPacked[i],
+                                     cfg ? cfg->rows_per_slab : 0, 0, 0, 0};
+            if (!packed_done) {
+                cudaError_t e = launch_pack_images(in, ws, g->n, batch, dt, s);
+                if (e != cudaSuccess) return cuda_fail(e, "pack launch");
+                packed_done = true;
+            }
+            st = launch_forward_packed(const_cast<radon_geometry*>(g), ws, out, dt, batch, &c, s, &why);
+            if (st == RADON_OK) return RADON_OK;
+            if (st != RADON_ERR_UNSUPPORTED) return fail(st, why);
+        }
+        // no packed shape fits: continue with the paths that need no workspace
     }
     if (forward && algo != RADON_ALGO_PLAIN) {
         // An explicit views-per-CTA is used as given.  Otherwise the shapes are tried in order of
@@ -318,6 +340,21 @@ radon_status radon_forward_ex(const radon_geometry* g, const void* img, void* si
 radon_status radon_backward_ex(const radon_geometry* g, const void* sino, void* img, radon_dtype dtype, int batch,
                                const radon_launch_config* config, void* stream) {
     return dispatch(g, sino, img, dtype, batch, config, stream, false);
+}
+
+size_t radon_forward_workspace_size(const radon_geometry* g, radon_dtype dtype, int batch) {
+    if (validate_geometry(g) != RADON_OK) return 0;
+    if (dtype != RADON_F32 && dtype != RADON_F16 && dtype != RADON_BF16) return 0;
+    if (batch < 0) return 0;
+    return packed_image_bytes(g->n, batch, dtype);
+}
+
+radon_status radon_forward_ws(const radon_geometry* g, const void* img, void* sino, radon_dtype dtype, int batch,
+                              const radon_launch_config* config, void* workspace, size_t workspace_bytes,
+                              void* stream) {
+    if (workspace != nullptr && ((uintptr_t)workspace & 15) != 0)
+        return fail(RADON_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
+    return dispatch(g, img, sino, dtype, batch, config, stream, true, workspace, workspace_bytes);
 }
 
 radon_status radon_get_device_error(void* stream) {

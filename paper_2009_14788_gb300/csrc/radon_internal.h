@@ -88,6 +88,14 @@ radon_status launch_backward_tiled(const radon_geometry* g, const void* sino, vo
 radon_status launch_forward_tiled(radon_geometry* g, const void* img, void* sino, radon_dtype dt, int batch,
                                   const radon_launch_config* cfg, cudaStream_t s, std::string* why);
 
+// forward_tiled.cu: the packed-input forward (the workspace already holds pack_images' output)
+radon_status launch_forward_packed(radon_geometry* g, const void* packed, void* sino, radon_dtype dt, int batch,
+                                   const radon_launch_config* cfg, cudaStream_t s, std::string* why);
+
+// pack.cu
+size_t packed_image_bytes(int n, int batch, radon_dtype dt);
+cudaError_t launch_pack_images(const void* img, void* workspace, int n, int batch, radon_dtype dt, cudaStream_t s);
+
 // kernels_common.cu
 cudaError_t read_and_clear_device_error(int* out);
 cudaError_t device_error_address(int** out);

@@ -124,8 +124,17 @@ def _check_out(out: torch.Tensor, like: torch.Tensor, shape) -> torch.Tensor:
     return out
 
 
-def forward_raw(geom: Geometry, x: torch.Tensor, config=None, out=None) -> torch.Tensor:
-    """y = A x through ``radon_forward`` / ``radon_forward_ex`` (no autograd)."""
+def forward_workspace_bytes(geom: Geometry, dtype: torch.dtype, batch: int) -> int:
+    """Bytes of the workspace the packed forward path uses (``radon_forward_workspace_size``)."""
+    return int(L.radon_forward_workspace_size(geom.handle, _DTYPES[dtype], int(batch)))
+
+
+def forward_raw(geom: Geometry, x: torch.Tensor, config=None, out=None, workspace="auto") -> torch.Tensor:
+    """y = A x through the C ABI (no autograd).
+
+    ``workspace``: "auto" allocates the packed-path workspace from PyTorch's caching allocator on
+    the current stream; a uint8 CUDA tensor is used as given; None runs the paths that need none.
+    """
     _check_tensor(x, "image", geom)
     if x.shape[-2:] != (geom.n, geom.n):
         raise ValueError("image must end in (%d, %d), got %s" % (geom.n, geom.n, tuple(x.shape)))
@@ -134,12 +143,26 @@ def forward_raw(geom: Geometry, x: torch.Tensor, config=None, out=None) -> torch
     shape = tuple(x.shape[:-2]) + geom.sino_shape
     y = torch.empty(shape, dtype=x.dtype, device=x.device) if out is None else _check_out(out, x, shape)
     stream = torch.cuda.current_stream(x.device).cuda_stream
+    ws_ptr, ws_bytes = None, 0
+    if isinstance(workspace, str) and workspace == "auto":
+        need = forward_workspace_bytes(geom, x.dtype, batch)
+        if need > 0 and batch > 0:
+            workspace = torch.empty(need, dtype=torch.uint8, device=x.device)
+        else:
+            workspace = None
+    if isinstance(workspace, torch.Tensor):
+        if workspace.device != x.device or not workspace.is_contiguous():
+            raise ValueError("workspace must be a contiguous tensor on %s" % x.device)
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
     with torch.cuda.device(x.device):
-        if config is None:
+        cfg = ctypes.byref(config) if config is not None else None
+        if ws_ptr is not None:
+            st = L.radon_forward_ws(geom.handle, x.data_ptr(), y.data_ptr(), _DTYPES[x.dtype], batch, cfg, ws_ptr,
+                                    ws_bytes, stream)
+        elif config is None:
             st = L.radon_forward(geom.handle, x.data_ptr(), y.data_ptr(), _DTYPES[x.dtype], batch, stream)
         else:
-            st = L.radon_forward_ex(geom.handle, x.data_ptr(), y.data_ptr(), _DTYPES[x.dtype], batch,
-                                    ctypes.byref(config), stream)
+            st = L.radon_forward_ex(geom.handle, x.data_ptr(), y.data_ptr(), _DTYPES[x.dtype], batch, cfg, stream)
     L.check(st, "radon_forward")
     return y
 

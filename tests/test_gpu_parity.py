@@ -280,14 +280,22 @@ def test_backward_tiled_unsupported_is_reported():
 FWD_TILED_CASES = [c for c in TILED_CASES if CASES[c]["n"] % 8 == 0]
 
 
+WS = ["packed", "repack"]   # forward with a workspace (batch packed once) / without (per-CTA repack)
+
+
+def _ws(kind):
+    return "auto" if kind == "packed" else None
+
+
+@pytest.mark.parametrize("ws", WS)
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float16, torch.bfloat16])
 @pytest.mark.parametrize("case", FWD_TILED_CASES)
-def test_forward_tiled_matches_oracle(case, dtype):
-    """TMA-staged slab forward, every storage type; ragged image group (3 of 4 / 8)."""
+def test_forward_tiled_matches_oracle(case, dtype, ws):
+    """TMA-staged slab forward, every storage type, both input paths; ragged image group."""
     g, og = make(case)
     x = _rand_images(g.n, 3, 70)
     xs = to_dev(x, dtype)
-    got = to_np(forward_raw(g, xs, launch_config("tiled")))
+    got = to_np(forward_raw(g, xs, launch_config("tiled"), workspace=_ws(ws)))
     assert L.radon_get_device_error(torch.cuda.current_stream().cuda_stream) == L.RADON_OK
     ref = O.forward(og, to_np(xs))
     if dtype == torch.float32:
@@ -297,15 +305,16 @@ def test_forward_tiled_matches_oracle(case, dtype):
         assert rel_l2(got, ref) <= TOL_16
 
 
+@pytest.mark.parametrize("ws", WS)
 @pytest.mark.parametrize("rows", [2, 8, 16])
 @pytest.mark.parametrize("views", [1, 2, 4, 8])
 @pytest.mark.parametrize("case", ["fan_n512_block", "parallel_n256_sub", "fan_close"])
-def test_forward_tiled_configs(case, views, rows):
+def test_forward_tiled_configs(case, views, rows, ws):
     g, og = make(case)
     x = _rand_images(g.n, 9, 80)
     cfg = launch_config("tiled", views_per_cta=views, rows_per_slab=rows)
     try:
-        got = to_np(forward_raw(g, to_dev(x), cfg))
+        got = to_np(forward_raw(g, to_dev(x), cfg, workspace=_ws(ws)))
     except L.RadonError as exc:
         # a configuration whose working band exceeds one TMA box is refused, never run
         assert exc.status == L.RADON_ERR_UNSUPPORTED and "TMA box" in str(exc)
@@ -333,5 +342,16 @@ def test_forward_tiled_refuses_unaligned_rows_auto_serves(case):
     g, og = make(case)
     x = _rand_images(g.n, 2, 90)
     with pytest.raises(L.RadonError, match="16 bytes"):
-        forward_raw(g, to_dev(x), launch_config("tiled"))
+        forward_raw(g, to_dev(x), launch_config("tiled"), workspace=None)
     assert rel_l2(to_np(forward_raw(g, to_dev(x))), O.forward(og, x)) <= TOL_F32
+
+
+def test_forward_workspace_too_small_uses_paths_without_one():
+    g, og = make("fan_n512_block")
+    x = _rand_images(g.n, 5, 93)
+    from paper_2009_14788_gb300 import forward_workspace_bytes
+    need = forward_workspace_bytes(g, torch.float32, 5)
+    assert need == 2 * 2 * g.n * g.n * 16          # 2 groups of 4 images, rows + transposed copy
+    small = torch.empty(need - 16, dtype=torch.uint8, device="cuda")
+    got = to_np(forward_raw(g, to_dev(x), workspace=small))
+    assert rel_l2(got, O.forward(og, x)) <= TOL_F32
