@@ -201,8 +201,7 @@ radon_status dispatch(const radon_geometry* g, const void* in, void* out, radon_
         if (st != RADON_ERR_UNSUPPORTED || algo == RADON_ALGO_TILED) return fail(st, why);
         // AUTO: this geometry / buffer does not fit the tiled kernel; the plain kernel serves it
     }
-    if (forward && algo != RADON_ALGO_PLAIN && ws != nullptr && ws_bytes >= packed_image_bytes(g->n, batch, dt) &&
-        (g->n * (dt == RADON_F32 ? 4 : 2)) % 16 == 0) {
+    if (forward && algo != RADON_ALGO_PLAIN && ws != nullptr && ws_bytes >= packed_image_bytes(g->n, batch, dt)) {
         // Packed path: pack the batch once, then copy bands of texels straight into shared memory.
         static const int kViewsPacked[4] = {8, 4, 2, 1};
         const bool fixed = cfg != nullptr && cfg->views_per_cta != 0;

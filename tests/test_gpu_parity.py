@@ -355,3 +355,17 @@ def test_forward_workspace_too_small_uses_paths_without_one():
     small = torch.empty(need - 16, dtype=torch.uint8, device="cuda")
     got = to_np(forward_raw(g, to_dev(x), workspace=small))
     assert rel_l2(got, O.forward(og, x)) <= TOL_F32
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("case", ["parallel_ragged", "fan_ragged", "one_pixel", "parallel_coarse"])
+def test_forward_packed_any_image_size(case, dtype):
+    """The packed path addresses 16-byte texels, so image sides that are not a multiple of 16
+    bytes (97, 75, 1, 60 in 16-bit) still take the tiled kernel."""
+    g, og = make(case)
+    x = _rand_images(g.n, 3, 94)
+    xs = to_dev(x, dtype)
+    got = to_np(forward_raw(g, xs, launch_config("tiled"), workspace="auto"))
+    assert L.radon_get_device_error(torch.cuda.current_stream().cuda_stream) == L.RADON_OK
+    ref = O.forward(og, to_np(xs))
+    assert rel_l2(got, ref) <= (TOL_F32 if dtype == torch.float32 else TOL_16)
