@@ -60,14 +60,22 @@ def test_backward_matches_oracle(case, algo):
 @pytest.mark.parametrize("algo", ALGOS)
 @pytest.mark.parametrize("case", ["parallel_n64_full", "fan_n512_sub", "parallel_ragged", "fan_steep"])
 def test_dot_product_on_gpu(case, algo):
+    """<A x, y> = <x, A^T y> with non-negative x, y (the gate), and with zero-mean x, y relative to
+    |A x| |y| (zero-mean data cancel in the inner product, so it is not a relative scale)."""
     g, _ = make(case)
     rng = np.random.default_rng(3)
-    x = to_dev(rng.standard_normal((2, g.n, g.n)))
-    y = to_dev(rng.standard_normal((2,) + g.sino_shape))
     cfg = launch_config(algo)
+    x = to_dev(rng.uniform(0.0, 1.0, (2, g.n, g.n)))
+    y = to_dev(rng.uniform(0.0, 1.0, (2,) + g.sino_shape))
     a = float((forward_raw(g, x, cfg).double() * y.double()).sum())
     b = float((x.double() * backward_raw(g, y, cfg).double()).sum())
     assert abs(a - b) / max(abs(a), abs(b)) <= TOL_DOT
+    x = to_dev(rng.standard_normal((2, g.n, g.n)))
+    y = to_dev(rng.standard_normal((2,) + g.sino_shape))
+    ax = forward_raw(g, x, cfg).double()
+    a = float((ax * y.double()).sum())
+    b = float((x.double() * backward_raw(g, y, cfg).double()).sum())
+    assert abs(a - b) / (float(ax.norm()) * float(y.double().norm())) <= 1e-6
 
 
 @pytest.mark.parametrize("dtype", [torch.float16, torch.bfloat16])
@@ -209,8 +217,8 @@ def test_full_size_dot_product(name):
     _, g = _full(name)
     rng = np.random.default_rng(9)
     b = 4
-    x = to_dev(rng.standard_normal((b, g.n, g.n)))
-    y = to_dev(rng.standard_normal((b,) + g.sino_shape))
+    x = to_dev(rng.uniform(0.0, 1.0, (b, g.n, g.n)))
+    y = to_dev(rng.uniform(0.0, 1.0, (b,) + g.sino_shape))
     a1 = float((forward_raw(g, x).double() * y.double()).sum())
     a2 = float((x.double() * backward_raw(g, y).double()).sum())
     assert abs(a1 - a2) / max(abs(a1), abs(a2)) <= TOL_DOT
