@@ -220,6 +220,24 @@ RADON_API radon_status radon_forward_ws(const radon_geometry* geometry, const vo
                                         void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * Forward projection that allocates nothing (the paper has no counterpart: this serves callers that
+ * cannot allocate device memory -- code being captured into a CUDA graph, real-time loops that forbid
+ * allocation after start-up, plain C hosts without a device allocator).  It runs the packed path of
+ * radon_forward_ws with its scratch in a fixed 32 MiB device array inside the library instead of a
+ * caller workspace.
+ *   - Same arguments and results as radon_forward.  A batch that needs more scratch than 32 MiB
+ *     (radon_forward_workspace_size) is rejected with RADON_ERR_INVALID_ARG: split it.
+ *   - Every GPU that loads the library holds the 32 MiB until the process exits.
+ *   - All calls share the array: each call overwrites what the previous one left there (nothing in
+ *     it needs to start at zero), and calls whose kernels overlap on the GPU (e.g. on two streams)
+ *     race on it -- order them.
+ *   - The first call on each device looks up the array's address with that device current; make
+ *     that first call before any stream capture begins.
+ */
+RADON_API radon_status radon_forward_static_scratch(const radon_geometry* geometry, const void* img, void* sino,
+                                                    radon_dtype dtype, int batch, void* stream);
+
+/*
  * Synchronises `stream`, then reads and clears the library's device error word.
  * Returns RADON_OK, RADON_ERR_TIMEOUT or RADON_ERR_DEVICE_BOUNDS (from kernels), or
  * RADON_ERR_CUDA if the synchronisation itself failed.

@@ -106,6 +106,8 @@ _SIGNATURES = [
     ("radon_forward_ws", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
       ctypes.POINTER(radon_launch_config), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("radon_forward_static_scratch", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     ("radon_get_device_error", ctypes.c_int, [ctypes.c_void_p]),
     ("radon_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("radon_last_error_message", ctypes.c_char_p, []),
@@ -203,6 +205,10 @@ def radon_forward_workspace_size(geom, dtype, batch):
 
 def radon_forward_ws(geom, img, sino, dtype, batch, config, workspace, workspace_bytes, stream):
     return _call("radon_forward_ws", geom, img, sino, dtype, batch, config, workspace, workspace_bytes, stream)
+
+
+def radon_forward_static_scratch(geom, img, sino, dtype, batch, stream):
+    return _call("radon_forward_static_scratch", geom, img, sino, dtype, batch, stream)
 
 
 def radon_get_device_error(stream):

@@ -67,6 +67,12 @@ struct radon_geometry {
 
 namespace radon {
 
+// radon_api.cpp: host-side validation and error reporting shared by the entry points
+radon_status fail(radon_status st, const std::string& msg);
+radon_status cuda_fail(cudaError_t e, const char* what);
+radon_status validate_call(const radon_geometry* g, const void* in, const void* out, radon_dtype dt, int batch);
+radon_status check_device(const radon_geometry* g);
+
 // geometry.cpp
 radon_status build_geometry(radon_geometry* g);  // fills host tables and sample count
 int backward_window_width(const radon_geometry* g, int tile);
