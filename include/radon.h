@@ -220,6 +220,24 @@ RADON_API radon_status radon_forward_ws(const radon_geometry* geometry, const vo
                                         void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * Device workspace, in bytes, that radon_backward_ws uses for `batch` sinograms of `dtype`: the
+ * batch packed into FP32 quads of images, 16 (or 8, for batches of at most 8) images per group,
+ * laid out [group][view][quad][detector][4].  Returns 0 for an invalid geometry, dtype or batch.
+ */
+RADON_API size_t radon_backward_workspace_size(const radon_geometry* geometry, radon_dtype dtype, int batch);
+
+/*
+ * Exact adjoint with a caller-owned device workspace (>= radon_backward_workspace_size bytes,
+ * 16-byte aligned, used in stream order, contents overwritten): the sinogram batch is packed once,
+ * then every CTA copies the detector windows of its pixel tile straight into shared memory (the
+ * fastest path).  A NULL or too small workspace behaves exactly like radon_backward_ex.  Allocates
+ * nothing; can be captured in a CUDA graph.
+ */
+RADON_API radon_status radon_backward_ws(const radon_geometry* geometry, const void* sino, void* img,
+                                         radon_dtype dtype, int batch, const radon_launch_config* config,
+                                         void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * Forward projection that allocates nothing (the paper has no counterpart: this serves callers that
  * cannot allocate device memory -- code being captured into a CUDA graph, real-time loops that forbid
  * allocation after start-up, plain C hosts without a device allocator).  It runs the packed path of

@@ -13,6 +13,7 @@ from .radon import (  # noqa: F401
     RadonFanbeam,
     RadonForwardFunction,
     backward_raw,
+    backward_workspace_bytes,
     forward_raw,
     forward_workspace_bytes,
     launch_config,
@@ -20,5 +21,5 @@ from .radon import (  # noqa: F401
 
 __all__ = [
     "Geometry", "Radon", "RadonFanbeam", "RadonForwardFunction", "RadonBackprojectionFunction", "forward_raw",
-    "backward_raw", "launch_config", "forward_workspace_bytes",
+    "backward_raw", "launch_config", "forward_workspace_bytes", "backward_workspace_bytes",
 ]

@@ -106,6 +106,10 @@ _SIGNATURES = [
     ("radon_forward_ws", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
       ctypes.POINTER(radon_launch_config), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("radon_backward_workspace_size", ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    ("radon_backward_ws", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+      ctypes.POINTER(radon_launch_config), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     ("radon_forward_static_scratch", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     ("radon_get_device_error", ctypes.c_int, [ctypes.c_void_p]),
@@ -205,6 +209,14 @@ def radon_forward_workspace_size(geom, dtype, batch):
 
 def radon_forward_ws(geom, img, sino, dtype, batch, config, workspace, workspace_bytes, stream):
     return _call("radon_forward_ws", geom, img, sino, dtype, batch, config, workspace, workspace_bytes, stream)
+
+
+def radon_backward_workspace_size(geom, dtype, batch):
+    return _call("radon_backward_workspace_size", geom, dtype, batch)
+
+
+def radon_backward_ws(geom, sino, img, dtype, batch, config, workspace, workspace_bytes, stream):
+    return _call("radon_backward_ws", geom, sino, img, dtype, batch, config, workspace, workspace_bytes, stream)
 
 
 def radon_forward_static_scratch(geom, img, sino, dtype, batch, stream):

@@ -138,3 +138,101 @@ radon_status launch_backward_tiled(const radon_geometry* g, const void* sino, vo
 }
 
 }  // namespace radon
+
+namespace radon {
+
+namespace {
+
+template <int BG, int KW>
+cudaError_t launch_packed_bg(const CUtensorMap& map, const BwdTiledArgs& a, dim3 grid, size_t smem, cudaStream_t s) {
+    auto kern = backward_packed_kernel<BG, KW>;
+    static size_t attr_bytes = 0;
+    if (smem > attr_bytes) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_bytes = smem;
+    }
+    kern<<<grid, kBwdPackedThreads, smem, s>>>(map, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int backward_packed_images_per_cta(int batch, const radon_launch_config* cfg) {
+    if (cfg != nullptr && cfg->images_per_cta != 0) return cfg->images_per_cta;
+    return batch > 8 ? 16 : 8;
+}
+
+radon_status launch_backward_packed(const radon_geometry* g, const void* packed, void* img, radon_dtype dt, int batch,
+                                    int bg, cudaStream_t s, std::string* why) {
+    if (bg != 8 && bg != 16) {
+        *why = "images_per_cta must be 8 or 16 for the packed adjoint";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    const double span = 2.0 * std::sqrt(2.0) / g->h + 2e-4;
+    const int kw_needed = (int)std::floor(span) + 1;
+    if (kw_needed > 6) {
+        *why = "sampling step too small for the tiled adjoint";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    const int kw = kw_needed <= 3 ? 3 : 6;
+    const int wd = g->bwd_window + 2;
+    if (wd > 256) {
+        *why = "detector window wider than a TMA box";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    const size_t smem = bwd_packed_smem_bytes(bg, wd);
+    if (smem > 227 * 1024) {
+        *why = "shared memory budget exceeded";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    const int groups = (batch + bg - 1) / bg;
+    const uint64_t dims[5] = {4, (uint64_t)g->D, (uint64_t)(bg / 4), (uint64_t)g->V, (uint64_t)groups};
+    const uint64_t strides[4] = {16, (uint64_t)g->D * 16, (uint64_t)g->D * 16 * (bg / 4),
+                                 (uint64_t)g->D * 16 * (bg / 4) * g->V};
+    const uint32_t box[5] = {4, (uint32_t)wd, (uint32_t)(bg / 4), 1, 1};
+    CUtensorMap map;
+    const int rc = encode_tiled(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void*>(packed), dims, strides, box,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
+    if (rc != 0) {
+        *why = "cuTensorMapEncodeTiled rejected the packed-sinogram descriptor (CUresult " + std::to_string(rc) + ")";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    BwdTiledArgs a;
+    a.rays = g->d_ray;
+    a.nks = g->d_nk;
+    a.views = g->d_view;
+    a.img = img;
+    a.n = g->n;
+    a.V = g->V;
+    a.D = g->D;
+    a.B = batch;
+    a.h = (float)g->h;
+    a.wd = wd;
+    a.wdb = wd;
+    a.align = 1;
+    a.stage_stride = 0;
+    a.tiles_x = (g->n + kBwdTile - 1) / kBwdTile;
+    a.err = device_error_word();
+    if (a.err == nullptr) {
+        *why = "device error word unavailable";
+        return RADON_ERR_CUDA;
+    }
+    a.stall_test = 0;
+    a.spin_limit = kSpinLimit;
+    a.tma_rank = 5;
+    a.out_dtype = dt;
+    dim3 grid((unsigned)(a.tiles_x * a.tiles_x), (unsigned)groups);
+    cudaError_t e;
+    if (bg == 16)
+        e = kw == 3 ? launch_packed_bg<16, 3>(map, a, grid, smem, s) : launch_packed_bg<16, 6>(map, a, grid, smem, s);
+    else
+        e = kw == 3 ? launch_packed_bg<8, 3>(map, a, grid, smem, s) : launch_packed_bg<8, 6>(map, a, grid, smem, s);
+    if (e != cudaSuccess) {
+        *why = std::string("packed adjoint launch: ") + cudaGetErrorString(e);
+        return RADON_ERR_CUDA;
+    }
+    return RADON_OK;
+}
+
+}  // namespace radon

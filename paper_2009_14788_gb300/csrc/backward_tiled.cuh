@@ -46,6 +46,7 @@ struct BwdTiledArgs {
     uint32_t spin_limit;
     int stall_test;    // 1: issue no copies (exercises the bounded-wait expiry path)
     int tma_rank;      // 1: 1-D descriptor; 2: the same layout described with a unit outer dimension
+    int out_dtype;     // packed variant: storage type of the output image (radon_dtype)
 };
 
 __host__ __device__ inline int bwd_nq(int bg) { return (bg + 3) / 4; }
@@ -63,6 +64,68 @@ __device__ __forceinline__ float bwd_det_coord(const ViewF& vf, float x, float y
     return fmaf(vf.ax, x, fmaf(vf.ay, y, vf.a0)) / fmaf(vf.bx, x, fmaf(vf.by, y, vf.b0));
 }
 
+// Detector window of a tile for one view: candidates of every pixel of the tile lie in
+// [dlo, floor(tmax + r)], with r the half width of a pixel's 2x2 support square on the detector.
+// Parallel beam: r is the constant |ax| + |ay|.  Fan beam: the largest half width at the four tile
+// corners, with a 5% margin for its variation across the tile (magnification and ray angle change
+// slowly over 16 pixels).  A wider window only adds candidates of weight zero.
+__device__ __forceinline__ void bwd_view_window(const ViewF vf, int ti, int tj, int n, int* dlo, float* r_out) {
+    const float x0 = (float)tj, x1 = (float)min(tj + kBwdTile - 1, n - 1);
+    const float y0 = (float)ti, y1 = (float)min(ti + kBwdTile - 1, n - 1);
+    const float t00 = bwd_det_coord(vf, x0, y0), t10 = bwd_det_coord(vf, x1, y0);
+    const float t01 = bwd_det_coord(vf, x0, y1), t11 = bwd_det_coord(vf, x1, y1);
+    const float tmin = fminf(fminf(t00, t10), fminf(t01, t11));
+    float r;
+    if (vf.bx == 0.0f && vf.by == 0.0f) {
+        r = (fabsf(vf.ax) + fabsf(vf.ay)) / vf.b0;
+    } else {
+        r = 0.0f;
+#pragma unroll
+        for (int cidx = 0; cidx < 4; ++cidx) {
+            const float cx = (cidx & 1) ? x1 : x0, cy = (cidx & 2) ? y1 : y0;
+            const float s0 = bwd_det_coord(vf, cx - 1.0f, cy - 1.0f), s1 = bwd_det_coord(vf, cx + 1.0f, cy - 1.0f);
+            const float s2 = bwd_det_coord(vf, cx - 1.0f, cy + 1.0f), s3 = bwd_det_coord(vf, cx + 1.0f, cy + 1.0f);
+            r = fmaxf(r, 0.5f * (fmaxf(fmaxf(s0, s1), fmaxf(s2, s3)) - fminf(fminf(s0, s1), fminf(s2, s3))));
+        }
+        r = fmaf(r, 1.05f, 0.02f);
+    }
+    r = fmaf(r, 1.0f, 0.01f);
+    *dlo = (int)floorf(tmin - r - 0.01f);
+    *r_out = r;
+}
+
+// Tile-relative parameters of ray (v, d) for the gather: A = (reference sample position relative to
+// the tile origin, step), Bq = (step / |step|^2, candidate half-window kr).  The reference sample is
+// the one nearest the tile centre (clamped to the ray), re-based from the split-precision table.
+// Rays outside the detector or missing the image get a far-away sentinel (weight zero everywhere).
+__device__ __forceinline__ void bwd_ray_params(const RayT* rays, const int* nks, int v, int d, int D, int ti, int tj,
+                                               float4* A_out, float4* B_out) {
+    float4 A = make_float4(1e9f, 1e9f, 0.0f, 0.0f), Bq = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (d >= 0 && d < D) {
+        const long long ridx = (long long)v * D + d;
+        const int nk = nks[ridx];
+        if (nk > 0) {
+            const RayT ray = rays[ridx];
+            const float dx = ray.dxh + ray.dxl, dy = ray.dyh + ray.dyl;
+            const float il = 1.0f / fmaf(dx, dx, dy * dy);
+            const float ex = ((float)(tj - ray.J0) + 7.5f) - ray.fx0;
+            const float ey = ((float)(ti - ray.I0) + 7.5f) - ray.fy0;
+            const float kf = fminf(fmaxf(rintf(fmaf(ex, dx, ey * dy) * il), 0.0f), (float)(nk - 1));
+            const float qx = kf * ray.dxh, qy = kf * ray.dyh;   // exact products
+            const float Qx = floorf(qx), Qy = floorf(qy);
+            A.x = ((float)(ray.J0 - tj) + Qx) + fmaf(kf, ray.dxl, ray.fx0 + (qx - Qx));
+            A.y = ((float)(ray.I0 - ti) + Qy) + fmaf(kf, ray.dyl, ray.fy0 + (qy - Qy));
+            A.z = dx;
+            A.w = dy;
+            Bq.x = dx * il;
+            Bq.y = dy * il;
+            Bq.z = (fabsf(dx) + fabsf(dy)) * il + 1e-4f;
+        }
+    }
+    *A_out = A;
+    *B_out = Bq;
+}
+
 // Warp 0: windows for the views of chunk c and the TMA copies into staging slot `slot`.
 template <typename T, int BG>
 __device__ void bwd_issue_chunk(const CUtensorMap* tmap, const BwdTiledArgs& a, int c, int slot, int ti, int tj,
@@ -71,32 +134,10 @@ __device__ void bwd_issue_chunk(const CUtensorMap* tmap, const BwdTiledArgs& a, 
     const int v0 = c * kBwdViews;
     const int nv = min(kBwdViews, a.V - v0);
     if (lane < nv) {
-        const ViewF vf = a.views[v0 + lane];
-        const float x0 = (float)tj, x1 = (float)min(tj + kBwdTile - 1, a.n - 1);
-        const float y0 = (float)ti, y1 = (float)min(ti + kBwdTile - 1, a.n - 1);
-        const float t00 = bwd_det_coord(vf, x0, y0), t10 = bwd_det_coord(vf, x1, y0);
-        const float t01 = bwd_det_coord(vf, x0, y1), t11 = bwd_det_coord(vf, x1, y1);
-        const float tmin = fminf(fminf(t00, t10), fminf(t01, t11));
-        // Half width of a pixel's 2x2 support square on the detector.  Parallel beam: the
-        // constant |ax| + |ay|.  Fan beam: the largest half width at the four tile corners, with a
-        // 5% margin for its variation across the tile (magnification and ray angle change slowly
-        // over 16 pixels).  A wider window only adds candidates of weight zero.
+        int dlo;
         float r;
-        if (vf.bx == 0.0f && vf.by == 0.0f) {
-            r = (fabsf(vf.ax) + fabsf(vf.ay)) / vf.b0;
-        } else {
-            r = 0.0f;
-#pragma unroll
-            for (int cidx = 0; cidx < 4; ++cidx) {
-                const float cx = (cidx & 1) ? x1 : x0, cy = (cidx & 2) ? y1 : y0;
-                const float s0 = bwd_det_coord(vf, cx - 1.0f, cy - 1.0f), s1 = bwd_det_coord(vf, cx + 1.0f, cy - 1.0f);
-                const float s2 = bwd_det_coord(vf, cx - 1.0f, cy + 1.0f), s3 = bwd_det_coord(vf, cx + 1.0f, cy + 1.0f);
-                r = fmaxf(r, 0.5f * (fmaxf(fmaxf(s0, s1), fmaxf(s2, s3)) - fminf(fminf(s0, s1), fminf(s2, s3))));
-            }
-            r = fmaf(r, 1.05f, 0.02f);
-        }
-        r = fmaf(r, 1.0f, 0.01f);
-        dlo_s[slot * kBwdViews + lane] = (int)floorf(tmin - r - 0.01f);
+        bwd_view_window(a.views[v0 + lane], ti, tj, a.n, &dlo, &r);
+        dlo_s[slot * kBwdViews + lane] = dlo;
         r_s[slot * kBwdViews + lane] = r;
     }
     __syncwarp();
@@ -222,29 +263,8 @@ __global__ void __launch_bounds__(kBwdThreads, 2) backward_tiled_kernel(const __
                 }
                 yq[(vl * NQ + q) * a.wd + dl] = make_float4(vals[0], vals[1], vals[2], vals[3]);
             }
-            float4 A = make_float4(1e9f, 1e9f, 0.0f, 0.0f), Bq = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            if (d >= 0 && d < a.D) {
-                const int r = v * a.D + d;
-                const int nk = a.nks[r];
-                if (nk > 0) {
-                    const RayT ray = a.rays[r];
-                    const float dx = ray.dxh + ray.dxl, dy = ray.dyh + ray.dyl;
-                    const float il = 1.0f / fmaf(dx, dx, dy * dy);
-                    // reference sample: the one nearest the tile centre, clamped to the ray
-                    const float ex = ((float)(tj - ray.J0) + 7.5f) - ray.fx0;
-                    const float ey = ((float)(ti - ray.I0) + 7.5f) - ray.fy0;
-                    const float kf = fminf(fmaxf(rintf(fmaf(ex, dx, ey * dy) * il), 0.0f), (float)(nk - 1));
-                    const float qx = kf * ray.dxh, qy = kf * ray.dyh;   // exact products
-                    const float Qx = floorf(qx), Qy = floorf(qy);
-                    A.x = ((float)(ray.J0 - tj) + Qx) + fmaf(kf, ray.dxl, ray.fx0 + (qx - Qx));
-                    A.y = ((float)(ray.I0 - ti) + Qy) + fmaf(kf, ray.dyl, ray.fy0 + (qy - Qy));
-                    A.z = dx;
-                    A.w = dy;
-                    Bq.x = dx * il;
-                    Bq.y = dy * il;
-                    Bq.z = (fabsf(dx) + fabsf(dy)) * il + 1e-4f;
-                }
-            }
+            float4 A, Bq;
+            bwd_ray_params(a.rays, a.nks, v, d, a.D, ti, tj, &A, &Bq);
             rp[(vl * a.wd + dl) * 2] = A;
             rp[(vl * a.wd + dl) * 2 + 1] = Bq;
         }
@@ -291,6 +311,175 @@ __global__ void __launch_bounds__(kBwdThreads, 2) backward_tiled_kernel(const __
 #pragma unroll
         for (int b = 0; b < BG; ++b)
             if (b0 + b < a.B) out[(long long)(b0 + b) * npix + p] = from_f32<T>(a.h * acc[b]);
+    }
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// Packed variant: the sinogram batch was packed once into FP32 image quads laid out
+// [group][view][quad][det][4] (pack.cu), so one 5-D TMA box per view lands the tile's detector
+// window directly in the gather's [quad][det] layout.  Warp-specialised: a producer warp computes
+// each view's window, issues the copies and re-bases the rays on the tile (its ray-table loads
+// overlap the consumers' work on the previous chunk); 8 consumer warps (one pixel per thread)
+// gather.  Full / empty mbarriers per buffer, no CTA-wide barrier in the view loop.
+constexpr int kBwdPackedViews = 4;
+constexpr int kBwdPackedThreads = kBwdThreads + 32;
+
+// Per-view slice of a staged window: padded so every TMA destination starts on 128 bytes.
+__host__ __device__ inline size_t bwd_packed_view_bytes(int bg, int wd) { return ((size_t)wd * bg * 4 + 127) / 128 * 128; }
+
+__host__ __device__ inline size_t bwd_packed_smem_bytes(int bg, int wd) {
+    const size_t ystage = (size_t)kBwdPackedViews * bwd_packed_view_bytes(bg, wd);   // per buffer
+    const size_t rpb = (size_t)kBwdPackedViews * wd * 32;             // per buffer
+    return 128 + 256 + 2 * ((ystage + 127) / 128 * 128) + 2 * ((rpb + 127) / 128 * 128);
+}
+
+template <int BG, int KW>
+__global__ void __launch_bounds__(kBwdPackedThreads, 2) backward_packed_kernel(const __grid_constant__ CUtensorMap map,
+                                                                              const BwdTiledArgs a) {
+    constexpr int NQ = BG / 4;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);        // [2]
+    uint64_t* empty = reinterpret_cast<uint64_t*>(smem + 16);  // [2]
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 32);
+    int* dlo_c = reinterpret_cast<int*>(smem + 64);             // [2][views]
+    float* r_c = reinterpret_cast<float*>(smem + 128);          // [2][views]
+    const size_t yv_bytes = bwd_packed_view_bytes(BG, a.wd);
+    const size_t ys_bytes = (size_t)kBwdPackedViews * yv_bytes;
+    const size_t rp_bytes = ((size_t)kBwdPackedViews * a.wd * 32 + 127) / 128 * 128;
+    unsigned char* ystage = smem + 256;
+    unsigned char* rpbuf = ystage + 2 * ys_bytes;
+
+    const int tid = threadIdx.x;
+    const int tile = blockIdx.x;
+    const int ti = (tile / a.tiles_x) * kBwdTile, tj = (tile - (tile / a.tiles_x) * a.tiles_x) * kBwdTile;
+    const int nchunks = (a.V + kBwdPackedViews - 1) / kBwdPackedViews;
+
+    if (tid == 0) {
+        mbar_init(&full[0], 33);
+        mbar_init(&full[1], 33);
+        mbar_init(&empty[0], kBwdThreads);
+        mbar_init(&empty[1], kBwdThreads);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (tid >= kBwdThreads) {
+        // ------------------------------------------------------------------ producer warp
+        const int lane = tid & 31;
+        for (int c = 0; c < nchunks; ++c) {
+            const int buf = c & 1;
+            const int v0 = c * kBwdPackedViews;
+            const int nv = min(kBwdPackedViews, a.V - v0);
+            bool ok = true;
+            if (c >= 2 && lane == 0) ok = mbar_wait_bounded(&empty[buf], (uint32_t)(((c >> 1) - 1) & 1), a.spin_limit);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) {
+                if (lane == 0) {
+                    record_device_error(a.err, RADON_ERR_TIMEOUT);
+                    *abort_flag = 1;
+                }
+                __syncwarp();
+                mbar_arrive(&full[buf]);
+                if (lane == 0) mbar_arrive(&full[buf]);   // 33 arrivals complete the phase without data
+                return;
+            }
+            int dlo = 0;
+            float r = 0.0f;
+            if (lane < nv) bwd_view_window(a.views[v0 + lane], ti, tj, a.n, &dlo, &r);
+            if (lane < nv) {
+                dlo_c[buf * kBwdPackedViews + lane] = dlo;
+                r_c[buf * kBwdPackedViews + lane] = r;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                fence_proxy_async_shared();
+                mbar_arrive_expect_tx(&full[buf], (uint32_t)(nv * a.wd * BG * 4));
+                for (int vl = 0; vl < nv; ++vl)
+                    tma_load_5d(ystage + buf * ys_bytes + (size_t)vl * yv_bytes, &map, &full[buf], 0,
+                                dlo_c[buf * kBwdPackedViews + vl], 0, v0 + vl, blockIdx.y);
+            }
+            float4* rp = reinterpret_cast<float4*>(rpbuf + buf * rp_bytes);
+            for (int e = lane; e < nv * a.wd; e += 32) {
+                const int vl = e / a.wd, dl = e - (e / a.wd) * a.wd;
+                float4 A, Bq;
+                bwd_ray_params(a.rays, a.nks, v0 + vl, dlo_c[buf * kBwdPackedViews + vl] + dl, a.D, ti, tj, &A, &Bq);
+                rp[(vl * a.wd + dl) * 2] = A;
+                rp[(vl * a.wd + dl) * 2 + 1] = Bq;
+            }
+            __syncwarp();
+            mbar_arrive(&full[buf]);   // every lane: its ray parameters are released
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------------- consumer warps
+    const int pi = tid / kBwdTile, pj = tid - (tid / kBwdTile) * kBwdTile;
+    const float px = (float)pj, py = (float)pi;
+    const float gx = (float)(tj + pj), gy = (float)(ti + pi);
+    const bool inside = (ti + pi) < a.n && (tj + pj) < a.n;
+    float acc[BG];
+#pragma unroll
+    for (int b = 0; b < BG; ++b) acc[b] = 0.0f;
+    for (int c = 0; c < nchunks; ++c) {
+        const int buf = c & 1;
+        const int v0 = c * kBwdPackedViews;
+        const int nv = min(kBwdPackedViews, a.V - v0);
+        if (!mbar_wait_bounded(&full[buf], (uint32_t)((c >> 1) & 1), a.spin_limit)) {
+            record_device_error(a.err, RADON_ERR_TIMEOUT);
+            return;
+        }
+        if (*abort_flag) return;
+        const float4* rpb = reinterpret_cast<const float4*>(rpbuf + buf * rp_bytes);
+        for (int vl = 0; vl < nv; ++vl) {
+            const ViewF vf = a.views[v0 + vl];
+            const int dlo = dlo_c[buf * kBwdPackedViews + vl];
+            const float r = r_c[buf * kBwdPackedViews + vl];
+            const float t = bwd_det_coord(vf, gx, gy);
+            const float flo = ceilf(t - r), fhi = floorf(t + r);
+            const int da = (int)fmaxf(flo, (float)max(dlo, 0));
+            const int db = (int)fminf(fhi, (float)min(a.D - 1, dlo + a.wd - 1));
+            if (inside && ((flo < (float)dlo && flo >= 0.0f) || (fhi > (float)(dlo + a.wd - 1) && fhi <= (float)(a.D - 1))))
+                record_device_error(a.err, RADON_ERR_DEVICE_BOUNDS);
+            const float4* rpv = rpb + vl * a.wd * 2;
+            const float4* yq = reinterpret_cast<const float4*>(ystage + buf * ys_bytes + (size_t)vl * yv_bytes);
+            for (int d = da; d <= db; ++d) {
+                const int dl = d - dlo;
+                const float w = bwd_ray_weight<KW>(px, py, rpv[dl * 2], rpv[dl * 2 + 1]);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const float4 y4 = yq[q * a.wd + dl];
+                    acc[4 * q + 0] = fmaf(w, y4.x, acc[4 * q + 0]);
+                    acc[4 * q + 1] = fmaf(w, y4.y, acc[4 * q + 1]);
+                    acc[4 * q + 2] = fmaf(w, y4.z, acc[4 * q + 2]);
+                    acc[4 * q + 3] = fmaf(w, y4.w, acc[4 * q + 3]);
+                }
+            }
+        }
+        mbar_arrive(&empty[buf]);
+    }
+    if (inside) {
+        const long long npix = (long long)a.n * a.n;
+        const long long p = (long long)(ti + pi) * a.n + (tj + pj);
+        const int b0 = blockIdx.y * BG;
+        if (a.out_dtype == RADON_F16) {
+            __half* out = reinterpret_cast<__half*>(a.img);
+#pragma unroll
+            for (int b = 0; b < BG; ++b)
+                if (b0 + b < a.B) out[(long long)(b0 + b) * npix + p] = __float2half_rn(a.h * acc[b]);
+        } else if (a.out_dtype == RADON_BF16) {
+            __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(a.img);
+#pragma unroll
+            for (int b = 0; b < BG; ++b)
+                if (b0 + b < a.B) out[(long long)(b0 + b) * npix + p] = __float2bfloat16_rn(a.h * acc[b]);
+        } else {
+            float* out = reinterpret_cast<float*>(a.img);
+#pragma unroll
+            for (int b = 0; b < BG; ++b)
+                if (b0 + b < a.B) out[(long long)(b0 + b) * npix + p] = a.h * acc[b];
+        }
     }
 }
 

@@ -71,7 +71,57 @@ __global__ void __launch_bounds__(256) pack_interleaved_kernel(const T* __restri
     }
 }
 
+// Sinogram batch -> FP32 image quads [group][view][quad][det][4] (group = bg images, quad = 4 of
+// them).  One thread per output quad; consecutive threads walk detectors (coalesced both ways).
+template <typename T>
+__global__ void __launch_bounds__(256) pack_sino_kernel(const T* __restrict__ y, float4* __restrict__ out, int V,
+                                                        int D, int B, int bg, long long total) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int nq = bg / 4;
+    const int d = (int)(idx % D);
+    long long rest = idx / D;
+    const int q = (int)(rest % nq);
+    rest /= nq;
+    const int v = (int)(rest % V);
+    const int g = (int)(rest / V);
+    float vals[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int b = g * bg + 4 * q + u;
+        vals[u] = b < B ? to_f32(y[((long long)b * V + v) * D + d]) : 0.0f;
+    }
+    out[idx] = make_float4(vals[0], vals[1], vals[2], vals[3]);
+}
+
 }  // namespace
+
+size_t packed_sino_bytes(int V, int D, int batch, int bg) {
+    const long long groups = (batch + bg - 1) / bg;
+    return (size_t)(groups * (long long)V * D * bg * 4);
+}
+
+cudaError_t launch_pack_sino(const void* sino, void* workspace, int V, int D, int batch, int bg, radon_dtype dt,
+                             cudaStream_t s) {
+    const long long groups = (batch + bg - 1) / bg;
+    const long long total = groups * (long long)V * (bg / 4) * D;
+    if (total == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    float4* out = reinterpret_cast<float4*>(workspace);
+    switch (dt) {
+        case RADON_F16:
+            pack_sino_kernel<__half><<<blocks, 256, 0, s>>>((const __half*)sino, out, V, D, batch, bg, total);
+            break;
+        case RADON_BF16:
+            pack_sino_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>((const __nv_bfloat16*)sino, out, V, D, batch, bg,
+                                                                   total);
+            break;
+        default:
+            pack_sino_kernel<float><<<blocks, 256, 0, s>>>((const float*)sino, out, V, D, batch, bg, total);
+            break;
+    }
+    return cudaGetLastError();
+}
 
 size_t packed_image_bytes(int n, int batch, radon_dtype dt) {
     const int bg = dt == RADON_F32 ? 4 : 8;

@@ -194,6 +194,19 @@ radon_status dispatch(const radon_geometry* g, const void* in, void* out, radon_
     if (st != RADON_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const int images = cfg ? cfg->images_per_cta : 0;
+    if (!forward && algo != RADON_ALGO_PLAIN && ws != nullptr) {
+        // Packed path: pack the sinogram batch once, then copy detector windows straight into
+        // shared memory.  A too small workspace or a geometry the kernel refuses continues below.
+        const int bg = backward_packed_images_per_cta(batch, cfg);
+        if (ws_bytes >= packed_sino_bytes(g->V, g->D, batch, bg)) {
+            cudaError_t e = launch_pack_sino(in, ws, g->V, g->D, batch, bg, dt, s);
+            if (e != cudaSuccess) return cuda_fail(e, "sinogram pack launch");
+            std::string why;
+            st = launch_backward_packed(g, ws, out, dt, batch, bg, s, &why);
+            if (st == RADON_OK) return RADON_OK;
+            if (st != RADON_ERR_UNSUPPORTED) return fail(st, why);
+        }
+    }
     if (!forward && algo != RADON_ALGO_PLAIN) {
         std::string why;
         st = launch_backward_tiled(g, in, out, dt, batch, images, s, &why);
@@ -354,6 +367,21 @@ radon_status radon_forward_ws(const radon_geometry* g, const void* img, void* si
     if (workspace != nullptr && ((uintptr_t)workspace & 15) != 0)
         return fail(RADON_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
     return dispatch(g, img, sino, dtype, batch, config, stream, true, workspace, workspace_bytes);
+}
+
+size_t radon_backward_workspace_size(const radon_geometry* g, radon_dtype dtype, int batch) {
+    if (validate_geometry(g) != RADON_OK) return 0;
+    if (dtype != RADON_F32 && dtype != RADON_F16 && dtype != RADON_BF16) return 0;
+    if (batch < 0) return 0;
+    return packed_sino_bytes(g->V, g->D, batch, backward_packed_images_per_cta(batch, nullptr));
+}
+
+radon_status radon_backward_ws(const radon_geometry* g, const void* sino, void* img, radon_dtype dtype, int batch,
+                               const radon_launch_config* config, void* workspace, size_t workspace_bytes,
+                               void* stream) {
+    if (workspace != nullptr && ((uintptr_t)workspace & 15) != 0)
+        return fail(RADON_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
+    return dispatch(g, sino, img, dtype, batch, config, stream, false, workspace, workspace_bytes);
 }
 
 radon_status radon_get_device_error(void* stream) {

@@ -167,8 +167,23 @@ def forward_raw(geom: Geometry, x: torch.Tensor, config=None, out=None, workspac
     return y
 
 
-def backward_raw(geom: Geometry, y: torch.Tensor, config=None, out=None) -> torch.Tensor:
-    """x = A^T y through ``radon_backward`` / ``radon_backward_ex`` (no autograd)."""
+def backward_workspace_bytes(geom: Geometry, dtype: torch.dtype, batch: int) -> int:
+    """Bytes of the workspace the packed adjoint path uses (``radon_backward_workspace_size``)."""
+    return int(L.radon_backward_workspace_size(geom.handle, _DTYPES[dtype], int(batch)))
+
+
+def _workspace(workspace, need, device):
+    if isinstance(workspace, str) and workspace == "auto":
+        return torch.empty(need, dtype=torch.uint8, device=device) if need > 0 else None
+    if isinstance(workspace, torch.Tensor):
+        if workspace.device != device or not workspace.is_contiguous():
+            raise ValueError("workspace must be a contiguous tensor on %s" % device)
+        return workspace
+    return None
+
+
+def backward_raw(geom: Geometry, y: torch.Tensor, config=None, out=None, workspace="auto") -> torch.Tensor:
+    """x = A^T y through the C ABI (no autograd); ``workspace`` as for ``forward_raw``."""
     _check_tensor(y, "sinogram", geom)
     if tuple(y.shape[-2:]) != geom.sino_shape:
         raise ValueError("sinogram must end in %s, got %s" % (geom.sino_shape, tuple(y.shape)))
@@ -177,12 +192,16 @@ def backward_raw(geom: Geometry, y: torch.Tensor, config=None, out=None) -> torc
     shape = tuple(y.shape[:-2]) + (geom.n, geom.n)
     x = torch.empty(shape, dtype=y.dtype, device=y.device) if out is None else _check_out(out, y, shape)
     stream = torch.cuda.current_stream(y.device).cuda_stream
+    ws = _workspace(workspace, backward_workspace_bytes(geom, y.dtype, batch) if batch > 0 else 0, y.device)
     with torch.cuda.device(y.device):
-        if config is None:
+        cfg = ctypes.byref(config) if config is not None else None
+        if ws is not None:
+            st = L.radon_backward_ws(geom.handle, y.data_ptr(), x.data_ptr(), _DTYPES[y.dtype], batch, cfg,
+                                     ws.data_ptr(), ws.numel() * ws.element_size(), stream)
+        elif config is None:
             st = L.radon_backward(geom.handle, y.data_ptr(), x.data_ptr(), _DTYPES[y.dtype], batch, stream)
         else:
-            st = L.radon_backward_ex(geom.handle, y.data_ptr(), x.data_ptr(), _DTYPES[y.dtype], batch,
-                                     ctypes.byref(config), stream)
+            st = L.radon_backward_ex(geom.handle, y.data_ptr(), x.data_ptr(), _DTYPES[y.dtype], batch, cfg, stream)
     L.check(st, "radon_backward")
     return x
 

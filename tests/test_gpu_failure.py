@@ -29,7 +29,7 @@ def test_bounded_wait_expiry_is_reported_and_context_survives(monkeypatch):
     stream = torch.cuda.current_stream().cuda_stream
     assert L.radon_get_device_error(stream) == L.RADON_OK
     monkeypatch.setenv("RADON_TEST_STALL_TMA", "1")
-    backward_raw(g, to_dev(y), launch_config("tiled"))
+    backward_raw(g, to_dev(y), launch_config("tiled"), workspace=None)
     assert L.radon_get_device_error(stream) == L.RADON_ERR_TIMEOUT
     assert "bounded wait" in L.radon_last_error_message()
     monkeypatch.delenv("RADON_TEST_STALL_TMA")

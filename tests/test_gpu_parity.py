@@ -236,27 +236,33 @@ TILED_CASES = ["parallel_n64_full", "parallel_n256_sub", "fan_n512_block", "para
                "parallel_fine", "parallel_coarse", "fan_ragged", "parallel_ragged", "one_ray", "one_pixel"]
 
 
+@pytest.mark.parametrize("ws", ["packed", "staged"])
 @pytest.mark.parametrize("images", [4, 8, 16])
 @pytest.mark.parametrize("batch", [1, 5, 17])
 @pytest.mark.parametrize("case", ["fan_n512_sub", "parallel_ragged", "fan_close"])
-def test_backward_tiled_image_groups(case, batch, images):
-    """Every images-per-CTA setting with full, ragged and single-image batches."""
+def test_backward_tiled_image_groups(case, batch, images, ws):
+    """Every images-per-CTA setting with full, ragged and single-image batches, with a workspace
+    (sinogram packed once; 8 or 16 images per CTA) and without (per-CTA staging; 4, 8 or 16)."""
+    if ws == "packed" and images == 4:
+        pytest.skip("the packed adjoint groups 8 or 16 images")
     g, og = make(case)
     y = _rand_sino(g.sino_shape, batch, 40 + batch)
-    got = to_np(backward_raw(g, to_dev(y), launch_config("tiled", images_per_cta=images)))
+    got = to_np(backward_raw(g, to_dev(y), launch_config("tiled", images_per_cta=images),
+                             workspace="auto" if ws == "packed" else None))
     ref = O.adjoint(og, y)
     assert rel_l2(got, ref) <= TOL_F32
     assert max_rel(got, ref) <= 2 * TOL_F32
 
 
+@pytest.mark.parametrize("ws", ["packed", "staged"])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float16, torch.bfloat16])
 @pytest.mark.parametrize("case", TILED_CASES)
-def test_backward_tiled_bounds_word_stays_clear(case, dtype):
+def test_backward_tiled_bounds_word_stays_clear(case, dtype, ws):
     """The tiled adjoint's own window check never fires, and results match the oracle."""
     g, og = make(case)
     y = _rand_sino(g.sino_shape, 3, 50)
     ys = to_dev(y, dtype)
-    got = to_np(backward_raw(g, ys, launch_config("tiled")))
+    got = to_np(backward_raw(g, ys, launch_config("tiled"), workspace="auto" if ws == "packed" else None))
     assert L.radon_get_device_error(torch.cuda.current_stream().cuda_stream) == L.RADON_OK
     tol = TOL_F32 if dtype == torch.float32 else TOL_16
     assert rel_l2(got, O.adjoint(og, to_np(ys))) <= tol
@@ -269,6 +275,8 @@ def test_tiled_refuses_extreme_magnification_and_auto_falls_back():
     y = _rand_sino(g.sino_shape, 2, 60)
     with pytest.raises(L.RadonError, match="TMA box"):
         backward_raw(g, to_dev(y), launch_config("tiled"))
+    with pytest.raises(L.RadonError, match="TMA box"):
+        backward_raw(g, to_dev(y), launch_config("tiled"), workspace=None)
     assert rel_l2(to_np(backward_raw(g, to_dev(y))), O.adjoint(og, y)) <= TOL_F32
 
 
@@ -280,8 +288,8 @@ def test_backward_tiled_unsupported_is_reported():
     view = buf[1:].view(1, *g.sino_shape)
     view.copy_(to_dev(y))
     with pytest.raises(L.RadonError):
-        backward_raw(g, view, launch_config("tiled"))
-    got = to_np(backward_raw(g, view, launch_config("auto")))
+        backward_raw(g, view, launch_config("tiled"), workspace=None)
+    got = to_np(backward_raw(g, view, launch_config("auto"), workspace=None))
     assert rel_l2(got, O.adjoint(og, y)) <= TOL_F32
 
 
