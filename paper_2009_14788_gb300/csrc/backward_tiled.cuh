@@ -331,7 +331,7 @@ __host__ __device__ inline size_t bwd_packed_view_bytes(int bg, int wd) { return
 __host__ __device__ inline size_t bwd_packed_smem_bytes(int bg, int wd) {
     const size_t ystage = (size_t)kBwdPackedViews * bwd_packed_view_bytes(bg, wd);   // per buffer
     const size_t rpb = (size_t)kBwdPackedViews * wd * 32;             // per buffer
-    return 128 + 256 + 2 * ((ystage + 127) / 128 * 128) + 2 * ((rpb + 127) / 128 * 128);
+    return 128 + 512 + 2 * ((ystage + 127) / 128 * 128) + 2 * ((rpb + 127) / 128 * 128);
 }
 
 template <int BG, int KW>
@@ -345,10 +345,11 @@ __global__ void __launch_bounds__(kBwdPackedThreads, 2) backward_packed_kernel(c
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 32);
     int* dlo_c = reinterpret_cast<int*>(smem + 64);             // [2][views]
     float* r_c = reinterpret_cast<float*>(smem + 128);          // [2][views]
+    ViewF* view_c = reinterpret_cast<ViewF*>(smem + 256);       // [2][views], 32 B each
     const size_t yv_bytes = bwd_packed_view_bytes(BG, a.wd);
     const size_t ys_bytes = (size_t)kBwdPackedViews * yv_bytes;
     const size_t rp_bytes = ((size_t)kBwdPackedViews * a.wd * 32 + 127) / 128 * 128;
-    unsigned char* ystage = smem + 256;
+    unsigned char* ystage = smem + 512;
     unsigned char* rpbuf = ystage + 2 * ys_bytes;
 
     const int tid = threadIdx.x;
@@ -388,10 +389,12 @@ __global__ void __launch_bounds__(kBwdPackedThreads, 2) backward_packed_kernel(c
             }
             int dlo = 0;
             float r = 0.0f;
-            if (lane < nv) bwd_view_window(a.views[v0 + lane], ti, tj, a.n, &dlo, &r);
             if (lane < nv) {
+                const ViewF vf = a.views[v0 + lane];
+                bwd_view_window(vf, ti, tj, a.n, &dlo, &r);
                 dlo_c[buf * kBwdPackedViews + lane] = dlo;
                 r_c[buf * kBwdPackedViews + lane] = r;
+                view_c[buf * kBwdPackedViews + lane] = vf;
             }
             __syncwarp();
             if (lane == 0) {
@@ -434,7 +437,7 @@ __global__ void __launch_bounds__(kBwdPackedThreads, 2) backward_packed_kernel(c
         if (*abort_flag) return;
         const float4* rpb = reinterpret_cast<const float4*>(rpbuf + buf * rp_bytes);
         for (int vl = 0; vl < nv; ++vl) {
-            const ViewF vf = a.views[v0 + vl];
+            const ViewF vf = view_c[buf * kBwdPackedViews + vl];
             const int dlo = dlo_c[buf * kBwdPackedViews + vl];
             const float r = r_c[buf * kBwdPackedViews + vl];
             const float t = bwd_det_coord(vf, gx, gy);
