@@ -144,7 +144,8 @@ namespace radon {
 namespace {
 
 template <int BG, int KW>
-cudaError_t launch_packed_bg(const CUtensorMap& map, const BwdTiledArgs& a, dim3 grid, size_t smem, cudaStream_t s) {
+cudaError_t launch_packed_bg(const CUtensorMap& map, const CUtensorMap& rmap, const BwdTiledArgs& a, dim3 grid,
+                             size_t smem, cudaStream_t s) {
     auto kern = backward_packed_kernel<BG, KW>;
     static size_t attr_bytes = 0;
     if (smem > attr_bytes) {
@@ -152,7 +153,7 @@ cudaError_t launch_packed_bg(const CUtensorMap& map, const BwdTiledArgs& a, dim3
         if (e != cudaSuccess) return e;
         attr_bytes = smem;
     }
-    kern<<<grid, kBwdPackedThreads, smem, s>>>(map, a);
+    kern<<<grid, kBwdPackedThreads, smem, s>>>(map, rmap, a);
     return cudaGetLastError();
 }
 
@@ -198,6 +199,17 @@ radon_status launch_backward_packed(const radon_geometry* g, const void* packed,
         *why = "cuTensorMapEncodeTiled rejected the packed-sinogram descriptor (CUresult " + std::to_string(rc) + ")";
         return RADON_ERR_UNSUPPORTED;
     }
+    // the ray table as rows of 8 words (bit copies), one row per ray, rays of view v at v * D
+    CUtensorMap rmap;
+    const uint64_t rdims[2] = {8, (uint64_t)g->V * g->D};
+    const uint64_t rstrides[1] = {32};
+    const uint32_t rbox[2] = {8, (uint32_t)wd};
+    const int rc2 = encode_tiled(&rmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, g->d_ray, rdims, rstrides, rbox,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
+    if (rc2 != 0) {
+        *why = "cuTensorMapEncodeTiled rejected the ray-table descriptor (CUresult " + std::to_string(rc2) + ")";
+        return RADON_ERR_UNSUPPORTED;
+    }
     BwdTiledArgs a;
     a.rays = g->d_ray;
     a.nks = g->d_nk;
@@ -208,6 +220,7 @@ radon_status launch_backward_packed(const radon_geometry* g, const void* packed,
     a.D = g->D;
     a.B = batch;
     a.h = (float)g->h;
+    a.ih2 = (float)(1.0 / (g->h * g->h));
     a.wd = wd;
     a.wdb = wd;
     a.align = 1;
@@ -225,9 +238,11 @@ radon_status launch_backward_packed(const radon_geometry* g, const void* packed,
     dim3 grid((unsigned)(a.tiles_x * a.tiles_x), (unsigned)groups);
     cudaError_t e;
     if (bg == 16)
-        e = kw == 3 ? launch_packed_bg<16, 3>(map, a, grid, smem, s) : launch_packed_bg<16, 6>(map, a, grid, smem, s);
+        e = kw == 3 ? launch_packed_bg<16, 3>(map, rmap, a, grid, smem, s)
+                    : launch_packed_bg<16, 6>(map, rmap, a, grid, smem, s);
     else
-        e = kw == 3 ? launch_packed_bg<8, 3>(map, a, grid, smem, s) : launch_packed_bg<8, 6>(map, a, grid, smem, s);
+        e = kw == 3 ? launch_packed_bg<8, 3>(map, rmap, a, grid, smem, s)
+                    : launch_packed_bg<8, 6>(map, rmap, a, grid, smem, s);
     if (e != cudaSuccess) {
         *why = std::string("packed adjoint launch: ") + cudaGetErrorString(e);
         return RADON_ERR_CUDA;

@@ -22,6 +22,7 @@
 #include "device_error.cuh"
 #include "dtype.cuh"
 #include "radon_internal.h"
+#include "f32x2.cuh"
 #include "tma.cuh"
 
 namespace radon {
@@ -47,6 +48,7 @@ struct BwdTiledArgs {
     int stall_test;    // 1: issue no copies (exercises the bounded-wait expiry path)
     int tma_rank;      // 1: 1-D descriptor; 2: the same layout described with a unit outer dimension
     int out_dtype;     // packed variant: storage type of the output image (radon_dtype)
+    float ih2;         // packed variant: 1 / h^2 (every ray's step has length h)
 };
 
 __host__ __device__ inline int bwd_nq(int bg) { return (bg + 3) / 4; }
@@ -124,6 +126,60 @@ __device__ __forceinline__ void bwd_ray_params(const RayT* rays, const int* nks,
     }
     *A_out = A;
     *B_out = Bq;
+}
+
+// Tile-relative position of a ray from its record (already in shared memory): A = (reference sample
+// position relative to the tile origin, step).  The sample count is not needed: samples beyond the
+// ray's ends lie outside the support box and carry zero weight on every pixel of the image, and a
+// ray that misses the image keeps its line (its samples all carry zero weight).  The reference is
+// the sample nearest the tile centre, not clamped to the ray: the table keeps k * dxh exact for k up
+// to kSplitMarginPx / h samples past either end, which covers every tile the ray's support touches;
+// for tiles farther away the products may round, but there every candidate weight is zero.
+// Rays outside the detector get a far-away sentinel with step zero (weight zero everywhere).
+__device__ __forceinline__ float4 bwd_ray_pos_rec(const RayT ray, bool valid, int ti, int tj, float ih2) {
+    float4 A = make_float4(1e9f, 1e9f, 0.0f, 0.0f);
+    const float dx = ray.dxh + ray.dxl, dy = ray.dyh + ray.dyl;
+    if (valid && (dx != 0.0f || dy != 0.0f)) {
+        const float ex = ((float)(tj - ray.J0) + 7.5f) - ray.fx0;
+        const float ey = ((float)(ti - ray.I0) + 7.5f) - ray.fy0;
+        const float kc = rintf(fmaf(ex, dx, ey * dy) * ih2);
+        const float qx = kc * ray.dxh, qy = kc * ray.dyh;
+        const float Qx = floorf(qx), Qy = floorf(qy);
+        A.x = ((float)(ray.J0 - tj) + Qx) + fmaf(kc, ray.dxl, ray.fx0 + (qx - Qx));
+        A.y = ((float)(ray.I0 - ti) + Qy) + fmaf(kc, ray.dyl, ray.fy0 + (qy - Qy));
+        A.z = dx;
+        A.w = dy;
+    }
+    return A;
+}
+
+// Bilinear weight of the pixel at p2 = (px, py) (tile-local) on the ray with tile-relative
+// position a0 = (rx, ry) and step d2 = (dx, dy): the sum over the KW samples whose index window
+// [ka, ka + KW) holds every sample within the pixel's 2 x 2 support square.  Steps have length h,
+// so step / |step|^2 = step * ih2.  The x and y halves run as f32x2 pairs.
+template <int KW>
+__device__ __forceinline__ float bwd_ray_weight_pair(f32x2 p2, f32x2 a0, f32x2 d2, f32x2 ih2_2, float ih2) {
+    const f32x2 e2 = f2_sub(a0, p2);   // A - p = -(p - A)
+    const f32x2 b2 = f2_mul(d2, ih2_2);
+    float ex, ey, bx, by, dx, dy;
+    f2_unpack(e2, &ex, &ey);
+    f2_unpack(b2, &bx, &by);
+    f2_unpack(d2, &dx, &dy);
+    const float kap = -fmaf(ex, bx, ey * by);
+    const float kr = fmaf(fabsf(dx) + fabsf(dy), ih2, 1e-4f);
+    const float ka = ceilf(kap - kr);
+    f32x2 r2 = f2_fma(f2_pack(ka, ka), d2, e2);   // ka * step - (p - A)
+    float w = 0.0f;
+#pragma unroll
+    for (int k = 0; k < KW; ++k) {
+        float rx, ry;
+        f2_unpack(r2, &rx, &ry);
+        const float wx = fmaxf(0.0f, 1.0f - fabsf(rx));
+        const float wy = fmaxf(0.0f, 1.0f - fabsf(ry));
+        w = fmaf(wx, wy, w);
+        if (k + 1 < KW) r2 = f2_add(r2, d2);
+    }
+    return w;
 }
 
 // Warp 0: windows for the views of chunk c and the TMA copies into staging slot `slot`.
@@ -318,152 +374,180 @@ __global__ void __launch_bounds__(kBwdThreads, 2) backward_tiled_kernel(const __
 // ---------------------------------------------------------------------------------------------
 // Packed variant: the sinogram batch was packed once into FP32 image quads laid out
 // [group][view][quad][det][4] (pack.cu), so one 5-D TMA box per view lands the tile's detector
-// window directly in the gather's [quad][det] layout.  Warp-specialised: a producer warp computes
-// each view's window, issues the copies and re-bases the rays on the tile (its ray-table loads
-// overlap the consumers' work on the previous chunk); 8 consumer warps (one pixel per thread)
-// gather.  Full / empty mbarriers per buffer, no CTA-wide barrier in the view loop.
+// window directly in the gather's [quad][det] layout, and one 2-D box copies the matching rows of the
+// ray table.  Warp-specialised over a ring of kBwdPackedStages chunks (kBwdPackedViews views each):
+// a producer warp computes each view's window and issues both copies, up to the ring's depth ahead;
+// the 256 consumer threads (one pixel each) re-base the landed rays on the tile, one ray per thread,
+// meet at a named barrier, and gather.  No global load sits on the consumers' path.
 constexpr int kBwdPackedViews = 4;
+constexpr int kBwdPackedStages = 4;
 constexpr int kBwdPackedThreads = kBwdThreads + 32;
+static_assert(sizeof(ViewF) == 32, "view maps are staged as 32-byte records");
 
 // Per-view slice of a staged window: padded so every TMA destination starts on 128 bytes.
 __host__ __device__ inline size_t bwd_packed_view_bytes(int bg, int wd) { return ((size_t)wd * bg * 4 + 127) / 128 * 128; }
+__host__ __device__ inline size_t bwd_packed_ray_bytes(int wd) { return ((size_t)wd * 32 + 127) / 128 * 128; }
+__host__ __device__ inline size_t bwd_packed_rp_bytes(int wd) { return ((size_t)kBwdPackedViews * wd * 16 + 127) / 128 * 128; }
+constexpr size_t kBwdPackedHeader = 1024;   // barriers, flags, windows and view maps of the ring
 
 __host__ __device__ inline size_t bwd_packed_smem_bytes(int bg, int wd) {
-    const size_t ystage = (size_t)kBwdPackedViews * bwd_packed_view_bytes(bg, wd);   // per buffer
-    const size_t rpb = (size_t)kBwdPackedViews * wd * 32;             // per buffer
-    return 128 + 512 + 2 * ((ystage + 127) / 128 * 128) + 2 * ((rpb + 127) / 128 * 128);
+    const size_t ystage = (size_t)kBwdPackedViews * bwd_packed_view_bytes(bg, wd);   // per stage
+    const size_t rstage = (size_t)kBwdPackedViews * bwd_packed_ray_bytes(wd);        // per stage
+    return 128 + kBwdPackedHeader + kBwdPackedStages * (ystage + rstage) + 2 * bwd_packed_rp_bytes(wd);
 }
 
 template <int BG, int KW>
-__global__ void __launch_bounds__(kBwdPackedThreads, 2) backward_packed_kernel(const __grid_constant__ CUtensorMap map,
+__global__ void __launch_bounds__(kBwdPackedThreads, 3) backward_packed_kernel(const __grid_constant__ CUtensorMap map,
+                                                                              const __grid_constant__ CUtensorMap rmap,
                                                                               const BwdTiledArgs a) {
     constexpr int NQ = BG / 4;
+    constexpr int S = kBwdPackedStages;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem);        // [2]
-    uint64_t* empty = reinterpret_cast<uint64_t*>(smem + 16);  // [2]
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 32);
-    int* dlo_c = reinterpret_cast<int*>(smem + 64);             // [2][views]
-    float* r_c = reinterpret_cast<float*>(smem + 128);          // [2][views]
-    ViewF* view_c = reinterpret_cast<ViewF*>(smem + 256);       // [2][views], 32 B each
+    uint64_t* tma_bar = reinterpret_cast<uint64_t*>(smem);        // [S]: a stage's copies landed
+    uint64_t* empty = reinterpret_cast<uint64_t*>(smem + 64);     // [S]: consumers released a stage
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 128);
+    int* dlo_c = reinterpret_cast<int*>(smem + 192);              // [S][views]
+    float* r_c = reinterpret_cast<float*>(smem + 256);            // [S][views]
+    ViewF* view_c = reinterpret_cast<ViewF*>(smem + 512);         // [S][views]
+    static_assert(S * kBwdPackedViews * 4 <= 64 && 512 + S * kBwdPackedViews * 32 <= kBwdPackedHeader,
+                  "ring header overflows its slots");
     const size_t yv_bytes = bwd_packed_view_bytes(BG, a.wd);
     const size_t ys_bytes = (size_t)kBwdPackedViews * yv_bytes;
-    const size_t rp_bytes = ((size_t)kBwdPackedViews * a.wd * 32 + 127) / 128 * 128;
-    unsigned char* ystage = smem + 512;
-    unsigned char* rpbuf = ystage + 2 * ys_bytes;
+    const size_t rv_bytes = bwd_packed_ray_bytes(a.wd);
+    const size_t rs_bytes = (size_t)kBwdPackedViews * rv_bytes;
+    const size_t rp_bytes = bwd_packed_rp_bytes(a.wd);
+    unsigned char* ystage = smem + kBwdPackedHeader;
+    unsigned char* rstage = ystage + S * ys_bytes;
+    unsigned char* rpbuf = rstage + S * rs_bytes;
 
     const int tid = threadIdx.x;
     const int tile = blockIdx.x;
     const int ti = (tile / a.tiles_x) * kBwdTile, tj = (tile - (tile / a.tiles_x) * a.tiles_x) * kBwdTile;
     const int nchunks = (a.V + kBwdPackedViews - 1) / kBwdPackedViews;
 
-    if (tid == 0) {
-        mbar_init(&full[0], 33);
-        mbar_init(&full[1], 33);
-        mbar_init(&empty[0], kBwdThreads);
-        mbar_init(&empty[1], kBwdThreads);
-        *abort_flag = 0;
-        fence_mbar_init();
+    if (tid < S) {
+        mbar_init(&tma_bar[tid], 1);
+        mbar_init(&empty[tid], kBwdThreads);
     }
+    if (tid == 0) *abort_flag = 0;
+    fence_mbar_init();
     __syncthreads();
 
     if (tid >= kBwdThreads) {
         // ------------------------------------------------------------------ producer warp
         const int lane = tid & 31;
-        for (int c = 0; c < nchunks; ++c) {
-            const int buf = c & 1;
+        int c = 0;
+        for (; c < nchunks; ++c) {
+            const int st = c % S;
+            bool ok = true;
+            if (c >= S && lane == 0) ok = mbar_wait_bounded(&empty[st], (uint32_t)((c / S - 1) & 1), a.spin_limit);
+            if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
             const int v0 = c * kBwdPackedViews;
             const int nv = min(kBwdPackedViews, a.V - v0);
-            bool ok = true;
-            if (c >= 2 && lane == 0) ok = mbar_wait_bounded(&empty[buf], (uint32_t)(((c >> 1) - 1) & 1), a.spin_limit);
-            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-            if (!ok) {
-                if (lane == 0) {
-                    record_device_error(a.err, RADON_ERR_TIMEOUT);
-                    *abort_flag = 1;
-                }
-                __syncwarp();
-                mbar_arrive(&full[buf]);
-                if (lane == 0) mbar_arrive(&full[buf]);   // 33 arrivals complete the phase without data
-                return;
-            }
-            int dlo = 0;
-            float r = 0.0f;
             if (lane < nv) {
                 const ViewF vf = a.views[v0 + lane];
+                int dlo;
+                float r;
                 bwd_view_window(vf, ti, tj, a.n, &dlo, &r);
-                dlo_c[buf * kBwdPackedViews + lane] = dlo;
-                r_c[buf * kBwdPackedViews + lane] = r;
-                view_c[buf * kBwdPackedViews + lane] = vf;
+                dlo_c[st * kBwdPackedViews + lane] = dlo;
+                r_c[st * kBwdPackedViews + lane] = r;
+                view_c[st * kBwdPackedViews + lane] = vf;
             }
             __syncwarp();
             if (lane == 0) {
                 fence_proxy_async_shared();
-                mbar_arrive_expect_tx(&full[buf], (uint32_t)(nv * a.wd * BG * 4));
-                for (int vl = 0; vl < nv; ++vl)
-                    tma_load_5d(ystage + buf * ys_bytes + (size_t)vl * yv_bytes, &map, &full[buf], 0,
-                                dlo_c[buf * kBwdPackedViews + vl], 0, v0 + vl, blockIdx.y);
-            }
-            float4* rp = reinterpret_cast<float4*>(rpbuf + buf * rp_bytes);
-            for (int e = lane; e < nv * a.wd; e += 32) {
-                const int vl = e / a.wd, dl = e - (e / a.wd) * a.wd;
-                float4 A, Bq;
-                bwd_ray_params(a.rays, a.nks, v0 + vl, dlo_c[buf * kBwdPackedViews + vl] + dl, a.D, ti, tj, &A, &Bq);
-                rp[(vl * a.wd + dl) * 2] = A;
-                rp[(vl * a.wd + dl) * 2 + 1] = Bq;
+                mbar_arrive_expect_tx(&tma_bar[st], (uint32_t)(nv * a.wd * (BG * 4 + 32)));
+                for (int vl = 0; vl < nv; ++vl) {
+                    const int dlo = dlo_c[st * kBwdPackedViews + vl];
+                    tma_load_5d(ystage + st * ys_bytes + (size_t)vl * yv_bytes, &map, &tma_bar[st], 0, dlo, 0, v0 + vl,
+                                blockIdx.y);
+                    tma_load_2d(rstage + st * rs_bytes + (size_t)vl * rv_bytes, &rmap, &tma_bar[st], 0,
+                                (v0 + vl) * a.D + dlo);
+                }
             }
             __syncwarp();
-            mbar_arrive(&full[buf]);   // every lane: its ray parameters are released
+        }
+        if (c < nchunks && lane == 0) {
+            // The consumers stopped releasing stages: record it, let the copies still in flight land
+            // (bounded), then complete chunk c's phase without data so any consumer still waiting
+            // sees the abort.
+            record_device_error(a.err, RADON_ERR_TIMEOUT);
+            *abort_flag = 1;
+            for (int cc = max(0, c - S + 1); cc < c; ++cc)
+                mbar_wait_bounded(&tma_bar[cc % S], (uint32_t)((cc / S) & 1), a.spin_limit);
+            mbar_arrive(&tma_bar[c % S]);
         }
         return;
     }
 
     // ---------------------------------------------------------------------- consumer warps
-    const int pi = tid / kBwdTile, pj = tid - (tid / kBwdTile) * kBwdTile;
-    const float px = (float)pj, py = (float)pi;
+    // each warp takes a 4 x 8 block of the tile: its pixels' detector footprints overlap more than
+    // those of a 2 x 16 strip, so the gather's shared loads touch fewer distinct addresses
+    const int warp = tid >> 5, lane = tid & 31;
+    const int pi = (warp >> 1) * 4 + (lane >> 3), pj = (warp & 1) * 8 + (lane & 7);
+    const f32x2 p2 = f2_pack((float)pj, (float)pi);
+    const f32x2 ih2_2 = f2_pack(a.ih2, a.ih2);
     const float gx = (float)(tj + pj), gy = (float)(ti + pi);
     const bool inside = (ti + pi) < a.n && (tj + pj) < a.n;
-    float acc[BG];
+    f32x2 acc[BG / 2];   // image pairs (2b, 2b + 1)
 #pragma unroll
-    for (int b = 0; b < BG; ++b) acc[b] = 0.0f;
+    for (int b = 0; b < BG / 2; ++b) acc[b] = 0ull;
     for (int c = 0; c < nchunks; ++c) {
-        const int buf = c & 1;
+        const int st = c % S;
         const int v0 = c * kBwdPackedViews;
         const int nv = min(kBwdPackedViews, a.V - v0);
-        if (!mbar_wait_bounded(&full[buf], (uint32_t)((c >> 1) & 1), a.spin_limit)) {
-            record_device_error(a.err, RADON_ERR_TIMEOUT);
+        bool bad = !mbar_wait_bounded(&tma_bar[st], (uint32_t)((c / S) & 1), a.spin_limit);
+        bad = bad || *abort_flag != 0;
+        float4* rp = reinterpret_cast<float4*>(rpbuf + (c & 1) * rp_bytes);
+        if (!bad) {
+            // re-base the landed rays on this tile: one ray per thread
+            for (int e = tid; e < nv * a.wd; e += kBwdThreads) {
+                const int vl = e / a.wd, dl = e - (e / a.wd) * a.wd;
+                const int d = dlo_c[st * kBwdPackedViews + vl] + dl;
+                const RayT ray = *reinterpret_cast<const RayT*>(rstage + st * rs_bytes + (size_t)vl * rv_bytes +
+                                                                (size_t)dl * 32);
+                rp[e] = bwd_ray_pos_rec(ray, d >= 0 && d < a.D, ti, tj, a.ih2);
+            }
+        }
+        // all consumers: parameters written (the buffer alternates, so the previous chunk's readers
+        // have all passed this barrier before it is overwritten) -- and one shared abort decision
+        if (named_barrier_or(1, kBwdThreads, bad)) {
+            if (tid == 0) record_device_error(a.err, RADON_ERR_TIMEOUT);
             return;
         }
-        if (*abort_flag) return;
-        const float4* rpb = reinterpret_cast<const float4*>(rpbuf + buf * rp_bytes);
         for (int vl = 0; vl < nv; ++vl) {
-            const ViewF vf = view_c[buf * kBwdPackedViews + vl];
-            const int dlo = dlo_c[buf * kBwdPackedViews + vl];
-            const float r = r_c[buf * kBwdPackedViews + vl];
-            const float t = bwd_det_coord(vf, gx, gy);
+            const ViewF vf = view_c[st * kBwdPackedViews + vl];
+            const int dlo = dlo_c[st * kBwdPackedViews + vl];
+            const float r = r_c[st * kBwdPackedViews + vl];
+            // approximate divide: the window [t - r, t + r] carries margins far above its error
+            const float t = __fdividef(fmaf(vf.ax, gx, fmaf(vf.ay, gy, vf.a0)), fmaf(vf.bx, gx, fmaf(vf.by, gy, vf.b0)));
             const float flo = ceilf(t - r), fhi = floorf(t + r);
             const int da = (int)fmaxf(flo, (float)max(dlo, 0));
             const int db = (int)fminf(fhi, (float)min(a.D - 1, dlo + a.wd - 1));
             if (inside && ((flo < (float)dlo && flo >= 0.0f) || (fhi > (float)(dlo + a.wd - 1) && fhi <= (float)(a.D - 1))))
                 record_device_error(a.err, RADON_ERR_DEVICE_BOUNDS);
-            const float4* rpv = rpb + vl * a.wd * 2;
-            const float4* yq = reinterpret_cast<const float4*>(ystage + buf * ys_bytes + (size_t)vl * yv_bytes);
+            const ulonglong2* rpv = reinterpret_cast<const ulonglong2*>(rp) + vl * a.wd;
+            const ulonglong2* yq = reinterpret_cast<const ulonglong2*>(ystage + st * ys_bytes + (size_t)vl * yv_bytes);
             for (int d = da; d <= db; ++d) {
                 const int dl = d - dlo;
-                const float w = bwd_ray_weight<KW>(px, py, rpv[dl * 2], rpv[dl * 2 + 1]);
+                const ulonglong2 rr = rpv[dl];
+                const float w = bwd_ray_weight_pair<KW>(p2, rr.x, rr.y, ih2_2, a.ih2);
+                const f32x2 w2 = f2_pack(w, w);
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) {
-                    const float4 y4 = yq[q * a.wd + dl];
-                    acc[4 * q + 0] = fmaf(w, y4.x, acc[4 * q + 0]);
-                    acc[4 * q + 1] = fmaf(w, y4.y, acc[4 * q + 1]);
-                    acc[4 * q + 2] = fmaf(w, y4.z, acc[4 * q + 2]);
-                    acc[4 * q + 3] = fmaf(w, y4.w, acc[4 * q + 3]);
+                    const ulonglong2 y4 = yq[q * a.wd + dl];
+                    acc[2 * q + 0] = f2_fma(w2, y4.x, acc[2 * q + 0]);
+                    acc[2 * q + 1] = f2_fma(w2, y4.y, acc[2 * q + 1]);
                 }
             }
         }
-        mbar_arrive(&empty[buf]);
+        mbar_arrive(&empty[st]);
     }
     if (inside) {
+        float accf[BG];
+#pragma unroll
+        for (int b = 0; b < BG / 2; ++b) f2_unpack(acc[b], &accf[2 * b], &accf[2 * b + 1]);
         const long long npix = (long long)a.n * a.n;
         const long long p = (long long)(ti + pi) * a.n + (tj + pj);
         const int b0 = blockIdx.y * BG;
@@ -471,17 +555,17 @@ __global__ void __launch_bounds__(kBwdPackedThreads, 2) backward_packed_kernel(c
             __half* out = reinterpret_cast<__half*>(a.img);
 #pragma unroll
             for (int b = 0; b < BG; ++b)
-                if (b0 + b < a.B) out[(long long)(b0 + b) * npix + p] = __float2half_rn(a.h * acc[b]);
+                if (b0 + b < a.B) out[(long long)(b0 + b) * npix + p] = __float2half_rn(a.h * accf[b]);
         } else if (a.out_dtype == RADON_BF16) {
             __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(a.img);
 #pragma unroll
             for (int b = 0; b < BG; ++b)
-                if (b0 + b < a.B) out[(long long)(b0 + b) * npix + p] = __float2bfloat16_rn(a.h * acc[b]);
+                if (b0 + b < a.B) out[(long long)(b0 + b) * npix + p] = __float2bfloat16_rn(a.h * accf[b]);
         } else {
             float* out = reinterpret_cast<float*>(a.img);
 #pragma unroll
             for (int b = 0; b < BG; ++b)
-                if (b0 + b < a.B) out[(long long)(b0 + b) * npix + p] = a.h * acc[b];
+                if (b0 + b < a.B) out[(long long)(b0 + b) * npix + p] = a.h * accf[b];
         }
     }
 }

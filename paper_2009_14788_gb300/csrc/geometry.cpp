@@ -180,9 +180,12 @@ radon_status build_geometry(radon_geometry* g) {
             RayT& rt = g->h_ray[idx];
             split_coord(px, &rt.J0, &rt.fx0);
             split_coord(py, &rt.I0, &rt.fy0);
-            // k' * dxh exact in FP32 for k' < nk: dxh keeps 24 - bits(nk) significant bits
+            // k' * dxh exact in FP32 for -M <= k' < nk + M: dxh keeps 24 - bits(nk + M) significant bits.
+            // The margin M covers the adjoint's reference sample, the one nearest a 16-pixel tile's
+            // centre, which may sit up to (tile half-diagonal + support) / h samples past a ray end.
+            const long margin = kSplitMarginPx * (long)std::ceil(1.0 / g->h) + 8;
             int kbits = 1;
-            while (kbits < 24 && ((long)1 << kbits) < (long)nk) ++kbits;
+            while (kbits < 24 && ((long)1 << kbits) < (long)nk + margin) ++kbits;
             const int hbits = std::max(1, 24 - kbits);
             const double hx = round_bits(sx, hbits), hy = round_bits(sy, hbits);
             rt.dxh = (float)hx;

@@ -15,13 +15,17 @@ namespace radon {
 
 constexpr uint64_t kGeometryMagic = 0x5241444f4e47454fULL;  // "RADONGEO"
 
+// Exactness margin of the split ray table, in pixels beyond either end of a ray.
+constexpr int kSplitMarginPx = 24;
+
 // One ray in pixel-index coordinates (column x = j, row y = i), stored in split precision so
 // kernels can re-base sample positions without FP32 drift.  Sample k' = 0..nk-1 sits at
 //     x = J0 + fx0 + k' (dxh + dxl),   y = I0 + fy0 + k' (dyh + dyl)
 // with J0, I0 integers, fx0, fy0 in [0, 1), and the step split so that k' * dxh is exact in
-// FP32 for every k' < nk (dxh carries at most 24 - ceil(log2 nk) significant bits) while dxl
-// holds the remainder.  The ray is oriented so that its major-axis step is >= 0: the y step for
-// views of the vertical class, the x step for the horizontal class.
+// FP32 for every k' in [-M, nk + M) (dxh carries at most 24 - ceil(log2(nk + M)) significant
+// bits, M = kSplitMarginPx / h + 8 samples) while dxl holds the remainder.  The ray is oriented
+// so that its major-axis step is >= 0: the y step for views of the vertical class, the x step
+// for the horizontal class.
 struct RayT {
     int J0, I0;
     float fx0, fy0;
