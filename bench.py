@@ -115,13 +115,24 @@ def _rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+ADJ_OPS_PER_SAMPLE = 18
+
+
+def roofline(samples, ms, sm_count, per_sm, clk_mhz, basis, traffic):
+    """Achieved vs peak bilinear samples/s of one kernel (``alu``: an on-chip pipe bounds it)."""
+    peak = sm_count * per_sm * clk_mhz * 1e6 / 1e9
+    achieved = samples / (ms * 1e-3) / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gsamples/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_basis": basis + " (sm_max_mhz of MEASURED_PEAKS.json)"}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2009_14788_gb300 import Geometry, backward_raw, forward_raw, launch_config
+    from paper_2009_14788_gb300 import Geometry, _lib as L, backward_raw, forward_raw, launch_config
     from paper_2009_14788_gb300.build import build
 
     world, rank, local = _dist()
@@ -162,7 +173,7 @@ def run_ours(args):
         if ev is not None:
             ev[2].record(stream)
 
-    def timed(cfg, steps, warmup, sets):
+    def timed(cfg, steps, warmup, sets, launches=None):
         for i in range(warmup):
             step(i, cfg, sets)
         torch.cuda.synchronize()
@@ -172,10 +183,13 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
+        n0 = L.radon_kernel_launch_count()
         t0.record(stream)
         for i in range(steps):
             step(i, cfg, sets, evs[i])
         t1.record(stream)
+        if launches is not None:
+            launches["count"] = int(L.radon_kernel_launch_count() - n0)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -200,7 +214,8 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    total_ms, fwd_ms, adj_ms = timed(chosen, args.steps, args.warmup, (xs, ys, outs_y, outs_x))
+    launches = {}
+    total_ms, fwd_ms, adj_ms = timed(chosen, args.steps, args.warmup, (xs, ys, outs_y, outs_x), launches)
     time.sleep(0.2)
     clk = clocks.stop()
 
@@ -243,23 +258,34 @@ def run_ours(args):
     mean_fwd = statistics.mean(fwd_ms)
     mean_adj = statistics.mean(adj_ms)
     dom = "forward" if mean_fwd >= mean_adj else "backward"
-    dom_ms = max(mean_fwd, mean_adj)
     peaks = _peaks()
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     bytes_per_texel = torch.empty((), dtype=dt).element_size()
-    per_sm = 128.0 / (4.0 * bytes_per_texel)          # shared-memory / L1 load pipe: 128 B/clk/SM
-    peak_gs = sm_count * per_sm * clk_mhz * 1e6 / 1e9
-    achieved_gs = B * S / (dom_ms * 1e-3) / 1e9
-    traffic = None
+    traffic_tab = {}
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
         try:
             with open(tfile) as f:
-                tinfo = json.load(f).get(args.workload, {}).get(args.storage, {}).get(dom)
-            traffic = tinfo
+                traffic_tab = json.load(f).get(args.workload, {}).get(args.storage, {})
         except (OSError, ValueError):
-            traffic = None
+            traffic_tab = {}
+    rooflines = {
+        # forward: 4 texels per sample through the shared-memory / L1 load pipe, 128 B/clk/SM
+        "forward": roofline(B * S, mean_fwd, sm_count, 128.0 / (4.0 * bytes_per_texel), clk_mhz,
+                            "%d SMs x %.0f samples/clk/SM (128 B/clk/SM load pipe / 4 texels x %d B) x %.0f MHz"
+                            % (sm_count, 128.0 / (4.0 * bytes_per_texel), bytes_per_texel, clk_mhz),
+                            traffic_tab.get("forward")),
+        # adjoint: FP32 issue, 128 lanes/clk/SM over ~18 FP32 operations per sample (4 weight pairs)
+        "backward": roofline(B * S, mean_adj, sm_count, 128.0 / ADJ_OPS_PER_SAMPLE, clk_mhz,
+                             "%d SMs x %.2f samples/clk/SM (128 FP32 lanes/clk/SM / %d ops per sample) x %.0f MHz"
+                             % (sm_count, 128.0 / ADJ_OPS_PER_SAMPLE, ADJ_OPS_PER_SAMPLE, clk_mhz),
+                             traffic_tab.get("backward")),
+    }
+
+    secondary = None
+    if rank == 0 and world == 1 and not args.no_secondary:
+        secondary = run_secondary(args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -291,25 +317,130 @@ def run_ours(args):
             "plain_f32": {"ms_per_step": plain_ms, "samples_per_s": samples_per_step / (plain_ms * 1e-3),
                           "fwd_ms": statistics.mean(p_fwd), "adj_ms": statistics.mean(p_adj)},
             "speedup_vs_plain_f32": plain_ms / ms_per_step,
-            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved_gs, "peak": peak_gs,
-                         "unit": "Gsamples/s", "frac": achieved_gs / peak_gs, "traffic": traffic,
-                         "peak_basis": "%d SMs x %.0f samples/clk/SM (128 B/clk/SM load pipe / 4 texels x %d B) x %.0f MHz (sm_max_mhz of MEASURED_PEAKS.json)" % (sm_count, per_sm, bytes_per_texel, clk_mhz)},
+            "roofline": dict(rooflines[dom], kernel=dom),
+            "roofline_forward": rooflines["forward"],
+            "roofline_backward": rooflines["backward"],
             "e2e": {"value": samples_per_step * world / (e2e_ms * 1e-3), "unit": "samples/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": launches["count"],
             "clocks": clk,
             "cpu_baseline": cpu,
         }
+        if secondary is not None:
+            line["secondary"] = secondary
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def _flush_l2(buf):
+    buf.zero_()   # a write larger than L2 between timed iterations (outside the timed brackets)
+
+
+def run_secondary(args):
+    """The two secondary points, each over a few L2-flushed iterations on the same GPU.
+
+    * Landweber (8 x 512^2 parallel, 60 views in [0, pi), 725 detectors, bf16 storage): the step
+      size by 20 power iterations, 10 Landweber iterations forward, and the reverse pass to the
+      gradients w.r.t. y and alpha (per-iteration checkpoints: 3 projections per iteration).
+    * The paper's batch benchmark shape (32 x 512^2 parallel, 512 views in [0, pi), 512
+      detectors): forward + adjoint, chosen 16-bit form against the plain FP32 form.
+    """
+    import torch
+
+    from paper_2009_14788_gb300 import Geometry, Landweber, backward_raw, forward_raw, launch_config
+    from synth import power_start, uniform_angles, workload_noise
+
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def time_it(fn, reps, warm=2):
+        for _ in range(warm):
+            fn()
+        ts = []
+        for _ in range(reps):
+            _flush_l2(flush)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    out = {}
+    # Landweber
+    w = WORKLOADS["landweber_b8_n512_v60_d725"]
+    ga = workload_geometry_args(w)
+    kind = ga.pop("kind")
+    g = Geometry(kind, **ga)
+    S = g.sample_count
+    K = w.extra["iterations"]
+    P = w.extra["power_iterations"]
+    x_true = workload_images(w)
+    sino_shape = (w.batch, g.n_angles, g.det_count)
+    xt = torch.from_numpy(x_true).to("cuda", torch.float32)
+    y32 = forward_raw(g, xt) + torch.from_numpy(workload_noise(w, sino_shape)).to("cuda", torch.float32)
+    y = y32.to(torch.bfloat16)
+    lw = Landweber(g)
+    v0 = torch.from_numpy(power_start(g.n, 2000 * w.number)).to("cuda", torch.float32)
+    ms_power = time_it(lambda: lw.estimate_alpha(P, v0=v0), 3)
+    alpha, lam = lw.estimate_alpha(P, v0=v0)
+    x0 = torch.zeros((w.batch, g.n, g.n), dtype=torch.bfloat16, device="cuda")
+    yg = y.clone().requires_grad_(True)
+    ag = alpha.clone().requires_grad_(True)
+    ms_fwd = time_it(lambda: lw.run(x0, yg, ag, K), 3)
+
+    def fwd_bwd():
+        xk = lw.run(x0, yg, ag, K)
+        loss = ((xk.float() - xt) ** 2).sum()
+        loss.backward()
+    ms_fb = time_it(fwd_bwd, 3)
+    proj_fwd = 2 * K * w.batch * S
+    proj_bwd = 3 * K * w.batch * S
+    out["landweber"] = {
+        "workload": w.name, "storage": "bf16", "iterations": K, "power_iterations": P,
+        "lambda": float(lam.item()), "alpha": float(alpha.item()),
+        "ms_power_iteration": ms_power, "ms_forward": ms_fwd, "ms_forward_backward": ms_fb,
+        "samples_per_s_forward": proj_fwd / (ms_fwd * 1e-3),
+        "samples_per_s_forward_backward": (proj_fwd + proj_bwd) / (ms_fb * 1e-3),
+        "samples_per_s_power_iteration": 2 * P * S / (ms_power * 1e-3),
+        "l2": "flushed (2x L2 write) before each timed iteration",
+    }
+    del g, xt, y32, y, yg, ag, x0
+    # paper-shaped batch point
+    g = Geometry("parallel", 512, uniform_angles(512, np.pi), det_count=512, det_spacing=1.0)
+    S = g.sample_count
+    B = 32
+    from synth import ellipse_phantom
+    xs = np.stack([ellipse_phantom(512, 10, 9000 + b) for b in range(B)])
+    res = {"workload": "parallel_b32_n512_v512_d512", "samples_per_image": S,
+           "l2": "flushed (2x L2 write) before each timed step"}
+    for label, dt, cfg in (("chosen_f16", torch.float16, launch_config("auto")),
+                           ("plain_f32", torch.float32, launch_config("plain"))):
+        x = torch.from_numpy(xs).to("cuda", dt)
+        yb = forward_raw(g, x, cfg)
+        oy, ox = torch.empty_like(yb), torch.empty_like(x)
+
+        def fa():
+            forward_raw(g, x, cfg, out=oy)
+            backward_raw(g, yb, cfg, out=ox)
+        ms = time_it(fa, 3 if label == "plain_f32" else 5, warm=1)
+        res[label] = {"ms_per_step": ms, "samples_per_s": 2 * B * S / (ms * 1e-3), "images_per_s": B / (ms * 1e-3)}
+        del x, yb, oy, ox
+    res["speedup_chosen_vs_plain_f32"] = res["plain_f32"]["ms_per_step"] / res["chosen_f16"]["ms_per_step"]
+    out["paper_batch"] = res
+    del flush
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_profile(args):
     """Only the chosen form's kernels: warmup + steps launches of forward and adjoint, no timing."""
     import torch
 
-    from paper_2009_14788_gb300 import Geometry, backward_raw, forward_raw, launch_config
+    from paper_2009_14788_gb300 import Geometry, _lib as L, backward_raw, forward_raw, launch_config
     from paper_2009_14788_gb300.build import build
 
     build()
@@ -408,6 +539,8 @@ def main():
     ap.add_argument("--algo", choices=["auto", "plain", "tiled"], default="auto")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the Landweber and paper-shaped secondary measurements")
     ap.add_argument("--reference-stride", type=int, default=16)
     ap.add_argument("--profile", action="store_true",
                     help="run --warmup + --steps fwd/adjoint launches of the chosen form only (for ncu)")

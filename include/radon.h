@@ -256,11 +256,100 @@ RADON_API radon_status radon_forward_static_scratch(const radon_geometry* geomet
                                                     radon_dtype dtype, int batch, void* stream);
 
 /*
+ * ---- Iterative reconstruction (Section 4.2: Landweber iteration, step size by power iteration) ----
+ *
+ * Output epilogue of the fused projections below.  Each output element is
+ *     out[i] = op_scale * s * P[i] + add_scale * add[i]
+ * where P is the projection (forward or adjoint, as radon_forward / radon_backward compute it),
+ * s = *op_scale_dev if op_scale_dev is not NULL (a device FP32 scalar, read by the kernels, so a
+ * step length can stay on the device) and 1 otherwise, and `add` is an optional device array of the
+ * output's dtype and layout (NULL: no addend).  `add` may be the output buffer itself (in-place
+ * update); otherwise it must not overlap the output.  The sum is formed in FP32 and rounded once to
+ * the storage type, so a 16-bit residual A x - y keeps its own relative precision instead of
+ * inheriting the rounding of A x.  {1, NULL, 0, NULL} gives exactly radon_forward / radon_backward.
+ * Landweber's update x - alpha A^T (A x - y) is two calls:
+ *     r  = forward_fused(x,  {1, NULL, -1, y})
+ *     x' = backward_fused(r, {-1, alpha_dev, 1, x}).
+ */
+typedef struct radon_epilogue {
+    float op_scale;
+    const float* op_scale_dev;
+    float add_scale;
+    const void* add;
+} radon_epilogue;
+
+/*
+ * Forward projection / exact adjoint with an output epilogue (NULL `epilogue` = identity).
+ * Otherwise the same as radon_forward_ws / radon_backward_ws: optional launch config, optional
+ * caller workspace (NULL or too small: the paths that need none).  `add` must be aligned to its
+ * element size and `op_scale_dev` to 4 bytes.  Allocates nothing; can be captured.
+ */
+RADON_API radon_status radon_forward_fused(const radon_geometry* geometry, const void* img, void* sino,
+                                           radon_dtype dtype, int batch, const radon_epilogue* epilogue,
+                                           const radon_launch_config* config, void* workspace,
+                                           size_t workspace_bytes, void* stream);
+RADON_API radon_status radon_backward_fused(const radon_geometry* geometry, const void* sino, void* img,
+                                            radon_dtype dtype, int batch, const radon_epilogue* epilogue,
+                                            const radon_launch_config* config, void* workspace,
+                                            size_t workspace_bytes, void* stream);
+
+/* Device workspace, in bytes, of radon_dot. */
+RADON_API size_t radon_dot_workspace_size(void);
+
+/*
+ * Inner product of two device arrays of `count` elements of `dtype` (the same for both):
+ *     *result = scale * <a, b> + (accumulate ? *result : 0)
+ * with `result` one device FP32.  Products are summed in FP32 per thread and in FP64 across
+ * threads and blocks, in a fixed order: the result is deterministic.  Two kernels, in stream order,
+ * using the caller's workspace (>= radon_dot_workspace_size bytes, 8-byte aligned).  Allocates
+ * nothing; can be captured.
+ */
+RADON_API radon_status radon_dot(const void* a, const void* b, radon_dtype dtype, int64_t count, float scale,
+                                 float* result, int accumulate, void* workspace, size_t workspace_bytes,
+                                 void* stream);
+
+/*
+ * y = alpha * s * x + beta * y over `count` elements, elementwise, with x of dtype `x_dtype` and y of
+ * `y_dtype` (they may differ: this also casts), s = *alpha_dev if alpha_dev is not NULL, else 1.
+ * With beta == 0, y is written without being read (it may hold anything, NaN included).  FP32
+ * arithmetic, one rounding to y's type.  Allocates nothing; can be captured.
+ */
+RADON_API radon_status radon_axpby(const void* x, radon_dtype x_dtype, void* y, radon_dtype y_dtype, int64_t count,
+                                   float alpha, const float* alpha_dev, float beta, void* stream);
+
+/*
+ * Device workspace, in bytes, of radon_power_iteration for this geometry (FP32 image and
+ * sinogram buffers, the projections' packed workspaces and the dot workspace).
+ */
+RADON_API size_t radon_power_iteration_workspace_size(const radon_geometry* geometry);
+
+/*
+ * Largest eigenvalue of A^T A by the power method, the step-size estimate of Landweber's iteration:
+ *     z = v0 / |v0|;  repeat `iterations` times:  w = A^T A z,  lambda = <z, w>,  z = w / |w|
+ * (lambda is the Rayleigh quotient of the last iterate).  v0 is one FP32 image [N][N] on the device
+ * (the caller draws it, e.g. N(0, 1) from a seeded generator; it is not modified).  All arithmetic
+ * runs in FP32 storage on the device; *lambda_out (one device FP32) receives the estimate and, if
+ * alpha_out is not NULL, *alpha_out receives Landweber's step alpha = 1 / lambda.  Workspace:
+ * >= radon_power_iteration_workspace_size bytes, 16-byte aligned.  Allocates nothing, never
+ * synchronises; can be captured.  A zero v0 or an operator that maps z to zero gives NaN.
+ */
+RADON_API radon_status radon_power_iteration(const radon_geometry* geometry, const float* v0, int iterations,
+                                             float* lambda_out, float* alpha_out, void* workspace,
+                                             size_t workspace_bytes, void* stream);
+
+/*
  * Synchronises `stream`, then reads and clears the library's device error word.
  * Returns RADON_OK, RADON_ERR_TIMEOUT or RADON_ERR_DEVICE_BOUNDS (from kernels), or
  * RADON_ERR_CUDA if the synchronisation itself failed.
  */
 RADON_API radon_status radon_get_device_error(void* stream);
+
+/*
+ * Number of kernels this library has launched in this process so far (every pack, projection and
+ * vector kernel, counted on the host when the launch is issued).  Thread-safe; for accounting, e.g.
+ * the launches inside a timed region are the difference of two reads.
+ */
+RADON_API uint64_t radon_kernel_launch_count(void);
 
 /* Static, never NULL. */
 RADON_API const char* radon_status_string(radon_status status);

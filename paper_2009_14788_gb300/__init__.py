@@ -6,20 +6,27 @@ PyTorch binding: ``Radon``, ``RadonFanbeam``, differentiable forward / backproje
 """
 
 from . import _lib  # noqa: F401
+from .landweber import Landweber, LandweberFunction, landweber  # noqa: F401
 from .radon import (  # noqa: F401
     Geometry,
     Radon,
     RadonBackprojectionFunction,
     RadonFanbeam,
     RadonForwardFunction,
+    axpby,
+    backward_fused,
     backward_raw,
     backward_workspace_bytes,
+    dot,
+    forward_fused,
     forward_raw,
     forward_workspace_bytes,
     launch_config,
+    power_iteration,
 )
 
 __all__ = [
     "Geometry", "Radon", "RadonFanbeam", "RadonForwardFunction", "RadonBackprojectionFunction", "forward_raw",
-    "backward_raw", "launch_config", "forward_workspace_bytes", "backward_workspace_bytes",
+    "backward_raw", "launch_config", "forward_workspace_bytes", "backward_workspace_bytes", "forward_fused",
+    "backward_fused", "dot", "axpby", "power_iteration", "Landweber", "LandweberFunction", "landweber",
 ]

@@ -76,6 +76,15 @@ class radon_launch_config(ctypes.Structure):
     ]
 
 
+class radon_epilogue(ctypes.Structure):
+    _fields_ = [
+        ("op_scale", ctypes.c_float),
+        ("op_scale_dev", ctypes.c_void_p),
+        ("add_scale", ctypes.c_float),
+        ("add", ctypes.c_void_p),
+    ]
+
+
 _c = None
 
 # (name, restype, argtypes) of every exported function
@@ -112,6 +121,24 @@ _SIGNATURES = [
       ctypes.POINTER(radon_launch_config), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     ("radon_forward_static_scratch", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    ("radon_forward_fused", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(radon_epilogue),
+      ctypes.POINTER(radon_launch_config), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("radon_backward_fused", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(radon_epilogue),
+      ctypes.POINTER(radon_launch_config), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("radon_dot_workspace_size", ctypes.c_size_t, []),
+    ("radon_dot", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p, ctypes.c_int,
+      ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("radon_axpby", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p,
+      ctypes.c_float, ctypes.c_void_p]),
+    ("radon_power_iteration_workspace_size", ctypes.c_size_t, [ctypes.c_void_p]),
+    ("radon_power_iteration", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+      ctypes.c_size_t, ctypes.c_void_p]),
+    ("radon_kernel_launch_count", ctypes.c_uint64, []),
     ("radon_get_device_error", ctypes.c_int, [ctypes.c_void_p]),
     ("radon_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("radon_last_error_message", ctypes.c_char_p, []),
@@ -221,6 +248,41 @@ def radon_backward_ws(geom, sino, img, dtype, batch, config, workspace, workspac
 
 def radon_forward_static_scratch(geom, img, sino, dtype, batch, stream):
     return _call("radon_forward_static_scratch", geom, img, sino, dtype, batch, stream)
+
+
+def radon_forward_fused(geom, img, sino, dtype, batch, epilogue, config, workspace, workspace_bytes, stream):
+    return _call("radon_forward_fused", geom, img, sino, dtype, batch, epilogue, config, workspace, workspace_bytes,
+                 stream)
+
+
+def radon_backward_fused(geom, sino, img, dtype, batch, epilogue, config, workspace, workspace_bytes, stream):
+    return _call("radon_backward_fused", geom, sino, img, dtype, batch, epilogue, config, workspace, workspace_bytes,
+                 stream)
+
+
+def radon_dot_workspace_size():
+    return _call("radon_dot_workspace_size")
+
+
+def radon_dot(a, b, dtype, count, scale, result, accumulate, workspace, workspace_bytes, stream):
+    return _call("radon_dot", a, b, dtype, count, scale, result, accumulate, workspace, workspace_bytes, stream)
+
+
+def radon_axpby(x, x_dtype, y, y_dtype, count, alpha, alpha_dev, beta, stream):
+    return _call("radon_axpby", x, x_dtype, y, y_dtype, count, alpha, alpha_dev, beta, stream)
+
+
+def radon_power_iteration_workspace_size(geom):
+    return _call("radon_power_iteration_workspace_size", geom)
+
+
+def radon_power_iteration(geom, v0, iterations, lambda_out, alpha_out, workspace, workspace_bytes, stream):
+    return _call("radon_power_iteration", geom, v0, iterations, lambda_out, alpha_out, workspace, workspace_bytes,
+                 stream)
+
+
+def radon_kernel_launch_count():
+    return _call("radon_kernel_launch_count")
 
 
 def radon_get_device_error(stream):

@@ -42,7 +42,7 @@ cudaError_t launch_t(int bg, int kw, const CUtensorMap& map, const BwdTiledArgs&
 }  // namespace
 
 radon_status launch_backward_tiled(const radon_geometry* g, const void* sino, void* img, radon_dtype dt, int batch,
-                                   int images_per_cta, cudaStream_t s, std::string* why) {
+                                   int images_per_cta, const Epilogue& ep, cudaStream_t s, std::string* why) {
     const int esz = dt == RADON_F32 ? 4 : 2;
     const int align = 16 / esz;
     // samples per candidate window: the window spans 2 (|dx|+|dy|)/h^2 <= 2 sqrt(2) / h samples
@@ -109,6 +109,7 @@ radon_status launch_backward_tiled(const radon_geometry* g, const void* sino, vo
     a.D = g->D;
     a.B = batch;
     a.h = (float)g->h;
+    a.ep = ep;
     a.wd = wd;
     a.wdb = wdb;
     a.align = align;
@@ -165,7 +166,7 @@ int backward_packed_images_per_cta(int batch, const radon_launch_config* cfg) {
 }
 
 radon_status launch_backward_packed(const radon_geometry* g, const void* packed, void* img, radon_dtype dt, int batch,
-                                    int bg, cudaStream_t s, std::string* why) {
+                                    int bg, const Epilogue& ep, cudaStream_t s, std::string* why) {
     if (bg != 8 && bg != 16) {
         *why = "images_per_cta must be 8 or 16 for the packed adjoint";
         return RADON_ERR_UNSUPPORTED;
@@ -220,6 +221,7 @@ radon_status launch_backward_packed(const radon_geometry* g, const void* packed,
     a.D = g->D;
     a.B = batch;
     a.h = (float)g->h;
+    a.ep = ep;
     a.ih2 = (float)(1.0 / (g->h * g->h));
     a.wd = wd;
     a.wdb = wd;

@@ -21,6 +21,7 @@
 
 #include "device_error.cuh"
 #include "dtype.cuh"
+#include "epilogue.cuh"
 #include "radon_internal.h"
 #include "f32x2.cuh"
 #include "tma.cuh"
@@ -49,6 +50,7 @@ struct BwdTiledArgs {
     int tma_rank;      // 1: 1-D descriptor; 2: the same layout described with a unit outer dimension
     int out_dtype;     // packed variant: storage type of the output image (radon_dtype)
     float ih2;         // packed variant: 1 / h^2 (every ray's step has length h)
+    Epilogue ep;
 };
 
 __host__ __device__ inline int bwd_nq(int bg) { return (bg + 3) / 4; }
@@ -366,7 +368,10 @@ __global__ void __launch_bounds__(kBwdThreads, 2) backward_tiled_kernel(const __
         const long long p = (long long)(ti + pi) * a.n + (tj + pj);
 #pragma unroll
         for (int b = 0; b < BG; ++b)
-            if (b0 + b < a.B) out[(long long)(b0 + b) * npix + p] = from_f32<T>(a.h * acc[b]);
+            if (b0 + b < a.B) {
+                const long long idx = (long long)(b0 + b) * npix + p;
+                out[idx] = from_f32<T>(epilogue_value<T>(a.ep, a.h * acc[b], idx));
+            }
     }
 }
 
@@ -551,22 +556,10 @@ __global__ void __launch_bounds__(kBwdPackedThreads, 3) backward_packed_kernel(c
         const long long npix = (long long)a.n * a.n;
         const long long p = (long long)(ti + pi) * a.n + (tj + pj);
         const int b0 = blockIdx.y * BG;
-        if (a.out_dtype == RADON_F16) {
-            __half* out = reinterpret_cast<__half*>(a.img);
 #pragma unroll
-            for (int b = 0; b < BG; ++b)
-                if (b0 + b < a.B) out[(long long)(b0 + b) * npix + p] = __float2half_rn(a.h * accf[b]);
-        } else if (a.out_dtype == RADON_BF16) {
-            __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(a.img);
-#pragma unroll
-            for (int b = 0; b < BG; ++b)
-                if (b0 + b < a.B) out[(long long)(b0 + b) * npix + p] = __float2bfloat16_rn(a.h * accf[b]);
-        } else {
-            float* out = reinterpret_cast<float*>(a.img);
-#pragma unroll
-            for (int b = 0; b < BG; ++b)
-                if (b0 + b < a.B) out[(long long)(b0 + b) * npix + p] = a.h * accf[b];
-        }
+        for (int b = 0; b < BG; ++b)
+            if (b0 + b < a.B)
+                epilogue_store_rt(a.ep, a.out_dtype, a.img, a.h * accf[b], (long long)(b0 + b) * npix + p);
     }
 }
 

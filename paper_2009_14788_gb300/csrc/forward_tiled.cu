@@ -27,7 +27,8 @@ cudaError_t launch_t(const CUtensorMap& mv, const CUtensorMap& mh, const FwdTile
 }  // namespace
 
 radon_status launch_forward_tiled(radon_geometry* g, const void* img, void* sino, radon_dtype dt, int batch,
-                                  const radon_launch_config* cfg, cudaStream_t s, std::string* why) {
+                                  const radon_launch_config* cfg, const Epilogue& ep, cudaStream_t s,
+                                  std::string* why) {
     const int esz = dt == RADON_F32 ? 4 : 2;
     const int align = 16 / esz;
     const int BG = 16 / esz;
@@ -90,6 +91,7 @@ radon_status launch_forward_tiled(radon_geometry* g, const void* img, void* sino
     a.D = g->D;
     a.B = batch;
     a.h = (float)g->h;
+    a.ep = ep;
     a.G = G;
     a.Dt = Dt;
     a.n_dr = (g->D + Dt - 1) / Dt;
@@ -148,7 +150,8 @@ cudaError_t launch_packed_t(const CUtensorMap& mr, const CUtensorMap& mc, const 
 }  // namespace
 
 radon_status launch_forward_packed(radon_geometry* g, const void* packed, void* sino, radon_dtype dt, int batch,
-                                   const radon_launch_config* cfg, cudaStream_t s, std::string* why) {
+                                   const radon_launch_config* cfg, const Epilogue& ep, cudaStream_t s,
+                                   std::string* why) {
     const int esz = dt == RADON_F32 ? 4 : 2;
     const int BG = 16 / esz;
     if (((uintptr_t)packed & 15) != 0) {
@@ -207,6 +210,7 @@ radon_status launch_forward_packed(radon_geometry* g, const void* packed, void* 
     a.D = g->D;
     a.B = batch;
     a.h = (float)g->h;
+    a.ep = ep;
     a.G = G;
     a.Dt = Dt;
     a.n_dr = (g->D + Dt - 1) / Dt;

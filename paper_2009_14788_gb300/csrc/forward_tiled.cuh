@@ -22,6 +22,7 @@
 
 #include "device_error.cuh"
 #include "dtype.cuh"
+#include "epilogue.cuh"
 #include "radon_internal.h"
 #include "tma.cuh"
 
@@ -49,6 +50,7 @@ struct FwdTiledArgs {
     int stage_bytes;
     int* err;
     uint32_t spin_limit;
+    Epilogue ep;
 };
 
 __host__ __device__ inline size_t fwd_comp_bytes(int R, int wc) { return (size_t)(R + 2) * wc * 16; }
@@ -341,7 +343,10 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
         const long long o = (long long)(v0 + vl) * a.D + d;
 #pragma unroll
         for (int b = 0; b < BG; ++b)
-            if (b0 + b < a.B) out[(long long)(b0 + b) * vd + o] = from_f32<T>(a.h * acc[b]);
+            if (b0 + b < a.B) {
+                const long long idx = (long long)(b0 + b) * vd + o;
+                out[idx] = from_f32<T>(epilogue_value<T>(a.ep, a.h * acc[b], idx));
+            }
     }
 }
 

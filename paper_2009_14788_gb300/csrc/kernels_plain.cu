@@ -5,6 +5,7 @@
 #include <cmath>
 
 #include "dtype.cuh"
+#include "epilogue.cuh"
 #include "radon_internal.h"
 
 namespace radon {
@@ -20,7 +21,7 @@ constexpr int kChunk = 32;
 template <typename T>
 __global__ void forward_plain_kernel(const T* __restrict__ img, T* __restrict__ sino, const RayT* __restrict__ rays,
                                      const int* __restrict__ nks, int n, int64_t rays_per_image, int64_t total,
-                                     float h) {
+                                     float h, const Epilogue ep) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
     const int64_t b = idx / rays_per_image;
@@ -54,7 +55,7 @@ __global__ void forward_plain_kernel(const T* __restrict__ img, T* __restrict__ 
             acc += (1.0f - c) * ((1.0f - a) * v00 + a * v01) + c * ((1.0f - a) * v10 + a * v11);
         }
     }
-    sino[idx] = from_f32<T>(h * acc);
+    sino[idx] = from_f32<T>(epilogue_value<T>(ep, h * acc, idx));
 }
 
 __device__ __forceinline__ float det_coord(const ViewF& vf, float x, float y) {
@@ -70,7 +71,7 @@ __device__ __forceinline__ float det_coord(const ViewF& vf, float x, float y) {
 template <typename T>
 __global__ void backward_plain_kernel(const T* __restrict__ sino, T* __restrict__ img, const RayT* __restrict__ rays,
                                       const int* __restrict__ nks, const ViewF* __restrict__ views, int n, int V,
-                                      int D, int64_t total, float h) {
+                                      int D, int64_t total, float h, const Epilogue ep) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
     const int64_t npix = (int64_t)n * n;
@@ -120,52 +121,53 @@ __global__ void backward_plain_kernel(const T* __restrict__ sino, T* __restrict_
             if (w != 0.0f) acc = fmaf(w, load_f32(y + r), acc);
         }
     }
-    img[idx] = from_f32<T>(h * acc);
+    img[idx] = from_f32<T>(epilogue_value<T>(ep, h * acc, idx));
 }
 
 template <typename T>
 cudaError_t forward_plain_t(const radon_geometry* g, const void* img, void* sino, int batch, int threads,
-                            cudaStream_t s) {
+                            const Epilogue& ep, cudaStream_t s) {
     const int64_t rays = (int64_t)g->V * g->D;
     const int64_t total = rays * batch;
     if (total == 0) return cudaSuccess;
     const int64_t blocks = (total + threads - 1) / threads;
     forward_plain_kernel<T><<<(unsigned)blocks, threads, 0, s>>>((const T*)img, (T*)sino, g->d_ray, g->d_nk, g->n,
-                                                                 rays, total, (float)g->h);
+                                                                 rays, total, (float)g->h, ep);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t backward_plain_t(const radon_geometry* g, const void* sino, void* img, int batch, int threads,
-                             cudaStream_t s) {
+                             const Epilogue& ep, cudaStream_t s) {
     const int64_t total = (int64_t)g->n * g->n * batch;
     if (total == 0) return cudaSuccess;
     const int64_t blocks = (total + threads - 1) / threads;
     backward_plain_kernel<T><<<(unsigned)blocks, threads, 0, s>>>((const T*)sino, (T*)img, g->d_ray, g->d_nk,
-                                                                  g->d_view, g->n, g->V, g->D, total, (float)g->h);
+                                                                  g->d_view, g->n, g->V, g->D, total, (float)g->h,
+                                                                  ep);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_forward_plain(const radon_geometry* g, const void* img, void* sino, radon_dtype dt, int batch,
-                                 int threads, cudaStream_t s) {
+                                 int threads, const Epilogue& ep, cudaStream_t s) {
     if (threads <= 0) threads = 256;
     switch (dt) {
-        case RADON_F32: return forward_plain_t<float>(g, img, sino, batch, threads, s);
-        case RADON_F16: return forward_plain_t<__half>(g, img, sino, batch, threads, s);
-        case RADON_BF16: return forward_plain_t<__nv_bfloat16>(g, img, sino, batch, threads, s);
+        case RADON_F32: return forward_plain_t<float>(g, img, sino, batch, threads, ep, s);
+        case RADON_F16: return forward_plain_t<__half>(g, img, sino, batch, threads, ep, s);
+        case RADON_BF16: return forward_plain_t<__nv_bfloat16>(g, img, sino, batch, threads, ep, s);
     }
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_backward_plain(const radon_geometry* g, const void* sino, void* img, radon_dtype dt, int batch,
-                                  int threads, cudaStream_t s) {
+                                  int threads, const Epilogue& ep, cudaStream_t s) {
     if (threads <= 0) threads = 256;
     switch (dt) {
-        case RADON_F32: return backward_plain_t<float>(g, sino, img, batch, threads, s);
-        case RADON_F16: return backward_plain_t<__half>(g, sino, img, batch, threads, s);
-        case RADON_BF16: return backward_plain_t<__nv_bfloat16>(g, sino, img, batch, threads, s);
+        case RADON_F32: return backward_plain_t<float>(g, sino, img, batch, threads, ep, s);
+        case RADON_F16: return backward_plain_t<__half>(g, sino, img, batch, threads, ep, s);
+        case RADON_BF16: return backward_plain_t<__nv_bfloat16>(g, sino, img, batch, threads, ep, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -2,6 +2,7 @@
 // kernel dispatch and error reporting.  Every argument check runs on the host before any CUDA
 // call, so a bad request never reaches the GPU.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -14,7 +15,10 @@ namespace radon {
 
 namespace {
 thread_local std::string g_last_error;
-}
+std::atomic<uint64_t> g_launches{0};
+}  // namespace
+
+void count_launches(int kernels) { g_launches.fetch_add((uint64_t)kernels, std::memory_order_relaxed); }
 
 const char* set_error(const std::string& msg) {
     g_last_error = msg;
@@ -177,11 +181,31 @@ radon_status create_common(int n, const double* angles, int n_angles, int det_co
     return RADON_OK;
 }
 
-radon_status dispatch(const radon_geometry* g, const void* in, void* out, radon_dtype dt, int batch,
-                      const radon_launch_config* cfg, void* stream, bool forward, void* ws = nullptr,
-                      size_t ws_bytes = 0) {
+namespace {
+
+radon_status validate_epilogue(const radon_epilogue* e, radon_dtype dt) {
+    if (e == nullptr) return RADON_OK;
+    const size_t esz = dt == RADON_F32 ? 4 : 2;
+    if (e->add != nullptr && ((uintptr_t)e->add % esz) != 0)
+        return fail(RADON_ERR_INVALID_ARG, "epilogue addend is not aligned to its element size");
+    if (e->op_scale_dev != nullptr && ((uintptr_t)e->op_scale_dev % 4) != 0)
+        return fail(RADON_ERR_INVALID_ARG, "epilogue op_scale_dev is not 4-byte aligned");
+    if (!std::isfinite(e->op_scale) || !std::isfinite(e->add_scale))
+        return fail(RADON_ERR_INVALID_ARG, "epilogue scales must be finite");
+    return RADON_OK;
+}
+
+}  // namespace
+
+radon_status project(const radon_geometry* g, const void* in, void* out, radon_dtype dt, int batch,
+                     const radon_launch_config* cfg, void* stream, bool forward, void* ws, size_t ws_bytes,
+                     const radon_epilogue* epi) {
     radon_status st = validate_call(g, in, out, dt, batch);
     if (st != RADON_OK) return st;
+    st = validate_epilogue(epi, dt);
+    if (st != RADON_OK) return st;
+    const Epilogue ep = epi ? Epilogue{epi->op_scale, epi->op_scale_dev, epi->add_scale, epi->add}
+                            : identity_epilogue();
     const int algo = cfg ? cfg->algo : RADON_ALGO_AUTO;
     if (algo != RADON_ALGO_AUTO && algo != RADON_ALGO_PLAIN && algo != RADON_ALGO_TILED)
         return fail(RADON_ERR_INVALID_ARG, "unknown algo");
@@ -202,15 +226,22 @@ radon_status dispatch(const radon_geometry* g, const void* in, void* out, radon_
             cudaError_t e = launch_pack_sino(in, ws, g->V, g->D, batch, bg, dt, s);
             if (e != cudaSuccess) return cuda_fail(e, "sinogram pack launch");
             std::string why;
-            st = launch_backward_packed(g, ws, out, dt, batch, bg, s, &why);
-            if (st == RADON_OK) return RADON_OK;
+            count_launches(1);
+            st = launch_backward_packed(g, ws, out, dt, batch, bg, ep, s, &why);
+            if (st == RADON_OK) {
+                count_launches(1);
+                return RADON_OK;
+            }
             if (st != RADON_ERR_UNSUPPORTED) return fail(st, why);
         }
     }
     if (!forward && algo != RADON_ALGO_PLAIN) {
         std::string why;
-        st = launch_backward_tiled(g, in, out, dt, batch, images, s, &why);
-        if (st == RADON_OK) return RADON_OK;
+        st = launch_backward_tiled(g, in, out, dt, batch, images, ep, s, &why);
+        if (st == RADON_OK) {
+            count_launches(1);
+            return RADON_OK;
+        }
         if (st != RADON_ERR_UNSUPPORTED || algo == RADON_ALGO_TILED) return fail(st, why);
         // AUTO: this geometry / buffer does not fit the tiled kernel; the plain kernel serves it
     }
@@ -226,10 +257,14 @@ radon_status dispatch(const radon_geometry* g, const void* in, void* out, radon_
             if (!packed_done) {
                 cudaError_t e = launch_pack_images(in, ws, g->n, batch, dt, s);
                 if (e != cudaSuccess) return cuda_fail(e, "pack launch");
+                count_launches(1);
                 packed_done = true;
             }
-            st = launch_forward_packed(const_cast<radon_geometry*>(g), ws, out, dt, batch, &c, s, &why);
-            if (st == RADON_OK) return RADON_OK;
+            st = launch_forward_packed(const_cast<radon_geometry*>(g), ws, out, dt, batch, &c, ep, s, &why);
+            if (st == RADON_OK) {
+                count_launches(1);
+                return RADON_OK;
+            }
             if (st != RADON_ERR_UNSUPPORTED) return fail(st, why);
         }
         // no packed shape fits: continue with the paths that need no workspace
@@ -244,8 +279,11 @@ radon_status dispatch(const radon_geometry* g, const void* in, void* out, radon_
         for (int i = 0; i < (fixed ? 1 : 4); ++i) {
             radon_launch_config c = {RADON_ALGO_TILED, fixed ? cfg->views_per_cta : kViews[i],
                                      cfg ? cfg->rows_per_slab : 0, 0, 0, 0};
-            st = launch_forward_tiled(const_cast<radon_geometry*>(g), in, out, dt, batch, &c, s, &why);
-            if (st == RADON_OK) return RADON_OK;
+            st = launch_forward_tiled(const_cast<radon_geometry*>(g), in, out, dt, batch, &c, ep, s, &why);
+            if (st == RADON_OK) {
+                count_launches(1);
+                return RADON_OK;
+            }
             if (st != RADON_ERR_UNSUPPORTED) return fail(st, why);
         }
         if (algo == RADON_ALGO_TILED) return fail(st, why);
@@ -253,11 +291,12 @@ radon_status dispatch(const radon_geometry* g, const void* in, void* out, radon_
     }
     cudaError_t e;
     if (forward) {
-        e = launch_forward_plain(g, in, out, dt, batch, threads, s);
+        e = launch_forward_plain(g, in, out, dt, batch, threads, ep, s);
     } else {
-        e = launch_backward_plain(g, in, out, dt, batch, threads, s);
+        e = launch_backward_plain(g, in, out, dt, batch, threads, ep, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, forward ? "forward launch" : "backward launch");
+    count_launches(1);
     return RADON_OK;
 }
 
@@ -336,22 +375,22 @@ int64_t radon_geometry_sample_count(const radon_geometry* g) {
 
 radon_status radon_forward(const radon_geometry* g, const void* img, void* sino, radon_dtype dtype, int batch,
                            void* stream) {
-    return dispatch(g, img, sino, dtype, batch, nullptr, stream, true);
+    return project(g, img, sino, dtype, batch, nullptr, stream, true, nullptr, 0, nullptr);
 }
 
 radon_status radon_backward(const radon_geometry* g, const void* sino, void* img, radon_dtype dtype, int batch,
                             void* stream) {
-    return dispatch(g, sino, img, dtype, batch, nullptr, stream, false);
+    return project(g, sino, img, dtype, batch, nullptr, stream, false, nullptr, 0, nullptr);
 }
 
 radon_status radon_forward_ex(const radon_geometry* g, const void* img, void* sino, radon_dtype dtype, int batch,
                               const radon_launch_config* config, void* stream) {
-    return dispatch(g, img, sino, dtype, batch, config, stream, true);
+    return project(g, img, sino, dtype, batch, config, stream, true, nullptr, 0, nullptr);
 }
 
 radon_status radon_backward_ex(const radon_geometry* g, const void* sino, void* img, radon_dtype dtype, int batch,
                                const radon_launch_config* config, void* stream) {
-    return dispatch(g, sino, img, dtype, batch, config, stream, false);
+    return project(g, sino, img, dtype, batch, config, stream, false, nullptr, 0, nullptr);
 }
 
 size_t radon_forward_workspace_size(const radon_geometry* g, radon_dtype dtype, int batch) {
@@ -366,7 +405,7 @@ radon_status radon_forward_ws(const radon_geometry* g, const void* img, void* si
                               void* stream) {
     if (workspace != nullptr && ((uintptr_t)workspace & 15) != 0)
         return fail(RADON_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
-    return dispatch(g, img, sino, dtype, batch, config, stream, true, workspace, workspace_bytes);
+    return project(g, img, sino, dtype, batch, config, stream, true, workspace, workspace_bytes, nullptr);
 }
 
 size_t radon_backward_workspace_size(const radon_geometry* g, radon_dtype dtype, int batch) {
@@ -381,8 +420,26 @@ radon_status radon_backward_ws(const radon_geometry* g, const void* sino, void* 
                                void* stream) {
     if (workspace != nullptr && ((uintptr_t)workspace & 15) != 0)
         return fail(RADON_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
-    return dispatch(g, sino, img, dtype, batch, config, stream, false, workspace, workspace_bytes);
+    return project(g, sino, img, dtype, batch, config, stream, false, workspace, workspace_bytes, nullptr);
 }
+
+radon_status radon_forward_fused(const radon_geometry* g, const void* img, void* sino, radon_dtype dtype, int batch,
+                                 const radon_epilogue* epilogue, const radon_launch_config* config, void* workspace,
+                                 size_t workspace_bytes, void* stream) {
+    if (workspace != nullptr && ((uintptr_t)workspace & 15) != 0)
+        return fail(RADON_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
+    return project(g, img, sino, dtype, batch, config, stream, true, workspace, workspace_bytes, epilogue);
+}
+
+radon_status radon_backward_fused(const radon_geometry* g, const void* sino, void* img, radon_dtype dtype, int batch,
+                                  const radon_epilogue* epilogue, const radon_launch_config* config, void* workspace,
+                                  size_t workspace_bytes, void* stream) {
+    if (workspace != nullptr && ((uintptr_t)workspace & 15) != 0)
+        return fail(RADON_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
+    return project(g, sino, img, dtype, batch, config, stream, false, workspace, workspace_bytes, epilogue);
+}
+
+uint64_t radon_kernel_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 radon_status radon_get_device_error(void* stream) {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);

@@ -40,6 +40,21 @@ struct ViewF {
     int pad;
 };
 
+// Output epilogue applied by every projector kernel at its store:
+//     out[i] = op_scale * s * P[i] + add_scale * add[i]
+// with P the projection (already multiplied by the step h), s = *op_scale_dev when that pointer
+// is set (a device scalar, e.g. a step length that stays on the device), and add an optional
+// addend in the output's dtype and layout (it may be the output buffer itself).  The identity
+// {1, NULL, 0, NULL} leaves P unchanged bit for bit.
+struct Epilogue {
+    float op_scale;
+    const float* op_scale_dev;
+    float add_scale;
+    const void* add;
+};
+
+inline Epilogue identity_epilogue() { return Epilogue{1.0f, nullptr, 0.0f, nullptr}; }
+
 struct Int2 {
     int x, y;
 };
@@ -76,6 +91,11 @@ radon_status fail(radon_status st, const std::string& msg);
 radon_status cuda_fail(cudaError_t e, const char* what);
 radon_status validate_call(const radon_geometry* g, const void* in, const void* out, radon_dtype dt, int batch);
 radon_status check_device(const radon_geometry* g);
+// The projection dispatcher behind every entry point: packed (with a workspace), tiled, then plain
+// kernels, in that order of preference; `epi` NULL = identity epilogue.
+radon_status project(const radon_geometry* g, const void* in, void* out, radon_dtype dt, int batch,
+                     const radon_launch_config* cfg, void* stream, bool forward, void* ws, size_t ws_bytes,
+                     const radon_epilogue* epi);
 
 // geometry.cpp
 radon_status build_geometry(radon_geometry* g);  // fills host tables and sample count
@@ -86,21 +106,23 @@ const char* set_error(const std::string& msg);   // thread-local message, return
 
 // kernels_plain.cu
 cudaError_t launch_forward_plain(const radon_geometry* g, const void* img, void* sino, radon_dtype dt, int batch,
-                                 int threads, cudaStream_t s);
+                                 int threads, const Epilogue& ep, cudaStream_t s);
 cudaError_t launch_backward_plain(const radon_geometry* g, const void* sino, void* img, radon_dtype dt, int batch,
-                                  int threads, cudaStream_t s);
+                                  int threads, const Epilogue& ep, cudaStream_t s);
 
 // backward_tiled.cu: RADON_ERR_UNSUPPORTED if the geometry / buffers do not fit the tiled kernel
 radon_status launch_backward_tiled(const radon_geometry* g, const void* sino, void* img, radon_dtype dt, int batch,
-                                   int images_per_cta, cudaStream_t s, std::string* why);
+                                   int images_per_cta, const Epilogue& ep, cudaStream_t s, std::string* why);
 
 // forward_tiled.cu: RADON_ERR_UNSUPPORTED if the geometry / buffers do not fit the tiled kernel
 radon_status launch_forward_tiled(radon_geometry* g, const void* img, void* sino, radon_dtype dt, int batch,
-                                  const radon_launch_config* cfg, cudaStream_t s, std::string* why);
+                                  const radon_launch_config* cfg, const Epilogue& ep, cudaStream_t s,
+                                  std::string* why);
 
 // forward_tiled.cu: the packed-input forward (the workspace already holds pack_images' output)
 radon_status launch_forward_packed(radon_geometry* g, const void* packed, void* sino, radon_dtype dt, int batch,
-                                   const radon_launch_config* cfg, cudaStream_t s, std::string* why);
+                                   const radon_launch_config* cfg, const Epilogue& ep, cudaStream_t s,
+                                   std::string* why);
 
 // pack.cu
 size_t packed_image_bytes(int n, int batch, radon_dtype dt);
@@ -112,7 +134,10 @@ cudaError_t launch_pack_sino(const void* sino, void* workspace, int V, int D, in
 // backward_tiled.cu: the packed-sinogram adjoint (the workspace already holds pack_sino's output)
 int backward_packed_images_per_cta(int batch, const radon_launch_config* cfg);
 radon_status launch_backward_packed(const radon_geometry* g, const void* packed, void* img, radon_dtype dt, int batch,
-                                    int images_per_cta, cudaStream_t s, std::string* why);
+                                    int images_per_cta, const Epilogue& ep, cudaStream_t s, std::string* why);
+
+// radon_api.cpp: process-wide count of kernels the library has launched (radon_kernel_launch_count)
+void count_launches(int kernels);
 
 // kernels_common.cu
 cudaError_t read_and_clear_device_error(int* out);

@@ -206,6 +206,120 @@ def backward_raw(geom: Geometry, y: torch.Tensor, config=None, out=None, workspa
     return x
 
 
+def _epilogue(op_scale, op_scale_dev, add_scale, add, like: torch.Tensor):
+    if op_scale_dev is not None:
+        if op_scale_dev.dtype != torch.float32 or op_scale_dev.device != like.device or op_scale_dev.numel() != 1:
+            raise ValueError("op_scale_dev must be one float32 element on %s" % like.device)
+    if add is not None:
+        if add.dtype != like.dtype or add.device != like.device or not add.is_contiguous():
+            raise ValueError("add must be a contiguous %s tensor on %s" % (like.dtype, like.device))
+    return L.radon_epilogue(float(op_scale), op_scale_dev.data_ptr() if op_scale_dev is not None else None,
+                            float(add_scale), add.data_ptr() if add is not None else None)
+
+
+def forward_fused(geom: Geometry, x: torch.Tensor, op_scale=1.0, op_scale_dev=None, add=None, add_scale=0.0,
+                  out=None, config=None, workspace="auto") -> torch.Tensor:
+    """out = op_scale * s * (A x) + add_scale * add, s = op_scale_dev[0] (``radon_forward_fused``).
+
+    ``add`` (the sinogram's shape and dtype) may be ``out`` itself; the sum is rounded once.
+    """
+    _check_tensor(x, "image", geom)
+    x = x.contiguous()
+    batch = x.numel() // (geom.n * geom.n)
+    shape = tuple(x.shape[:-2]) + geom.sino_shape
+    y = torch.empty(shape, dtype=x.dtype, device=x.device) if out is None else _check_out(out, x, shape)
+    if add is not None and tuple(add.shape) != shape:
+        raise ValueError("add must have shape %s" % (shape,))
+    ep = _epilogue(op_scale, op_scale_dev, add_scale, add, y)
+    ws = _workspace(workspace, forward_workspace_bytes(geom, x.dtype, batch) if batch > 0 else 0, x.device)
+    stream = torch.cuda.current_stream(x.device).cuda_stream
+    with torch.cuda.device(x.device):
+        st = L.radon_forward_fused(geom.handle, x.data_ptr(), y.data_ptr(), _DTYPES[x.dtype], batch, ctypes.byref(ep),
+                                   ctypes.byref(config) if config is not None else None,
+                                   ws.data_ptr() if ws is not None else None,
+                                   ws.numel() if ws is not None else 0, stream)
+    L.check(st, "radon_forward_fused")
+    return y
+
+
+def backward_fused(geom: Geometry, y: torch.Tensor, op_scale=1.0, op_scale_dev=None, add=None, add_scale=0.0,
+                   out=None, config=None, workspace="auto") -> torch.Tensor:
+    """out = op_scale * s * (A^T y) + add_scale * add, s = op_scale_dev[0] (``radon_backward_fused``)."""
+    _check_tensor(y, "sinogram", geom)
+    if tuple(y.shape[-2:]) != geom.sino_shape:
+        raise ValueError("sinogram must end in %s, got %s" % (geom.sino_shape, tuple(y.shape)))
+    y = y.contiguous()
+    batch = y.numel() // (geom.n_angles * geom.det_count)
+    shape = tuple(y.shape[:-2]) + (geom.n, geom.n)
+    x = torch.empty(shape, dtype=y.dtype, device=y.device) if out is None else _check_out(out, y, shape)
+    if add is not None and tuple(add.shape) != shape:
+        raise ValueError("add must have shape %s" % (shape,))
+    ep = _epilogue(op_scale, op_scale_dev, add_scale, add, x)
+    ws = _workspace(workspace, backward_workspace_bytes(geom, y.dtype, batch) if batch > 0 else 0, y.device)
+    stream = torch.cuda.current_stream(y.device).cuda_stream
+    with torch.cuda.device(y.device):
+        st = L.radon_backward_fused(geom.handle, y.data_ptr(), x.data_ptr(), _DTYPES[y.dtype], batch, ctypes.byref(ep),
+                                    ctypes.byref(config) if config is not None else None,
+                                    ws.data_ptr() if ws is not None else None,
+                                    ws.numel() if ws is not None else 0, stream)
+    L.check(st, "radon_backward_fused")
+    return x
+
+
+def dot(a: torch.Tensor, b: torch.Tensor, result=None, scale=1.0, accumulate=False, workspace=None) -> torch.Tensor:
+    """result = scale * <a, b> (+ result if ``accumulate``) as one device float32 (``radon_dot``)."""
+    if a.dtype != b.dtype or a.numel() != b.numel() or a.device != b.device:
+        raise ValueError("a and b must have the same dtype, size and device")
+    if a.dtype not in _DTYPES:
+        raise ValueError("unsupported dtype %s" % a.dtype)
+    a, b = a.contiguous(), b.contiguous()
+    if result is None:
+        result = torch.empty(1, dtype=torch.float32, device=a.device)
+    need = int(L.radon_dot_workspace_size())
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=a.device)
+    stream = torch.cuda.current_stream(a.device).cuda_stream
+    with torch.cuda.device(a.device):
+        st = L.radon_dot(a.data_ptr(), b.data_ptr(), _DTYPES[a.dtype], a.numel(), float(scale), result.data_ptr(),
+                         1 if accumulate else 0, workspace.data_ptr(), workspace.numel(), stream)
+    L.check(st, "radon_dot")
+    return result
+
+
+def axpby(x: torch.Tensor, y: torch.Tensor, alpha=1.0, alpha_dev=None, beta=0.0) -> torch.Tensor:
+    """y = alpha * s * x + beta * y in place (s = alpha_dev[0]); x and y may differ in dtype (``radon_axpby``)."""
+    if x.numel() != y.numel() or x.device != y.device or not x.is_contiguous() or not y.is_contiguous():
+        raise ValueError("x and y must be contiguous tensors of the same size on one device")
+    if alpha_dev is not None and (alpha_dev.dtype != torch.float32 or alpha_dev.device != x.device):
+        raise ValueError("alpha_dev must be a float32 tensor on %s" % x.device)
+    stream = torch.cuda.current_stream(x.device).cuda_stream
+    with torch.cuda.device(x.device):
+        st = L.radon_axpby(x.data_ptr(), _DTYPES[x.dtype], y.data_ptr(), _DTYPES[y.dtype], x.numel(), float(alpha),
+                           alpha_dev.data_ptr() if alpha_dev is not None else None, float(beta), stream)
+    L.check(st, "radon_axpby")
+    return y
+
+
+def power_iteration(geom: Geometry, v0: torch.Tensor, iterations: int = 20):
+    """(lambda, alpha = 1 / lambda) of A^T A by the power method from ``v0`` (``radon_power_iteration``).
+
+    Both are one-element float32 device tensors; nothing is synchronised.
+    """
+    if v0.dtype != torch.float32 or v0.numel() != geom.n * geom.n or not v0.is_cuda:
+        raise ValueError("v0 must be one float32 %dx%d image on the GPU" % (geom.n, geom.n))
+    v0 = v0.contiguous()
+    lam = torch.empty(1, dtype=torch.float32, device=v0.device)
+    alpha = torch.empty(1, dtype=torch.float32, device=v0.device)
+    need = int(L.radon_power_iteration_workspace_size(geom.handle))
+    ws = torch.empty(need, dtype=torch.uint8, device=v0.device)
+    stream = torch.cuda.current_stream(v0.device).cuda_stream
+    with torch.cuda.device(v0.device):
+        st = L.radon_power_iteration(geom.handle, v0.data_ptr(), int(iterations), lam.data_ptr(), alpha.data_ptr(),
+                                     ws.data_ptr(), need, stream)
+    L.check(st, "radon_power_iteration")
+    return lam, alpha
+
+
 class RadonForwardFunction(torch.autograd.Function):
     """y = A x; dL/dx = A^T dL/dy (the adjoint kernel)."""
 

@@ -14,4 +14,4 @@ from .phantoms import (  # noqa: F401
     uniform_angles,
 )
 from .workloads import (  # noqa: F401
-    WORKLOADS, Workload, uneven_items, workload_geometry_args, workload_images, workload_noise)
+    WORKLOADS, Workload, power_start, uneven_items, workload_geometry_args, workload_images, workload_noise)

@@ -98,3 +98,8 @@ def workload_images(w: Workload, indices=None) -> list[np.ndarray] | np.ndarray:
 def workload_noise(w: Workload, shape) -> np.ndarray:
     sigma = w.extra.get("noise_sigma", 0.0)
     return np.random.default_rng(2000 * w.number).normal(0.0, sigma, size=shape)
+
+
+def power_start(n: int, seed: int) -> np.ndarray:
+    """The power method's start vector: N(0, 1) pixels from ``numpy.random.default_rng(seed)``."""
+    return np.random.default_rng(seed).standard_normal((n, n))

@@ -124,6 +124,51 @@ def test_launch_argument_checks_without_gpu():
     L.radon_geometry_destroy(None)
 
 
+def test_iterative_entry_points_reject_bad_arguments_without_gpu():
+    st, h = _create()
+    assert st == L.RADON_OK
+    buf = (ctypes.c_double * 64)()
+    p = ctypes.addressof(buf)
+    ws_bytes = int(L.radon_dot_workspace_size())
+    assert ws_bytes >= 8
+    # radon_dot: dtype, count, result pointer, alignment, workspace, non-finite scale
+    assert L.radon_dot(p, p, 7, 4, 1.0, p, 0, p, ws_bytes, None) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_dot(p, p, 0, -1, 1.0, p, 0, p, ws_bytes, None) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_dot(p, p, 0, 4, 1.0, None, 0, p, ws_bytes, None) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_dot(p + 2, p, 0, 4, 1.0, p, 0, p, ws_bytes, None) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_dot(None, p, 0, 4, 1.0, p, 0, p, ws_bytes, None) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_dot(p, p, 0, 4, 1.0, p, 0, p, ws_bytes - 8, None) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_dot(p, p, 0, 4, 1.0, p, 0, p + 4, ws_bytes, None) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_dot(p, p, 0, 4, float("inf"), p, 0, p, ws_bytes, None) == L.RADON_ERR_INVALID_ARG
+    # radon_axpby: dtypes, count, NULL operands, alignment, scalars
+    assert L.radon_axpby(p, 0, p, 9, 4, 1.0, None, 0.0, None) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_axpby(p, 0, p, 0, -2, 1.0, None, 0.0, None) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_axpby(None, 0, p, 0, 4, 1.0, None, 0.0, None) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_axpby(p + 1, 1, p, 0, 4, 1.0, None, 0.0, None) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_axpby(p, 0, p, 0, 4, 1.0, p + 2, 0.0, None) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_axpby(p, 0, p, 0, 4, float("nan"), None, 0.0, None) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_axpby(p, 0, p, 0, 0, 1.0, None, 0.0, None) == L.RADON_OK             # nothing to do
+    # radon_power_iteration: host-only geometry, pointers, iterations, workspace
+    need = int(L.radon_power_iteration_workspace_size(h))
+    assert need > 0 and int(L.radon_power_iteration_workspace_size(None)) == 0
+    assert L.radon_power_iteration(h, p, 20, p, None, p, need, None) == L.RADON_ERR_INVALID_ARG
+    assert "host-only" in L.radon_last_error_message()
+    assert L.radon_power_iteration(None, p, 20, p, None, p, need, None) == L.RADON_ERR_INVALID_ARG
+    # radon_forward_fused / radon_backward_fused: misaligned addend or scalar, non-finite scales
+    ep = L.radon_epilogue(1.0, None, -1.0, p + 1)
+    assert L.radon_forward_fused(h, p, p + 64, 0, 1, ctypes.byref(ep), None, None, 0, None) == L.RADON_ERR_INVALID_ARG
+    ep = L.radon_epilogue(1.0, p + 2, 0.0, None)
+    assert L.radon_backward_fused(h, p, p + 64, 0, 1, ctypes.byref(ep), None, None, 0, None) == \
+        L.RADON_ERR_INVALID_ARG
+    ep = L.radon_epilogue(float("inf"), None, 0.0, None)
+    assert L.radon_forward_fused(h, p, p + 64, 0, 1, ctypes.byref(ep), None, None, 0, None) == L.RADON_ERR_INVALID_ARG
+    assert "finite" in L.radon_last_error_message()
+    ep = L.radon_epilogue(1.0, None, 0.0, None)
+    assert L.radon_forward_fused(h, p, p + 64, 0, 1, ctypes.byref(ep), None, p + 8, 0, None) == \
+        L.RADON_ERR_INVALID_ARG                                                           # workspace alignment
+    L.radon_geometry_destroy(h)
+
+
 def test_defaults_follow_the_paper():
     g = Geometry("parallel", 40, uniform_angles(5, math.pi), host_only=True)
     assert (g.det_count, g.det_spacing, g.step) == (40, 1.0, 1.0)
