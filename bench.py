@@ -136,6 +136,9 @@ def run_ours(args):
     from paper_2009_14788_gb300.build import build
 
     world, rank, local = _dist()
+    if WORKLOADS[args.workload].kind not in ("parallel", "fan"):
+        raise SystemExit("the timed step takes a parallel or fan workload; %s is measured in the secondary "
+                         "section of the default run" % args.workload)
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -345,6 +348,9 @@ def run_secondary(args):
       gradients w.r.t. y and alpha (per-iteration checkpoints: 3 projections per iteration).
     * The paper's batch benchmark shape (32 x 512^2 parallel, 512 views in [0, pi), 512
       detectors): forward + adjoint, chosen 16-bit form against the plain FP32 form.
+    * The uneven batch (64 images, 16 each of 128^2 .. 1024^2, each with its own parallel geometry,
+      fp16): one forward plan and one adjoint plan (autotuned at creation) replayed as one CUDA
+      graph, against one library call per image and direction.
     """
     import torch
 
@@ -431,6 +437,60 @@ def run_secondary(args):
         del x, yb, oy, ox
     res["speedup_chosen_vs_plain_f32"] = res["plain_f32"]["ms_per_step"] / res["chosen_f16"]["ms_per_step"]
     out["paper_batch"] = res
+    del xs
+    # the uneven batch: 64 images of 128^2..1024^2, each with its own geometry, in one persistent
+    # launch per direction, both captured in one CUDA graph; against one library call per image
+    from paper_2009_14788_gb300 import BatchPlan
+    from synth import uneven_items
+    w = WORKLOADS["uneven_b64_n128-1024"]
+    items = uneven_items(w)
+    geoms = []
+    for k in range(len(items)):
+        a = workload_geometry_args(w, k)
+        kind = a.pop("kind")
+        geoms.append(Geometry(kind, **a))
+    S_tot = sum(g.sample_count for g in geoms)
+    imgs = workload_images(w)
+    xs16 = [torch.from_numpy(x[None]).to("cuda", torch.float16) for x in imgs]
+    ys16 = [forward_raw(g, x.float()).to(torch.float16) for g, x in zip(geoms, xs16)]
+    oy = [torch.empty_like(y) for y in ys16]
+    ox = [torch.empty_like(x) for x in xs16]
+    t0 = time.perf_counter()
+    pf = BatchPlan(list(zip(geoms, xs16, oy)), "forward")
+    pa = BatchPlan(list(zip(geoms, ys16, ox)), "adjoint")
+    t_plan = time.perf_counter() - t0
+    cs = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(cs):
+        pf.launch()
+        pa.launch()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=cs):
+            pf.launch()
+            pa.launch()
+    ms_graph = time_it(graph.replay, 5)
+    ms_fwd = time_it(pf.launch, 5)
+    ms_adj = time_it(pa.launch, 5)
+
+    def per_item():
+        for g, x, y, a_, b_ in zip(geoms, xs16, ys16, oy, ox):
+            forward_raw(g, x, out=a_)
+            backward_raw(g, y, out=b_)
+    ms_loop = time_it(per_item, 3, warm=1)
+    cfg_f = sorted({(items[k]["n"], pf.item_config(k)) for k in range(len(items))})
+    cfg_a = sorted({(items[k]["n"], pa.item_config(k)) for k in range(len(items))})
+    out["uneven"] = {
+        "workload": w.name, "storage": "f16", "images": len(items), "samples_per_pass": S_tot,
+        "ms_graph_fwd_adj": ms_graph, "ms_plan_fwd": ms_fwd, "ms_plan_adj": ms_adj,
+        "samples_per_s": 2 * S_tot / (ms_graph * 1e-3), "images_per_s": len(items) / (ms_graph * 1e-3),
+        "per_image_calls_ms": ms_loop, "speedup_vs_per_image_calls": ms_loop / ms_graph,
+        "plan_create_s": t_plan, "autotuned_forward_views_by_size": cfg_f,
+        "autotuned_adjoint_views_by_size": cfg_a, "work_items": [pf.info["work_items"], pa.info["work_items"]],
+        "ctas": [pf.info["ctas"], pa.info["ctas"]],
+        "l2": "flushed (2x L2 write) before each timed launch",
+    }
+    pf.close()
+    pa.close()
     del flush
     torch.cuda.empty_cache()
     return out
@@ -445,10 +505,31 @@ def run_profile(args):
 
     build()
     w = WORKLOADS[args.workload]
+    dt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[args.storage]
+    if w.kind == "uneven":
+        # the uneven batch: one forward plan and one adjoint plan (default tile shapes, no autotuning)
+        from paper_2009_14788_gb300 import BatchPlan
+        from synth import uneven_items
+        geoms = []
+        for k in range(len(uneven_items(w))):
+            a = workload_geometry_args(w, k)
+            kd = a.pop("kind")
+            geoms.append(Geometry(kd, **a))
+        xs = [torch.from_numpy(x[None]).to("cuda", dt) for x in workload_images(w)]
+        ys = [torch.zeros((1,) + g.sino_shape, dtype=dt, device="cuda") for g in geoms]
+        ox = [torch.empty_like(x) for x in xs]
+        pf = BatchPlan(list(zip(geoms, xs, ys)), "forward", autotune=False)
+        pa = BatchPlan(list(zip(geoms, ys, ox)), "adjoint", autotune=False)
+        for _ in range(1 + args.warmup + args.steps):
+            pf.launch()
+            pa.launch()
+        torch.cuda.synchronize()
+        print("profile run: %s %s, %d launches of each plan" % (args.workload, args.storage,
+                                                                1 + args.warmup + args.steps))
+        return
     gargs = workload_geometry_args(w)
     kind = gargs.pop("kind")
     geom = Geometry(kind, **gargs)
-    dt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[args.storage]
     cfg = launch_config(args.algo)
     x = torch.from_numpy(workload_images(w)).to(device="cuda", dtype=dt)
     y = forward_raw(geom, x, cfg)
@@ -533,8 +614,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(k for k, v in WORKLOADS.items()
-                                                                           if v.kind in ("parallel", "fan")))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS),
+                    help="timed runs take the parallel / fan workloads; --profile takes any")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f16")
     ap.add_argument("--algo", choices=["auto", "plain", "tiled"], default="auto")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -345,6 +345,70 @@ RADON_API radon_status radon_power_iteration(const radon_geometry* geometry, con
 RADON_API radon_status radon_get_device_error(void* stream);
 
 /*
+ * ---- Uneven batches in one persistent launch (Section 4.1: batch processing, here of images of
+ * different sizes, each with its own geometry) ----
+ *
+ * A plan covers n items; item i projects (direction 0) or back-projects (direction 1) items[i].batch
+ * images with geometry items[i].geometry from items[i].in to items[i].out (device buffers laid out as
+ * for radon_forward / radon_backward).  Every image of every item becomes a unit; the plan splits the
+ * units into work items -- blocks of rays (forward) or 16 x 16 pixel tiles (adjoint) -- ordered
+ * largest first, and one persistent kernel (one CTA per SM slot) takes them from a device counter
+ * until the list is empty, so small and large images share the GPU without a tail of idle SMs.
+ *   - Forward: the plan keeps a packed copy of every image (each pixel's 2 x 2 bilinear neighbourhood
+ *     in one 8-byte texel, FP32: 16 bytes, in the image frame and transposed), refreshed by a pack
+ *     kernel at every launch; each sample is one texel load.
+ *   - Adjoint: per chunk of views the CTA re-bases the rays crossing its tile and stages their
+ *     sinogram values in shared memory, then every thread gathers its pixel.
+ *   - Tile shapes (forward: views x detectors per ray block; adjoint: views per chunk) are picked per
+ *     image size by a built-in autotuner that times each candidate on the plan's own buffers at
+ *     creation (and writes the outputs while doing so), unless options fix them.
+ * The caller keeps the geometries and buffers alive until radon_batch_plan_destroy; the buffer
+ * addresses are baked into the plan.
+ */
+typedef struct radon_item {
+    const radon_geometry* geometry;
+    const void* in;
+    void* out;
+    int batch;
+} radon_item;
+
+typedef struct radon_plan radon_plan;
+
+typedef struct radon_plan_options {
+    int autotune;            /* 1: time the candidates (default); 0: library defaults */
+    int forward_views;       /* > 0: views per forward ray block (1, 2, 4 or 8; detectors = 256 / views) */
+    int adjoint_views;       /* > 0: views per adjoint chunk (4, 8 or 16) */
+} radon_plan_options;
+
+/*
+ * Builds a plan (allocates device memory, uploads the work list, autotunes; synchronises; not
+ * capturable).  All items share `dtype` and must live on the current device; items with batch 0 are
+ * skipped.  `options` may be NULL (autotune on).  RADON_ERR_INVALID_ARG for a bad item (NULL or
+ * host-only geometry, NULL buffer, batch < 0), RADON_ERR_OOM if device memory runs out.
+ */
+RADON_API radon_status radon_batch_plan_create(const radon_item* items, int n, int direction, radon_dtype dtype,
+                                               const radon_plan_options* options, radon_plan** out);
+
+/*
+ * Runs the plan on `stream`: resets the work counter, packs (forward), then one persistent kernel.
+ * Allocates nothing, never synchronises; can be captured in a CUDA graph (replays read the items'
+ * input buffers as they are at replay time).
+ */
+RADON_API radon_status radon_batch_plan_launch(radon_plan* plan, void* stream);
+
+/* What the plan built: units (images), work items, persistent CTAs, and the tile shape of item i. */
+typedef struct radon_plan_info {
+    int units;
+    int work_items;
+    int ctas;
+    int direction;
+} radon_plan_info;
+RADON_API radon_status radon_batch_plan_get_info(const radon_plan* plan, radon_plan_info* info);
+RADON_API radon_status radon_batch_plan_item_config(const radon_plan* plan, int item, int* views);
+
+RADON_API void radon_batch_plan_destroy(radon_plan* plan);
+
+/*
  * Number of kernels this library has launched in this process so far (every pack, projection and
  * vector kernel, counted on the host when the launch is issued).  Thread-safe; for accounting, e.g.
  * the launches inside a timed region are the difference of two reads.

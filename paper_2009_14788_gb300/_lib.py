@@ -85,6 +85,32 @@ class radon_epilogue(ctypes.Structure):
     ]
 
 
+class radon_item(ctypes.Structure):
+    _fields_ = [
+        ("geometry", ctypes.c_void_p),
+        ("in_", ctypes.c_void_p),
+        ("out", ctypes.c_void_p),
+        ("batch", ctypes.c_int),
+    ]
+
+
+class radon_plan_options(ctypes.Structure):
+    _fields_ = [
+        ("autotune", ctypes.c_int),
+        ("forward_views", ctypes.c_int),
+        ("adjoint_views", ctypes.c_int),
+    ]
+
+
+class radon_plan_info(ctypes.Structure):
+    _fields_ = [
+        ("units", ctypes.c_int),
+        ("work_items", ctypes.c_int),
+        ("ctas", ctypes.c_int),
+        ("direction", ctypes.c_int),
+    ]
+
+
 _c = None
 
 # (name, restype, argtypes) of every exported function
@@ -138,6 +164,13 @@ _SIGNATURES = [
     ("radon_power_iteration", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
       ctypes.c_size_t, ctypes.c_void_p]),
+    ("radon_batch_plan_create", ctypes.c_int,
+     [ctypes.POINTER(radon_item), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(radon_plan_options),
+      ctypes.POINTER(ctypes.c_void_p)]),
+    ("radon_batch_plan_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("radon_batch_plan_get_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(radon_plan_info)]),
+    ("radon_batch_plan_item_config", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("radon_batch_plan_destroy", None, [ctypes.c_void_p]),
     ("radon_kernel_launch_count", ctypes.c_uint64, []),
     ("radon_get_device_error", ctypes.c_int, [ctypes.c_void_p]),
     ("radon_status_string", ctypes.c_char_p, [ctypes.c_int]),
@@ -279,6 +312,26 @@ def radon_power_iteration_workspace_size(geom):
 def radon_power_iteration(geom, v0, iterations, lambda_out, alpha_out, workspace, workspace_bytes, stream):
     return _call("radon_power_iteration", geom, v0, iterations, lambda_out, alpha_out, workspace, workspace_bytes,
                  stream)
+
+
+def radon_batch_plan_create(items, n, direction, dtype, options, out_ptr):
+    return _call("radon_batch_plan_create", items, n, direction, dtype, options, out_ptr)
+
+
+def radon_batch_plan_launch(plan, stream):
+    return _call("radon_batch_plan_launch", plan, stream)
+
+
+def radon_batch_plan_get_info(plan, info_ptr):
+    return _call("radon_batch_plan_get_info", plan, info_ptr)
+
+
+def radon_batch_plan_item_config(plan, item, views_ptr):
+    return _call("radon_batch_plan_item_config", plan, item, views_ptr)
+
+
+def radon_batch_plan_destroy(plan):
+    return _call("radon_batch_plan_destroy", plan)
 
 
 def radon_kernel_launch_count():

@@ -1,0 +1,679 @@
+// Uneven batches in one persistent launch: many images of different sizes, each with its own
+// geometry (Section 4.1's batch processing, generalised to a mixed batch).
+//
+// A plan turns every image of every item into a unit and every unit into work items -- blocks of
+// rays for the forward projection, 16 x 16 pixel tiles for the adjoint -- listed largest first.  One
+// persistent kernel (as many CTAs as fit on the GPU at once) takes work items from a device counter
+// until the list is exhausted, so a 1024^2 image with 1000 views and a 128^2 image with 90 views
+// share the SMs without a tail.  Items have batch 1 in the typical mixed batch, so nothing is
+// amortised across images as in the batch-interleaved kernels; instead:
+//   * forward: a pack kernel stores each pixel's 2 x 2 bilinear neighbourhood as one texel (four
+//     16-bit values in 8 bytes, or four FP32 in 16), once in the image frame and once transposed;
+//     every sample is one texel load through L1.  A warp holds 32 neighbouring detectors of one view,
+//     whose samples at a given step lie along the detector direction; the frame whose rows run along
+//     that direction keeps them within a few cache lines;
+//   * adjoint: per chunk of views the CTA computes each view's detector window for its tile,
+//     re-bases every ray of the windows on the tile (one ray per thread) and stages the rays'
+//     sinogram values in shared memory; then every thread gathers its pixel from shared memory.
+// Tile shapes (forward: views x detectors per ray block; adjoint: views per chunk) are chosen per
+// image size by timing each candidate on the plan's own buffers when the plan is created.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "backward_tiled.cuh"
+#include "device_error.cuh"
+#include "dtype.cuh"
+#include "radon_internal.h"
+
+namespace radon {
+
+namespace {
+
+constexpr uint64_t kPlanMagic = 0x5241444f4e504c4eULL;   // "RADONPLN"
+constexpr int kPlanThreads = 256;
+constexpr int kMaxChunkViews = 16;
+
+struct Unit {
+    const void* in;
+    void* out;
+    const RayT* rays;
+    const int* nks;
+    const ViewF* views;
+    long long q_off;   // forward: first texel of this unit's packed image (row frame; transposed follows)
+    int n, V, D;
+    float h, ih2;
+    int wd;            // adjoint: detector window of a 16 x 16 tile
+    int cfg;           // forward: views per ray block; adjoint: views per chunk
+};
+
+struct Work {
+    int unit;
+    int tile;
+};
+
+// ------------------------------------------------------------------------------------------ pack
+
+template <typename T>
+struct Quad;   // texel: the 2 x 2 neighbourhood (i, j), (i, j+1), (i+1, j), (i+1, j+1)
+
+template <>
+struct Quad<float> {
+    using type = float4;
+    __device__ static type make(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+    __device__ static void unpack(const type& q, float* v) {
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+    }
+};
+
+template <typename H>
+struct Quad16 {
+    using type = uint2;
+    __device__ static unsigned bits(H v) {
+        unsigned short u;
+        memcpy(&u, &v, 2);
+        return u;
+    }
+    __device__ static type make(H a, H b, H c, H d) {
+        return make_uint2(bits(a) | (bits(b) << 16), bits(c) | (bits(d) << 16));
+    }
+};
+
+template <>
+struct Quad<__half> : Quad16<__half> {
+    __device__ static void unpack(const type& q, float* v) {
+        __half2 lo, hi;
+        memcpy(&lo, &q.x, 4);
+        memcpy(&hi, &q.y, 4);
+        const float2 a = __half22float2(lo), b = __half22float2(hi);
+        v[0] = a.x;
+        v[1] = a.y;
+        v[2] = b.x;
+        v[3] = b.y;
+    }
+};
+
+template <>
+struct Quad<__nv_bfloat16> : Quad16<__nv_bfloat16> {
+    __device__ static void unpack(const type& q, float* v) {
+        v[0] = __uint_as_float(q.x << 16);
+        v[1] = __uint_as_float(q.x & 0xffff0000u);
+        v[2] = __uint_as_float(q.y << 16);
+        v[3] = __uint_as_float(q.y & 0xffff0000u);
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ T pix(const T* x, int n, int i, int j) {
+    return (i >= 0 && i < n && j >= 0 && j < n) ? x[(long long)i * n + j] : from_f32<T>(0.0f);
+}
+
+// One thread per texel of every unit (both frames); `prefix[u]` = first texel of unit u.
+template <typename T>
+__global__ void __launch_bounds__(256) plan_pack_kernel(const Unit* __restrict__ units, const long long* __restrict__ prefix,
+                                                        int n_units, long long total,
+                                                        typename Quad<T>::type* __restrict__ quads) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+        int lo = 0, hi = n_units - 1;   // last unit with prefix <= g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const Unit& u = units[lo];
+        const T* x = static_cast<const T*>(u.in);
+        const long long p = (long long)u.n + 1;
+        long long e = g - prefix[lo];
+        const int frame = e >= p * p ? 1 : 0;
+        if (frame) e -= p * p;
+        const int i = (int)(e / p) - 1, j = (int)(e - (e / p) * p) - 1;
+        quads[g] = frame == 0 ? Quad<T>::make(pix(x, u.n, i, j), pix(x, u.n, i, j + 1), pix(x, u.n, i + 1, j),
+                                              pix(x, u.n, i + 1, j + 1))
+                              : Quad<T>::make(pix(x, u.n, j, i), pix(x, u.n, j + 1, i), pix(x, u.n, j, i + 1),
+                                              pix(x, u.n, j + 1, i + 1));
+    }
+}
+
+// ------------------------------------------------------------------------------------- forward
+
+// Ray (v, d) of unit u: h * sum_k bilinear(sample k), every sample one texel load.  Positions are
+// re-based from the split-precision table every 32 samples (as in the plain kernel).
+template <typename T>
+__device__ float plan_ray(const Unit& u, const typename Quad<T>::type* __restrict__ quads, int v, int d) {
+    const long long r = (long long)v * u.D + d;
+    const int nk = u.nks[r];
+    if (nk == 0) return 0.0f;
+    const RayT ray = u.rays[r];
+    // frame: rows of the transposed image for rays running mostly along x (neighbouring rays then
+    // differ mostly in y, which the transposed frame lays out along its rows)
+    const bool tr = fabsf(ray.dxh + ray.dxl) > fabsf(ray.dyh + ray.dyl);
+    const int J0 = tr ? ray.I0 : ray.J0, I0 = tr ? ray.J0 : ray.I0;
+    const float fX0 = tr ? ray.fy0 : ray.fx0, fY0 = tr ? ray.fx0 : ray.fy0;
+    const float dXh = tr ? ray.dyh : ray.dxh, dYh = tr ? ray.dxh : ray.dyh;
+    const float dXl = tr ? ray.dyl : ray.dxl, dYl = tr ? ray.dxl : ray.dyl;
+    const float dX = dXh + dXl, dY = dYh + dYl;
+    const int p = u.n + 1;
+    const typename Quad<T>::type* q = quads + u.q_off + (tr ? (long long)p * p : 0ll);
+    float acc = 0.0f;
+    for (int kb = 0; kb < nk; kb += 32) {
+        const float kbf = (float)kb;
+        const float qx = kbf * dXh, qy = kbf * dYh;   // exact products
+        const float QX = floorf(qx), QY = floorf(qy);
+        const float sX = fmaf(kbf, dXl, fX0 + (qx - QX));
+        const float sY = fmaf(kbf, dYl, fY0 + (qy - QY));
+        const int jb = J0 + (int)QX, ib = I0 + (int)QY;
+        const int kend = min(nk - kb, 32);
+        for (int kk = 0; kk < kend; ++kk) {
+            const float lx = fmaf((float)kk, dX, sX), ly = fmaf((float)kk, dY, sY);
+            const float flx = floorf(lx), fly = floorf(ly);
+            // samples lie strictly inside the support box, so j, i are in [-1, n-1]; the clamps only
+            // absorb FP32 rounding at the box edge, where the far texel values are zero
+            const int j = min(max(jb + (int)flx, -1), u.n - 1), i = min(max(ib + (int)fly, -1), u.n - 1);
+            const float a = fminf(fmaxf(lx - (float)(j - jb), 0.0f), 1.0f);
+            const float b = fminf(fmaxf(ly - (float)(i - ib), 0.0f), 1.0f);
+            float t[4];
+            Quad<T>::unpack(q[(long long)(i + 1) * p + (j + 1)], t);
+            const float top = fmaf(a, t[1] - t[0], t[0]), bot = fmaf(a, t[3] - t[2], t[2]);
+            acc += fmaf(b, bot - top, top);
+        }
+    }
+    return u.h * acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPlanThreads) plan_forward_kernel(const Unit* __restrict__ units,
+                                                                    const Work* __restrict__ work, int n_work,
+                                                                    unsigned* counter,
+                                                                    const typename Quad<T>::type* __restrict__ quads) {
+    __shared__ int s_w;
+    for (;;) {
+        if (threadIdx.x == 0) s_w = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int wi = s_w;
+        __syncthreads();
+        if (wi >= n_work) return;
+        const Work w = work[wi];
+        const Unit& u = units[w.unit];
+        const int G = u.cfg, Dt = kPlanThreads / G;
+        const int n_dr = (u.D + Dt - 1) / Dt;
+        const int vg = w.tile / n_dr, dr = w.tile - (w.tile / n_dr) * n_dr;
+        const int v = vg * G + (int)threadIdx.x / Dt, d = dr * Dt + (int)threadIdx.x % Dt;
+        if (v < u.V && d < u.D) {
+            const float y = plan_ray<T>(u, quads, v, d);
+            static_cast<T*>(u.out)[(long long)v * u.D + d] = from_f32<T>(y);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------- adjoint
+
+struct AdjShared {
+    ViewF view[kMaxChunkViews];
+    int dlo[kMaxChunkViews];
+    float r[kMaxChunkViews];
+    int w;
+};
+
+template <typename T, int KW>
+__global__ void __launch_bounds__(kPlanThreads) plan_adjoint_kernel(const Unit* __restrict__ units,
+                                                                    const Work* __restrict__ work, int n_work,
+                                                                    unsigned* counter, int max_wd, int* err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AdjShared* sh = reinterpret_cast<AdjShared*>(smem_raw);
+    float4* rp = reinterpret_cast<float4*>(smem_raw + (sizeof(AdjShared) + 15) / 16 * 16);   // [chunk * wd]
+    float* ys = reinterpret_cast<float*>(rp + kMaxChunkViews * max_wd);                       // [chunk * wd]
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int pi = (warp >> 1) * 4 + (lane >> 3), pj = (warp & 1) * 8 + (lane & 7);   // 4 x 8 per warp
+    const f32x2 p2 = f2_pack((float)pj, (float)pi);
+    for (;;) {
+        if (tid == 0) sh->w = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int wi = sh->w;
+        if (wi >= n_work) return;
+        const Work w = work[wi];
+        const Unit& u = units[w.unit];
+        const int tiles_x = (u.n + kBwdTile - 1) / kBwdTile;
+        const int ti = (w.tile / tiles_x) * kBwdTile, tj = (w.tile - (w.tile / tiles_x) * tiles_x) * kBwdTile;
+        const float gx = (float)(tj + pj), gy = (float)(ti + pi);
+        const bool inside = (ti + pi) < u.n && (tj + pj) < u.n;
+        const f32x2 ih2_2 = f2_pack(u.ih2, u.ih2);
+        const T* y = static_cast<const T*>(u.in);
+        const int CV = u.cfg, wd = u.wd;
+        float acc = 0.0f;
+        for (int c0 = 0; c0 < u.V; c0 += CV) {
+            const int nv = min(CV, u.V - c0);
+            if (tid < nv) {
+                const ViewF vf = u.views[c0 + tid];
+                int dlo;
+                float r;
+                bwd_view_window(vf, ti, tj, u.n, &dlo, &r);
+                sh->view[tid] = vf;
+                sh->dlo[tid] = dlo;
+                sh->r[tid] = r;
+            }
+            __syncthreads();
+            for (int e = tid; e < nv * wd; e += kPlanThreads) {
+                const int vl = e / wd, dl = e - (e / wd) * wd;
+                const int d = sh->dlo[vl] + dl;
+                const bool valid = d >= 0 && d < u.D;
+                const long long ridx = (long long)(c0 + vl) * u.D + (valid ? d : 0);
+                const RayT ray = u.rays[ridx];
+                rp[e] = bwd_ray_pos_rec(ray, valid, ti, tj, u.ih2);
+                ys[e] = valid ? to_f32(y[ridx]) : 0.0f;
+            }
+            __syncthreads();
+            for (int vl = 0; vl < nv; ++vl) {
+                const ViewF vf = sh->view[vl];
+                const int dlo = sh->dlo[vl];
+                const float r = sh->r[vl];
+                const float t = __fdividef(fmaf(vf.ax, gx, fmaf(vf.ay, gy, vf.a0)), fmaf(vf.bx, gx, fmaf(vf.by, gy, vf.b0)));
+                const float flo = ceilf(t - r), fhi = floorf(t + r);
+                const int da = (int)fmaxf(flo, (float)max(dlo, 0));
+                const int db = (int)fminf(fhi, (float)min(u.D - 1, dlo + wd - 1));
+                if (inside && ((flo < (float)dlo && flo >= 0.0f) || (fhi > (float)(dlo + wd - 1) && fhi <= (float)(u.D - 1))))
+                    record_device_error(err, RADON_ERR_DEVICE_BOUNDS);
+                const ulonglong2* rpv = reinterpret_cast<const ulonglong2*>(rp) + vl * wd;
+                const float* yv = ys + vl * wd;
+                for (int d = da; d <= db; ++d) {
+                    const ulonglong2 rr = rpv[d - dlo];
+                    acc = fmaf(bwd_ray_weight_pair<KW>(p2, rr.x, rr.y, ih2_2, u.ih2), yv[d - dlo], acc);
+                }
+            }
+            __syncthreads();
+        }
+        if (inside)
+            static_cast<T*>(u.out)[(long long)(ti + pi) * u.n + (tj + pj)] = from_f32<T>(u.h * acc);
+    }
+}
+
+size_t adj_smem_bytes(int max_wd) {
+    return (sizeof(AdjShared) + 15) / 16 * 16 + (size_t)kMaxChunkViews * max_wd * (16 + 4);
+}
+
+// --------------------------------------------------------------------------------------- plan
+
+size_t texel_bytes(radon_dtype dt) { return dt == RADON_F32 ? 16 : 8; }
+
+}  // namespace
+
+}  // namespace radon
+
+using namespace radon;
+
+struct radon_plan {
+    uint64_t magic = kPlanMagic;
+    int direction = 0;
+    radon_dtype dtype = RADON_F32;
+    int device = 0;
+    int kw = 3;
+    int max_wd = 0;
+    int ctas = 0;
+    size_t smem = 0;
+    std::vector<Unit> units;
+    std::vector<int> unit_item;
+    std::vector<int> item_cfg;
+    std::vector<Work> work;
+    std::vector<long long> prefix;   // forward: texel offsets, n_units + 1
+    Unit* d_units = nullptr;
+    Work* d_work = nullptr;
+    long long* d_prefix = nullptr;
+    unsigned* d_counter = nullptr;
+    void* d_quads = nullptr;
+    long long total_texels = 0;
+};
+
+namespace radon {
+
+namespace {
+
+void free_plan(radon_plan* p) {
+    if (p == nullptr) return;
+    cudaFree(p->d_units);
+    cudaFree(p->d_work);
+    cudaFree(p->d_prefix);
+    cudaFree(p->d_counter);
+    cudaFree(p->d_quads);
+    p->magic = 0;
+    delete p;
+}
+
+// Work list for `cfg` over the units in `sel`, largest work items first.
+std::vector<Work> build_work(const radon_plan* p, const std::vector<int>& sel) {
+    std::vector<int> order(sel);
+    auto cost = [&](int ui) -> double {
+        const Unit& u = p->units[ui];
+        return p->direction == 0 ? (double)u.n : (double)u.V;   // per work item
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    std::vector<Work> w;
+    for (int ui : order) {
+        const Unit& u = p->units[ui];
+        int tiles;
+        if (p->direction == 0) {
+            const int G = u.cfg, Dt = kPlanThreads / G;
+            tiles = ((u.V + G - 1) / G) * ((u.D + Dt - 1) / Dt);
+        } else {
+            const int t = (u.n + kBwdTile - 1) / kBwdTile;
+            tiles = t * t;
+        }
+        for (int t = 0; t < tiles; ++t) w.push_back(Work{ui, t});
+    }
+    return w;
+}
+
+radon_status upload_work(radon_plan* p, const std::vector<Work>& w, Work** dst) {
+    cudaFree(*dst);
+    *dst = nullptr;
+    if (w.empty()) return RADON_OK;
+    cudaError_t e = cudaMalloc(dst, w.size() * sizeof(Work));
+    if (e != cudaSuccess) return fail(RADON_ERR_OOM, "cudaMalloc of the work list failed");
+    e = cudaMemcpy(*dst, w.data(), w.size() * sizeof(Work), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "work list upload");
+    return RADON_OK;
+}
+
+radon_status upload_units(radon_plan* p) {
+    cudaError_t e = cudaMemcpy(p->d_units, p->units.data(), p->units.size() * sizeof(Unit), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "unit table upload");
+    return RADON_OK;
+}
+
+template <typename T>
+radon_status launch_t(const radon_plan* p, const Work* d_work, int n_work, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return cuda_fail(e, "work counter reset");
+    if (n_work == 0) return RADON_OK;
+    using Q = typename Quad<T>::type;
+    if (p->direction == 0) {
+        const unsigned blocks = (unsigned)std::min<long long>((p->total_texels + 255) / 256, 152LL * 64);
+        plan_pack_kernel<T><<<blocks, 256, 0, s>>>(p->d_units, p->d_prefix, (int)p->units.size(), p->total_texels,
+                                                   static_cast<Q*>(p->d_quads));
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "plan pack launch");
+        plan_forward_kernel<T><<<p->ctas, kPlanThreads, 0, s>>>(p->d_units, d_work, n_work, p->d_counter,
+                                                               static_cast<const Q*>(p->d_quads));
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "plan forward launch");
+        count_launches(2);
+    } else {
+        int* err = device_error_word();
+        if (err == nullptr) return fail(RADON_ERR_CUDA, "device error word unavailable");
+        if (p->kw == 3)
+            plan_adjoint_kernel<T, 3><<<p->ctas, kPlanThreads, p->smem, s>>>(p->d_units, d_work, n_work, p->d_counter,
+                                                                            p->max_wd, err);
+        else
+            plan_adjoint_kernel<T, 6><<<p->ctas, kPlanThreads, p->smem, s>>>(p->d_units, d_work, n_work, p->d_counter,
+                                                                            p->max_wd, err);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "plan adjoint launch");
+        count_launches(1);
+    }
+    return RADON_OK;
+}
+
+radon_status launch_plan(const radon_plan* p, const Work* d_work, int n_work, cudaStream_t s) {
+    switch (p->dtype) {
+        case RADON_F16: return launch_t<__half>(p, d_work, n_work, s);
+        case RADON_BF16: return launch_t<__nv_bfloat16>(p, d_work, n_work, s);
+        default: return launch_t<float>(p, d_work, n_work, s);
+    }
+}
+
+template <typename T>
+radon_status occupancy_t(radon_plan* p) {
+    int per_sm = 0;
+    cudaError_t e;
+    if (p->direction == 0) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_forward_kernel<T>, kPlanThreads, 0);
+    } else if (p->kw == 3) {
+        e = cudaFuncSetAttribute(plan_adjoint_kernel<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_adjoint_kernel<T, 3>, kPlanThreads, p->smem);
+    } else {
+        e = cudaFuncSetAttribute(plan_adjoint_kernel<T, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_adjoint_kernel<T, 6>, kPlanThreads, p->smem);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "plan occupancy query");
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    p->ctas = std::max(1, per_sm) * sms;
+    return RADON_OK;
+}
+
+radon_status occupancy(radon_plan* p) {
+    switch (p->dtype) {
+        case RADON_F16: return occupancy_t<__half>(p);
+        case RADON_BF16: return occupancy_t<__nv_bfloat16>(p);
+        default: return occupancy_t<float>(p);
+    }
+}
+
+// Times `reps` launches of the plan restricted to units `sel`; returns the median in ms.
+radon_status time_subset(radon_plan* p, const std::vector<int>& sel, float* ms) {
+    const std::vector<Work> w = build_work(p, sel);
+    Work* d = nullptr;
+    radon_status st = upload_work(p, w, &d);
+    if (st != RADON_OK) return st;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<float> t;
+    for (int r = 0; r < 4 && st == RADON_OK; ++r) {
+        cudaEventRecord(e0, 0);
+        st = launch_plan(p, d, (int)w.size(), 0);
+        cudaEventRecord(e1, 0);
+        if (st == RADON_OK && cudaEventSynchronize(e1) == cudaSuccess) {
+            float x = 0.f;
+            cudaEventElapsedTime(&x, e0, e1);
+            if (r > 0) t.push_back(x);   // the first run warms up
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d);
+    if (st != RADON_OK) return st;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "autotune run");
+    std::sort(t.begin(), t.end());
+    *ms = t.empty() ? 0.f : t[t.size() / 2];
+    return RADON_OK;
+}
+
+}  // namespace
+
+}  // namespace radon
+
+extern "C" RADON_API radon_status radon_batch_plan_create(const radon_item* items, int n, int direction,
+                                                          radon_dtype dtype, const radon_plan_options* options,
+                                                          radon_plan** out) {
+    if (out == nullptr) return fail(RADON_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 0 || (n > 0 && items == nullptr)) return fail(RADON_ERR_INVALID_ARG, "items is NULL or n < 0");
+    if (direction != 0 && direction != 1) return fail(RADON_ERR_INVALID_ARG, "direction must be 0 (forward) or 1 (adjoint)");
+    if (dtype != RADON_F32 && dtype != RADON_F16 && dtype != RADON_BF16)
+        return fail(RADON_ERR_INVALID_ARG, "dtype must be RADON_F32, RADON_F16 or RADON_BF16");
+    const int fv = options ? options->forward_views : 0, av = options ? options->adjoint_views : 0;
+    if (fv < 0 || (fv > 0 && fv != 1 && fv != 2 && fv != 4 && fv != 8))
+        return fail(RADON_ERR_INVALID_ARG, "forward_views must be 0, 1, 2, 4 or 8");
+    if (av < 0 || (av > 0 && av != 4 && av != 8 && av != 16))
+        return fail(RADON_ERR_INVALID_ARG, "adjoint_views must be 0, 4, 8 or 16");
+    const bool autotune = options == nullptr || options->autotune != 0;
+    const size_t es = dtype == RADON_F32 ? 4 : 2;
+    for (int i = 0; i < n; ++i) {
+        const radon_item& it = items[i];
+        const radon_geometry* g = it.geometry;
+        if (g == nullptr || g->magic != kGeometryMagic)
+            return fail(RADON_ERR_INVALID_ARG, "item " + std::to_string(i) + ": geometry is not a live geometry");
+        if (g->host_only) return fail(RADON_ERR_INVALID_ARG, "item " + std::to_string(i) + ": host-only geometry");
+        if (it.batch < 0) return fail(RADON_ERR_INVALID_ARG, "item " + std::to_string(i) + ": batch < 0");
+        if (it.batch > 0 && (it.in == nullptr || it.out == nullptr))
+            return fail(RADON_ERR_INVALID_ARG, "item " + std::to_string(i) + ": NULL buffer");
+        if (it.batch > 0 && (((uintptr_t)it.in % es) != 0 || ((uintptr_t)it.out % es) != 0))
+            return fail(RADON_ERR_INVALID_ARG, "item " + std::to_string(i) + ": buffer not aligned to its element size");
+    }
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    for (int i = 0; i < n; ++i)
+        if (items[i].geometry->device != dev)
+            return fail(RADON_ERR_INVALID_ARG, "item " + std::to_string(i) + ": geometry on another device");
+    radon_plan* p = new (std::nothrow) radon_plan();
+    if (p == nullptr) return fail(RADON_ERR_OOM, "host allocation failed");
+    p->direction = direction;
+    p->dtype = dtype;
+    p->device = dev;
+    p->item_cfg.assign(n, 0);
+    for (int i = 0; i < n; ++i) {
+        const radon_item& it = items[i];
+        const radon_geometry* g = it.geometry;
+        const long long in_sz = direction == 0 ? (long long)g->n * g->n : (long long)g->V * g->D;
+        const long long out_sz = direction == 0 ? (long long)g->V * g->D : (long long)g->n * g->n;
+        for (int b = 0; b < it.batch; ++b) {
+            Unit u;
+            u.in = static_cast<const unsigned char*>(it.in) + (size_t)b * in_sz * es;
+            u.out = static_cast<unsigned char*>(it.out) + (size_t)b * out_sz * es;
+            u.rays = g->d_ray;
+            u.nks = g->d_nk;
+            u.views = g->d_view;
+            u.q_off = 0;
+            u.n = g->n;
+            u.V = g->V;
+            u.D = g->D;
+            u.h = (float)g->h;
+            u.ih2 = (float)(1.0 / (g->h * g->h));
+            u.wd = g->bwd_window + 2;
+            u.cfg = direction == 0 ? (fv > 0 ? fv : 8) : (av > 0 ? av : 8);
+            p->units.push_back(u);
+            p->unit_item.push_back(i);
+            p->max_wd = std::max(p->max_wd, u.wd);
+            if (direction == 1) {
+                // samples per candidate window: the window spans 2 (|dx|+|dy|)/h^2 <= 2 sqrt(2) / h
+                const int kw_needed = (int)std::floor(2.0 * std::sqrt(2.0) / g->h + 2e-4) + 1;
+                if (kw_needed > 6) {
+                    free_plan(p);
+                    return fail(RADON_ERR_UNSUPPORTED, "item " + std::to_string(i) +
+                                                           ": sampling step too small for the adjoint plan");
+                }
+                if (kw_needed > 3) p->kw = 6;
+            }
+        }
+    }
+    radon_status st = RADON_OK;
+    const size_t nu = p->units.size();
+    if (direction == 0) {
+        p->prefix.assign(nu + 1, 0);
+        for (size_t k = 0; k < nu; ++k) {
+            const long long q = (long long)(p->units[k].n + 1) * (p->units[k].n + 1);
+            p->units[k].q_off = p->prefix[k];
+            p->prefix[k + 1] = p->prefix[k] + 2 * q;
+        }
+        p->total_texels = p->prefix[nu];
+    } else {
+        p->smem = adj_smem_bytes(std::max(p->max_wd, 1));
+        if (p->smem > 227 * 1024) {
+            free_plan(p);
+            return fail(RADON_ERR_UNSUPPORTED, "detector window too wide for the adjoint plan's shared memory");
+        }
+    }
+    if (nu > 0) {
+        if (cudaMalloc(&p->d_units, nu * sizeof(Unit)) != cudaSuccess ||
+            cudaMalloc(&p->d_counter, sizeof(unsigned)) != cudaSuccess ||
+            (direction == 0 && (cudaMalloc(&p->d_prefix, (nu + 1) * sizeof(long long)) != cudaSuccess ||
+                                cudaMalloc(&p->d_quads, (size_t)p->total_texels * texel_bytes(dtype)) != cudaSuccess))) {
+            cudaGetLastError();
+            free_plan(p);
+            return fail(RADON_ERR_OOM, "device allocation for the plan failed");
+        }
+        if (direction == 0) {
+            e = cudaMemcpy(p->d_prefix, p->prefix.data(), (nu + 1) * sizeof(long long), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                free_plan(p);
+                return cuda_fail(e, "plan upload");
+            }
+        }
+        st = occupancy(p);
+        if (st == RADON_OK) st = upload_units(p);
+        // Autotuner: per image size, time each candidate tile shape on that size's units alone.
+        const bool fixed = direction == 0 ? fv > 0 : av > 0;
+        if (st == RADON_OK && autotune && !fixed) {
+            static const int kFwdCand[4] = {8, 4, 2, 1};
+            static const int kAdjCand[3] = {4, 8, 16};
+            const int* cand = direction == 0 ? kFwdCand : kAdjCand;
+            const int nc = direction == 0 ? 4 : 3;
+            std::map<int, std::vector<int>> by_size;
+            for (size_t k = 0; k < nu; ++k) by_size[p->units[k].n].push_back((int)k);
+            for (auto& kv : by_size) {
+                float best = 3.0e38f;
+                int best_c = cand[0];
+                for (int c = 0; c < nc && st == RADON_OK; ++c) {
+                    for (int k : kv.second) p->units[k].cfg = cand[c];
+                    st = upload_units(p);
+                    float ms = 0.f;
+                    if (st == RADON_OK) st = time_subset(p, kv.second, &ms);
+                    if (st == RADON_OK && ms < best) {
+                        best = ms;
+                        best_c = cand[c];
+                    }
+                }
+                for (int k : kv.second) p->units[k].cfg = best_c;
+            }
+            if (st == RADON_OK) st = upload_units(p);
+        }
+    }
+    if (st == RADON_OK) {
+        std::vector<int> all(nu);
+        for (size_t k = 0; k < nu; ++k) all[k] = (int)k;
+        p->work = build_work(p, all);
+        st = upload_work(p, p->work, &p->d_work);
+    }
+    if (st != RADON_OK) {
+        free_plan(p);
+        return st;
+    }
+    for (size_t k = 0; k < nu; ++k) p->item_cfg[p->unit_item[k]] = p->units[k].cfg;
+    *out = p;
+    return RADON_OK;
+}
+
+extern "C" RADON_API radon_status radon_batch_plan_launch(radon_plan* p, void* stream) {
+    if (p == nullptr || p->magic != kPlanMagic) return fail(RADON_ERR_INVALID_ARG, "plan is not a live plan");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != p->device) return fail(RADON_ERR_INVALID_ARG, "plan lives on another device");
+    if (p->units.empty()) return RADON_OK;
+    return launch_plan(p, p->d_work, (int)p->work.size(), (cudaStream_t)stream);
+}
+
+extern "C" RADON_API radon_status radon_batch_plan_get_info(const radon_plan* p, radon_plan_info* info) {
+    if (p == nullptr || p->magic != kPlanMagic) return fail(RADON_ERR_INVALID_ARG, "plan is not a live plan");
+    if (info == nullptr) return fail(RADON_ERR_INVALID_ARG, "info is NULL");
+    info->units = (int)p->units.size();
+    info->work_items = (int)p->work.size();
+    info->ctas = p->ctas;
+    info->direction = p->direction;
+    return RADON_OK;
+}
+
+extern "C" RADON_API radon_status radon_batch_plan_item_config(const radon_plan* p, int item, int* views) {
+    if (p == nullptr || p->magic != kPlanMagic) return fail(RADON_ERR_INVALID_ARG, "plan is not a live plan");
+    if (item < 0 || item >= (int)p->item_cfg.size() || views == nullptr)
+        return fail(RADON_ERR_INVALID_ARG, "item out of range or views is NULL");
+    *views = p->item_cfg[item];
+    return RADON_OK;
+}
+
+extern "C" RADON_API void radon_batch_plan_destroy(radon_plan* p) {
+    if (p == nullptr || p->magic != kPlanMagic) return;
+    free_plan(p);
+}

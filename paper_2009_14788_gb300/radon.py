@@ -320,6 +320,82 @@ def power_iteration(geom: Geometry, v0: torch.Tensor, iterations: int = 20):
     return lam, alpha
 
 
+class BatchPlan:
+    """One persistent launch over an uneven batch (``radon_batch_plan_*``).
+
+    ``items``: a list of ``(geometry, input, output)``; inputs are image batches ``[B, N, N]`` (or
+    ``[N, N]``) for ``direction="forward"`` and sinograms ``[B, V, D]`` for ``"adjoint"``, outputs
+    the matching results, all contiguous CUDA tensors of one dtype on one device.  The plan keeps
+    references to the tensors (their addresses are baked in) and writes the outputs at every
+    ``launch()``; creation autotunes the tile shapes per image size unless ``autotune=False`` or a
+    shape is given.  ``launch()`` is capturable in a CUDA graph.
+    """
+
+    def __init__(self, items, direction="forward", autotune=True, forward_views=0, adjoint_views=0):
+        if direction not in ("forward", "adjoint"):
+            raise ValueError("direction must be 'forward' or 'adjoint'")
+        self._h = None
+        self.direction = direction
+        self._keep = []
+        arr = (L.radon_item * max(1, len(items)))()
+        dtype = None
+        device = None
+        for k, (geom, inp, out) in enumerate(items):
+            if direction == "forward":
+                ishape, oshape = (geom.n, geom.n), geom.sino_shape
+            else:
+                ishape, oshape = geom.sino_shape, (geom.n, geom.n)
+            for t, shp, what in ((inp, ishape, "input"), (out, oshape, "output")):
+                if not t.is_cuda or not t.is_contiguous() or tuple(t.shape[-2:]) != tuple(shp):
+                    raise ValueError("item %d: %s must be a contiguous CUDA tensor ending in %s" % (k, what, shp))
+            if inp.numel() // (ishape[0] * ishape[1]) != out.numel() // (oshape[0] * oshape[1]):
+                raise ValueError("item %d: input and output batch sizes differ" % k)
+            dtype = inp.dtype if dtype is None else dtype
+            device = inp.device if device is None else device
+            if inp.dtype != dtype or out.dtype != dtype or inp.device != device or out.device != device:
+                raise ValueError("item %d: every tensor must share one dtype and device" % k)
+            arr[k] = L.radon_item(geom.handle, inp.data_ptr(), out.data_ptr(), inp.numel() // (ishape[0] * ishape[1]))
+            self._keep += [geom, inp, out]
+        self.dtype = dtype if dtype is not None else torch.float32
+        opts = L.radon_plan_options(1 if autotune else 0, int(forward_views), int(adjoint_views))
+        h = ctypes.c_void_p()
+        with torch.cuda.device(device if device is not None else torch.cuda.current_device()):
+            st = L.radon_batch_plan_create(arr, len(items), 0 if direction == "forward" else 1, _DTYPES[self.dtype],
+                                           ctypes.byref(opts), ctypes.byref(h))
+        L.check(st, "radon_batch_plan_create")
+        self._h = h
+        self._lib = L.load()
+        self.device = device
+        self.n_items = len(items)
+
+    def launch(self):
+        stream = torch.cuda.current_stream(self.device).cuda_stream if self.device is not None else None
+        L.check(L.radon_batch_plan_launch(self._h, stream), "radon_batch_plan_launch")
+
+    @property
+    def info(self) -> dict:
+        inf = L.radon_plan_info()
+        L.check(L.radon_batch_plan_get_info(self._h, ctypes.byref(inf)), "radon_batch_plan_get_info")
+        return {"units": inf.units, "work_items": inf.work_items, "ctas": inf.ctas,
+                "direction": "forward" if inf.direction == 0 else "adjoint"}
+
+    def item_config(self, item: int) -> int:
+        v = ctypes.c_int()
+        L.check(L.radon_batch_plan_item_config(self._h, int(item), ctypes.byref(v)), "radon_batch_plan_item_config")
+        return v.value
+
+    def close(self):
+        if self._h is not None:
+            self._lib.radon_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class RadonForwardFunction(torch.autograd.Function):
     """y = A x; dL/dx = A^T dL/dy (the adjoint kernel)."""
 

@@ -75,6 +75,27 @@ def rel_l2(got, ref) -> float:
     return float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300))
 
 
+def ulp16(ref, dtype) -> np.ndarray:
+    """One unit in the last place of ``dtype`` (float16 / bfloat16) at each |ref|."""
+    a = np.maximum(np.abs(np.asarray(ref, dtype=np.float64)), 1e-30)
+    e = np.floor(np.log2(a))
+    bits = 10 if dtype == torch.float16 else 7
+    if dtype == torch.float16:
+        e = np.maximum(e, -14.0)   # subnormal spacing below 2^-14
+    return np.exp2(e - bits)
+
+
+def within_16(got, ref, dtype) -> bool:
+    """The 16-bit storage gate.  rel-L2 <= 2e-3 bounds the RMS of many independent roundings; an
+    output of fewer than 64 elements is gated element-wise at one storage ulp instead (a single
+    correctly rounded bfloat16 value may be 2^-8 = 3.9e-3 off in relative terms)."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    if got.size >= 64:
+        return rel_l2(got, ref) <= TOL_16
+    return bool(np.all(np.abs(got - ref) <= ulp16(ref, dtype) * (1 + 1e-9)))
+
+
 def max_rel(got, ref) -> float:
     """Element-wise: worst |got - ref| relative to the largest |ref|."""
     got = np.asarray(got, dtype=np.float64)

@@ -169,6 +169,37 @@ def test_iterative_entry_points_reject_bad_arguments_without_gpu():
     L.radon_geometry_destroy(h)
 
 
+def test_batch_plan_rejects_bad_arguments_without_gpu():
+    st, h = _create()
+    assert st == L.RADON_OK
+    buf = (ctypes.c_double * 16)()
+    p = ctypes.addressof(buf)
+    out = ctypes.c_void_p()
+    items = (L.radon_item * 2)(L.radon_item(h, p, p + 64, 1), L.radon_item(h, p, p + 64, 1))
+    # a host-only geometry cannot be planned
+    assert L.radon_batch_plan_create(items, 2, 0, 0, None, ctypes.byref(out)) == L.RADON_ERR_INVALID_ARG
+    assert "host-only" in L.radon_last_error_message() and not out.value
+    assert L.radon_batch_plan_create(None, 2, 0, 0, None, ctypes.byref(out)) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_batch_plan_create(items, -1, 0, 0, None, ctypes.byref(out)) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_batch_plan_create(items, 2, 2, 0, None, ctypes.byref(out)) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_batch_plan_create(items, 2, 0, 5, None, ctypes.byref(out)) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_batch_plan_create(items, 2, 0, 0, None, None) == L.RADON_ERR_INVALID_ARG
+    opts = L.radon_plan_options(1, 3, 0)
+    assert L.radon_batch_plan_create(items, 2, 0, 0, ctypes.byref(opts), ctypes.byref(out)) == L.RADON_ERR_INVALID_ARG
+    opts = L.radon_plan_options(1, 0, 5)
+    assert L.radon_batch_plan_create(items, 2, 1, 0, ctypes.byref(opts), ctypes.byref(out)) == L.RADON_ERR_INVALID_ARG
+    bad = (L.radon_item * 1)(L.radon_item(None, p, p + 64, 1))
+    assert L.radon_batch_plan_create(bad, 1, 0, 0, None, ctypes.byref(out)) == L.RADON_ERR_INVALID_ARG
+    # a dead handle is refused by every plan call
+    info = L.radon_plan_info()
+    v = ctypes.c_int()
+    assert L.radon_batch_plan_launch(None, None) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_batch_plan_get_info(None, ctypes.byref(info)) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_batch_plan_item_config(None, 0, ctypes.byref(v)) == L.RADON_ERR_INVALID_ARG
+    L.radon_batch_plan_destroy(None)
+    L.radon_geometry_destroy(h)
+
+
 def test_defaults_follow_the_paper():
     g = Geometry("parallel", 40, uniform_angles(5, math.pi), host_only=True)
     assert (g.det_count, g.det_spacing, g.step) == (40, 1.0, 1.0)

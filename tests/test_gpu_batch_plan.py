@@ -1,0 +1,179 @@
+"""Uneven batches in one persistent launch (Section 4.1, mixed sizes and geometries) against the
+FP64 oracle: every item of a plan, in both directions, in FP32 (rel-L2 1e-5) and 16-bit storage
+(2e-3); tile shapes that do not change a single bit; CUDA-graph replay; and the full 64-image
+mixed workload with one complete item per image size checked against the oracle."""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from gpu_cases import TOL_16, TOL_F32, rel_l2, to_dev, to_np, within_16
+from paper_2009_14788_gb300 import BatchPlan, Geometry
+from synth import WORKLOADS, ellipse_phantom, uneven_items, uniform_angles, workload_geometry_args, workload_images
+
+pytestmark = pytest.mark.gpu
+
+# a small mixed set: sizes that span several tiles and ragged tails, both geometries, odd counts
+MIXED = [
+    dict(kind="parallel", n=64, angles=uniform_angles(37, math.pi), det_count=91, det_spacing=1.0),
+    dict(kind="parallel", n=33, angles=uniform_angles(90, math.pi) + 0.01, det_count=47, det_spacing=1.0),
+    dict(kind="fan", n=48, angles=uniform_angles(29, 2 * math.pi) + 0.2, det_count=77, source_distance=130.0,
+         det_distance=70.0),
+    dict(kind="parallel", n=17, angles=uniform_angles(11, math.pi) + 0.3, det_count=25, det_spacing=0.9, step=0.8),
+    dict(kind="parallel", n=1, angles=uniform_angles(5, math.pi), det_count=3),
+    dict(kind="fan", n=80, angles=uniform_angles(45, 2 * math.pi), det_count=130, det_spacing=1.3,
+         source_distance=200.0, det_distance=150.0),
+]
+BATCH = [1, 2, 1, 3, 1, 1]
+
+
+def _geoms(args):
+    a = dict(args)
+    kind = a.pop("kind")
+    return Geometry(kind, **a), O.Geometry.from_args(args)
+
+
+def _mixed(dtype, direction, seed=0):
+    rng = np.random.default_rng(seed)
+    gs, ins, refs, outs = [], [], [], []
+    for k, (args, b) in enumerate(zip(MIXED, BATCH)):
+        g, og = _geoms(args)
+        if direction == "forward":
+            x = np.stack([ellipse_phantom(g.n, 5, 100 * seed + 10 * k + i) for i in range(b)])
+            xin = to_dev(x, dtype)
+            refs.append(O.forward(og, to_np(xin)))
+            outs.append(torch.empty((b,) + og.sino_shape, dtype=dtype, device="cuda"))
+        else:
+            y = rng.normal(size=(b,) + og.sino_shape)
+            xin = to_dev(y, dtype)
+            refs.append(O.adjoint(og, to_np(xin)))
+            outs.append(torch.empty((b, g.n, g.n), dtype=dtype, device="cuda"))
+        gs.append(g)
+        ins.append(xin)
+    return gs, ins, outs, refs
+
+
+@pytest.mark.parametrize("direction", ["forward", "adjoint"])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16, torch.bfloat16], ids=["f32", "f16", "bf16"])
+def test_plan_matches_oracle(direction, dtype):
+    gs, ins, outs, refs = _mixed(dtype, direction)
+    plan = BatchPlan(list(zip(gs, ins, outs)), direction)
+    plan.launch()
+    torch.cuda.synchronize()
+    for k, (o, r) in enumerate(zip(outs, refs)):
+        if dtype == torch.float32:
+            assert rel_l2(to_np(o), r) <= TOL_F32, k
+        else:
+            assert within_16(to_np(o), r, dtype), (k, rel_l2(to_np(o), r))
+    info = plan.info
+    assert info["units"] == sum(BATCH) and info["work_items"] > 0 and info["direction"] == direction
+    assert info["ctas"] % torch.cuda.get_device_properties(0).multi_processor_count == 0
+    cands = (1, 2, 4, 8) if direction == "forward" else (4, 8, 16)
+    assert all(plan.item_config(k) in cands for k in range(len(gs)))
+
+
+@pytest.mark.parametrize("direction", ["forward", "adjoint"])
+def test_tile_shapes_do_not_change_a_bit(direction):
+    """Every candidate the autotuner may pick computes each output in the same order."""
+    gs, ins, outs, _ = _mixed(torch.float32, direction, seed=3)
+    results = []
+    for v in ((1, 2, 4, 8) if direction == "forward" else (4, 8, 16)):
+        kw = dict(forward_views=v) if direction == "forward" else dict(adjoint_views=v)
+        plan = BatchPlan(list(zip(gs, ins, outs)), direction, autotune=False, **kw)
+        assert all(plan.item_config(k) == v for k in range(len(gs)))
+        plan.launch()
+        torch.cuda.synchronize()
+        results.append([o.clone() for o in outs])
+    for other in results[1:]:
+        for a, b in zip(results[0], other):
+            assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("direction", ["forward", "adjoint"])
+def test_plan_replays_in_a_cuda_graph(direction):
+    gs, ins, outs, _ = _mixed(torch.float16, direction, seed=5)
+    plan = BatchPlan(list(zip(gs, ins, outs)), direction)
+    stream = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        plan.launch()          # warm up on the capture stream
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=stream):
+            plan.launch()
+    for rep in range(2):
+        for t in ins:
+            t.mul_(1.5 if rep == 0 else -0.25)   # new inputs, same buffers
+        graph.replay()
+        torch.cuda.synchronize()
+        got = [o.clone() for o in outs]
+        plan.launch()
+        torch.cuda.synchronize()
+        for a, b in zip(got, outs):
+            assert torch.equal(a, b)
+
+
+def test_empty_and_zero_batch_items():
+    g, _ = _geoms(MIXED[0])
+    x = torch.zeros((0, g.n, g.n), dtype=torch.float32, device="cuda")
+    y = torch.zeros((0,) + g.sino_shape, dtype=torch.float32, device="cuda")
+    plan = BatchPlan([(g, x, y)], "forward")
+    assert plan.info["units"] == 0 and plan.info["work_items"] == 0
+    plan.launch()
+    empty = BatchPlan([], "adjoint")
+    empty.launch()
+    torch.cuda.synchronize()
+
+
+def test_mismatched_items_are_refused():
+    g, _ = _geoms(MIXED[0])
+    x = torch.zeros((1, g.n, g.n), dtype=torch.float32, device="cuda")
+    y16 = torch.zeros((1,) + g.sino_shape, dtype=torch.float16, device="cuda")
+    with pytest.raises(ValueError):
+        BatchPlan([(g, x, y16)], "forward")
+    with pytest.raises(ValueError):
+        BatchPlan([(g, x, torch.zeros((2,) + g.sino_shape, device="cuda"))], "forward")
+
+
+def _full_uneven():
+    w = WORKLOADS["uneven_b64_n128-1024"]
+    items = uneven_items(w)
+    geoms = []
+    for k in range(len(items)):
+        a = workload_geometry_args(w, k)
+        kind = a.pop("kind")
+        geoms.append(Geometry(kind, **a))
+    return w, items, geoms
+
+
+def test_full_uneven_workload_one_item_per_size_against_oracle():
+    """All 64 images (16 each of 128^2 .. 1024^2, own view counts) in one forward plan and one adjoint
+    plan, fp16; for each image size the item with the fewest views is checked whole against the oracle,
+    and every output is finite and non-trivial."""
+    w, items, geoms = _full_uneven()
+    imgs = workload_images(w)
+    xs = [to_dev(x[None], torch.float16) for x in imgs]
+    sinos = [torch.empty((1,) + g.sino_shape, dtype=torch.float16, device="cuda") for g in geoms]
+    fwd = BatchPlan(list(zip(geoms, xs, sinos)), "forward")
+    fwd.launch()
+    # the adjoint's inputs: seeded sinograms drawn on the host (never the GPU's own forward output)
+    rng = np.random.default_rng(6000)
+    ys = [to_dev(rng.uniform(0.0, 1.0, (1,) + g.sino_shape), torch.float16) for g in geoms]
+    backs = [torch.empty((1, g.n, g.n), dtype=torch.float16, device="cuda") for g in geoms]
+    adj = BatchPlan(list(zip(geoms, ys, backs)), "adjoint")
+    adj.launch()
+    torch.cuda.synchronize()
+    for k in range(len(items)):
+        assert torch.isfinite(sinos[k]).all() and torch.isfinite(backs[k]).all()
+    for n in w.extra["sizes"]:
+        ks = [k for k in range(len(items)) if items[k]["n"] == n]
+        k = min(ks, key=lambda i: items[i]["n_views"])
+        og = O.Geometry.from_args(workload_geometry_args(w, k))
+        ref_y = O.forward(og, to_np(xs[k]))
+        assert rel_l2(to_np(sinos[k]), ref_y) <= TOL_16, (n, k)
+        ref_x = O.adjoint(og, to_np(ys[k]))
+        assert rel_l2(to_np(backs[k]), ref_x) <= TOL_16, (n, k)
