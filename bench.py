@@ -118,6 +118,37 @@ def _rel_l2(a, b):
 ADJ_OPS_PER_SAMPLE = 18
 
 
+def max_over_ranks(values, device=None):
+    """Element-wise maximum of ``values`` over the ranks of the default process group (if any)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_value(units_per_rank_step, world, ms_per_step):
+    """Units all ranks processed per second: every rank runs its own replica of the step (weak
+    scaling), and the step time is the slowest rank's."""
+    return units_per_rank_step * world / (ms_per_step * 1e-3)
+
+
+def workload_config(workload, storage, algo, geom=None):
+    """The ``config`` object of the JSON line (both arms): the workload and its geometry."""
+    from paper_2009_14788_gb300 import Geometry
+    w = WORKLOADS[workload]
+    if geom is None:
+        gargs = workload_geometry_args(w)
+        kind = gargs.pop("kind")
+        geom = Geometry(kind, host_only=True, **gargs)
+    return {"workload": workload, "geometry": geom.kind, "batch": w.batch, "n": geom.n, "views": geom.n_angles,
+            "det_count": geom.det_count, "det_spacing": geom.det_spacing, "source_distance": geom.source_distance,
+            "det_distance": geom.det_distance, "storage": storage, "algo": algo,
+            "samples_per_image": geom.sample_count,
+            "parallelism": "replica per GPU (batch sharding, no exchange)"}
+
+
 def roofline(samples, ms, sm_count, per_sm, clk_mhz, basis, traffic):
     """Achieved vs peak bilinear samples/s of one kernel (``alu``: an on-chip pipe bounds it)."""
     peak = sm_count * per_sm * clk_mhz * 1e6 / 1e9
@@ -250,13 +281,10 @@ def run_ours(args):
     d2h = hox[0].numel() * hox[0].element_size() + hoy[0].numel() * hoy[0].element_size()
 
     # max over ranks
-    t = torch.tensor([total_ms, e2e_ms], device="cuda", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms, e2e_ms = float(t[0]), float(t[1])
+    total_ms, e2e_ms = max_over_ranks([total_ms, e2e_ms], device="cuda")
     ms_per_step = total_ms / args.steps
     samples_per_step = 2 * B * S
-    value = samples_per_step * world / (ms_per_step * 1e-3)
+    value = whole_job_value(samples_per_step, world, ms_per_step)
 
     mean_fwd = statistics.mean(fwd_ms)
     mean_adj = statistics.mean(adj_ms)
@@ -308,12 +336,9 @@ def run_ours(args):
             "vs_baseline": None,
             "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": args.workload, "geometry": kind, "batch": B, "n": geom.n,
-                       "views": geom.n_angles, "det_count": geom.det_count, "det_spacing": geom.det_spacing,
-                       "source_distance": geom.source_distance, "det_distance": geom.det_distance,
-                       "storage": args.storage, "algo": args.algo, "samples_per_image": S,
-                       "l2": "rotating %d input/output sets, %.0f MB total (> 2x L2)" % (n_sets, n_sets * bytes_per_set / 2**20),
-                       "parallelism": "replica per GPU (batch sharding, no exchange)"},
+            "config": dict(workload_config(args.workload, args.storage, args.algo, geom),
+                           l2="rotating %d input/output sets, %.0f MB total (> 2x L2)" % (
+                               n_sets, n_sets * bytes_per_set / 2**20)),
             "images_per_s": B * world / (ms_per_step * 1e-3),
             "fwd_ms": mean_fwd,
             "adj_ms": mean_adj,
@@ -323,7 +348,7 @@ def run_ours(args):
             "roofline": dict(rooflines[dom], kernel=dom),
             "roofline_forward": rooflines["forward"],
             "roofline_backward": rooflines["backward"],
-            "e2e": {"value": samples_per_step * world / (e2e_ms * 1e-3), "unit": "samples/s",
+            "e2e": {"value": whole_job_value(samples_per_step, world, e2e_ms), "unit": "samples/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": launches["count"],
             "clocks": clk,
@@ -600,7 +625,8 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": args.workload, "sample": "every %d-th view" % stride},
+            "config": dict(workload_config(args.workload, args.storage, args.algo),
+                           sample="every %d-th view" % stride),
             "cpu_baseline": {"value": value, "unit": "samples/s", "cores": O.num_threads(), "kind": "oracle",
                              "sample": "fwd + adjoint of all %d images on every %d-th view (%d of %d views) per step"
                                        % (x.shape[0], stride, g.n_angles, w.n_views)},
