@@ -16,6 +16,7 @@ cores on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -301,6 +302,9 @@ def run_ours(args):
                 traffic_tab = json.load(f).get(args.workload, {}).get(args.storage, {})
         except (OSError, ValueError):
             traffic_tab = {}
+    probe = ctypes.c_double(0.0)
+    L.check(L.radon_probe_gather_ceiling(L.RADON_F32 if args.storage == "f32" else L.RADON_F16, ctypes.byref(probe)),
+            "radon_probe_gather_ceiling")
     rooflines = {
         # forward: 4 texels per sample through the shared-memory / L1 load pipe, 128 B/clk/SM
         "forward": roofline(B * S, mean_fwd, sm_count, 128.0 / (4.0 * bytes_per_texel), clk_mhz,
@@ -314,6 +318,8 @@ def run_ours(args):
                              traffic_tab.get("backward")),
     }
 
+    rooflines["forward"]["probe_ceiling"] = probe.value / 1e9
+    rooflines["forward"]["frac_of_probe"] = rooflines["forward"]["achieved"] / (probe.value / 1e9)
     secondary = None
     if rank == 0 and world == 1 and not args.no_secondary:
         secondary = run_secondary(args)

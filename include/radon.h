@@ -55,7 +55,7 @@
 extern "C" {
 #endif
 
-#define RADON_ABI_VERSION 1
+#define RADON_ABI_VERSION 2
 
 #if defined(__GNUC__)
 #define RADON_API __attribute__((visibility("default")))
@@ -186,7 +186,18 @@ RADON_API radon_status radon_forward(const radon_geometry* geometry, const void*
 RADON_API radon_status radon_backward(const radon_geometry* geometry, const void* sino, void* img, radon_dtype dtype,
                             int batch, void* stream);
 
-/* Explicit kernel selection (comparison forms and the autotuner). */
+/*
+ * Explicit kernel selection (comparison forms and the autotuner).
+ *
+ * `weights` selects the forward projection's bilinear-weight precision for FP16 storage (Section
+ * 3.3's half-precision path): 0 (default) rounds each sample's four weights to FP16 and forms every
+ * product of a weight and a texel value exactly in one mixed-precision FMA accumulated in FP32 --
+ * nothing converts the texel values, which makes the inner loop bound by the shared-memory load pipe;
+ * the weight rounding (relative <= 2^-12 per weight) shifts a ray sum by at most ~1e-4 of its size,
+ * below FP16's own output rounding.  1 keeps FP32 weights (texel values converted to FP32, FP32 FMAs),
+ * the paper's all-single-precision arithmetic.  BF16 and FP32 storage always use FP32 weights, and so
+ * does every fused call whose epilogue has an addend (the Landweber residual keeps its own precision).
+ */
 typedef struct {
     int algo;            /* radon_algo */
     int views_per_cta;   /* TILED forward: views per CTA (0 = default) */
@@ -194,6 +205,7 @@ typedef struct {
     int images_per_cta;  /* TILED: images sharing the geometry work in one CTA (0 = default) */
     int tile;            /* TILED backward: pixel tile side (0 = default) */
     int threads;         /* threads per CTA (0 = default) */
+    int weights;         /* forward, FP16 storage: 0 = FP16 weights (default), 1 = FP32 weights */
 } radon_launch_config;
 
 RADON_API radon_status radon_forward_ex(const radon_geometry* geometry, const void* img, void* sino, radon_dtype dtype,
@@ -407,6 +419,16 @@ RADON_API radon_status radon_batch_plan_get_info(const radon_plan* plan, radon_p
 RADON_API radon_status radon_batch_plan_item_config(const radon_plan* plan, int item, int* views);
 
 RADON_API void radon_batch_plan_destroy(radon_plan* plan);
+
+/*
+ * Measures the achievable rate of the forward projection's inner loop on the current GPU: a kernel
+ * that marches straight rays through a shared-memory-resident tile of batch-interleaved texels (four
+ * 16-byte loads, one floor / weight evaluation and FP32 accumulation for every image of the texel per
+ * sample, no geometry, no TMA) on every SM.  *samples_per_second receives image-samples per second
+ * (one probe sample serves the 8 (F16; BF16 costs the same) or 4 (F32) images of a texel), the
+ * ceiling the forward's measured rate is compared with.  Synchronises the device; not capturable.
+ */
+RADON_API radon_status radon_probe_gather_ceiling(radon_dtype dtype, double* samples_per_second);
 
 /*
  * Number of kernels this library has launched in this process so far (every pack, projection and

@@ -73,6 +73,7 @@ class radon_launch_config(ctypes.Structure):
         ("images_per_cta", ctypes.c_int),
         ("tile", ctypes.c_int),
         ("threads", ctypes.c_int),
+        ("weights", ctypes.c_int),
     ]
 
 
@@ -171,6 +172,7 @@ _SIGNATURES = [
     ("radon_batch_plan_get_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(radon_plan_info)]),
     ("radon_batch_plan_item_config", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("radon_batch_plan_destroy", None, [ctypes.c_void_p]),
+    ("radon_probe_gather_ceiling", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     ("radon_kernel_launch_count", ctypes.c_uint64, []),
     ("radon_get_device_error", ctypes.c_int, [ctypes.c_void_p]),
     ("radon_status_string", ctypes.c_char_p, [ctypes.c_int]),
@@ -332,6 +334,10 @@ def radon_batch_plan_item_config(plan, item, views_ptr):
 
 def radon_batch_plan_destroy(plan):
     return _call("radon_batch_plan_destroy", plan)
+
+
+def radon_probe_gather_ceiling(dtype, out_ptr):
+    return _call("radon_probe_gather_ceiling", dtype, out_ptr)
 
 
 def radon_kernel_launch_count():

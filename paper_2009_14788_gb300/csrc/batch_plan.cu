@@ -179,7 +179,8 @@ __device__ float plan_ray(const Unit& u, const typename Quad<T>::type* __restric
             const float a = fminf(fmaxf(lx - (float)(j - jb), 0.0f), 1.0f);
             const float b = fminf(fmaxf(ly - (float)(i - ib), 0.0f), 1.0f);
             float t[4];
-            Quad<T>::unpack(q[(long long)(i + 1) * p + (j + 1)], t);
+            const typename Quad<T>::type tex = __ldg(q + (long long)(i + 1) * p + (j + 1));   // one 8/16-byte load
+            Quad<T>::unpack(tex, t);
             const float top = fmaf(a, t[1] - t[0], t[0]), bot = fmaf(a, t[3] - t[2], t[2]);
             acc += fmaf(b, bot - top, top);
         }

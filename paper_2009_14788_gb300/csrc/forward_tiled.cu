@@ -10,10 +10,16 @@ namespace {
 
 constexpr uint32_t kSpinLimit = 1u << 22;   // bounded mbarrier polls (~seconds) before giving up
 
-template <typename T>
+// FP16 storage takes FP16 weights in mixed-precision FMAs unless the config asks for FP32 weights or
+// the epilogue adds to the projection (a fused residual keeps its own precision).
+bool fp16_weights(const radon_launch_config* cfg, const Epilogue& ep) {
+    return !(cfg != nullptr && cfg->weights == 1) && ep.add == nullptr;
+}
+
+template <typename T, bool MIXED>
 cudaError_t launch_t(const CUtensorMap& mv, const CUtensorMap& mh, const FwdTiledArgs& a, dim3 grid, size_t smem,
                      cudaStream_t s) {
-    auto kern = forward_tiled_kernel<T>;
+    auto kern = forward_tiled_kernel<T, MIXED>;
     static size_t attr_bytes = 0;
     if (smem > attr_bytes) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -58,7 +64,7 @@ radon_status launch_forward_tiled(radon_geometry* g, const void* img, void* sino
         *why = "working band wider than a TMA box";
         return RADON_ERR_UNSUPPORTED;
     }
-    const int wc = wbox + ((2 - wbox % 8) + 8) % 8;   // row pitch = 2 (mod 8) texels spreads banks
+    const int wc = (wbox + 7) / 8 * 8;   // row pitch = 0 (mod 8) texels: fewest shared-memory bank conflicts
     const int stage_bytes = std::max(wbox * (R + 2) * 16, rbox_h * wbox * 16);
     const size_t smem = fwd_smem_bytes(stage_bytes, R, wc);
     if (smem > 227 * 1024) {
@@ -108,6 +114,7 @@ radon_status launch_forward_tiled(radon_geometry* g, const void* img, void* sino
         return RADON_ERR_CUDA;
     }
     a.spin_limit = kSpinLimit;
+    a.stages = 2;
     const long long nblk = (long long)g->group_count[gi] * a.n_dr;
     if (nblk > 0x7fffffffLL) {
         *why = "too many CTAs";
@@ -116,9 +123,12 @@ radon_status launch_forward_tiled(radon_geometry* g, const void* img, void* sino
     dim3 grid((unsigned)nblk, (unsigned)((batch + BG - 1) / BG));
     cudaError_t e;
     switch (dt) {
-        case RADON_F16: e = launch_t<__half>(mv, mh, a, grid, smem, s); break;
-        case RADON_BF16: e = launch_t<__nv_bfloat16>(mv, mh, a, grid, smem, s); break;
-        default: e = launch_t<float>(mv, mh, a, grid, smem, s); break;
+        case RADON_F16:
+            e = fp16_weights(cfg, ep) ? launch_t<__half, true>(mv, mh, a, grid, smem, s)
+                                      : launch_t<__half, false>(mv, mh, a, grid, smem, s);
+            break;
+        case RADON_BF16: e = launch_t<__nv_bfloat16, false>(mv, mh, a, grid, smem, s); break;
+        default: e = launch_t<float, false>(mv, mh, a, grid, smem, s); break;
     }
     if (e != cudaSuccess) {
         *why = std::string("tiled forward launch: ") + cudaGetErrorString(e);
@@ -133,10 +143,10 @@ namespace radon {
 
 namespace {
 
-template <typename T>
+template <typename T, bool MIXED>
 cudaError_t launch_packed_t(const CUtensorMap& mr, const CUtensorMap& mc, const FwdTiledArgs& a, dim3 grid,
                             size_t smem, cudaStream_t s) {
-    auto kern = forward_packed_kernel<T>;
+    auto kern = forward_packed_kernel<T, MIXED>;
     static size_t attr_bytes = 0;
     if (smem > attr_bytes) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -171,12 +181,15 @@ radon_status launch_forward_packed(radon_geometry* g, const void* packed, void* 
     }
     const int maxw = forward_band_width(g, G, Dt, R);
     int wbox = maxw + 2;
-    wbox += ((2 - wbox % 8) + 8) % 8;   // row pitch = 2 (mod 8) texels spreads shared-memory banks
+    wbox = (wbox + 7) / 8 * 8;   // row pitch = 0 (mod 8) texels: fewest shared-memory bank conflicts (measured)
     if (wbox > 256) {
         *why = "working band wider than a TMA box";
         return RADON_ERR_UNSUPPORTED;
     }
-    const size_t smem = fwd_packed_smem_bytes(R, wbox);
+    // As many ring stages (up to 4) as keep three CTAs resident per SM (3 x (smem + 1 KB) <= 228 KB).
+    int stages = 2;
+    while (stages < kFwdMaxStages && fwd_packed_smem_bytes(R, wbox, stages + 1) <= 75 * 1024) ++stages;
+    const size_t smem = fwd_packed_smem_bytes(R, wbox, stages);
     if (smem > 227 * 1024) {
         *why = "shared memory budget exceeded";
         return RADON_ERR_UNSUPPORTED;
@@ -227,13 +240,17 @@ radon_status launch_forward_packed(radon_geometry* g, const void* packed, void* 
         return RADON_ERR_CUDA;
     }
     a.spin_limit = kSpinLimit;
+    a.stages = stages;
     const long long nblk = (long long)g->group_count[gi] * a.n_dr;
     dim3 grid((unsigned)nblk, (unsigned)groups);
     cudaError_t e;
     switch (dt) {
-        case RADON_F16: e = launch_packed_t<__half>(mr, mc, a, grid, smem, s); break;
-        case RADON_BF16: e = launch_packed_t<__nv_bfloat16>(mr, mc, a, grid, smem, s); break;
-        default: e = launch_packed_t<float>(mr, mc, a, grid, smem, s); break;
+        case RADON_F16:
+            e = fp16_weights(cfg, ep) ? launch_packed_t<__half, true>(mr, mc, a, grid, smem, s)
+                                      : launch_packed_t<__half, false>(mr, mc, a, grid, smem, s);
+            break;
+        case RADON_BF16: e = launch_packed_t<__nv_bfloat16, false>(mr, mc, a, grid, smem, s); break;
+        default: e = launch_packed_t<float, false>(mr, mc, a, grid, smem, s); break;
     }
     if (e != cudaSuccess) {
         *why = std::string("packed forward launch: ") + cudaGetErrorString(e);

@@ -51,12 +51,15 @@ struct FwdTiledArgs {
     int* err;
     uint32_t spin_limit;
     Epilogue ep;
+    int stages;           // compute buffers in the ring (packed: 2..4; repacking: 2)
 };
+
+constexpr int kFwdMaxStages = 4;
 
 __host__ __device__ inline size_t fwd_comp_bytes(int R, int wc) { return (size_t)(R + 2) * wc * 16; }
 
-__host__ __device__ inline size_t fwd_packed_smem_bytes(int R, int wbox) {
-    return 128 + 128 + 2 * ((fwd_comp_bytes(R, wbox) + 127) / 128 * 128);
+__host__ __device__ inline size_t fwd_packed_smem_bytes(int R, int wbox, int stages) {
+    return 128 + 128 + (size_t)stages * ((fwd_comp_bytes(R, wbox) + 127) / 128 * 128);
 }
 
 __host__ __device__ inline size_t fwd_smem_bytes(int stage_bytes, int R, int wc) {
@@ -64,13 +67,19 @@ __host__ __device__ inline size_t fwd_smem_bytes(int stage_bytes, int R, int wc)
 }
 
 // 16-byte texel: BG values of one pixel (element b = image b), accumulated with weight w.
-template <typename T>
+// MIXED (FP16 storage only): the weight is rounded once to FP16 and each product of two FP16 values
+// is formed exactly and added in FP32 by one mixed-precision FMA (fma.rn.f32.f16), so nothing converts
+// the texel values and the inner loop is bound by the shared-memory load pipe; the weight's rounding
+// (relative <= 2^-12) is the only change.  Otherwise FP32 weights and FP32 FMAs on converted values.
+template <typename T, bool MIXED = false>
 struct Texel;
 
 template <>
-struct Texel<float> {
+struct Texel<float, false> {
     static constexpr int BG = 4;
-    __device__ __forceinline__ static void fma(float* acc, float w, const uint4& t) {
+    using W = float;
+    __device__ __forceinline__ static W weight(float w) { return w; }
+    __device__ __forceinline__ static void fma(float* acc, W w, const uint4& t) {
         acc[0] = fmaf(w, __uint_as_float(t.x), acc[0]);
         acc[1] = fmaf(w, __uint_as_float(t.y), acc[1]);
         acc[2] = fmaf(w, __uint_as_float(t.z), acc[2]);
@@ -79,16 +88,41 @@ struct Texel<float> {
 };
 
 template <>
-struct Texel<__half> {
+struct Texel<__half, false> {
     static constexpr int BG = 8;
-    __device__ __forceinline__ static void fma2(float* acc, float w, unsigned u) {
+    using W = float;
+    __device__ __forceinline__ static W weight(float w) { return w; }
+    __device__ __forceinline__ static void fma2(float* acc, W w, unsigned u) {
         __half2 h2;
         memcpy(&h2, &u, 4);
         const float2 f = __half22float2(h2);
         acc[0] = fmaf(w, f.x, acc[0]);
         acc[1] = fmaf(w, f.y, acc[1]);
     }
-    __device__ __forceinline__ static void fma(float* acc, float w, const uint4& t) {
+    __device__ __forceinline__ static void fma(float* acc, W w, const uint4& t) {
+        fma2(acc, w, t.x);
+        fma2(acc + 2, w, t.y);
+        fma2(acc + 4, w, t.z);
+        fma2(acc + 6, w, t.w);
+    }
+};
+
+__device__ __forceinline__ float mixed_fma_f16(unsigned short w, unsigned short q, float c) {
+    float d;
+    asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(d) : "h"(w), "h"(q), "f"(c));
+    return d;
+}
+
+template <>
+struct Texel<__half, true> {
+    static constexpr int BG = 8;
+    using W = unsigned short;
+    __device__ __forceinline__ static W weight(float w) { return __half_as_ushort(__float2half_rn(w)); }
+    __device__ __forceinline__ static void fma2(float* acc, W w, unsigned u) {
+        acc[0] = mixed_fma_f16(w, (unsigned short)(u & 0xffffu), acc[0]);
+        acc[1] = mixed_fma_f16(w, (unsigned short)(u >> 16), acc[1]);
+    }
+    __device__ __forceinline__ static void fma(float* acc, W w, const uint4& t) {
         fma2(acc, w, t.x);
         fma2(acc + 2, w, t.y);
         fma2(acc + 4, w, t.z);
@@ -97,13 +131,15 @@ struct Texel<__half> {
 };
 
 template <>
-struct Texel<__nv_bfloat16> {
+struct Texel<__nv_bfloat16, false> {
     static constexpr int BG = 8;
-    __device__ __forceinline__ static void fma2(float* acc, float w, unsigned u) {
+    using W = float;
+    __device__ __forceinline__ static W weight(float w) { return w; }
+    __device__ __forceinline__ static void fma2(float* acc, W w, unsigned u) {
         acc[0] = fmaf(w, __uint_as_float(u << 16), acc[0]);
         acc[1] = fmaf(w, __uint_as_float(u & 0xffff0000u), acc[1]);
     }
-    __device__ __forceinline__ static void fma(float* acc, float w, const uint4& t) {
+    __device__ __forceinline__ static void fma(float* acc, W w, const uint4& t) {
         fma2(acc, w, t.x);
         fma2(acc + 2, w, t.y);
         fma2(acc + 4, w, t.z);
@@ -117,28 +153,43 @@ struct FwdBand {
     int bad;    // the band exceeded wbox (recorded; rays outside it are skipped)
 };
 
-// Producer warp: band of slab s (every lane returns it): the columns crossed by the lines of the
-// CTA's extreme rays over the slab's buffer rows (+-1 row), clamped to the support, 2 columns of
-// margin.  `align_x` aligns the start (TMA needs 16-byte aligned starts along the innermost axis).
-__device__ __forceinline__ FwdBand fwd_band(const FwdTiledArgs& a, int s, int v0, int cnt, int cls, int d0,
-                                            int align_x) {
+// Producer warp: the lines of the CTA's extreme rays (the first and last detector of each view), one
+// per lane in the compute frame, loaded once per CTA: the band of every slab follows from them.
+struct FwdEdge {
+    float X0, Y0, sl;   // a point of the line and its slope dX / dY
+    bool valid, flat;   // flat: the line runs along the slab rows (covers the whole support)
+};
+
+__device__ __forceinline__ FwdEdge fwd_edge(const FwdTiledArgs& a, int v0, int cnt, int cls, int d0) {
     const int lane = threadIdx.x & 31;
-    const int ylo = -4 + s * a.R, yhi = ylo + a.R + 1;   // buffer rows [ylo, yhi]
-    float lo = 3.0e38f, hi = -3.0e38f;
+    FwdEdge e{0.f, 0.f, 0.f, false, false};
     if (lane < 2 * cnt) {
         const int vl = lane >> 1;
         const int d = (lane & 1) ? min(d0 + a.Dt - 1, a.D - 1) : d0;
         const RayT r = a.rays[(long long)(v0 + vl) * a.D + d];
-        const float X0 = cls ? (float)r.I0 + r.fy0 : (float)r.J0 + r.fx0;
-        const float Y0 = cls ? (float)r.J0 + r.fx0 : (float)r.I0 + r.fy0;
+        e.X0 = cls ? (float)r.I0 + r.fy0 : (float)r.J0 + r.fx0;
+        e.Y0 = cls ? (float)r.J0 + r.fx0 : (float)r.I0 + r.fy0;
         const float dX = cls ? r.dyh + r.dyl : r.dxh + r.dxl;
         const float dY = cls ? r.dxh + r.dxl : r.dyh + r.dyl;
-        if (fabsf(dY) <= 1e-6f * fabsf(dX)) {
+        e.flat = fabsf(dY) <= 1e-6f * fabsf(dX);
+        e.sl = e.flat ? 0.0f : dX / dY;
+        e.valid = true;
+    }
+    return e;
+}
+
+// Producer warp: band of slab s (every lane returns it): the columns crossed by the lines of the
+// CTA's extreme rays over the slab's buffer rows (+-1 row), clamped to the support, 2 columns of
+// margin.  `align_x` aligns the start (TMA needs 16-byte aligned starts along the innermost axis).
+__device__ __forceinline__ FwdBand fwd_band(const FwdTiledArgs& a, const FwdEdge& e, int s, int align_x) {
+    const int ylo = -4 + s * a.R, yhi = ylo + a.R + 1;   // buffer rows [ylo, yhi]
+    float lo = 3.0e38f, hi = -3.0e38f;
+    if (e.valid) {
+        if (e.flat) {
             lo = -3.0f;
             hi = (float)a.n + 2.0f;
         } else {
-            const float sl = dX / dY;
-            const float xa = fmaf((float)(ylo - 1) - Y0, sl, X0), xb = fmaf((float)(yhi + 1) - Y0, sl, X0);
+            const float xa = fmaf((float)(ylo - 1) - e.Y0, e.sl, e.X0), xb = fmaf((float)(yhi + 1) - e.Y0, e.sl, e.X0);
             lo = fminf(xa, xb);
             hi = fmaxf(xa, xb);
         }
@@ -162,10 +213,10 @@ __device__ __forceinline__ FwdBand fwd_band(const FwdTiledArgs& a, int s, int v0
 // Producer warp (repacking pipeline): band of slab s and, from lane 0, its TMA copy into staging.
 template <typename T>
 __device__ FwdBand fwd_issue_slab(const CUtensorMap* map_v, const CUtensorMap* map_h, const FwdTiledArgs& a, int s,
-                                  int v0, int cnt, int cls, int d0, int b0, uint64_t* tma_bar, unsigned char* stage) {
+                                  const FwdEdge& edge, int cls, int b0, uint64_t* tma_bar, unsigned char* stage) {
     const int lane = threadIdx.x & 31;
     const int ylo = -4 + s * a.R;
-    const FwdBand band = fwd_band(a, s, v0, cnt, cls, d0, cls ? 1 : a.align);
+    const FwdBand band = fwd_band(a, edge, s, cls ? 1 : a.align);
     if (lane == 0) {
         fence_proxy_async_shared();
         if (cls == 0) {
@@ -248,11 +299,11 @@ __device__ void fwd_repack(const FwdTiledArgs& a, int cls, int yoff, const unsig
 
 // Consumer warps: one ray per thread, marched slab by slab through the double-buffered compute
 // buffers (texels [row][col][image], row pitch wc), released through `empty` after each slab.
-template <typename T>
+template <typename T, bool MIXED>
 __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int d0, int b0, uint64_t* full,
                             uint64_t* empty, const int* band_xc0, const int* band_bad, volatile int* abort_flag,
                             const unsigned char* comp_base, size_t comp_stride, int wc) {
-    constexpr int BG = Texel<T>::BG;
+    constexpr int BG = Texel<T, false>::BG;
     const int tid = threadIdx.x;
     const int vl = tid / a.Dt, d = d0 + (tid - (tid / a.Dt) * a.Dt);
     const bool active = vl < cnt && d < a.D;
@@ -275,8 +326,8 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
     for (int b = 0; b < BG; ++b) acc[b] = 0.0f;
 
     for (int s = 0; s < a.n_slabs; ++s) {
-        const int buf = s & 1;
-        if (!mbar_wait_bounded(&full[buf], (uint32_t)((s >> 1) & 1), a.spin_limit)) {
+        const int buf = s % a.stages;
+        if (!mbar_wait_bounded(&full[buf], (uint32_t)((s / a.stages) & 1), a.spin_limit)) {
             record_device_error(a.err, RADON_ERR_TIMEOUT);
             return;
         }
@@ -326,10 +377,11 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
                         const uint4 q00 = p[0], q01 = p[1], q10 = p[wcu], q11 = p[wcu + 1];
                         const float ax = fxm - (tx - M), ay = fym - (ty - M);   // in [-1/2, 1/2]
                         const float wx1 = 0.5f + ax, wx0 = 0.5f - ax, wy1 = 0.5f + ay, wy0 = 0.5f - ay;
-                        Texel<T>::fma(acc, wx0 * wy0, q00);
-                        Texel<T>::fma(acc, wx1 * wy0, q01);
-                        Texel<T>::fma(acc, wx0 * wy1, q10);
-                        Texel<T>::fma(acc, wx1 * wy1, q11);
+                        using TX = Texel<T, MIXED>;
+                        TX::fma(acc, TX::weight(wx0 * wy0), q00);
+                        TX::fma(acc, TX::weight(wx1 * wy0), q01);
+                        TX::fma(acc, TX::weight(wx0 * wy1), q10);
+                        TX::fma(acc, TX::weight(wx1 * wy1), q11);
                     }
                     k += i;
                 }
@@ -350,11 +402,11 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
     }
 }
 
-template <typename T>
+template <typename T, bool MIXED>
 __global__ void __launch_bounds__(kFwdThreads, 3) forward_tiled_kernel(const __grid_constant__ CUtensorMap map_v,
                                                                       const __grid_constant__ CUtensorMap map_h,
                                                                       const FwdTiledArgs a) {
-    constexpr int BG = Texel<T>::BG;
+    constexpr int BG = Texel<T, false>::BG;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
     uint64_t* tma_bar = reinterpret_cast<uint64_t*>(smem);
@@ -389,7 +441,8 @@ __global__ void __launch_bounds__(kFwdThreads, 3) forward_tiled_kernel(const __g
     if (warp == kFwdConsumerWarps) {
         // ------------------------------------------------------------------ producer warp
         const int lane = tid & 31;
-        FwdBand band = fwd_issue_slab<T>(&map_v, &map_h, a, 0, v0, cnt, cls, d0, b0, tma_bar, stage);
+        const FwdEdge edge = fwd_edge(a, v0, cnt, cls, d0);
+        FwdBand band = fwd_issue_slab<T>(&map_v, &map_h, a, 0, edge, cls, b0, tma_bar, stage);
         for (int s = 0; s < a.n_slabs; ++s) {
             const int buf = s & 1;
             bool ok = true;
@@ -416,29 +469,29 @@ __global__ void __launch_bounds__(kFwdThreads, 3) forward_tiled_kernel(const __g
             __syncwarp();
             mbar_arrive(&full[buf]);        // every lane: its repacked texels are released
             if (s + 1 < a.n_slabs)
-                band = fwd_issue_slab<T>(&map_v, &map_h, a, s + 1, v0, cnt, cls, d0, b0, tma_bar, stage);
+                band = fwd_issue_slab<T>(&map_v, &map_h, a, s + 1, edge, cls, b0, tma_bar, stage);
         }
         return;
     }
 
-    fwd_consume<T>(a, cls, v0, cnt, d0, b0, full, empty, band_xc0, band_bad, abort_flag, comp_base, comp_stride,
+    fwd_consume<T, MIXED>(a, cls, v0, cnt, d0, b0, full, empty, band_xc0, band_bad, abort_flag, comp_base, comp_stride,
                    a.wc);
 }
 
 // Packed variant: the image batch was packed once into 16-byte texels (rows / cols copies, see
 // pack.cu), so the producer warp only bounds each band and copies it with one 4-D TMA load straight
 // into the compute buffer it will become (row pitch = band width); no staging, no repack.
-template <typename T>
+template <typename T, bool MIXED>
 __global__ void __launch_bounds__(kFwdThreads, 3) forward_packed_kernel(const __grid_constant__ CUtensorMap map_rows,
                                                                        const __grid_constant__ CUtensorMap map_cols,
                                                                        const FwdTiledArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + 8);    // [2]: TMA completion
-    uint64_t* empty = reinterpret_cast<uint64_t*>(smem + 24);  // [2]: consumers released
-    int* band_xc0 = reinterpret_cast<int*>(smem + 40);          // [2]
-    int* band_bad = reinterpret_cast<int*>(smem + 48);          // [2]
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 56);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);         // [stages]: TMA completion
+    uint64_t* empty = reinterpret_cast<uint64_t*>(smem + 32);   // [stages]: consumers released
+    int* band_xc0 = reinterpret_cast<int*>(smem + 64);          // [stages]
+    int* band_bad = reinterpret_cast<int*>(smem + 80);          // [stages]
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 96);
     const size_t comp_stride = (fwd_comp_bytes(a.R, a.wbox) + 127) / 128 * 128;
     unsigned char* comp_base = smem + 128;
 
@@ -448,26 +501,26 @@ __global__ void __launch_bounds__(kFwdThreads, 3) forward_packed_kernel(const __
     const Int2 grp = a.groups[grp_idx];
     const int v0 = grp.x, cnt = grp.y & 0xffff, cls = grp.y >> 16;
     const int d0 = dr * a.Dt;
-    const int b0 = blockIdx.y * Texel<T>::BG;
+    const int b0 = blockIdx.y * Texel<T, false>::BG;
 
-    if (tid == 0) {
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
-        mbar_init(&empty[0], kFwdRays);
-        mbar_init(&empty[1], kFwdRays);
-        *abort_flag = 0;
-        fence_mbar_init();
+    if (tid < a.stages) {
+        mbar_init(&full[tid], 1);
+        mbar_init(&empty[tid], kFwdRays);
     }
+    if (tid == 0) *abort_flag = 0;
+    fence_mbar_init();
     __syncthreads();
 
     if (warp == kFwdConsumerWarps) {
         const int lane = tid & 31;
         const CUtensorMap* map = cls ? &map_cols : &map_rows;
+        const FwdEdge edge = fwd_edge(a, v0, cnt, cls, d0);
         for (int s = 0; s < a.n_slabs; ++s) {
-            const int buf = s & 1;
-            const FwdBand band = fwd_band(a, s, v0, cnt, cls, d0, 1);
+            const int buf = s % a.stages;
+            const FwdBand band = fwd_band(a, edge, s, 1);
             bool ok = true;
-            if (s >= 2 && lane == 0) ok = mbar_wait_bounded(&empty[buf], (uint32_t)(((s >> 1) - 1) & 1), a.spin_limit);
+            if (s >= a.stages && lane == 0)
+                ok = mbar_wait_bounded(&empty[buf], (uint32_t)((s / a.stages - 1) & 1), a.spin_limit);
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (lane == 0) {
                 if (!ok) {
@@ -488,7 +541,7 @@ __global__ void __launch_bounds__(kFwdThreads, 3) forward_packed_kernel(const __
         }
         return;
     }
-    fwd_consume<T>(a, cls, v0, cnt, d0, b0, full, empty, band_xc0, band_bad, abort_flag, comp_base, comp_stride,
+    fwd_consume<T, MIXED>(a, cls, v0, cnt, d0, b0, full, empty, band_xc0, band_bad, abort_flag, comp_base, comp_stride,
                    a.wbox);
 }
 

@@ -1,0 +1,112 @@
+// Gather-ceiling probe: the forward projection's inner loop with the geometry taken away.
+//
+// Every CTA fills a shared-memory tile of batch-interleaved texels (the packed forward's layout:
+// 16 bytes = 8 16-bit or 4 FP32 images per texel), then each thread marches a straight "ray" through
+// it -- per sample one position, one floor / weight evaluation, four 16-byte shared loads of the
+// 2 x 2 texels and the forward consumers' own accumulation code (Texel<T>) for every image of the
+// texel -- the work the forward kernel's consumers do per sample, minus ray tables, TMA and slabs.  Its sample rate is the
+// achievable ceiling of that inner loop on this GPU, the denominator the measured forward rate is
+// compared with beside the nominal load-pipe figure.
+#include <cmath>
+#include <type_traits>
+
+#include "dtype.cuh"
+#include "forward_tiled.cuh"
+#include "radon_internal.h"
+
+namespace radon {
+
+namespace {
+
+constexpr int kProbeThreads = 256;
+constexpr int kProbeTile = 64;          // texels per row
+constexpr int kProbeRows = 40;          // rows (40 KB of texels)
+constexpr int kProbeSamples = 4096;     // samples per thread
+
+template <typename T>
+__global__ void __launch_bounds__(kProbeThreads) probe_kernel(float* sink) {
+    using TX = Texel<T, std::is_same<T, __half>::value>;   // the forward's default per storage type
+    constexpr int BG = TX::BG;
+    __shared__ uint4 tile[kProbeTile * kProbeRows];
+    for (int e = threadIdx.x; e < kProbeTile * kProbeRows; e += kProbeThreads) {
+        const unsigned v = 0x3c003c00u ^ (unsigned)(e * 2654435761u & 0x03ff03ffu);   // finite 16-bit or FP32 bits
+        tile[e] = make_uint4(v, v ^ 0x00010001u, v ^ 0x00020002u, v ^ 0x00030003u);
+    }
+    __syncthreads();
+    // a warp = 32 parallel rays one pixel apart, as the forward's warps hold neighbouring detectors of
+    // one view: direction (sin a, cos a), a in [0, pi/4) per warp; lane l starts at (2 + l + 0.3, 2.2)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float ang = 0.7853982f * (float)((warp * 37 + blockIdx.x * 11) & 63) / 64.0f;
+    const float dx = sinf(ang) * 0.55f, dy = cosf(ang) * 0.55f;   // x < 2.3 + 31 + 21.4 + 1 < 64, y < 2.2 + 30.3 + 1 < 40
+    const float x0 = 2.3f + (float)lane, y0 = 2.2f;
+    float acc[BG];
+#pragma unroll
+    for (int b = 0; b < BG; ++b) acc[b] = 0.0f;
+    for (int k = 0; k < kProbeSamples; ++k) {
+        // positions wrap inside the tile interior every 56 samples (no geometry, no bounds checks)
+        const float kk = (float)(k % 56);
+        const float fx = fmaf(kk, dx, x0), fy = fmaf(kk, dy, y0);
+        const float flx = floorf(fx), fly = floorf(fy);
+        const float ax = fx - flx, ay = fy - fly;
+        const int idx = (int)fly * kProbeTile + (int)flx;
+        const uint4 q00 = tile[idx], q01 = tile[idx + 1], q10 = tile[idx + kProbeTile], q11 = tile[idx + kProbeTile + 1];
+        const float wx1 = ax, wx0 = 1.0f - ax, wy1 = ay, wy0 = 1.0f - ay;
+        // the forward consumers' accumulation (Texel<T>, forward_tiled.cuh), weights rounded as there
+        TX::fma(acc, TX::weight(wx0 * wy0), q00);
+        TX::fma(acc, TX::weight(wx1 * wy0), q01);
+        TX::fma(acc, TX::weight(wx0 * wy1), q10);
+        TX::fma(acc, TX::weight(wx1 * wy1), q11);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int b = 0; b < BG; ++b) s += acc[b];
+    if (s == 1234.5f) sink[0] = s;   // keeps the loop live; never true for these inputs in practice
+}
+
+}  // namespace
+
+}  // namespace radon
+
+using namespace radon;
+
+extern "C" RADON_API radon_status radon_probe_gather_ceiling(radon_dtype dtype, double* samples_per_second) {
+    if (samples_per_second == nullptr) return fail(RADON_ERR_INVALID_ARG, "samples_per_second is NULL");
+    if (dtype != RADON_F32 && dtype != RADON_F16)
+        return fail(RADON_ERR_INVALID_ARG, "the probe takes RADON_F32 or RADON_F16 (BF16 has the F16 cost)");
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = dtype == RADON_F16
+                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, probe_kernel<__half>, kProbeThreads, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, probe_kernel<float>, kProbeThreads, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "probe setup");
+    const int blocks = sms * (per_sm > 0 ? per_sm : 1) * 4;
+    float* sink = nullptr;
+    e = cudaMalloc(&sink, sizeof(float));
+    if (e != cudaSuccess) return fail(RADON_ERR_OOM, "probe allocation failed");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 3.0e38f;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0, 0);
+        if (dtype == RADON_F16) probe_kernel<__half><<<blocks, kProbeThreads>>>(sink);
+        else probe_kernel<float><<<blocks, kProbeThreads>>>(sink);
+        cudaEventRecord(e1, 0);
+        e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;   // the first run warms up
+        count_launches(1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (e != cudaSuccess) return cuda_fail(e, "probe run");
+    // one probe sample covers BG images of the texel, as one forward sample per image does
+    const double bg = dtype == RADON_F16 ? 8.0 : 4.0;
+    *samples_per_second = (double)blocks * kProbeThreads * kProbeSamples * bg / (best * 1e-3);
+    return RADON_OK;
+}

@@ -209,6 +209,8 @@ radon_status project(const radon_geometry* g, const void* in, void* out, radon_d
     const int algo = cfg ? cfg->algo : RADON_ALGO_AUTO;
     if (algo != RADON_ALGO_AUTO && algo != RADON_ALGO_PLAIN && algo != RADON_ALGO_TILED)
         return fail(RADON_ERR_INVALID_ARG, "unknown algo");
+    if (cfg != nullptr && cfg->weights != 0 && cfg->weights != 1)
+        return fail(RADON_ERR_INVALID_ARG, "weights must be 0 (FP16 weights for FP16 storage) or 1 (FP32 weights)");
     const int threads = cfg ? cfg->threads : 0;
     if (threads < 0 || threads > 1024 || (threads % 32) != 0)
         return fail(RADON_ERR_INVALID_ARG, "threads must be 0 or a multiple of 32 up to 1024");
@@ -253,7 +255,7 @@ radon_status project(const radon_geometry* g, const void* in, void* out, radon_d
         bool packed_done = false;
         for (int i = 0; i < (fixed ? 1 : 4); ++i) {
             radon_launch_config c = {RADON_ALGO_TILED, fixed ? cfg->views_per_cta : kViewsPacked[i],
-                                     cfg ? cfg->rows_per_slab : 0, 0, 0, 0};
+                                     cfg ? cfg->rows_per_slab : 0, 0, 0, 0, cfg ? cfg->weights : 0};
             if (!packed_done) {
                 cudaError_t e = launch_pack_images(in, ws, g->n, batch, dt, s);
                 if (e != cudaSuccess) return cuda_fail(e, "pack launch");
@@ -278,7 +280,7 @@ radon_status project(const radon_geometry* g, const void* in, void* out, radon_d
         std::string why;
         for (int i = 0; i < (fixed ? 1 : 4); ++i) {
             radon_launch_config c = {RADON_ALGO_TILED, fixed ? cfg->views_per_cta : kViews[i],
-                                     cfg ? cfg->rows_per_slab : 0, 0, 0, 0};
+                                     cfg ? cfg->rows_per_slab : 0, 0, 0, 0, cfg ? cfg->weights : 0};
             st = launch_forward_tiled(const_cast<radon_geometry*>(g), in, out, dt, batch, &c, ep, s, &why);
             if (st == RADON_OK) {
                 count_launches(1);

@@ -81,7 +81,7 @@ extern "C" RADON_API radon_status radon_forward_static_scratch(const radon_geome
     static const int kViews[4] = {8, 4, 2, 1};
     std::string why;
     for (int i = 0; i < 4; ++i) {
-        radon_launch_config c = {RADON_ALGO_TILED, kViews[i], 0, 0, 0, 0};
+        radon_launch_config c = {RADON_ALGO_TILED, kViews[i], 0, 0, 0, 0, 0};
         st = launch_forward_packed(const_cast<radon_geometry*>(geometry), scratch, sino, dtype, batch, &c,
                                    identity_epilogue(), s, &why);
         if (st == RADON_OK) {

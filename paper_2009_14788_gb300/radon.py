@@ -22,10 +22,12 @@ _DTYPES = {torch.float32: L.RADON_F32, torch.float16: L.RADON_F16, torch.bfloat1
 ALGOS = {"auto": L.RADON_ALGO_AUTO, "plain": L.RADON_ALGO_PLAIN, "tiled": L.RADON_ALGO_TILED}
 
 
-def launch_config(algo="auto", views_per_cta=0, rows_per_slab=0, images_per_cta=0, tile=0, threads=0):
-    """A ``radon_launch_config`` (kernel family and tile parameters; 0 = library default)."""
+def launch_config(algo="auto", views_per_cta=0, rows_per_slab=0, images_per_cta=0, tile=0, threads=0, weights=0):
+    """A ``radon_launch_config`` (kernel family and tile parameters; 0 = library default).
+
+    ``weights=1`` keeps FP32 bilinear weights in the FP16 forward (see include/radon.h)."""
     return L.radon_launch_config(ALGOS[algo] if isinstance(algo, str) else int(algo), views_per_cta, rows_per_slab,
-                                 images_per_cta, tile, threads)
+                                 images_per_cta, tile, threads, weights)
 
 
 class Geometry:

@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol():
     for n in sorted(names):
         assert hasattr(lib, n), n
     assert names == set(L.exported_names())
-    assert L.radon_abi_version() == 1
+    assert L.radon_abi_version() == 2
 
 
 def test_status_strings():
@@ -106,7 +106,7 @@ def test_launch_argument_checks_without_gpu():
     assert st == L.RADON_OK
     buf = (ctypes.c_float * 4)()
     p = ctypes.addressof(buf)
-    cfg = L.radon_launch_config(0, 0, 0, 0, 0, 0)
+    cfg = L.radon_launch_config(0, 0, 0, 0, 0, 0, 0)
     assert L.radon_forward(None, p, p + 4, 0, 1, None) == L.RADON_ERR_INVALID_ARG
     assert L.radon_forward(h, p, p + 4, 7, 1, None) == L.RADON_ERR_INVALID_ARG        # dtype
     assert L.radon_forward(h, p, p + 4, 0, -1, None) == L.RADON_ERR_INVALID_ARG       # batch
@@ -115,6 +115,10 @@ def test_launch_argument_checks_without_gpu():
     cfg.threads = 48
     assert L.radon_forward_ex(h, p, p + 4, 0, 1, ctypes.byref(cfg), None) == L.RADON_ERR_INVALID_ARG
     cfg.threads = 0
+    cfg.weights = 2
+    assert L.radon_forward_ex(h, p, p + 4, 0, 1, ctypes.byref(cfg), None) == L.RADON_ERR_INVALID_ARG
+    assert "weights" in L.radon_last_error_message()
+    cfg.weights = 0
     cfg.algo = 9
     assert L.radon_backward_ex(h, p, p + 4, 0, 1, ctypes.byref(cfg), None) == L.RADON_ERR_INVALID_ARG
     assert L.radon_forward(h, p, p + 4, 0, 1, None) == L.RADON_ERR_INVALID_ARG        # host-only geometry
