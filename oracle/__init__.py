@@ -15,7 +15,11 @@ justification in the design notes):
   to the magnified image width over the detector count,
   ``(S + Ddet) / S * N / D`` (Section 3.1.2; reproduces the worked value 2.0);
 * Landweber iteration ``x <- x - alpha A^T (A x - y)`` (Section 4.2) with the
-  step from a power iteration on ``A^T A`` (Section 4.2), and its reverse mode.
+  step from a power iteration on ``A^T A`` (Section 4.2), and its reverse mode;
+* filtered backprojection (Section 3.1.3): each view's projection is filtered in
+  the frequency domain by the DFT of the zero-padded band-limited ramp kernel of
+  Kak & Slaney, Chapter 3, Eq. 61, times a window, then backprojected with the
+  exact adjoint; the scale pi / V makes ``adjoint(filter_sinogram(A x)) ~ x``.
 
 Parity status of every function is pinned by tests in ``tests/test_oracle_*.py``
 (closed forms, exact symmetries, analytic projections, dense-matrix transposes,
@@ -270,9 +274,75 @@ def landweber_grads(g: Geometry, x0, y, alpha: float, iterations: int, x_true):
     return loss, dy, dalpha
 
 
+FILTERS = ("ram-lak", "shepp-logan", "cosine", "hamming", "hann")
+
+
+def ramp_kernel(m: np.ndarray) -> np.ndarray:
+    """Band-limited ramp filter at integer offsets m (unit detector spacing), Kak & Slaney Ch. 3
+    Eq. 61: 1/4 at m = 0, 0 at even m, -1 / (pi^2 m^2) at odd m."""
+    m = np.asarray(m, dtype=np.int64)
+    h = np.zeros(m.shape, dtype=np.float64)
+    h[m == 0] = 0.25
+    odd = (m % 2) != 0
+    h[odd] = -1.0 / (np.pi ** 2 * m[odd].astype(np.float64) ** 2)
+    return h
+
+
+def filter_length(det_count: int) -> int:
+    """Zero-padded length: the smallest power of two >= 2 D - 1, so that the circular convolution
+    of the padded projection equals the linear one."""
+    p = 1
+    while p < 2 * det_count - 1:
+        p *= 2
+    return max(p, 2)
+
+
+def window(name: str, f: np.ndarray) -> np.ndarray:
+    """Frequency window at normalised frequency f in [-1/2, 1/2] cycles per detector bin."""
+    f = np.asarray(f, dtype=np.float64)
+    if name == "ram-lak":
+        return np.ones_like(f)
+    if name == "shepp-logan":
+        return np.sinc(f)                      # sin(pi f) / (pi f)
+    if name == "cosine":
+        return np.cos(np.pi * f)
+    if name == "hamming":
+        return 0.54 + 0.46 * np.cos(2 * np.pi * f)
+    if name == "hann":
+        return 0.5 + 0.5 * np.cos(2 * np.pi * f)
+    raise ValueError("unknown filter %r (one of %s)" % (name, ", ".join(FILTERS)))
+
+
+def frequency_filter(name: str, det_count: int) -> np.ndarray:
+    """The length-P Fourier filter: DFT of the zero-padded spatial ramp kernel times the window."""
+    p = filter_length(det_count)
+    m = np.arange(p)
+    m = np.where(m <= p // 2, m, m - p)        # offsets of the circular layout
+    ramp = np.fft.fft(ramp_kernel(m)).real     # the kernel is even: the DFT is real
+    return ramp * window(name, np.fft.fftfreq(p))
+
+
+def filter_sinogram(g: Geometry, sino: np.ndarray, name: str = "ram-lak") -> np.ndarray:
+    """(pi / V) times each view's projection filtered along the detector: zero-pad to P, FFT,
+    multiply by the Fourier filter, inverse FFT, keep the first D bins."""
+    y = np.asarray(sino, dtype=np.float64)
+    D = y.shape[-1]
+    p = filter_length(D)
+    H = frequency_filter(name, D)
+    Y = np.fft.fft(y, n=p, axis=-1)
+    q = np.fft.ifft(Y * H, axis=-1).real[..., :D]
+    return (np.pi / g.n_angles) * q
+
+
+def fbp(g: Geometry, sino: np.ndarray, name: str = "ram-lak") -> np.ndarray:
+    """Filtered backprojection: the exact adjoint of the filtered sinogram."""
+    return adjoint(g, filter_sinogram(g, sino, name))
+
+
 __all__ = [
     "Geometry", "build", "ray", "sample_count", "ray_sample_counts", "forward", "adjoint",
     "num_threads", "dense_matrix", "dense_matrix_adjoint", "power_iteration", "landweber",
-    "landweber_grads",
+    "landweber_grads", "FILTERS", "ramp_kernel", "filter_length", "window", "frequency_filter",
+    "filter_sinogram", "fbp",
 ]
 
