@@ -382,6 +382,7 @@ def run_secondary(args):
     * The uneven batch (64 images, 16 each of 128^2 .. 1024^2, each with its own parallel geometry,
       fp16): one forward plan and one adjoint plan (autotuned at creation) replayed as one CUDA
       graph, against one library call per image and direction.
+    * Filtered backprojection at the paper's FBP setting (512^2, 512 views, 725 detectors, Ram-Lak).
     """
     import torch
 
@@ -522,6 +523,27 @@ def run_secondary(args):
     }
     pf.close()
     pa.close()
+    # filtered backprojection at the paper's setting (Section 3.1.3): 512^2, 512 views in [0, pi),
+    # ceil(512 sqrt 2) = 725 detectors, Ram-Lak; batch 1 (latency) and 16 (throughput), FP32
+    from paper_2009_14788_gb300 import filter_sinogram
+    D = int(np.ceil(512 * np.sqrt(2.0)))
+    g = Geometry("parallel", 512, uniform_angles(512, np.pi), det_count=D, det_spacing=1.0)
+    res = {"workload": "parallel_n512_v512_d725_ramlak", "storage": "f32",
+           "l2": "flushed (2x L2 write) before each timed call"}
+    for B in (1, 16):
+        x = torch.from_numpy(np.stack([ellipse_phantom(512, 10, 4242 + b) for b in range(B)])).to("cuda", torch.float32)
+        y = forward_raw(g, x)
+        q = torch.empty_like(y)
+        rec = torch.empty_like(x)
+        ms_f = time_it(lambda: filter_sinogram(g, y, "ram-lak", out=q), 5)
+
+        def fbp():
+            filter_sinogram(g, y, "ram-lak", out=q)
+            backward_raw(g, q, out=rec)
+        ms_fbp = time_it(fbp, 5)
+        res["batch%d" % B] = {"ms_filter": ms_f, "ms_fbp": ms_fbp, "images_per_s": B / (ms_fbp * 1e-3)}
+        del x, y, q, rec
+    out["fbp"] = res
     del flush
     torch.cuda.empty_cache()
     return out

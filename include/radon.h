@@ -357,6 +357,32 @@ RADON_API radon_status radon_power_iteration(const radon_geometry* geometry, con
 RADON_API radon_status radon_get_device_error(void* stream);
 
 /*
+ * ---- Filtered backprojection (Section 3.1.3) ----
+ *
+ * Each view's projection is filtered along the detector in the frequency domain by the DFT of the
+ * band-limited ramp kernel of Kak & Slaney (Chapter 3, Eq. 61: 1/4 at offset 0, -1/(pi^2 m^2) at odd
+ * offsets m, 0 at even ones) zero-padded to P = the smallest power of two >= max(2D - 1, 2), times a window
+ * of the normalised frequency f in [-1/2, 1/2] cycles per bin, and scaled by pi / V; the exact
+ * adjoint of the result is the reconstruction (parallel beam; no fan-beam weighting is applied).
+ */
+typedef enum {
+    RADON_FILTER_RAM_LAK = 0,   /* window 1 */
+    RADON_FILTER_SHEPP_LOGAN,   /* sin(pi f) / (pi f) */
+    RADON_FILTER_COSINE,        /* cos(pi f) */
+    RADON_FILTER_HAMMING,       /* 0.54 + 0.46 cos(2 pi f) */
+    RADON_FILTER_HANN           /* 0.5 + 0.5 cos(2 pi f) */
+} radon_filter;
+
+/*
+ * out = the filtered sinogram batch ([batch][V][D], same dtype as `sino`, FP32 arithmetic).  The
+ * zero-padded circular convolution equals a linear one over the D bins, so the kernel sums it
+ * directly with taps precomputed in FP64 when the geometry was created (the two routes agree to
+ * rounding).  `out` must not overlap `sino`.  Allocates nothing; can be captured.
+ */
+RADON_API radon_status radon_filter_sinogram(const radon_geometry* geometry, const void* sino, void* out,
+                                             radon_dtype dtype, int batch, radon_filter filter, void* stream);
+
+/*
  * ---- Uneven batches in one persistent launch (Section 4.1: batch processing, here of images of
  * different sizes, each with its own geometry) ----
  *

@@ -9,6 +9,7 @@ from . import _lib  # noqa: F401
 from .landweber import Landweber, LandweberFunction, landweber  # noqa: F401
 from .radon import (  # noqa: F401
     BatchPlan,
+    FilterSinogramFunction,
     Geometry,
     Radon,
     RadonBackprojectionFunction,
@@ -19,6 +20,7 @@ from .radon import (  # noqa: F401
     backward_raw,
     backward_workspace_bytes,
     dot,
+    filter_sinogram,
     forward_fused,
     forward_raw,
     forward_workspace_bytes,
@@ -30,4 +32,5 @@ __all__ = [
     "Geometry", "Radon", "RadonFanbeam", "RadonForwardFunction", "RadonBackprojectionFunction", "forward_raw",
     "backward_raw", "launch_config", "forward_workspace_bytes", "backward_workspace_bytes", "forward_fused",
     "backward_fused", "dot", "axpby", "power_iteration", "Landweber", "LandweberFunction", "landweber", "BatchPlan",
+    "filter_sinogram", "FilterSinogramFunction",
 ]

@@ -24,6 +24,8 @@ RADON_F32 = 0
 RADON_F16 = 1
 RADON_BF16 = 2
 
+FILTERS = {"ram-lak": 0, "shepp-logan": 1, "cosine": 2, "hamming": 3, "hann": 4}
+
 RADON_ALGO_AUTO = 0
 RADON_ALGO_PLAIN = 1
 RADON_ALGO_TILED = 2
@@ -173,6 +175,8 @@ _SIGNATURES = [
     ("radon_batch_plan_item_config", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("radon_batch_plan_destroy", None, [ctypes.c_void_p]),
     ("radon_probe_gather_ceiling", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    ("radon_filter_sinogram", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     ("radon_kernel_launch_count", ctypes.c_uint64, []),
     ("radon_get_device_error", ctypes.c_int, [ctypes.c_void_p]),
     ("radon_status_string", ctypes.c_char_p, [ctypes.c_int]),
@@ -338,6 +342,10 @@ def radon_batch_plan_destroy(plan):
 
 def radon_probe_gather_ceiling(dtype, out_ptr):
     return _call("radon_probe_gather_ceiling", dtype, out_ptr)
+
+
+def radon_filter_sinogram(geom, sino, out, dtype, batch, filter_kind, stream):
+    return _call("radon_filter_sinogram", geom, sino, out, dtype, batch, filter_kind, stream)
 
 
 def radon_kernel_launch_count():

@@ -94,7 +94,7 @@ radon_status upload(radon_geometry* g) {
     if ((e = cudaMemcpy(g->d_groups, g->h_groups.data(), g->h_groups.size() * sizeof(Int2), cudaMemcpyHostToDevice)) !=
         cudaSuccess)
         return cuda_fail(e, "cudaMemcpy view groups");
-    return RADON_OK;
+    return upload_filter_taps(g);
 }
 
 void release(radon_geometry* g) {
@@ -103,6 +103,7 @@ void release(radon_geometry* g) {
     if (g->d_nk) cudaFree(g->d_nk);
     if (g->d_view) cudaFree(g->d_view);
     if (g->d_groups) cudaFree(g->d_groups);
+    if (g->d_filter_taps) cudaFree(g->d_filter_taps);
     g->magic = 0;
     delete g;
 }

@@ -82,6 +82,9 @@ struct radon_geometry {
     radon::RayT* d_ray = nullptr;
     int* d_nk = nullptr;
     radon::ViewF* d_view = nullptr;
+    // FBP filter taps, (pi / V) k[m] for m = -(D-1) .. D-1 as (hi, lo) FP32 pairs, one row of 2D - 1
+    // per radon_filter kind
+    float2* d_filter_taps = nullptr;
 };
 
 namespace radon {
@@ -138,6 +141,9 @@ radon_status launch_backward_packed(const radon_geometry* g, const void* packed,
 
 // radon_api.cpp: process-wide count of kernels the library has launched (radon_kernel_launch_count)
 void count_launches(int kernels);
+
+// filter.cu: the FBP filter taps of every kind, computed in FP64 and uploaded at geometry creation
+radon_status upload_filter_taps(radon_geometry* g);
 
 // kernels_common.cu
 cudaError_t read_and_clear_device_error(int* out);

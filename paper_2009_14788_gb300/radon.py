@@ -322,6 +322,37 @@ def power_iteration(geom: Geometry, v0: torch.Tensor, iterations: int = 20):
     return lam, alpha
 
 
+def filter_sinogram(geom: Geometry, y: torch.Tensor, filter_name: str = "ram-lak", out=None) -> torch.Tensor:
+    """Each view filtered along the detector for FBP (``radon_filter_sinogram``; no autograd)."""
+    if filter_name not in L.FILTERS:
+        raise ValueError("filter must be one of %s" % ", ".join(L.FILTERS))
+    _check_tensor(y, "sinogram", geom)
+    if tuple(y.shape[-2:]) != geom.sino_shape:
+        raise ValueError("sinogram must end in %s, got %s" % (geom.sino_shape, tuple(y.shape)))
+    y = y.contiguous()
+    batch = y.numel() // (geom.n_angles * geom.det_count)
+    q = torch.empty_like(y) if out is None else _check_out(out, y, tuple(y.shape))
+    stream = torch.cuda.current_stream(y.device).cuda_stream
+    with torch.cuda.device(y.device):
+        st = L.radon_filter_sinogram(geom.handle, y.data_ptr(), q.data_ptr(), _DTYPES[y.dtype], batch,
+                                     L.FILTERS[filter_name], stream)
+    L.check(st, "radon_filter_sinogram")
+    return q
+
+
+class FilterSinogramFunction(torch.autograd.Function):
+    """q = F y with F the (symmetric Toeplitz) FBP filter: dL/dy = F dL/dq."""
+
+    @staticmethod
+    def forward(ctx, y, geom, filter_name):
+        ctx.geom, ctx.filter_name = geom, filter_name
+        return filter_sinogram(geom, y, filter_name)
+
+    @staticmethod
+    def backward(ctx, grad):
+        return filter_sinogram(ctx.geom, grad.contiguous(), ctx.filter_name), None, None
+
+
 class BatchPlan:
     """One persistent launch over an uneven batch (``radon_batch_plan_*``).
 
@@ -449,6 +480,14 @@ class Radon:
         return RadonBackprojectionFunction.apply(sino, self.geometry, self.config)
 
     backward = backprojection
+
+    def filter_sinogram(self, sino: torch.Tensor, filter_name: str = "ram-lak") -> torch.Tensor:
+        """Section 3.1.3: the sinogram filtered for filtered backprojection (differentiable)."""
+        return FilterSinogramFunction.apply(sino, self.geometry, filter_name)
+
+    def fbp(self, sino: torch.Tensor, filter_name: str = "ram-lak") -> torch.Tensor:
+        """Filtered backprojection: ``backprojection(filter_sinogram(sino))`` (parallel beam)."""
+        return self.backprojection(self.filter_sinogram(sino, filter_name))
 
     __call__ = forward
 

@@ -204,6 +204,20 @@ def test_batch_plan_rejects_bad_arguments_without_gpu():
     L.radon_geometry_destroy(h)
 
 
+def test_filter_rejects_bad_arguments_without_gpu():
+    st, h = _create()
+    assert st == L.RADON_OK
+    buf = (ctypes.c_float * 64)()
+    p = ctypes.addressof(buf)
+    assert L.radon_filter_sinogram(h, p, p + 128, 0, 1, 9, None) == L.RADON_ERR_INVALID_ARG      # unknown filter
+    assert L.radon_filter_sinogram(h, p, p + 128, 0, 1, 0, None) == L.RADON_ERR_INVALID_ARG      # host-only
+    assert "host-only" in L.radon_last_error_message()
+    assert L.radon_filter_sinogram(None, p, p + 128, 0, 1, 0, None) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_filter_sinogram(h, p, p + 128, 0, -1, 0, None) == L.RADON_ERR_INVALID_ARG
+    assert sorted(L.FILTERS.values()) == list(range(5))
+    L.radon_geometry_destroy(h)
+
+
 def test_defaults_follow_the_paper():
     g = Geometry("parallel", 40, uniform_angles(5, math.pi), host_only=True)
     assert (g.det_count, g.det_spacing, g.step) == (40, 1.0, 1.0)
