@@ -19,7 +19,11 @@ justification in the design notes):
 * filtered backprojection (Section 3.1.3): each view's projection is filtered in
   the frequency domain by the DFT of the zero-padded band-limited ramp kernel of
   Kak & Slaney, Chapter 3, Eq. 61, times a window, then backprojected with the
-  exact adjoint; the scale pi / V makes ``adjoint(filter_sinogram(A x)) ~ x``.
+  exact adjoint; the scale pi / V makes ``adjoint(filter_sinogram(A x)) ~ x``;
+* CGNE (Section 4.2, after Hanke's "Conjugate gradient type methods for ill-posed
+  problems"): conjugate gradients on the normal equation A^T A x = A^T y, which
+  minimises |A x - y| over x_0 + K_k(A^T A, A^T r_0); CG for a symmetric positive
+  (semi-)definite operator.  Every image of a batch is its own problem.
 
 Parity status of every function is pinned by tests in ``tests/test_oracle_*.py``
 (closed forms, exact symmetries, analytic projections, dense-matrix transposes,
@@ -339,10 +343,68 @@ def fbp(g: Geometry, sino: np.ndarray, name: str = "ram-lak") -> np.ndarray:
     return adjoint(g, filter_sinogram(g, sino, name))
 
 
+def _per_item_dot(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Inner products of the items of a batch (leading axis), FP64."""
+    return np.sum(a.reshape(a.shape[0], -1) * b.reshape(b.shape[0], -1), axis=1)
+
+
+def cgne(g: Geometry, x0: np.ndarray, y: np.ndarray, iterations: int, history: bool = False):
+    """CG on A^T A x = A^T y, one problem per image (x0 [B,N,N] or [N,N], y the matching sinograms).
+
+    r = y - A x, s = A^T r, p = s, gamma = |s|^2; per step: q = A p, alpha = gamma / |q|^2,
+    x += alpha p, r -= alpha q, s = A^T r, gamma' = |s|^2, p = s + (gamma' / gamma) p.
+    Returns x_K (and the list of residual norms |y - A x_k| per item if ``history``)."""
+    single = np.ndim(x0) == 2
+    x = np.array(x0, dtype=np.float64, copy=True)
+    yy = np.asarray(y, dtype=np.float64)
+    if single:
+        x, yy = x[None], yy[None]
+    r = yy - forward(g, x)
+    s = adjoint(g, r)
+    p = s.copy()
+    gamma = _per_item_dot(s, s)
+    hist = [np.sqrt(_per_item_dot(r, r))]
+    for _ in range(iterations):
+        q = forward(g, p)
+        qq = _per_item_dot(q, q)
+        alpha = np.where(qq > 0, gamma / np.where(qq > 0, qq, 1.0), 0.0)
+        x += alpha[:, None, None] * p
+        r -= alpha[:, None, None] * q
+        s = adjoint(g, r)
+        gnew = _per_item_dot(s, s)
+        beta = np.where(gamma > 0, gnew / np.where(gamma > 0, gamma, 1.0), 0.0)
+        p = s + beta[:, None, None] * p
+        gamma = gnew
+        hist.append(np.sqrt(_per_item_dot(r, r)))
+    out = x[0] if single else x
+    return (out, hist) if history else out
+
+
+def cg(apply_op, x0: np.ndarray, b: np.ndarray, iterations: int):
+    """Conjugate gradients for M x = b with M symmetric positive (semi-)definite, given as
+    ``apply_op`` on a batch [B, ...]; one problem per item."""
+    x = np.array(x0, dtype=np.float64, copy=True)
+    r = np.asarray(b, dtype=np.float64) - apply_op(x)
+    p = r.copy()
+    rr = _per_item_dot(r, r)
+    expand = (slice(None),) + (None,) * (x.ndim - 1)
+    for _ in range(iterations):
+        mp = apply_op(p)
+        pmp = _per_item_dot(p, mp)
+        alpha = np.where(pmp > 0, rr / np.where(pmp > 0, pmp, 1.0), 0.0)
+        x += alpha[expand] * p
+        r -= alpha[expand] * mp
+        rnew = _per_item_dot(r, r)
+        beta = np.where(rr > 0, rnew / np.where(rr > 0, rr, 1.0), 0.0)
+        p = r + beta[expand] * p
+        rr = rnew
+    return x
+
+
 __all__ = [
     "Geometry", "build", "ray", "sample_count", "ray_sample_counts", "forward", "adjoint",
     "num_threads", "dense_matrix", "dense_matrix_adjoint", "power_iteration", "landweber",
     "landweber_grads", "FILTERS", "ramp_kernel", "filter_length", "window", "frequency_filter",
-    "filter_sinogram", "fbp",
+    "filter_sinogram", "fbp", "cgne", "cg",
 ]
 
