@@ -382,7 +382,8 @@ def run_secondary(args):
     * The uneven batch (64 images, 16 each of 128^2 .. 1024^2, each with its own parallel geometry,
       fp16): one forward plan and one adjoint plan (autotuned at creation) replayed as one CUDA
       graph, against one library call per image and direction.
-    * Filtered backprojection at the paper's FBP setting (512^2, 512 views, 725 detectors, Ram-Lak).
+    * Filtered backprojection at the paper's FBP setting (512^2, 512 views, 725 detectors, Ram-Lak),
+      and CGNE (20 iterations) at the same setting.
     """
     import torch
 
@@ -544,6 +545,19 @@ def run_secondary(args):
         res["batch%d" % B] = {"ms_filter": ms_f, "ms_fbp": ms_fbp, "images_per_s": B / (ms_fbp * 1e-3)}
         del x, y, q, rec
     out["fbp"] = res
+    # CGNE at the same setting (Section 4.2 runs 500 iterations): 20 iterations, batch 1 and 8
+    from paper_2009_14788_gb300 import cgne
+    res = {"workload": "parallel_n512_v512_d725", "storage": "f32", "iterations": 20,
+           "l2": "flushed (2x L2 write) before each timed call"}
+    for B in (1, 8):
+        x = torch.from_numpy(np.stack([ellipse_phantom(512, 10, 4242 + b) for b in range(B)])).to("cuda", torch.float32)
+        y = forward_raw(g, x)
+        x0 = torch.zeros_like(x)
+        ms = time_it(lambda: cgne(g, x0, y, 20), 3, warm=1)
+        res["batch%d" % B] = {"ms": ms, "ms_per_iteration": ms / 20,
+                              "samples_per_s": 2 * 20 * B * g.sample_count / (ms * 1e-3)}
+        del x, y, x0
+    out["cgne"] = res
     del flush
     torch.cuda.empty_cache()
     return out

@@ -357,6 +357,43 @@ RADON_API radon_status radon_power_iteration(const radon_geometry* geometry, con
 RADON_API radon_status radon_get_device_error(void* stream);
 
 /*
+ * ---- Conjugate-gradient solvers (Section 2.1's solvers module, Section 4.2; M. Hanke, "Conjugate
+ * gradient type methods for ill-posed problems") ----
+ *
+ * Batched vector kernels with one scalar per item, for per-image conjugate-gradient recursions:
+ *   radon_dot_batched:   result[i] = scale <a_i, b_i> (+ result[i] if accumulate), items of `count`
+ *                        elements, deterministic (FP32 per thread, FP64 across threads and blocks);
+ *                        workspace >= radon_dot_batched_workspace_size(batch) bytes, 8-byte aligned;
+ *   radon_axpby_batched: y_i = alpha s_i x_i + beta t_i y_i, s_i = alpha_dev[i] (NULL: 1),
+ *                        t_i = beta_dev[i] (NULL: 1); y is not read when beta == 0 and beta_dev NULL;
+ *   radon_safe_divide:   out[i] = num[i] / den[i] where den[i] > 0, else 0 (device FP32 arrays).
+ * All allocate nothing and can be captured; batch <= 65535 for the dot.
+ */
+RADON_API size_t radon_dot_batched_workspace_size(int batch);
+RADON_API radon_status radon_dot_batched(const void* a, const void* b, radon_dtype dtype, int batch, int64_t count,
+                                         float scale, float* result, int accumulate, void* workspace,
+                                         size_t workspace_bytes, void* stream);
+RADON_API radon_status radon_axpby_batched(const void* x, radon_dtype x_dtype, void* y, radon_dtype y_dtype,
+                                           int batch, int64_t count, float alpha, const float* alpha_dev, float beta,
+                                           const float* beta_dev, void* stream);
+RADON_API radon_status radon_safe_divide(const float* num, const float* den, float* out, int batch, void* stream);
+
+/*
+ * CGNE: conjugate gradients on the normal equation A^T A x = A^T y, every image its own problem:
+ *   r = y - A x;  s = A^T r;  p = s;  gamma = |s|^2;  per iteration:
+ *   q = A p;  alpha = gamma / |q|^2;  x += alpha p;  r -= alpha q;  s = A^T r;
+ *   gamma' = |s|^2;  p = s + (gamma' / gamma) p;  gamma = gamma'
+ * (a zero denominator gives a zero step).  x ([batch][N][N], FP32) holds the start on entry and the
+ * iterate after `iterations` steps on return; y is the FP32 sinogram batch.  Runs entirely on the
+ * device in stream order with the caller's workspace (>= radon_cgne_workspace_size bytes, 16-byte
+ * aligned): allocates nothing, never synchronises, can be captured.  FP32 storage only
+ * (RADON_ERR_UNSUPPORTED otherwise): the recursion's orthogonality does not survive 16-bit vectors.
+ */
+RADON_API size_t radon_cgne_workspace_size(const radon_geometry* geometry, int batch);
+RADON_API radon_status radon_cgne(const radon_geometry* geometry, const void* y, void* x, radon_dtype dtype, int batch,
+                                  int iterations, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * ---- Filtered backprojection (Section 3.1.3) ----
  *
  * Each view's projection is filtered along the detector in the frequency domain by the DFT of the

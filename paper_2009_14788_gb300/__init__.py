@@ -7,6 +7,7 @@ PyTorch binding: ``Radon``, ``RadonFanbeam``, differentiable forward / backproje
 
 from . import _lib  # noqa: F401
 from .landweber import Landweber, LandweberFunction, landweber  # noqa: F401
+from .solvers import cg, cgne  # noqa: F401
 from .radon import (  # noqa: F401
     BatchPlan,
     FilterSinogramFunction,
@@ -32,5 +33,5 @@ __all__ = [
     "Geometry", "Radon", "RadonFanbeam", "RadonForwardFunction", "RadonBackprojectionFunction", "forward_raw",
     "backward_raw", "launch_config", "forward_workspace_bytes", "backward_workspace_bytes", "forward_fused",
     "backward_fused", "dot", "axpby", "power_iteration", "Landweber", "LandweberFunction", "landweber", "BatchPlan",
-    "filter_sinogram", "FilterSinogramFunction",
+    "filter_sinogram", "FilterSinogramFunction", "cg", "cgne",
 ]

@@ -177,6 +177,19 @@ _SIGNATURES = [
     ("radon_probe_gather_ceiling", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     ("radon_filter_sinogram", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    ("radon_dot_batched_workspace_size", ctypes.c_size_t, [ctypes.c_int]),
+    ("radon_dot_batched", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p,
+      ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("radon_axpby_batched", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_float,
+      ctypes.c_void_p, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
+    ("radon_safe_divide", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    ("radon_cgne_workspace_size", ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int]),
+    ("radon_cgne", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+      ctypes.c_size_t, ctypes.c_void_p]),
     ("radon_kernel_launch_count", ctypes.c_uint64, []),
     ("radon_get_device_error", ctypes.c_int, [ctypes.c_void_p]),
     ("radon_status_string", ctypes.c_char_p, [ctypes.c_int]),
@@ -346,6 +359,31 @@ def radon_probe_gather_ceiling(dtype, out_ptr):
 
 def radon_filter_sinogram(geom, sino, out, dtype, batch, filter_kind, stream):
     return _call("radon_filter_sinogram", geom, sino, out, dtype, batch, filter_kind, stream)
+
+
+def radon_dot_batched_workspace_size(batch):
+    return _call("radon_dot_batched_workspace_size", batch)
+
+
+def radon_dot_batched(a, b, dtype, batch, count, scale, result, accumulate, workspace, workspace_bytes, stream):
+    return _call("radon_dot_batched", a, b, dtype, batch, count, scale, result, accumulate, workspace,
+                 workspace_bytes, stream)
+
+
+def radon_axpby_batched(x, x_dtype, y, y_dtype, batch, count, alpha, alpha_dev, beta, beta_dev, stream):
+    return _call("radon_axpby_batched", x, x_dtype, y, y_dtype, batch, count, alpha, alpha_dev, beta, beta_dev, stream)
+
+
+def radon_safe_divide(num, den, out, batch, stream):
+    return _call("radon_safe_divide", num, den, out, batch, stream)
+
+
+def radon_cgne_workspace_size(geom, batch):
+    return _call("radon_cgne_workspace_size", geom, batch)
+
+
+def radon_cgne(geom, y, x, dtype, batch, iterations, workspace, workspace_bytes, stream):
+    return _call("radon_cgne", geom, y, x, dtype, batch, iterations, workspace, workspace_bytes, stream)
 
 
 def radon_kernel_launch_count():
