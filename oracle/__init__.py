@@ -23,7 +23,11 @@ justification in the design notes):
 * CGNE (Section 4.2, after Hanke's "Conjugate gradient type methods for ill-posed
   problems"): conjugate gradients on the normal equation A^T A x = A^T y, which
   minimises |A x - y| over x_0 + K_k(A^T A, A^T r_0); CG for a symmetric positive
-  (semi-)definite operator.  Every image of a batch is its own problem.
+  (semi-)definite operator.  Every image of a batch is its own problem;
+* the pixel-driven interpolating backprojector (the kind the paper compares with,
+  Section 3.1): per view, the sinogram linearly interpolated at the detector
+  coordinate of the pixel centre, weighted by the density of rays there
+  (|grad t|, detector bins per pixel) so that it approximates the exact adjoint.
 
 Parity status of every function is pinned by tests in ``tests/test_oracle_*.py``
 (closed forms, exact symmetries, analytic projections, dense-matrix transposes,
@@ -401,10 +405,53 @@ def cg(apply_op, x0: np.ndarray, b: np.ndarray, iterations: int):
     return x
 
 
+def detector_coordinate(g: Geometry, v: int):
+    """Continuous detector index t(x, y) of every pixel centre for view v, and |grad t| (bins per
+    pixel): parallel t = (c . n) / ds + (D - 1) / 2; fan (source -S u, flat detector at Ddet along
+    u): s = (S + Ddet) (c . n) / (c . u + S), the intersection of the source-pixel line with the
+    detector, t = s / ds + (D - 1) / 2."""
+    th = float(g.angles[v])
+    n = np.array([np.cos(th), np.sin(th)])
+    u = np.array([-np.sin(th), np.cos(th)])
+    c0 = (g.n - 1) / 2.0
+    X, Y = np.meshgrid(np.arange(g.n) - c0, np.arange(g.n) - c0)     # [i, j] -> (x = j - c0, y = i - c0)
+    cn = X * n[0] + Y * n[1]
+    ds = g.det_spacing
+    if g.kind == "fan":
+        S, Dd = g.source_distance, g.det_distance
+        cu = X * u[0] + Y * u[1]
+        den = cu + S
+        s = (S + Dd) * cn / den
+        grad = (S + Dd) * np.sqrt(den ** 2 + cn ** 2) / den ** 2
+    else:
+        s = cn
+        grad = np.ones_like(cn)
+    return s / ds + (g.det_count - 1) / 2.0, grad / ds
+
+
+def backproject_interpolating(g: Geometry, sino: np.ndarray) -> np.ndarray:
+    """sum_v |grad t_v| * (sino[v] linearly interpolated at t_v(pixel)), bins outside [0, D) zero."""
+    y = np.asarray(sino, dtype=np.float64)
+    single = y.ndim == 2
+    if single:
+        y = y[None]
+    out = np.zeros((y.shape[0], g.n, g.n))
+    D = g.det_count
+    for v in range(g.n_angles):
+        t, w = detector_coordinate(g, v)
+        i0 = np.floor(t).astype(np.int64)
+        f = t - i0
+        row = np.concatenate([y[:, v, :], np.zeros((y.shape[0], 1))], axis=1)   # index D reads as zero
+        lo = np.where((i0 >= 0) & (i0 < D), i0, D)
+        hi = np.where((i0 + 1 >= 0) & (i0 + 1 < D), i0 + 1, D)
+        out += w * ((1.0 - f) * row[:, lo] + f * row[:, hi])
+    return out[0] if single else out
+
+
 __all__ = [
     "Geometry", "build", "ray", "sample_count", "ray_sample_counts", "forward", "adjoint",
     "num_threads", "dense_matrix", "dense_matrix_adjoint", "power_iteration", "landweber",
     "landweber_grads", "FILTERS", "ramp_kernel", "filter_length", "window", "frequency_filter",
-    "filter_sinogram", "fbp", "cgne", "cg",
+    "filter_sinogram", "fbp", "cgne", "cg", "detector_coordinate", "backproject_interpolating",
 ]
 
