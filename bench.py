@@ -384,6 +384,7 @@ def run_secondary(args):
       graph, against one library call per image and direction.
     * Filtered backprojection at the paper's FBP setting (512^2, 512 views, 725 detectors, Ram-Lak),
       and CGNE (20 iterations) at the same setting.
+    * The pixel-driven interpolating backprojector against the exact adjoint on the headline workload.
     """
     import torch
 
@@ -558,6 +559,20 @@ def run_secondary(args):
                               "samples_per_s": 2 * 20 * B * g.sample_count / (ms * 1e-3)}
         del x, y, x0
     out["cgne"] = res
+    # the pixel-driven interpolating backprojector against the exact adjoint, headline workload
+    from paper_2009_14788_gb300 import backproject_interpolating
+    w = WORKLOADS[DEFAULT_WORKLOAD]
+    ga = workload_geometry_args(w)
+    kind = ga.pop("kind")
+    g = Geometry(kind, **ga)
+    x = torch.from_numpy(workload_images(w)).to("cuda", torch.float16)
+    y = forward_raw(g, x)
+    ox = torch.empty_like(x)
+    ms_i = time_it(lambda: backproject_interpolating(g, y, out=ox), 5)
+    ms_a = time_it(lambda: backward_raw(g, y, out=ox), 5)
+    out["interpolating_backprojection"] = {"workload": w.name, "storage": "f16", "ms": ms_i,
+                                           "exact_adjoint_ms": ms_a, "speedup_vs_exact_adjoint": ms_a / ms_i}
+    del x, y, ox
     del flush
     torch.cuda.empty_cache()
     return out

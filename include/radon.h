@@ -357,6 +357,28 @@ RADON_API radon_status radon_power_iteration(const radon_geometry* geometry, con
 RADON_API radon_status radon_get_device_error(void* stream);
 
 /*
+ * Pixel-driven interpolating backprojector (the kind of backprojection the paper's comparisons use,
+ * Section 3.1): img[b][i][j] = sum_v |grad t_v| * sino[b][v] linearly interpolated at t_v(j, i), where
+ * t_v is the continuous detector index of the pixel centre (parallel: (c . n) / ds + (D-1)/2; fan:
+ * where the source-to-pixel line meets the flat detector) and |grad t_v| the density of rays there in
+ * bins per pixel (1 / ds for parallel beams); bins outside [0, D) read as zero.  It approximates the
+ * exact adjoint (radon_backward) at a fraction of the cost but is not its transpose.  Same buffers and
+ * rules as radon_backward; allocates nothing; can be captured.
+ */
+RADON_API radon_status radon_backproject_interpolating(const radon_geometry* geometry, const void* sino, void* img,
+                                                       radon_dtype dtype, int batch, void* stream);
+
+/*
+ * The same with a caller workspace (>= radon_backward_workspace_size bytes, 16-byte aligned): the
+ * sinogram batch is packed once and every 16 x 16 tile's detector windows arrive in shared memory by
+ * TMA through the exact adjoint's pipeline, two interpolation taps per pixel and view.  A NULL or too
+ * small workspace, or a shape that pipeline refuses, falls back to radon_backproject_interpolating.
+ */
+RADON_API radon_status radon_backproject_interpolating_ws(const radon_geometry* geometry, const void* sino, void* img,
+                                                          radon_dtype dtype, int batch, void* workspace,
+                                                          size_t workspace_bytes, void* stream);
+
+/*
  * ---- Conjugate-gradient solvers (Section 2.1's solvers module, Section 4.2; M. Hanke, "Conjugate
  * gradient type methods for ill-posed problems") ----
  *

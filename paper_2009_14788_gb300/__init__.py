@@ -17,6 +17,7 @@ from .radon import (  # noqa: F401
     RadonFanbeam,
     RadonForwardFunction,
     axpby,
+    backproject_interpolating,
     backward_fused,
     backward_raw,
     backward_workspace_bytes,
@@ -34,4 +35,5 @@ __all__ = [
     "backward_raw", "launch_config", "forward_workspace_bytes", "backward_workspace_bytes", "forward_fused",
     "backward_fused", "dot", "axpby", "power_iteration", "Landweber", "LandweberFunction", "landweber", "BatchPlan",
     "filter_sinogram", "FilterSinogramFunction", "cg", "cgne",
+    "backproject_interpolating",
 ]

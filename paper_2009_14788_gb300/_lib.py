@@ -190,6 +190,11 @@ _SIGNATURES = [
     ("radon_cgne", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
       ctypes.c_size_t, ctypes.c_void_p]),
+    ("radon_backproject_interpolating", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    ("radon_backproject_interpolating_ws", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+      ctypes.c_void_p]),
     ("radon_kernel_launch_count", ctypes.c_uint64, []),
     ("radon_get_device_error", ctypes.c_int, [ctypes.c_void_p]),
     ("radon_status_string", ctypes.c_char_p, [ctypes.c_int]),
@@ -384,6 +389,14 @@ def radon_cgne_workspace_size(geom, batch):
 
 def radon_cgne(geom, y, x, dtype, batch, iterations, workspace, workspace_bytes, stream):
     return _call("radon_cgne", geom, y, x, dtype, batch, iterations, workspace, workspace_bytes, stream)
+
+
+def radon_backproject_interpolating(geom, sino, img, dtype, batch, stream):
+    return _call("radon_backproject_interpolating", geom, sino, img, dtype, batch, stream)
+
+
+def radon_backproject_interpolating_ws(geom, sino, img, dtype, batch, workspace, workspace_bytes, stream):
+    return _call("radon_backproject_interpolating_ws", geom, sino, img, dtype, batch, workspace, workspace_bytes, stream)
 
 
 def radon_kernel_launch_count():

@@ -166,18 +166,19 @@ int backward_packed_images_per_cta(int batch, const radon_launch_config* cfg) {
 }
 
 radon_status launch_backward_packed(const radon_geometry* g, const void* packed, void* img, radon_dtype dt, int batch,
-                                    int bg, const Epilogue& ep, cudaStream_t s, std::string* why) {
+                                    int bg, const Epilogue& ep, cudaStream_t s, std::string* why, bool interpolating) {
     if (bg != 8 && bg != 16) {
         *why = "images_per_cta must be 8 or 16 for the packed adjoint";
         return RADON_ERR_UNSUPPORTED;
     }
     const double span = 2.0 * std::sqrt(2.0) / g->h + 2e-4;
     const int kw_needed = (int)std::floor(span) + 1;
-    if (kw_needed > 6) {
+    if (!interpolating && kw_needed > 6) {
         *why = "sampling step too small for the tiled adjoint";
         return RADON_ERR_UNSUPPORTED;
     }
-    const int kw = kw_needed <= 3 ? 3 : 6;
+    // KW = 0 selects the interpolating backprojector (two taps per view, no rays)
+    const int kw = interpolating ? 0 : (kw_needed <= 3 ? 3 : 6);
     const int wd = g->bwd_window + 2;
     if (wd > 256) {
         *why = "detector window wider than a TMA box";
@@ -239,12 +240,15 @@ radon_status launch_backward_packed(const radon_geometry* g, const void* packed,
     a.out_dtype = dt;
     dim3 grid((unsigned)(a.tiles_x * a.tiles_x), (unsigned)groups);
     cudaError_t e;
+    if (interpolating) a.h = 1.0f;   // the interpolating backprojector's sum carries no step factor
     if (bg == 16)
-        e = kw == 3 ? launch_packed_bg<16, 3>(map, rmap, a, grid, smem, s)
-                    : launch_packed_bg<16, 6>(map, rmap, a, grid, smem, s);
+        e = kw == 0 ? launch_packed_bg<16, 0>(map, rmap, a, grid, smem, s)
+                    : kw == 3 ? launch_packed_bg<16, 3>(map, rmap, a, grid, smem, s)
+                              : launch_packed_bg<16, 6>(map, rmap, a, grid, smem, s);
     else
-        e = kw == 3 ? launch_packed_bg<8, 3>(map, rmap, a, grid, smem, s)
-                    : launch_packed_bg<8, 6>(map, rmap, a, grid, smem, s);
+        e = kw == 0 ? launch_packed_bg<8, 0>(map, rmap, a, grid, smem, s)
+                    : kw == 3 ? launch_packed_bg<8, 3>(map, rmap, a, grid, smem, s)
+                              : launch_packed_bg<8, 6>(map, rmap, a, grid, smem, s);
     if (e != cudaSuccess) {
         *why = std::string("packed adjoint launch: ") + cudaGetErrorString(e);
         return RADON_ERR_CUDA;

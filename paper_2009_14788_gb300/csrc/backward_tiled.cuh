@@ -462,13 +462,14 @@ __global__ void __launch_bounds__(kBwdPackedThreads, 3) backward_packed_kernel(c
             __syncwarp();
             if (lane == 0) {
                 fence_proxy_async_shared();
-                mbar_arrive_expect_tx(&tma_bar[st], (uint32_t)(nv * a.wd * (BG * 4 + 32)));
+                mbar_arrive_expect_tx(&tma_bar[st], (uint32_t)(nv * a.wd * (BG * 4 + (KW > 0 ? 32 : 0))));
                 for (int vl = 0; vl < nv; ++vl) {
                     const int dlo = dlo_c[st * kBwdPackedViews + vl];
                     tma_load_5d(ystage + st * ys_bytes + (size_t)vl * yv_bytes, &map, &tma_bar[st], 0, dlo, 0, v0 + vl,
                                 blockIdx.y);
-                    tma_load_2d(rstage + st * rs_bytes + (size_t)vl * rv_bytes, &rmap, &tma_bar[st], 0,
-                                (v0 + vl) * a.D + dlo);
+                    if (KW > 0)   // the interpolating backprojector needs no rays
+                        tma_load_2d(rstage + st * rs_bytes + (size_t)vl * rv_bytes, &rmap, &tma_bar[st], 0,
+                                    (v0 + vl) * a.D + dlo);
                 }
             }
             __syncwarp();
@@ -505,7 +506,7 @@ __global__ void __launch_bounds__(kBwdPackedThreads, 3) backward_packed_kernel(c
         bool bad = !mbar_wait_bounded(&tma_bar[st], (uint32_t)((c / S) & 1), a.spin_limit);
         bad = bad || *abort_flag != 0;
         float4* rp = reinterpret_cast<float4*>(rpbuf + (c & 1) * rp_bytes);
-        if (!bad) {
+        if (KW > 0 && !bad) {
             // re-base the landed rays on this tile: one ray per thread
             for (int e = tid; e < nv * a.wd; e += kBwdThreads) {
                 const int vl = e / a.wd, dl = e - (e / a.wd) * a.wd;
@@ -520,6 +521,43 @@ __global__ void __launch_bounds__(kBwdPackedThreads, 3) backward_packed_kernel(c
         if (named_barrier_or(1, kBwdThreads, bad)) {
             if (tid == 0) record_device_error(a.err, RADON_ERR_TIMEOUT);
             return;
+        }
+        if constexpr (KW == 0) {
+            // interpolating backprojector: the sinogram linearly interpolated at the pixel's detector
+            // coordinate t (IEEE division: the weights need t to ~1e-5 bins), weighted by the ray
+            // density |grad t|; both taps lie in the staged window by construction of its bounds
+            for (int vl = 0; vl < nv; ++vl) {
+                const ViewF vf = view_c[st * kBwdPackedViews + vl];
+                const int dlo = dlo_c[st * kBwdPackedViews + vl];
+                const float den = fmaf(vf.bx, gx, fmaf(vf.by, gy, vf.b0));
+                const float t = fmaf(vf.ax, gx, fmaf(vf.ay, gy, vf.a0)) / den;
+                const float ga = fmaf(-t, vf.bx, vf.ax), gb = fmaf(-t, vf.by, vf.ay);
+                const float w = sqrtf(fmaf(ga, ga, gb * gb)) / fabsf(den);
+                const float fl = floorf(t);
+                const int k = (int)fl;
+                const float f = t - fl;
+                const int lo = max(dlo, 0), hi = min(a.D - 1, dlo + a.wd - 1);
+                if (inside && ((k < dlo && k >= 0) || (k + 1 > dlo + a.wd - 1 && k + 1 <= a.D - 1)))
+                    record_device_error(a.err, RADON_ERR_DEVICE_BOUNDS);
+                const ulonglong2* yq = reinterpret_cast<const ulonglong2*>(ystage + st * ys_bytes + (size_t)vl * yv_bytes);
+                const f32x2 w0 = f2_pack(w * (1.0f - f), w * (1.0f - f)), w1 = f2_pack(w * f, w * f);
+                const bool in0 = k >= lo && k <= hi, in1 = k + 1 >= lo && k + 1 <= hi;
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    if (in0) {
+                        const ulonglong2 y4 = yq[q * a.wd + (k - dlo)];
+                        acc[2 * q + 0] = f2_fma(w0, y4.x, acc[2 * q + 0]);
+                        acc[2 * q + 1] = f2_fma(w0, y4.y, acc[2 * q + 1]);
+                    }
+                    if (in1) {
+                        const ulonglong2 y4 = yq[q * a.wd + (k + 1 - dlo)];
+                        acc[2 * q + 0] = f2_fma(w1, y4.x, acc[2 * q + 0]);
+                        acc[2 * q + 1] = f2_fma(w1, y4.y, acc[2 * q + 1]);
+                    }
+                }
+            }
+            mbar_arrive(&empty[st]);
+            continue;
         }
         for (int vl = 0; vl < nv; ++vl) {
             const ViewF vf = view_c[st * kBwdPackedViews + vl];

@@ -137,7 +137,8 @@ cudaError_t launch_pack_sino(const void* sino, void* workspace, int V, int D, in
 // backward_tiled.cu: the packed-sinogram adjoint (the workspace already holds pack_sino's output)
 int backward_packed_images_per_cta(int batch, const radon_launch_config* cfg);
 radon_status launch_backward_packed(const radon_geometry* g, const void* packed, void* img, radon_dtype dt, int batch,
-                                    int images_per_cta, const Epilogue& ep, cudaStream_t s, std::string* why);
+                                    int images_per_cta, const Epilogue& ep, cudaStream_t s, std::string* why,
+                                    bool interpolating = false);
 
 // radon_api.cpp: process-wide count of kernels the library has launched (radon_kernel_launch_count)
 void count_launches(int kernels);

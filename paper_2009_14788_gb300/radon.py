@@ -322,6 +322,30 @@ def power_iteration(geom: Geometry, v0: torch.Tensor, iterations: int = 20):
     return lam, alpha
 
 
+def backproject_interpolating(geom: Geometry, y: torch.Tensor, out=None, workspace="auto") -> torch.Tensor:
+    """Pixel-driven interpolating backprojection (``radon_backproject_interpolating[_ws]``):
+    approximates the exact adjoint, cheaper; not differentiable (it is not the forward's transpose).
+    ``workspace`` as for ``backward_raw`` ("auto": the packed TMA pipeline; None: the plain kernel)."""
+    _check_tensor(y, "sinogram", geom)
+    if tuple(y.shape[-2:]) != geom.sino_shape:
+        raise ValueError("sinogram must end in %s, got %s" % (geom.sino_shape, tuple(y.shape)))
+    y = y.contiguous()
+    batch = y.numel() // (geom.n_angles * geom.det_count)
+    shape = tuple(y.shape[:-2]) + (geom.n, geom.n)
+    x = torch.empty(shape, dtype=y.dtype, device=y.device) if out is None else _check_out(out, y, shape)
+    ws = _workspace(workspace, backward_workspace_bytes(geom, y.dtype, batch) if batch > 0 else 0, y.device)
+    stream = torch.cuda.current_stream(y.device).cuda_stream
+    with torch.cuda.device(y.device):
+        if ws is not None:
+            st = L.radon_backproject_interpolating_ws(geom.handle, y.data_ptr(), x.data_ptr(), _DTYPES[y.dtype], batch,
+                                                      ws.data_ptr(), ws.numel() * ws.element_size(), stream)
+        else:
+            st = L.radon_backproject_interpolating(geom.handle, y.data_ptr(), x.data_ptr(), _DTYPES[y.dtype], batch,
+                                                   stream)
+    L.check(st, "radon_backproject_interpolating")
+    return x
+
+
 def filter_sinogram(geom: Geometry, y: torch.Tensor, filter_name: str = "ram-lak", out=None) -> torch.Tensor:
     """Each view filtered along the detector for FBP (``radon_filter_sinogram``; no autograd)."""
     if filter_name not in L.FILTERS:
@@ -484,6 +508,10 @@ class Radon:
     def filter_sinogram(self, sino: torch.Tensor, filter_name: str = "ram-lak") -> torch.Tensor:
         """Section 3.1.3: the sinogram filtered for filtered backprojection (differentiable)."""
         return FilterSinogramFunction.apply(sino, self.geometry, filter_name)
+
+    def backprojection_interpolating(self, sino: torch.Tensor) -> torch.Tensor:
+        """Pixel-driven interpolating backprojection (approximates ``backprojection``; no autograd)."""
+        return backproject_interpolating(self.geometry, sino)
 
     def fbp(self, sino: torch.Tensor, filter_name: str = "ram-lak") -> torch.Tensor:
         """Filtered backprojection: ``backprojection(filter_sinogram(sino))`` (parallel beam)."""
