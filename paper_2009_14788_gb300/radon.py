@@ -481,6 +481,32 @@ class RadonBackprojectionFunction(torch.autograd.Function):
         return forward_raw(ctx.geom, grad.contiguous(), ctx.config), None, None
 
 
+class _CastFunction(torch.autograd.Function):
+    """A differentiable dtype cast through ``radon_axpby`` (forward to ``dtype``, gradient back)."""
+
+    @staticmethod
+    def forward(ctx, x, dtype):
+        ctx.src = x.dtype
+        out = torch.empty(x.shape, dtype=dtype, device=x.device)
+        return axpby(x.contiguous(), out, 1.0, beta=0.0)
+
+    @staticmethod
+    def backward(ctx, grad):
+        out = torch.empty(grad.shape, dtype=ctx.src, device=grad.device)
+        return axpby(grad.contiguous(), out, 1.0, beta=0.0), None
+
+
+def _autocast(t: torch.Tensor) -> torch.Tensor:
+    """Under ``torch.autocast("cuda", dtype=float16 | bfloat16)`` an FP32 input takes the autocast type,
+    so the operators run their 16-bit storage paths without the caller changing dtypes (the paper's
+    transparent half precision, Section 2); outside autocast, or for other types, it passes as is."""
+    if t.dtype == torch.float32 and t.is_cuda and torch.is_autocast_enabled("cuda"):
+        dt = torch.get_autocast_dtype("cuda")
+        if dt in (torch.float16, torch.bfloat16):
+            return _CastFunction.apply(t, dt)
+    return t
+
+
 class Radon:
     """Parallel-beam projector (Section 3.1.1): ``Radon(resolution, angles, det_count=None, det_spacing=1.0)``."""
 
@@ -498,20 +524,20 @@ class Radon:
         return self.geometry.sample_count
 
     def forward(self, x: torch.Tensor) -> torch.Tensor:
-        return RadonForwardFunction.apply(x, self.geometry, self.config)
+        return RadonForwardFunction.apply(_autocast(x), self.geometry, self.config)
 
     def backprojection(self, sino: torch.Tensor) -> torch.Tensor:
-        return RadonBackprojectionFunction.apply(sino, self.geometry, self.config)
+        return RadonBackprojectionFunction.apply(_autocast(sino), self.geometry, self.config)
 
     backward = backprojection
 
     def filter_sinogram(self, sino: torch.Tensor, filter_name: str = "ram-lak") -> torch.Tensor:
         """Section 3.1.3: the sinogram filtered for filtered backprojection (differentiable)."""
-        return FilterSinogramFunction.apply(sino, self.geometry, filter_name)
+        return FilterSinogramFunction.apply(_autocast(sino), self.geometry, filter_name)
 
     def backprojection_interpolating(self, sino: torch.Tensor) -> torch.Tensor:
         """Pixel-driven interpolating backprojection (approximates ``backprojection``; no autograd)."""
-        return backproject_interpolating(self.geometry, sino)
+        return backproject_interpolating(self.geometry, _autocast(sino))
 
     def fbp(self, sino: torch.Tensor, filter_name: str = "ram-lak") -> torch.Tensor:
         """Filtered backprojection: ``backprojection(filter_sinogram(sino))`` (parallel beam)."""
