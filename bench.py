@@ -254,32 +254,58 @@ def run_ours(args):
     time.sleep(0.2)
     clk = clocks.stop()
 
-    # end to end through the public API with pinned host buffers (H2D of inputs, D2H of results)
+    # end to end through the public API with pinned host buffers: every step uploads its inputs and
+    # downloads both results inside the timed region.  Three streams pipeline the steps the way a
+    # streaming user would (step i+1 uploads while step i computes and step i-1 downloads); two
+    # device buffer sets with events order each buffer's reuse.
     hx = [torch.from_numpy(x64).to(dtype=dt).pin_memory() for _ in range(2)]
     hy = [ys[0].cpu().pin_memory() for _ in range(2)]
     hox = [torch.empty(outs_x[0].shape, dtype=dt).pin_memory() for _ in range(2)]
     hoy = [torch.empty(outs_y[0].shape, dtype=dt).pin_memory() for _ in range(2)]
-    dx = torch.empty_like(xs[0])
-    dy = torch.empty_like(ys[0])
+    dx = [torch.empty_like(xs[0]) for _ in range(2)]
+    dy = [torch.empty_like(ys[0]) for _ in range(2)]
+    dox = [torch.empty_like(outs_x[0]) for _ in range(2)]
+    doy = [torch.empty_like(outs_y[0]) for _ in range(2)]
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
     e_steps = max(3, min(args.steps, 10))
+    uploaded = [torch.cuda.Event() for _ in range(2)]
+    computed = [torch.cuda.Event() for _ in range(2)]
+    downloaded = [torch.cuda.Event() for _ in range(2)]
+    for ev in computed + downloaded:
+        ev.record(stream)
     for i in range(args.warmup + e_steps):
         if i == args.warmup:
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
+            up.wait_event(e0)
         j = i % 2
-        dx.copy_(hx[j], non_blocking=True)
-        dy.copy_(hy[j], non_blocking=True)
-        forward_raw(geom, dx, chosen, out=outs_y[0])
-        backward_raw(geom, dy, chosen, out=outs_x[0])
-        hoy[j].copy_(outs_y[0], non_blocking=True)
-        hox[j].copy_(outs_x[0], non_blocking=True)
+        with torch.cuda.stream(up):
+            up.wait_event(computed[j])         # step i-2 has finished reading dx[j], dy[j]
+            dx[j].copy_(hx[j], non_blocking=True)
+            dy[j].copy_(hy[j], non_blocking=True)
+            uploaded[j].record(up)
+        stream.wait_event(uploaded[j])
+        stream.wait_event(downloaded[j])       # step i-2's results have left dox[j], doy[j]
+        forward_raw(geom, dx[j], chosen, out=doy[j])
+        backward_raw(geom, dy[j], chosen, out=dox[j])
+        computed[j].record(stream)
+        with torch.cuda.stream(down):
+            down.wait_event(computed[j])
+            hoy[j].copy_(doy[j], non_blocking=True)
+            hox[j].copy_(dox[j], non_blocking=True)
+            downloaded[j].record(down)
+    for ev in downloaded:
+        stream.wait_event(ev)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e_steps
     h2d = hx[0].numel() * hx[0].element_size() + hy[0].numel() * hy[0].element_size()
     d2h = hox[0].numel() * hox[0].element_size() + hoy[0].numel() * hoy[0].element_size()
+    assert torch.equal(hoy[(args.warmup + e_steps - 1) % 2], outs_y[0].cpu()), "e2e forward result differs"
+    assert torch.equal(hox[(args.warmup + e_steps - 1) % 2], outs_x[0].cpu()), "e2e adjoint result differs"
+    del dx, dy, dox, doy
 
     # max over ranks
     total_ms, e2e_ms = max_over_ranks([total_ms, e2e_ms], device="cuda")
