@@ -489,9 +489,11 @@ __global__ void __launch_bounds__(kBwdPackedThreads, 3) backward_packed_kernel(c
 
     // ---------------------------------------------------------------------- consumer warps
     // each warp takes a 4 x 8 block of the tile: its pixels' detector footprints overlap more than
-    // those of a 2 x 16 strip, so the gather's shared loads touch fewer distinct addresses
+    // those of a 2 x 16 strip, so the gather's shared loads touch fewer distinct addresses.  A
+    // 16-byte shared load is served eight lanes at a time, so each group of eight lanes is a 4 x 2
+    // sub-block (narrower on the detector than a row of 8: 2.6 % faster on the fan workload)
     const int warp = tid >> 5, lane = tid & 31;
-    const int pi = (warp >> 1) * 4 + (lane >> 3), pj = (warp & 1) * 8 + (lane & 7);
+    const int pi = (warp >> 1) * 4 + ((lane & 7) >> 1), pj = (warp & 1) * 8 + (lane >> 3) * 2 + (lane & 1);
     const f32x2 p2 = f2_pack((float)pj, (float)pi);
     const f32x2 ih2_2 = f2_pack(a.ih2, a.ih2);
     const float gx = (float)(tj + pj), gy = (float)(ti + pi);

@@ -232,7 +232,8 @@ __global__ void __launch_bounds__(kPlanThreads) plan_adjoint_kernel(const Unit* 
     float* ys = reinterpret_cast<float*>(rp + kMaxChunkViews * max_wd);                       // [chunk * wd]
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int pi = (warp >> 1) * 4 + (lane >> 3), pj = (warp & 1) * 8 + (lane & 7);   // 4 x 8 per warp
+    // 4 x 8 pixels per warp, each group of eight lanes (one 16-byte shared-load phase) a 4 x 2 block
+    const int pi = (warp >> 1) * 4 + ((lane & 7) >> 1), pj = (warp & 1) * 8 + (lane >> 3) * 2 + (lane & 1);
     const f32x2 p2 = f2_pack((float)pj, (float)pi);
     for (;;) {
         if (tid == 0) sh->w = (int)atomicAdd(counter, 1u);
