@@ -658,6 +658,27 @@ def _oracle_sample_geometry(w, stride):
     return O.Geometry.from_args(gargs)
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    import platform
+    import subprocess
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def cpu_oracle_sample(w, seconds):
     """The FP64 oracle as it stands on the host cores: fwd + adjoint of the whole image batch on every
     ``stride``-th view, with the stride picked so the run takes roughly ``seconds``."""
@@ -673,7 +694,8 @@ def cpu_oracle_sample(w, seconds):
         y = O.forward(g, x)
         O.adjoint(g, y)
         dt = time.perf_counter() - t0
-        result = {"value": 2 * x.shape[0] * S / dt, "unit": "samples/s", "cores": O.num_threads(), "kind": "oracle",
+        result = {"value": 2 * x.shape[0] * S / dt, "unit": "samples/s", "cores": O.num_threads(), "cpu": cpu_model(),
+                  "kind": "oracle",
                   "sample": "fwd + adjoint of all %d images on every %d-th view (%d of %d views), %.1f s" % (
                       x.shape[0], stride, g.n_angles, w.n_views, dt),
                   "seconds": dt}
@@ -710,7 +732,8 @@ def run_reference(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": dict(workload_config(args.workload, args.storage, args.algo),
                            sample="every %d-th view" % stride),
-            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": O.num_threads(), "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": O.num_threads(), "cpu": cpu_model(),
+                             "kind": "oracle",
                              "sample": "fwd + adjoint of all %d images on every %d-th view (%d of %d views) per step"
                                        % (x.shape[0], stride, g.n_angles, w.n_views)},
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
