@@ -558,9 +558,7 @@ __global__ void __launch_bounds__(kBwdPackedThreads, 3) backward_packed_kernel(c
                     }
                 }
             }
-            mbar_arrive(&empty[st]);
-            continue;
-        }
+        } else {
         for (int vl = 0; vl < nv; ++vl) {
             const ViewF vf = view_c[st * kBwdPackedViews + vl];
             const int dlo = dlo_c[st * kBwdPackedViews + vl];
@@ -586,6 +584,7 @@ __global__ void __launch_bounds__(kBwdPackedThreads, 3) backward_packed_kernel(c
                     acc[2 * q + 1] = f2_fma(w2, y4.y, acc[2 * q + 1]);
                 }
             }
+        }
         }
         mbar_arrive(&empty[st]);
     }
