@@ -184,6 +184,38 @@ __device__ __forceinline__ float bwd_ray_weight_pair(f32x2 p2, f32x2 a0, f32x2 d
     return w;
 }
 
+// The ray-dependent part of bwd_ray_weight_pair's window start, hoisted out of the per-pixel work:
+// kap - kr = (p - A).b - kr = p.b + C with b = step / |step|^2 and C = -A.b - kr (a sentinel ray
+// has step zero, so C = -1e-4 and every weight stays zero).
+__device__ __forceinline__ float bwd_ray_window_c(const float4 A, float ih2) {
+    const float bx = A.z * ih2, by = A.w * ih2;
+    const float kr = fmaf(fabsf(A.z) + fabsf(A.w), ih2, 1e-4f);
+    return -fmaf(A.x, bx, A.y * by) - kr;
+}
+
+// bwd_ray_weight_pair with the window constant C of bwd_ray_window_c: the same samples and tent
+// products (the window start may round differently, which only moves a zero-weight sample).
+template <int KW>
+__device__ __forceinline__ float bwd_ray_weight_c(f32x2 p2, float px, float py, f32x2 a0, f32x2 d2, f32x2 ih2_2,
+                                                  float C) {
+    const f32x2 e2 = f2_sub(a0, p2);   // A - p
+    float bx, by;
+    f2_unpack(f2_mul(d2, ih2_2), &bx, &by);
+    const float ka = ceilf(fmaf(px, bx, fmaf(py, by, C)));
+    f32x2 r2 = f2_fma(f2_pack(ka, ka), d2, e2);   // ka * step - (p - A)
+    float w = 0.0f;
+#pragma unroll
+    for (int k = 0; k < KW; ++k) {
+        float rx, ry;
+        f2_unpack(r2, &rx, &ry);
+        const float wx = fmaxf(0.0f, 1.0f - fabsf(rx));
+        const float wy = fmaxf(0.0f, 1.0f - fabsf(ry));
+        w = fmaf(wx, wy, w);
+        if (k + 1 < KW) r2 = f2_add(r2, d2);
+    }
+    return w;
+}
+
 // Warp 0: windows for the views of chunk c and the TMA copies into staging slot `slot`.
 template <typename T, int BG>
 __device__ void bwd_issue_chunk(const CUtensorMap* tmap, const BwdTiledArgs& a, int c, int slot, int ti, int tj,

@@ -230,6 +230,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_adjoint_kernel(const Unit* 
     AdjShared* sh = reinterpret_cast<AdjShared*>(smem_raw);
     float4* rp = reinterpret_cast<float4*>(smem_raw + (sizeof(AdjShared) + 15) / 16 * 16);   // [chunk * wd]
     float* ys = reinterpret_cast<float*>(rp + kMaxChunkViews * max_wd);                       // [chunk * wd]
+    float* rc = ys + kMaxChunkViews * max_wd;                                                  // [chunk * wd]
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     // 4 x 8 pixels per warp, each group of eight lanes (one 16-byte shared-load phase) a 4 x 2 block
@@ -268,7 +269,9 @@ __global__ void __launch_bounds__(kPlanThreads) plan_adjoint_kernel(const Unit* 
                 const bool valid = d >= 0 && d < u.D;
                 const long long ridx = (long long)(c0 + vl) * u.D + (valid ? d : 0);
                 const RayT ray = u.rays[ridx];
-                rp[e] = bwd_ray_pos_rec(ray, valid, ti, tj, u.ih2);
+                const float4 A = bwd_ray_pos_rec(ray, valid, ti, tj, u.ih2);
+                rp[e] = A;
+                rc[e] = bwd_ray_window_c(A, u.ih2);
                 ys[e] = valid ? to_f32(y[ridx]) : 0.0f;
             }
             __syncthreads();
@@ -284,9 +287,10 @@ __global__ void __launch_bounds__(kPlanThreads) plan_adjoint_kernel(const Unit* 
                     record_device_error(err, RADON_ERR_DEVICE_BOUNDS);
                 const ulonglong2* rpv = reinterpret_cast<const ulonglong2*>(rp) + vl * wd;
                 const float* yv = ys + vl * wd;
+                const float* cv = rc + vl * wd;
                 for (int d = da; d <= db; ++d) {
                     const ulonglong2 rr = rpv[d - dlo];
-                    acc = fmaf(bwd_ray_weight_pair<KW>(p2, rr.x, rr.y, ih2_2, u.ih2), yv[d - dlo], acc);
+                    acc = fmaf(bwd_ray_weight_c<KW>(p2, (float)pj, (float)pi, rr.x, rr.y, ih2_2, cv[d - dlo]), yv[d - dlo], acc);
                 }
             }
             __syncthreads();
@@ -297,7 +301,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_adjoint_kernel(const Unit* 
 }
 
 size_t adj_smem_bytes(int max_wd) {
-    return (sizeof(AdjShared) + 15) / 16 * 16 + (size_t)kMaxChunkViews * max_wd * (16 + 4);
+    return (sizeof(AdjShared) + 15) / 16 * 16 + (size_t)kMaxChunkViews * max_wd * (16 + 4 + 4);
 }
 
 // --------------------------------------------------------------------------------------- plan
