@@ -189,6 +189,13 @@ RADON_API radon_status radon_backward(const radon_geometry* geometry, const void
 /*
  * Explicit kernel selection (comparison forms and the autotuner).
  *
+ * Under RADON_ALGO_AUTO a batch of ONE image with no tile parameters (views_per_cta, rows_per_slab,
+ * images_per_cta, tile and threads all 0) runs the single-image kernels -- the uneven-batch plan's
+ * per-image forward (one texel load per sample, FP32 weights; it needs the workspace of
+ * radon_forward_ws) and adjoint (one weight per candidate ray) -- because a batch-interleaved group
+ * would carry the image in one of its 4 to 16 slots: 2-2.6x faster forward and 1.25-1.4x faster
+ * adjoint at 512^2.  Larger batches, or explicit parameters, run the batch-interleaved kernels.
+ *
  * `weights` selects the forward projection's bilinear-weight precision for FP16 storage (Section
  * 3.3's half-precision path): 0 (default) rounds each sample's four weights to FP16 and forms every
  * product of a weight and a texel value exactly in one mixed-precision FMA accumulated in FP32 --
@@ -216,7 +223,9 @@ RADON_API radon_status radon_backward_ex(const radon_geometry* geometry, const v
 /*
  * Device workspace, in bytes, that radon_forward_ws uses for `batch` images of `dtype`: the batch
  * packed into 16-byte texels holding 4 (FP32) or 8 (16-bit) images each, once in row order and once
- * transposed.  Returns 0 for an invalid geometry, dtype or batch.
+ * transposed; for batch 1, at least the single-image forward's quad texels (each pixel's 2 x 2
+ * neighbourhood, 16 bytes for FP32 and 8 for 16-bit storage, (N + 1)^2 of them in each of the two
+ * frames).  Returns 0 for an invalid geometry, dtype or batch.
  */
 RADON_API size_t radon_forward_workspace_size(const radon_geometry* geometry, radon_dtype dtype, int batch);
 

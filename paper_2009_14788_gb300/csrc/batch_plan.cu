@@ -27,6 +27,7 @@
 #include "backward_tiled.cuh"
 #include "device_error.cuh"
 #include "dtype.cuh"
+#include "epilogue.cuh"
 #include "radon_internal.h"
 
 namespace radon {
@@ -188,6 +189,22 @@ __device__ float plan_ray(const Unit& u, const typename Quad<T>::type* __restric
     return u.h * acc;
 }
 
+// Work item `tile` of unit u (a block of G views x 256 / G detectors, one ray per thread), stored
+// through the epilogue (the identity for plans).
+template <typename T>
+__device__ __forceinline__ void plan_forward_tile(const Unit& u, int tile, const typename Quad<T>::type* __restrict__ quads,
+                                                  const Epilogue& ep) {
+    const int G = u.cfg, Dt = kPlanThreads / G;
+    const int n_dr = (u.D + Dt - 1) / Dt;
+    const int vg = tile / n_dr, dr = tile - (tile / n_dr) * n_dr;
+    const int v = vg * G + (int)threadIdx.x / Dt, d = dr * Dt + (int)threadIdx.x % Dt;
+    if (v < u.V && d < u.D) {
+        const float y = plan_ray<T>(u, quads, v, d);
+        const long long idx = (long long)v * u.D + d;
+        static_cast<T*>(u.out)[idx] = from_f32<T>(epilogue_value<T>(ep, y, idx));
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kPlanThreads) plan_forward_kernel(const Unit* __restrict__ units,
                                                                     const Work* __restrict__ work, int n_work,
@@ -201,16 +218,33 @@ __global__ void __launch_bounds__(kPlanThreads) plan_forward_kernel(const Unit* 
         __syncthreads();
         if (wi >= n_work) return;
         const Work w = work[wi];
-        const Unit& u = units[w.unit];
-        const int G = u.cfg, Dt = kPlanThreads / G;
-        const int n_dr = (u.D + Dt - 1) / Dt;
-        const int vg = w.tile / n_dr, dr = w.tile - (w.tile / n_dr) * n_dr;
-        const int v = vg * G + (int)threadIdx.x / Dt, d = dr * Dt + (int)threadIdx.x % Dt;
-        if (v < u.V && d < u.D) {
-            const float y = plan_ray<T>(u, quads, v, d);
-            static_cast<T*>(u.out)[(long long)v * u.D + d] = from_f32<T>(y);
-        }
+        plan_forward_tile<T>(units[w.unit], w.tile, quads, Epilogue{1.0f, nullptr, 0.0f, nullptr});
     }
+}
+
+// Single image (a batch-1 call): the same work items, one CTA each, the unit passed by value.
+template <typename T>
+__global__ void __launch_bounds__(256) single_pack_kernel(const Unit u, typename Quad<T>::type* __restrict__ quads) {
+    const T* x = static_cast<const T*>(u.in);
+    const long long p = (long long)u.n + 1, total = 2 * p * p;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+        long long e = g;
+        const int frame = e >= p * p ? 1 : 0;
+        if (frame) e -= p * p;
+        const int i = (int)(e / p) - 1, j = (int)(e - (e / p) * p) - 1;
+        quads[g] = frame == 0 ? Quad<T>::make(pix(x, u.n, i, j), pix(x, u.n, i, j + 1), pix(x, u.n, i + 1, j),
+                                              pix(x, u.n, i + 1, j + 1))
+                              : Quad<T>::make(pix(x, u.n, j, i), pix(x, u.n, j + 1, i), pix(x, u.n, j, i + 1),
+                                              pix(x, u.n, j + 1, i + 1));
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPlanThreads) single_forward_kernel(const Unit u,
+                                                                      const typename Quad<T>::type* __restrict__ quads,
+                                                                      const Epilogue ep) {
+    plan_forward_tile<T>(u, (int)blockIdx.x, quads, ep);
 }
 
 // ------------------------------------------------------------------------------------- adjoint
@@ -222,82 +256,112 @@ struct AdjShared {
     int w;
 };
 
+// Staging buffers of the adjoint's view chunks in dynamic shared memory.
+struct AdjBuffers {
+    AdjShared* sh;
+    float4* rp;   // [chunk * wd] re-based ray positions and steps
+    float* ys;    // [chunk * wd] sinogram values
+    float* rc;    // [chunk * wd] window constants
+};
+
+__device__ __forceinline__ AdjBuffers adj_buffers(unsigned char* smem_raw, int max_wd) {
+    AdjBuffers b;
+    b.sh = reinterpret_cast<AdjShared*>(smem_raw);
+    b.rp = reinterpret_cast<float4*>(smem_raw + (sizeof(AdjShared) + 15) / 16 * 16);
+    b.ys = reinterpret_cast<float*>(b.rp + kMaxChunkViews * max_wd);
+    b.rc = b.ys + kMaxChunkViews * max_wd;
+    return b;
+}
+
+// Work item `tile` of unit u (a 16 x 16 pixel tile over all views), stored through the epilogue
+// (the identity for plans).  Every thread of the CTA calls it (it holds CTA barriers).
 template <typename T, int KW>
-__global__ void __launch_bounds__(kPlanThreads) plan_adjoint_kernel(const Unit* __restrict__ units,
-                                                                    const Work* __restrict__ work, int n_work,
-                                                                    unsigned* counter, int max_wd, int* err) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    AdjShared* sh = reinterpret_cast<AdjShared*>(smem_raw);
-    float4* rp = reinterpret_cast<float4*>(smem_raw + (sizeof(AdjShared) + 15) / 16 * 16);   // [chunk * wd]
-    float* ys = reinterpret_cast<float*>(rp + kMaxChunkViews * max_wd);                       // [chunk * wd]
-    float* rc = ys + kMaxChunkViews * max_wd;                                                  // [chunk * wd]
+__device__ void plan_adjoint_tile(const Unit& u, int tile, const AdjBuffers& b, const Epilogue& ep, int* err) {
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     // 4 x 8 pixels per warp, each group of eight lanes (one 16-byte shared-load phase) a 4 x 2 block
     const int pi = (warp >> 1) * 4 + ((lane & 7) >> 1), pj = (warp & 1) * 8 + (lane >> 3) * 2 + (lane & 1);
     const f32x2 p2 = f2_pack((float)pj, (float)pi);
-    for (;;) {
-        if (tid == 0) sh->w = (int)atomicAdd(counter, 1u);
+    const int tiles_x = (u.n + kBwdTile - 1) / kBwdTile;
+    const int ti = (tile / tiles_x) * kBwdTile, tj = (tile - (tile / tiles_x) * tiles_x) * kBwdTile;
+    const float gx = (float)(tj + pj), gy = (float)(ti + pi);
+    const bool inside = (ti + pi) < u.n && (tj + pj) < u.n;
+    const f32x2 ih2_2 = f2_pack(u.ih2, u.ih2);
+    const T* y = static_cast<const T*>(u.in);
+    const int CV = u.cfg, wd = u.wd;
+    float acc = 0.0f;
+    for (int c0 = 0; c0 < u.V; c0 += CV) {
+        const int nv = min(CV, u.V - c0);
+        if (tid < nv) {
+            const ViewF vf = u.views[c0 + tid];
+            int dlo;
+            float r;
+            bwd_view_window(vf, ti, tj, u.n, &dlo, &r);
+            b.sh->view[tid] = vf;
+            b.sh->dlo[tid] = dlo;
+            b.sh->r[tid] = r;
+        }
         __syncthreads();
-        const int wi = sh->w;
+        for (int e = tid; e < nv * wd; e += kPlanThreads) {
+            const int vl = e / wd, dl = e - (e / wd) * wd;
+            const int d = b.sh->dlo[vl] + dl;
+            const bool valid = d >= 0 && d < u.D;
+            const long long ridx = (long long)(c0 + vl) * u.D + (valid ? d : 0);
+            const RayT ray = u.rays[ridx];
+            const float4 A = bwd_ray_pos_rec(ray, valid, ti, tj, u.ih2);
+            b.rp[e] = A;
+            b.rc[e] = bwd_ray_window_c(A, u.ih2);
+            b.ys[e] = valid ? to_f32(y[ridx]) : 0.0f;
+        }
+        __syncthreads();
+        for (int vl = 0; vl < nv; ++vl) {
+            const ViewF vf = b.sh->view[vl];
+            const int dlo = b.sh->dlo[vl];
+            const float r = b.sh->r[vl];
+            const float t = __fdividef(fmaf(vf.ax, gx, fmaf(vf.ay, gy, vf.a0)), fmaf(vf.bx, gx, fmaf(vf.by, gy, vf.b0)));
+            const float flo = ceilf(t - r), fhi = floorf(t + r);
+            const int da = (int)fmaxf(flo, (float)max(dlo, 0));
+            const int db = (int)fminf(fhi, (float)min(u.D - 1, dlo + wd - 1));
+            if (inside && ((flo < (float)dlo && flo >= 0.0f) || (fhi > (float)(dlo + wd - 1) && fhi <= (float)(u.D - 1))))
+                record_device_error(err, RADON_ERR_DEVICE_BOUNDS);
+            const ulonglong2* rpv = reinterpret_cast<const ulonglong2*>(b.rp) + vl * wd;
+            const float* yv = b.ys + vl * wd;
+            const float* cv = b.rc + vl * wd;
+            for (int d = da; d <= db; ++d) {
+                const ulonglong2 rr = rpv[d - dlo];
+                acc = fmaf(bwd_ray_weight_c<KW>(p2, (float)pj, (float)pi, rr.x, rr.y, ih2_2, cv[d - dlo]), yv[d - dlo], acc);
+            }
+        }
+        __syncthreads();
+    }
+    if (inside) {
+        const long long idx = (long long)(ti + pi) * u.n + (tj + pj);
+        static_cast<T*>(u.out)[idx] = from_f32<T>(epilogue_value<T>(ep, u.h * acc, idx));
+    }
+}
+
+template <typename T, int KW>
+__global__ void __launch_bounds__(kPlanThreads) plan_adjoint_kernel(const Unit* __restrict__ units,
+                                                                    const Work* __restrict__ work, int n_work,
+                                                                    unsigned* counter, int max_wd, int* err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const AdjBuffers b = adj_buffers(smem_raw, max_wd);
+    for (;;) {
+        // the previous tile's last barrier orders its reads of `w` before this write
+        if (threadIdx.x == 0) b.sh->w = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int wi = b.sh->w;
         if (wi >= n_work) return;
         const Work w = work[wi];
-        const Unit& u = units[w.unit];
-        const int tiles_x = (u.n + kBwdTile - 1) / kBwdTile;
-        const int ti = (w.tile / tiles_x) * kBwdTile, tj = (w.tile - (w.tile / tiles_x) * tiles_x) * kBwdTile;
-        const float gx = (float)(tj + pj), gy = (float)(ti + pi);
-        const bool inside = (ti + pi) < u.n && (tj + pj) < u.n;
-        const f32x2 ih2_2 = f2_pack(u.ih2, u.ih2);
-        const T* y = static_cast<const T*>(u.in);
-        const int CV = u.cfg, wd = u.wd;
-        float acc = 0.0f;
-        for (int c0 = 0; c0 < u.V; c0 += CV) {
-            const int nv = min(CV, u.V - c0);
-            if (tid < nv) {
-                const ViewF vf = u.views[c0 + tid];
-                int dlo;
-                float r;
-                bwd_view_window(vf, ti, tj, u.n, &dlo, &r);
-                sh->view[tid] = vf;
-                sh->dlo[tid] = dlo;
-                sh->r[tid] = r;
-            }
-            __syncthreads();
-            for (int e = tid; e < nv * wd; e += kPlanThreads) {
-                const int vl = e / wd, dl = e - (e / wd) * wd;
-                const int d = sh->dlo[vl] + dl;
-                const bool valid = d >= 0 && d < u.D;
-                const long long ridx = (long long)(c0 + vl) * u.D + (valid ? d : 0);
-                const RayT ray = u.rays[ridx];
-                const float4 A = bwd_ray_pos_rec(ray, valid, ti, tj, u.ih2);
-                rp[e] = A;
-                rc[e] = bwd_ray_window_c(A, u.ih2);
-                ys[e] = valid ? to_f32(y[ridx]) : 0.0f;
-            }
-            __syncthreads();
-            for (int vl = 0; vl < nv; ++vl) {
-                const ViewF vf = sh->view[vl];
-                const int dlo = sh->dlo[vl];
-                const float r = sh->r[vl];
-                const float t = __fdividef(fmaf(vf.ax, gx, fmaf(vf.ay, gy, vf.a0)), fmaf(vf.bx, gx, fmaf(vf.by, gy, vf.b0)));
-                const float flo = ceilf(t - r), fhi = floorf(t + r);
-                const int da = (int)fmaxf(flo, (float)max(dlo, 0));
-                const int db = (int)fminf(fhi, (float)min(u.D - 1, dlo + wd - 1));
-                if (inside && ((flo < (float)dlo && flo >= 0.0f) || (fhi > (float)(dlo + wd - 1) && fhi <= (float)(u.D - 1))))
-                    record_device_error(err, RADON_ERR_DEVICE_BOUNDS);
-                const ulonglong2* rpv = reinterpret_cast<const ulonglong2*>(rp) + vl * wd;
-                const float* yv = ys + vl * wd;
-                const float* cv = rc + vl * wd;
-                for (int d = da; d <= db; ++d) {
-                    const ulonglong2 rr = rpv[d - dlo];
-                    acc = fmaf(bwd_ray_weight_c<KW>(p2, (float)pj, (float)pi, rr.x, rr.y, ih2_2, cv[d - dlo]), yv[d - dlo], acc);
-                }
-            }
-            __syncthreads();
-        }
-        if (inside)
-            static_cast<T*>(u.out)[(long long)(ti + pi) * u.n + (tj + pj)] = from_f32<T>(u.h * acc);
+        plan_adjoint_tile<T, KW>(units[w.unit], w.tile, b, Epilogue{1.0f, nullptr, 0.0f, nullptr}, err);
     }
+}
+
+// Single image (a batch-1 call): one CTA per tile, the unit passed by value.
+template <typename T, int KW>
+__global__ void __launch_bounds__(kPlanThreads) single_adjoint_kernel(const Unit u, const Epilogue ep, int* err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    plan_adjoint_tile<T, KW>(u, (int)blockIdx.x, adj_buffers(smem_raw, u.wd), ep, err);
 }
 
 size_t adj_smem_bytes(int max_wd) {
@@ -308,7 +372,114 @@ size_t adj_smem_bytes(int max_wd) {
 
 size_t texel_bytes(radon_dtype dt) { return dt == RADON_F32 ? 16 : 8; }
 
+// One image through the plan's kernels, without a plan: the unit is a kernel argument and every
+// work item is its own CTA, so a call allocates nothing and can be captured.
+constexpr int kSingleForwardViews = 8;    // views per ray block (the plan's default)
+constexpr int kSingleAdjointViews = 16;   // views per staged chunk (the autotuner's pick at every size)
+
+Unit single_unit(const radon_geometry* g, const void* in, void* out, int cfg) {
+    Unit u;
+    u.in = in;
+    u.out = out;
+    u.rays = g->d_ray;
+    u.nks = g->d_nk;
+    u.views = g->d_view;
+    u.q_off = 0;
+    u.n = g->n;
+    u.V = g->V;
+    u.D = g->D;
+    u.h = (float)g->h;
+    u.ih2 = (float)(1.0 / (g->h * g->h));
+    u.wd = g->bwd_window + 2;
+    u.cfg = cfg;
+    return u;
+}
+
+template <typename T>
+radon_status single_forward_t(const radon_geometry* g, const void* img, void* sino, void* ws, const Epilogue& ep,
+                              cudaStream_t s) {
+    using Q = typename Quad<T>::type;
+    const Unit u = single_unit(g, img, sino, kSingleForwardViews);
+    const long long texels = 2LL * (g->n + 1) * (g->n + 1);
+    const unsigned pack_blocks = (unsigned)std::min<long long>((texels + 255) / 256, 152LL * 64);
+    single_pack_kernel<T><<<pack_blocks, 256, 0, s>>>(u, static_cast<Q*>(ws));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "single-image pack launch");
+    count_launches(1);
+    const int Dt = kPlanThreads / kSingleForwardViews;
+    const long long blocks = (long long)((g->V + kSingleForwardViews - 1) / kSingleForwardViews) * ((g->D + Dt - 1) / Dt);
+    single_forward_kernel<T><<<(unsigned)blocks, kPlanThreads, 0, s>>>(u, static_cast<const Q*>(ws), ep);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "single-image forward launch");
+    count_launches(1);
+    return RADON_OK;
+}
+
+template <typename T, int KW>
+radon_status single_backward_tk(const Unit& u, long long tiles, size_t smem, const Epilogue& ep, int* err,
+                                cudaStream_t s) {
+    auto kern = single_adjoint_kernel<T, KW>;
+    static size_t attr_bytes = 0;
+    if (smem > attr_bytes) {
+        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e, "single-image adjoint shared memory");
+        attr_bytes = smem;
+    }
+    kern<<<(unsigned)tiles, kPlanThreads, smem, s>>>(u, ep, err);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "single-image adjoint launch");
+    count_launches(1);
+    return RADON_OK;
+}
+
+template <typename T>
+radon_status single_backward_t(const radon_geometry* g, const void* sino, void* img, const Epilogue& ep, cudaStream_t s,
+                               std::string* why) {
+    const Unit u = single_unit(g, sino, img, kSingleAdjointViews);
+    const int kw_needed = (int)std::floor(2.0 * std::sqrt(2.0) / g->h + 2e-4) + 1;
+    if (kw_needed > 6) {
+        *why = "sampling step too small for the single-image adjoint";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    const size_t smem = adj_smem_bytes(u.wd);
+    if (smem > 227 * 1024) {
+        *why = "detector window too wide for the single-image adjoint";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    int* err = device_error_word();
+    if (err == nullptr) {
+        *why = "device error word unavailable";
+        return RADON_ERR_CUDA;
+    }
+    const long long tiles_x = (g->n + kBwdTile - 1) / kBwdTile;
+    return kw_needed <= 3 ? single_backward_tk<T, 3>(u, tiles_x * tiles_x, smem, ep, err, s)
+                          : single_backward_tk<T, 6>(u, tiles_x * tiles_x, smem, ep, err, s);
+}
+
 }  // namespace
+
+size_t single_forward_workspace_bytes(const radon_geometry* g, radon_dtype dt) {
+    const size_t p = (size_t)g->n + 1;
+    return 2 * p * p * texel_bytes(dt);
+}
+
+radon_status launch_forward_single(const radon_geometry* g, const void* img, void* sino, radon_dtype dt, void* ws,
+                                   const Epilogue& ep, cudaStream_t s) {
+    switch (dt) {
+        case RADON_F16: return single_forward_t<__half>(g, img, sino, ws, ep, s);
+        case RADON_BF16: return single_forward_t<__nv_bfloat16>(g, img, sino, ws, ep, s);
+        default: return single_forward_t<float>(g, img, sino, ws, ep, s);
+    }
+}
+
+radon_status launch_backward_single(const radon_geometry* g, const void* sino, void* img, radon_dtype dt,
+                                    const Epilogue& ep, cudaStream_t s, std::string* why) {
+    switch (dt) {
+        case RADON_F16: return single_backward_t<__half>(g, sino, img, ep, s, why);
+        case RADON_BF16: return single_backward_t<__nv_bfloat16>(g, sino, img, ep, s, why);
+        default: return single_backward_t<float>(g, sino, img, ep, s, why);
+    }
+}
 
 }  // namespace radon
 

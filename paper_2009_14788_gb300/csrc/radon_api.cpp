@@ -221,6 +221,23 @@ radon_status project(const radon_geometry* g, const void* in, void* out, radon_d
     if (st != RADON_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const int images = cfg ? cfg->images_per_cta : 0;
+    // One image under AUTO with no tile parameters: the single-image kernels (a batch-interleaved
+    // group would carry the image in one of its 4 / 8 / 16 slots).  The forward needs its quad
+    // texels in the workspace; without one it continues below.
+    const bool single = algo == RADON_ALGO_AUTO && batch == 1 &&
+                        (cfg == nullptr || (cfg->views_per_cta == 0 && cfg->rows_per_slab == 0 &&
+                                            cfg->images_per_cta == 0 && cfg->tile == 0 && cfg->threads == 0));
+    if (single && !forward) {
+        std::string why;
+        st = launch_backward_single(g, in, out, dt, ep, s, &why);
+        if (st == RADON_OK) return RADON_OK;
+        if (st != RADON_ERR_UNSUPPORTED) return fail(st, why);
+    }
+    if (single && forward && ws != nullptr && ws_bytes >= single_forward_workspace_bytes(g, dt)) {
+        st = launch_forward_single(g, in, out, dt, ws, ep, s);
+        if (st != RADON_OK) return st;
+        return RADON_OK;
+    }
     if (!forward && algo != RADON_ALGO_PLAIN && ws != nullptr) {
         // Packed path: pack the sinogram batch once, then copy detector windows straight into
         // shared memory.  A too small workspace or a geometry the kernel refuses continues below.
@@ -400,6 +417,8 @@ size_t radon_forward_workspace_size(const radon_geometry* g, radon_dtype dtype, 
     if (validate_geometry(g) != RADON_OK) return 0;
     if (dtype != RADON_F32 && dtype != RADON_F16 && dtype != RADON_BF16) return 0;
     if (batch < 0) return 0;
+    // a single image runs the single-image forward, whose quad texels carry a one-pixel border
+    if (batch == 1) return std::max(packed_image_bytes(g->n, batch, dtype), single_forward_workspace_bytes(g, dtype));
     return packed_image_bytes(g->n, batch, dtype);
 }
 

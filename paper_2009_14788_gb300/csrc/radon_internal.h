@@ -127,6 +127,16 @@ radon_status launch_forward_packed(radon_geometry* g, const void* packed, void* 
                                    const radon_launch_config* cfg, const Epilogue& ep, cudaStream_t s,
                                    std::string* why);
 
+// batch_plan.cu: one image (a batch-1 call) through the uneven-batch plan's kernels -- one texel load
+// per forward sample, one weight per adjoint candidate -- instead of a batch-interleaved group that
+// the image would fill to one eighth.  The forward packs the image's quad texels into `ws`
+// (single_forward_workspace_bytes, 16-byte aligned); the adjoint needs no workspace.
+size_t single_forward_workspace_bytes(const radon_geometry* g, radon_dtype dt);
+radon_status launch_forward_single(const radon_geometry* g, const void* img, void* sino, radon_dtype dt, void* ws,
+                                   const Epilogue& ep, cudaStream_t s);
+radon_status launch_backward_single(const radon_geometry* g, const void* sino, void* img, radon_dtype dt,
+                                    const Epilogue& ep, cudaStream_t s, std::string* why);
+
 // pack.cu
 size_t packed_image_bytes(int n, int batch, radon_dtype dt);
 cudaError_t launch_pack_images(const void* img, void* workspace, int n, int batch, radon_dtype dt, cudaStream_t s);
