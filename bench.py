@@ -451,8 +451,8 @@ def run_secondary(args):
     y = y32.to(torch.bfloat16)
     lw = Landweber(g)
     v0 = torch.from_numpy(power_start(g.n, 2000 * w.number)).to("cuda", torch.float32)
-    ms_power = time_it(lambda: lw.estimate_alpha(P, v0=v0), 3)
-    alpha, lam = lw.estimate_alpha(P, v0=v0)
+    ms_power = time_it(lambda: lw.power(P, v0=v0), 3)
+    alpha, lam = lw.power(P, v0=v0)
     x0 = torch.zeros((w.batch, g.n, g.n), dtype=torch.bfloat16, device="cuda")
     yg = y.clone().requires_grad_(True)
     ag = alpha.clone().requires_grad_(True)

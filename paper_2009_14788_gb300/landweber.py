@@ -109,7 +109,17 @@ class Landweber:
         self.geometry: Geometry = radon.geometry if hasattr(radon, "geometry") else radon
         self.config = config if config is not None else getattr(radon, "config", None)
 
-    def estimate_alpha(self, iterations: int = 20, v0: torch.Tensor | None = None, seed: int = 0, device=None):
+    def estimate_alpha(self, img_size: int | None = None, device=None, n_iter: int = 20,
+                       v0: torch.Tensor | None = None, seed: int = 0) -> torch.Tensor:
+        """The step size alpha = 1 / lambda_max(A^T A) as a one-element float32 device tensor, from
+        ``n_iter`` power steps (the paper's call ``estimate_alpha(image_size, device)``, whose result
+        is then scaled, e.g. by 0.95).  ``img_size``, if given, must be the geometry's N."""
+        if img_size is not None and int(img_size) != self.geometry.n:
+            raise ValueError("img_size %d does not match the geometry's %d" % (int(img_size), self.geometry.n))
+        alpha, _ = self.power(n_iter, v0=v0, seed=seed, device=device)
+        return alpha
+
+    def power(self, iterations: int = 20, v0: torch.Tensor | None = None, seed: int = 0, device=None):
         """(alpha, lambda) from ``iterations`` power steps, as one-element float32 device tensors.
 
         ``v0`` is the start vector (float32 N x N on the GPU); if omitted it is drawn N(0, 1) from

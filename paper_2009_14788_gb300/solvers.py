@@ -1,11 +1,16 @@
 """Conjugate-gradient solvers (Section 2.1's solvers module, used in Section 4.2), every image of a
 batch its own problem, every vector operation in libradon's batched kernels.
 
-* ``cgne(radon, x0, y, iterations)``: CG on the normal equation A^T A x = A^T y (Hanke's CGNE), run
+* ``cgne(radon, x0, y, max_iter)``: CG on the normal equation A^T A x = A^T y (Hanke's CGNE), run
   entirely on the device by ``radon_cgne``.
-* ``cg(apply_op, x0, b, iterations)``: CG for a symmetric positive (semi-)definite operator given as
-  a callable on batches (e.g. a regularised normal operator built from the projector), with per-item
-  step lengths from ``radon_dot_batched`` / ``radon_safe_divide`` / ``radon_axpby_batched``.
+* ``cg(apply_op, x0, b, max_iter)``: CG for a symmetric positive (semi-)definite operator given as
+  a callable on tensors shaped like x0 (e.g. a regularised normal operator built from the projector),
+  with per-item step lengths from ``radon_dot_batched`` / ``radon_safe_divide`` /
+  ``radon_axpby_batched``.
+
+Both run exactly ``max_iter`` iterations (the paper's solvers take the count under that name;
+``iterations=`` is accepted as well); a zero denominator gives a zero step, so a converged problem
+stays put.
 """
 
 from __future__ import annotations
@@ -48,8 +53,19 @@ class _Vec:
         return out
 
 
-def cgne(radon, x0: torch.Tensor, y: torch.Tensor, iterations: int) -> torch.Tensor:
+def _count(max_iter, iterations) -> int:
+    if (max_iter is None) == (iterations is None):
+        raise ValueError("give the iteration count once, as max_iter (or iterations)")
+    n = int(max_iter if max_iter is not None else iterations)
+    if n < 0:
+        raise ValueError("the iteration count must be >= 0")
+    return n
+
+
+def cgne(radon, x0: torch.Tensor, y: torch.Tensor, max_iter: int | None = None, *,
+         iterations: int | None = None) -> torch.Tensor:
     """x_K of CGNE from x0 (``[B, N, N]`` or ``[N, N]``, FP32) for sinograms y (``radon_cgne``)."""
+    iterations = _count(max_iter, iterations)
     geom: Geometry = radon.geometry if hasattr(radon, "geometry") else radon
     if x0.dtype != torch.float32 or y.dtype != torch.float32:
         raise ValueError("CGNE runs on FP32 tensors")
@@ -69,11 +85,15 @@ def cgne(radon, x0: torch.Tensor, y: torch.Tensor, iterations: int) -> torch.Ten
     return x[0] if single else x
 
 
-def cg(apply_op, x0: torch.Tensor, b: torch.Tensor, iterations: int) -> torch.Tensor:
-    """x_K of CG for apply_op(x) = b, every item along the leading axis its own problem."""
+def cg(apply_op, x0: torch.Tensor, b: torch.Tensor, max_iter: int | None = None, *,
+       iterations: int | None = None) -> torch.Tensor:
+    """x_K of CG for apply_op(x) = b: a ``[B, ...]`` tensor holds B problems (one per item along the
+    leading axis), a one- or two-dimensional tensor (one image) one problem; apply_op receives and
+    returns tensors shaped like x0."""
+    iterations = _count(max_iter, iterations)
     if x0.shape != b.shape or x0.dtype != b.dtype:
         raise ValueError("x0 and b must share shape and dtype")
-    batch = x0.shape[0]
+    batch = x0.shape[0] if x0.dim() >= 3 else 1
     v = _Vec(batch, x0.device)
     f32 = dict(dtype=torch.float32, device=x0.device)
     x = v.axpby(x0.contiguous(), torch.empty_like(x0, memory_format=torch.contiguous_format), 1.0)
