@@ -115,6 +115,7 @@ radon_status launch_forward_tiled(radon_geometry* g, const void* img, void* sino
     }
     a.spin_limit = kSpinLimit;
     a.stages = 2;
+    a.vec_store = (g->D % 2 == 0 && ((uintptr_t)sino % (2 * esz)) == 0) ? 1 : 0;
     const long long nblk = (long long)g->group_count[gi] * a.n_dr;
     if (nblk > 0x7fffffffLL) {
         *why = "too many CTAs";
@@ -241,6 +242,7 @@ radon_status launch_forward_packed(radon_geometry* g, const void* packed, void* 
     }
     a.spin_limit = kSpinLimit;
     a.stages = stages;
+    a.vec_store = (g->D % 2 == 0 && ((uintptr_t)sino % (2 * esz)) == 0) ? 1 : 0;
     const long long nblk = (long long)g->group_count[gi] * a.n_dr;
     dim3 grid((unsigned)nblk, (unsigned)groups);
     cudaError_t e;

@@ -52,7 +52,25 @@ struct FwdTiledArgs {
     uint32_t spin_limit;
     Epilogue ep;
     int stages;           // compute buffers in the ring (packed: 2..4; repacking: 2)
+    int vec_store;        // 1: D even and the sinogram aligned to two elements (paired stores)
 };
+
+// Two consecutive outputs as one 4-byte (16-bit storage) or 8-byte (FP32) store; `p` is aligned to
+// two elements.
+template <typename T>
+__device__ __forceinline__ void store_pair(T* p, float lo, float hi);
+template <>
+__device__ __forceinline__ void store_pair<float>(float* p, float lo, float hi) {
+    *reinterpret_cast<float2*>(p) = make_float2(lo, hi);
+}
+template <>
+__device__ __forceinline__ void store_pair<__half>(__half* p, float lo, float hi) {
+    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(lo, hi);
+}
+template <>
+__device__ __forceinline__ void store_pair<__nv_bfloat16>(__nv_bfloat16* p, float lo, float hi) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(lo, hi);
+}
 
 constexpr int kFwdMaxStages = 4;
 
@@ -389,16 +407,30 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
         }
         mbar_arrive(&empty[buf]);   // this thread's reads of the buffer are done
     }
-    if (active) {
-        T* out = reinterpret_cast<T*>(a.sino);
-        const long long vd = (long long)a.V * a.D;
-        const long long o = (long long)(v0 + vl) * a.D + d;
+    // Stores: consecutive lanes hold consecutive detectors of one view (coalesced).  With vec_store
+    // (D even and the output aligned to two elements, so every even detector's index is even) and the
+    // whole warp present, each even lane also takes its odd neighbour's value and writes both as one
+    // two-element vector.
+    T* out = reinterpret_cast<T*>(a.sino);
+    const long long vd = (long long)a.V * a.D;
+    const long long o = (long long)(v0 + vl) * a.D + d;
+    const bool pairs = a.vec_store != 0 && __activemask() == 0xffffffffu;
 #pragma unroll
-        for (int b = 0; b < BG; ++b)
-            if (b0 + b < a.B) {
-                const long long idx = (long long)(b0 + b) * vd + o;
-                out[idx] = from_f32<T>(epilogue_value<T>(a.ep, a.h * acc[b], idx));
-            }
+    for (int b = 0; b < BG; ++b) {
+        const bool mine = active && b0 + b < a.B;
+        const long long idx = (long long)(b0 + b) * vd + o;
+        const float val = mine ? epilogue_value<T>(a.ep, a.h * acc[b], idx) : 0.0f;
+        if (pairs) {
+            const float nval = __shfl_xor_sync(0xffffffffu, val, 1);
+            const bool nmine = __shfl_xor_sync(0xffffffffu, mine ? 1 : 0, 1) != 0;
+            const bool even = (threadIdx.x & 1) == 0;
+            if (mine && even && nmine)
+                store_pair<T>(out + idx, val, nval);
+            else if (mine && (even || !nmine))
+                out[idx] = from_f32<T>(val);
+        } else if (mine) {
+            out[idx] = from_f32<T>(val);
+        }
     }
 }
 
