@@ -483,7 +483,8 @@ typedef struct radon_plan radon_plan;
 typedef struct radon_plan_options {
     int autotune;            /* 1: time the candidates (default); 0: library defaults */
     int forward_views;       /* > 0: views per forward ray block (1, 2, 4 or 8; detectors = 256 / views) */
-    int adjoint_views;       /* > 0: views per adjoint chunk (4, 8 or 16) */
+    int adjoint_views;       /* > 0: views per adjoint chunk (4, 8, 16 or 32; RADON_ERR_UNSUPPORTED if 32
+                                views of the widest detector window do not fit one CTA's shared memory) */
 } radon_plan_options;
 
 /*

@@ -36,7 +36,7 @@ namespace {
 
 constexpr uint64_t kPlanMagic = 0x5241444f4e504c4eULL;   // "RADONPLN"
 constexpr int kPlanThreads = 256;
-constexpr int kMaxChunkViews = 16;
+constexpr int kMaxChunkViews = 32;   // adjoint: views per staged chunk at most (16 where 32 do not fit)
 
 struct Unit {
     const void* in;
@@ -264,12 +264,13 @@ struct AdjBuffers {
     float* rc;    // [chunk * wd] window constants
 };
 
-__device__ __forceinline__ AdjBuffers adj_buffers(unsigned char* smem_raw, int max_wd) {
+// `cap` views per chunk at most, `max_wd` rays per view window.
+__device__ __forceinline__ AdjBuffers adj_buffers(unsigned char* smem_raw, int max_wd, int cap) {
     AdjBuffers b;
     b.sh = reinterpret_cast<AdjShared*>(smem_raw);
     b.rp = reinterpret_cast<float4*>(smem_raw + (sizeof(AdjShared) + 15) / 16 * 16);
-    b.ys = reinterpret_cast<float*>(b.rp + kMaxChunkViews * max_wd);
-    b.rc = b.ys + kMaxChunkViews * max_wd;
+    b.ys = reinterpret_cast<float*>(b.rp + cap * max_wd);
+    b.rc = b.ys + cap * max_wd;
     return b;
 }
 
@@ -343,9 +344,9 @@ __device__ void plan_adjoint_tile(const Unit& u, int tile, const AdjBuffers& b, 
 template <typename T, int KW>
 __global__ void __launch_bounds__(kPlanThreads) plan_adjoint_kernel(const Unit* __restrict__ units,
                                                                     const Work* __restrict__ work, int n_work,
-                                                                    unsigned* counter, int max_wd, int* err) {
+                                                                    unsigned* counter, int max_wd, int cap, int* err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const AdjBuffers b = adj_buffers(smem_raw, max_wd);
+    const AdjBuffers b = adj_buffers(smem_raw, max_wd, cap);
     for (;;) {
         // the previous tile's last barrier orders its reads of `w` before this write
         if (threadIdx.x == 0) b.sh->w = (int)atomicAdd(counter, 1u);
@@ -361,11 +362,19 @@ __global__ void __launch_bounds__(kPlanThreads) plan_adjoint_kernel(const Unit* 
 template <typename T, int KW>
 __global__ void __launch_bounds__(kPlanThreads) single_adjoint_kernel(const Unit u, const Epilogue ep, int* err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    plan_adjoint_tile<T, KW>(u, (int)blockIdx.x, adj_buffers(smem_raw, u.wd), ep, err);
+    plan_adjoint_tile<T, KW>(u, (int)blockIdx.x, adj_buffers(smem_raw, u.wd, u.cfg), ep, err);
 }
 
-size_t adj_smem_bytes(int max_wd) {
-    return (sizeof(AdjShared) + 15) / 16 * 16 + (size_t)kMaxChunkViews * max_wd * (16 + 4 + 4);
+size_t adj_smem_bytes(int max_wd, int cap) {
+    return (sizeof(AdjShared) + 15) / 16 * 16 + (size_t)cap * max_wd * (16 + 4 + 4);
+}
+
+// Views per chunk at most for windows of max_wd rays: 32 where the staging fits one CTA's shared
+// memory, else 16; 0 if not even 16 fit.
+int adj_chunk_cap(int max_wd) {
+    if (adj_smem_bytes(max_wd, kMaxChunkViews) <= 227 * 1024) return kMaxChunkViews;
+    if (adj_smem_bytes(max_wd, 16) <= 227 * 1024) return 16;
+    return 0;
 }
 
 // --------------------------------------------------------------------------------------- plan
@@ -375,7 +384,7 @@ size_t texel_bytes(radon_dtype dt) { return dt == RADON_F32 ? 16 : 8; }
 // One image through the plan's kernels, without a plan: the unit is a kernel argument and every
 // work item is its own CTA, so a call allocates nothing and can be captured.
 constexpr int kSingleForwardViews = 8;    // views per ray block (the plan's default)
-constexpr int kSingleAdjointViews = 16;   // views per staged chunk (the autotuner's pick at every size)
+constexpr int kSingleAdjointViews = 32;   // views per staged chunk (the autotuner's pick at every size)
 
 Unit single_unit(const radon_geometry* g, const void* in, void* out, int cfg) {
     Unit u;
@@ -435,17 +444,18 @@ radon_status single_backward_tk(const Unit& u, long long tiles, size_t smem, con
 template <typename T>
 radon_status single_backward_t(const radon_geometry* g, const void* sino, void* img, const Epilogue& ep, cudaStream_t s,
                                std::string* why) {
-    const Unit u = single_unit(g, sino, img, kSingleAdjointViews);
     const int kw_needed = (int)std::floor(2.0 * std::sqrt(2.0) / g->h + 2e-4) + 1;
     if (kw_needed > 6) {
         *why = "sampling step too small for the single-image adjoint";
         return RADON_ERR_UNSUPPORTED;
     }
-    const size_t smem = adj_smem_bytes(u.wd);
-    if (smem > 227 * 1024) {
+    const int cap = adj_chunk_cap(g->bwd_window + 2);
+    if (cap == 0) {
         *why = "detector window too wide for the single-image adjoint";
         return RADON_ERR_UNSUPPORTED;
     }
+    const Unit u = single_unit(g, sino, img, std::min(kSingleAdjointViews, cap));
+    const size_t smem = adj_smem_bytes(u.wd, u.cfg);
     int* err = device_error_word();
     if (err == nullptr) {
         *why = "device error word unavailable";
@@ -492,6 +502,7 @@ struct radon_plan {
     int device = 0;
     int kw = 3;
     int max_wd = 0;
+    int cap = kMaxChunkViews;   // adjoint: views per chunk at most (its shared memory holds that many)
     int ctas = 0;
     size_t smem = 0;
     std::vector<Unit> units;
@@ -585,10 +596,10 @@ radon_status launch_t(const radon_plan* p, const Work* d_work, int n_work, cudaS
         if (err == nullptr) return fail(RADON_ERR_CUDA, "device error word unavailable");
         if (p->kw == 3)
             plan_adjoint_kernel<T, 3><<<p->ctas, kPlanThreads, p->smem, s>>>(p->d_units, d_work, n_work, p->d_counter,
-                                                                            p->max_wd, err);
+                                                                            p->max_wd, p->cap, err);
         else
             plan_adjoint_kernel<T, 6><<<p->ctas, kPlanThreads, p->smem, s>>>(p->d_units, d_work, n_work, p->d_counter,
-                                                                            p->max_wd, err);
+                                                                            p->max_wd, p->cap, err);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "plan adjoint launch");
         count_launches(1);
@@ -682,8 +693,8 @@ extern "C" RADON_API radon_status radon_batch_plan_create(const radon_item* item
     const int fv = options ? options->forward_views : 0, av = options ? options->adjoint_views : 0;
     if (fv < 0 || (fv > 0 && fv != 1 && fv != 2 && fv != 4 && fv != 8))
         return fail(RADON_ERR_INVALID_ARG, "forward_views must be 0, 1, 2, 4 or 8");
-    if (av < 0 || (av > 0 && av != 4 && av != 8 && av != 16))
-        return fail(RADON_ERR_INVALID_ARG, "adjoint_views must be 0, 4, 8 or 16");
+    if (av < 0 || (av > 0 && av != 4 && av != 8 && av != 16 && av != 32))
+        return fail(RADON_ERR_INVALID_ARG, "adjoint_views must be 0, 4, 8, 16 or 32");
     const bool autotune = options == nullptr || options->autotune != 0;
     const size_t es = dtype == RADON_F32 ? 4 : 2;
     for (int i = 0; i < n; ++i) {
@@ -756,11 +767,17 @@ extern "C" RADON_API radon_status radon_batch_plan_create(const radon_item* item
         }
         p->total_texels = p->prefix[nu];
     } else {
-        p->smem = adj_smem_bytes(std::max(p->max_wd, 1));
-        if (p->smem > 227 * 1024) {
+        p->cap = adj_chunk_cap(std::max(p->max_wd, 1));
+        if (p->cap == 0) {
             free_plan(p);
             return fail(RADON_ERR_UNSUPPORTED, "detector window too wide for the adjoint plan's shared memory");
         }
+        if (av > p->cap) {
+            free_plan(p);
+            return fail(RADON_ERR_UNSUPPORTED, "adjoint_views " + std::to_string(av) +
+                                                   " exceeds the shared memory of these detector windows");
+        }
+        p->smem = adj_smem_bytes(std::max(p->max_wd, 1), p->cap);
     }
     if (nu > 0) {
         if (cudaMalloc(&p->d_units, nu * sizeof(Unit)) != cudaSuccess ||
@@ -784,9 +801,9 @@ extern "C" RADON_API radon_status radon_batch_plan_create(const radon_item* item
         const bool fixed = direction == 0 ? fv > 0 : av > 0;
         if (st == RADON_OK && autotune && !fixed) {
             static const int kFwdCand[4] = {8, 4, 2, 1};
-            static const int kAdjCand[3] = {4, 8, 16};
+            static const int kAdjCand[4] = {4, 8, 16, 32};
             const int* cand = direction == 0 ? kFwdCand : kAdjCand;
-            const int nc = direction == 0 ? 4 : 3;
+            const int nc = direction == 0 ? 4 : (p->cap >= 32 ? 4 : 3);
             std::map<int, std::vector<int>> by_size;
             for (size_t k = 0; k < nu; ++k) by_size[p->units[k].n].push_back((int)k);
             for (auto& kv : by_size) {

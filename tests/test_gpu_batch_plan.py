@@ -73,7 +73,7 @@ def test_plan_matches_oracle(direction, dtype):
     info = plan.info
     assert info["units"] == sum(BATCH) and info["work_items"] > 0 and info["direction"] == direction
     assert info["ctas"] % torch.cuda.get_device_properties(0).multi_processor_count == 0
-    cands = (1, 2, 4, 8) if direction == "forward" else (4, 8, 16)
+    cands = (1, 2, 4, 8) if direction == "forward" else (4, 8, 16, 32)
     assert all(plan.item_config(k) in cands for k in range(len(gs)))
 
 
@@ -82,7 +82,7 @@ def test_tile_shapes_do_not_change_a_bit(direction):
     """Every candidate the autotuner may pick computes each output in the same order."""
     gs, ins, outs, _ = _mixed(torch.float32, direction, seed=3)
     results = []
-    for v in ((1, 2, 4, 8) if direction == "forward" else (4, 8, 16)):
+    for v in ((1, 2, 4, 8) if direction == "forward" else (4, 8, 16, 32)):
         kw = dict(forward_views=v) if direction == "forward" else dict(adjoint_views=v)
         plan = BatchPlan(list(zip(gs, ins, outs)), direction, autotune=False, **kw)
         assert all(plan.item_config(k) == v for k in range(len(gs)))
