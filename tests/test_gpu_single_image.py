@@ -7,7 +7,6 @@ kernels); with fused epilogues; against the batched and workspace-free paths; an
 
 from __future__ import annotations
 
-
 import numpy as np
 import pytest
 import torch
