@@ -46,22 +46,26 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms while the timed region runs."""
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms around the timed region; each sample
+    carries its host arrival time, and the summary covers the samples inside the region marked by
+    ``region(t0, t1)`` (all samples if none fell inside)."""
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 50
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
         self.lines = []
         self._t = None
+        self._region = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -71,7 +75,11 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def region(self, t0: float, t1: float):
+        """Host monotonic times bracketing the timed region."""
+        self._region = (t0, t1)
 
     def stop(self):
         if self.proc is None:
@@ -83,23 +91,27 @@ class ClockSampler:
             self.proc.kill()
         if self._t is not None:
             self._t.join(timeout=2)
-        sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        parsed = []
+        for t, ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                parsed.append((t, float(parts[1]), float(parts[2]),
+                               {n for n, v in zip(names, parts[5:9]) if v.lower() == "active"}))
             except ValueError:
                 continue
-            for name, val in zip(names, parts[5:9]):
-                if val.lower() == "active":
-                    reasons.add(name)
-        if not sm:
+        if not parsed:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+        inside = parsed
+        if self._region is not None:
+            # a line arrives up to one period after the GPU state it reports
+            t0, t1 = self._region
+            inside = [p for p in parsed if t0 <= p[0] <= t1 + self.PERIOD_MS / 1000.0] or parsed
+        reasons = set().union(*(p[3] for p in inside))
+        return {"sm_mhz": statistics.median(p[1] for p in inside), "sm_max_mhz": max(p[2] for p in parsed),
+                "samples": len(inside), "samples_total": len(parsed), "period_ms": self.PERIOD_MS,
                 "reasons": sorted(reasons)}
 
 
@@ -250,7 +262,9 @@ def run_ours(args):
     clocks.start()
     time.sleep(0.3)
     launches = {}
+    th0 = time.monotonic()
     total_ms, fwd_ms, adj_ms = timed(chosen, args.steps, args.warmup, (xs, ys, outs_y, outs_x), launches)
+    clocks.region(th0, time.monotonic())
     time.sleep(0.2)
     clk = clocks.stop()
 
@@ -743,7 +757,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS),
