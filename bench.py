@@ -716,7 +716,42 @@ def cpu_oracle_sample(w, seconds):
         if dt * 3 > seconds or stride == 1:
             break
         stride = max(1, stride // 4)
+    one = cpu_oracle_one_core(w.name)
+    if one is not None:
+        result["one_core"] = one
     return result
+
+
+ONE_CORE_STRIDE = 64
+
+
+def cpu_oracle_one_core(workload: str):
+    """The same oracle on one host core (OpenMP limited to one thread in a child interpreter), on every
+    64th view of the workload: samples/s, or None if the child fails."""
+    import subprocess
+    code = (
+        "import json, sys, time\n"
+        "sys.path.insert(0, %r)\n"
+        "import oracle as O\n"
+        "from bench import _oracle_sample_geometry\n"
+        "from synth import WORKLOADS, workload_images\n"
+        "w = WORKLOADS[%r]\n"
+        "x = workload_images(w)\n"
+        "g = _oracle_sample_geometry(w, %d)\n"
+        "O.forward(g, x[:1])\n"
+        "t0 = time.perf_counter(); y = O.forward(g, x); O.adjoint(g, y); dt = time.perf_counter() - t0\n"
+        "print(json.dumps({'samples': 2 * x.shape[0] * O.sample_count(g), 'seconds': dt, 'views': g.n_angles,\n"
+        "                  'threads': O.num_threads(), 'images': int(x.shape[0])}))\n"
+    ) % (os.path.dirname(os.path.abspath(__file__)), workload, ONE_CORE_STRIDE)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError):
+        return None
+    return {"value": d["samples"] / d["seconds"], "unit": "samples/s", "cores": d["threads"],
+            "sample": "fwd + adjoint of all %d images on every %d-th view (%d views), %.1f s" % (
+                d["images"], ONE_CORE_STRIDE, d["views"], d["seconds"])}
 
 
 def run_reference(args):
