@@ -209,7 +209,8 @@ typedef struct {
     int algo;            /* radon_algo */
     int views_per_cta;   /* TILED forward: views per CTA (0 = default) */
     int rows_per_slab;   /* TILED forward: image rows staged per step (0 = default) */
-    int images_per_cta;  /* TILED: images sharing the geometry work in one CTA (0 = default) */
+    int images_per_cta;  /* TILED: images sharing the geometry work in one CTA (0 = default; the packed
+                            adjoint takes 8, 16 or 32, the staged one 4, 8 or 16) */
     int tile;            /* TILED backward: pixel tile side (0 = default) */
     int threads;         /* threads per CTA (0 = default) */
     int weights;         /* forward, FP16 storage: 0 = FP16 weights (default), 1 = FP32 weights */
@@ -242,8 +243,10 @@ RADON_API radon_status radon_forward_ws(const radon_geometry* geometry, const vo
 
 /*
  * Device workspace, in bytes, that radon_backward_ws uses for `batch` sinograms of `dtype`: the
- * batch packed into FP32 quads of images, 16 (or 8, for batches of at most 8) images per group,
- * laid out [group][view][quad][detector][4].  Returns 0 for an invalid geometry, dtype or batch.
+ * batch packed into FP32 quads of images, laid out [group][view][quad][detector][4], with 8 images
+ * per group for batches of at most 8, 16 up to 16, and above that 32 where whole groups of 32 cost
+ * less than groups of 16 (a 32-image CTA costs ~1.56x a 16-image one) and their staging fits one
+ * CTA's shared memory, else 16.  Returns 0 for an invalid geometry, dtype or batch.
  */
 RADON_API size_t radon_backward_workspace_size(const radon_geometry* geometry, radon_dtype dtype, int batch);
 

@@ -160,15 +160,21 @@ cudaError_t launch_packed_bg(const CUtensorMap& map, const CUtensorMap& rmap, co
 
 }  // namespace
 
-int backward_packed_images_per_cta(int batch, const radon_launch_config* cfg) {
+int backward_packed_images_per_cta(const radon_geometry* g, int batch, const radon_launch_config* cfg) {
     if (cfg != nullptr && cfg->images_per_cta != 0) return cfg->images_per_cta;
-    return batch > 8 ? 16 : 8;
+    if (batch <= 8) return 8;
+    if (batch <= 16) return 16;
+    // A 32-image CTA costs ~1.56x a 16-image one (each weight serves twice the images; 96 registers,
+    // 2 CTAs/SM): take it when its groups cost less and its staging fits one CTA's shared memory.
+    const long long g32 = (batch + 31) / 32, g16 = (batch + 15) / 16;
+    if (25 * g32 < 16 * g16 && bwd_packed_smem_bytes(32, g->bwd_window + 2) <= 227 * 1024) return 32;
+    return 16;
 }
 
 radon_status launch_backward_packed(const radon_geometry* g, const void* packed, void* img, radon_dtype dt, int batch,
                                     int bg, const Epilogue& ep, cudaStream_t s, std::string* why, bool interpolating) {
-    if (bg != 8 && bg != 16) {
-        *why = "images_per_cta must be 8 or 16 for the packed adjoint";
+    if (bg != 8 && bg != 16 && bg != 32) {
+        *why = "images_per_cta must be 8, 16 or 32 for the packed adjoint";
         return RADON_ERR_UNSUPPORTED;
     }
     const double span = 2.0 * std::sqrt(2.0) / g->h + 2e-4;
@@ -241,7 +247,11 @@ radon_status launch_backward_packed(const radon_geometry* g, const void* packed,
     dim3 grid((unsigned)(a.tiles_x * a.tiles_x), (unsigned)groups);
     cudaError_t e;
     if (interpolating) a.h = 1.0f;   // the interpolating backprojector's sum carries no step factor
-    if (bg == 16)
+    if (bg == 32)
+        e = kw == 0 ? launch_packed_bg<32, 0>(map, rmap, a, grid, smem, s)
+                    : kw == 3 ? launch_packed_bg<32, 3>(map, rmap, a, grid, smem, s)
+                              : launch_packed_bg<32, 6>(map, rmap, a, grid, smem, s);
+    else if (bg == 16)
         e = kw == 0 ? launch_packed_bg<16, 0>(map, rmap, a, grid, smem, s)
                     : kw == 3 ? launch_packed_bg<16, 3>(map, rmap, a, grid, smem, s)
                               : launch_packed_bg<16, 6>(map, rmap, a, grid, smem, s);

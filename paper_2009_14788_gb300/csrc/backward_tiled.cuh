@@ -434,7 +434,7 @@ __host__ __device__ inline size_t bwd_packed_smem_bytes(int bg, int wd) {
 }
 
 template <int BG, int KW>
-__global__ void __launch_bounds__(kBwdPackedThreads, 3) backward_packed_kernel(const __grid_constant__ CUtensorMap map,
+__global__ void __launch_bounds__(kBwdPackedThreads, BG >= 32 ? 2 : 3) backward_packed_kernel(const __grid_constant__ CUtensorMap map,
                                                                               const __grid_constant__ CUtensorMap rmap,
                                                                               const BwdTiledArgs a) {
     constexpr int NQ = BG / 4;

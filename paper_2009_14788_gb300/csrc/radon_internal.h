@@ -145,7 +145,7 @@ cudaError_t launch_pack_sino(const void* sino, void* workspace, int V, int D, in
                              cudaStream_t s);
 
 // backward_tiled.cu: the packed-sinogram adjoint (the workspace already holds pack_sino's output)
-int backward_packed_images_per_cta(int batch, const radon_launch_config* cfg);
+int backward_packed_images_per_cta(const radon_geometry* g, int batch, const radon_launch_config* cfg);
 radon_status launch_backward_packed(const radon_geometry* g, const void* packed, void* img, radon_dtype dt, int batch,
                                     int images_per_cta, const Epilogue& ep, cudaStream_t s, std::string* why,
                                     bool interpolating = false);
