@@ -3,8 +3,6 @@ every storage type, ragged sizes, a detector of one bin) and its relation to the
 
 from __future__ import annotations
 
-import math
-
 import numpy as np
 import pytest
 import torch
