@@ -100,6 +100,7 @@ radon_status launch_forward_tiled(radon_geometry* g, const void* img, void* sino
     a.ep = ep;
     a.G = G;
     a.Dt = Dt;
+    a.pair_views = G >= 2 && g->fwd_pair_views ? 1 : 0;
     a.n_dr = (g->D + Dt - 1) / Dt;
     a.R = R;
     a.n_slabs = (g->n + 4 + R - 1) / R;
@@ -227,6 +228,7 @@ radon_status launch_forward_packed(radon_geometry* g, const void* packed, void* 
     a.ep = ep;
     a.G = G;
     a.Dt = Dt;
+    a.pair_views = G >= 2 && g->fwd_pair_views ? 1 : 0;
     a.n_dr = (g->D + Dt - 1) / Dt;
     a.R = R;
     a.n_slabs = (g->n + 4 + R - 1) / R;

@@ -40,6 +40,7 @@ struct FwdTiledArgs {
     int n, V, D, B;
     float h;
     int G, Dt;            // views and detectors per CTA (G * Dt == kFwdRays)
+    int pair_views;       // 1: each 8-lane load phase holds two views x four detectors
     int n_dr;             // detector ranges
     int R;                // slab rows (even)
     int n_slabs;
@@ -323,7 +324,19 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
                             const unsigned char* comp_base, size_t comp_stride, int wc) {
     constexpr int BG = Texel<T, false>::BG;
     const int tid = threadIdx.x;
-    const int vl = tid / a.Dt, d = d0 + (tid - (tid / a.Dt) * a.Dt);
+    // Thread -> (view, detector) of the CTA.  By default consecutive threads take consecutive detectors
+    // of one view; with pair_views each 8-lane phase of a 16-byte shared load takes views 2m, 2m + 1 x
+    // four consecutive detectors (lanes 2j, 2j + 1 still hold neighbouring detectors of one view).
+    int vl, dl;
+    if (a.pair_views) {
+        const int per = a.Dt >> 2, P = tid >> 3;
+        vl = (P / per) * 2 + ((tid >> 2) & 1);
+        dl = (P - (P / per) * per) * 4 + (tid & 3);
+    } else {
+        vl = tid / a.Dt;
+        dl = tid - vl * a.Dt;
+    }
+    const int d = d0 + dl;
     const bool active = vl < cnt && d < a.D;
     int J0 = 0, I0 = 0, nk = 0;
     float fX0 = 0.f, fY0 = 0.f, dXh = 0.f, dYh = 0.f, dXl = 0.f, dYl = 0.f;

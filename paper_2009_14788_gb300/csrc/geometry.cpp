@@ -200,6 +200,14 @@ radon_status build_geometry(radon_geometry* g) {
     g->samples = total;
     g->max_nk = max_nk;
     g->bwd_window = backward_window_width(g, 16);
+    // The tiled forward gives each 8-lane phase of its 16-byte shared loads two neighbouring views x
+    // four detectors when the rays of consecutive views stay within 5 pixels of each other inside the
+    // image ((n / 2) |theta_{v+1} - theta_v| <= 5): their texels then fall in fewer bank groups than
+    // eight detectors of one view.  With wider view steps the pair spreads over more columns and one
+    // view per phase is faster (measured over view counts 60 to 720, parallel and fan beam).
+    double gap = 0.0;
+    for (int v = 0; v + 1 < V; ++v) gap = std::max(gap, std::fabs(g->angles[v + 1] - g->angles[v]));
+    g->fwd_pair_views = V >= 2 && 0.5 * g->n * gap <= 5.0 ? 1 : 0;
     // Groups of up to G consecutive views of one orientation class (the tiled forward's CTAs):
     // entry = (first view, count | class << 16), for G = 1, 2, 4, 8.
     g->h_groups.clear();

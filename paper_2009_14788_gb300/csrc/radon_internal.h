@@ -68,6 +68,7 @@ struct radon_geometry {
     int64_t samples = 0;
     int max_nk = 0;
     int bwd_window = 0;               // widest detector window of a 16x16 tile (tiled adjoint)
+    int fwd_pair_views = 0;           // tiled forward: two views x four detectors per load phase
     std::vector<radon::Int2> h_groups;  // view groups for G = 1, 2, 4, 8 (concatenated)
     int group_offset[4] = {0, 0, 0, 0};
     int group_count[4] = {0, 0, 0, 0};

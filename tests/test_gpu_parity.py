@@ -341,6 +341,34 @@ def test_forward_tiled_configs(case, views, rows, ws):
     assert max_rel(got, ref) <= 2 * TOL_F32
 
 
+@pytest.mark.parametrize("ws", WS)
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16, torch.bfloat16], ids=["f32", "f16", "bf16"])
+@pytest.mark.parametrize("case", ["fan_n512_block", "parallel_n64_full"])
+def test_forward_paired_view_phases_give_the_same_bits(case, dtype, ws):
+    """Closely spaced views ((n / 2) |theta_{v+1} - theta_v| <= 5 pixels): CTAs of 2 to 8 views give
+    each 8-lane load phase two views x four detectors, a CTA of one view cannot.  Every ray sums the
+    same samples in the same order either way, so all shapes give the same bits, and match the oracle."""
+    g, og = make(case)
+    xs = to_dev(_rand_images(g.n, 9, 81), dtype)
+    outs = []
+    for v in (1, 2, 4, 8):
+        try:
+            outs.append(forward_raw(g, xs, launch_config("tiled", views_per_cta=v, rows_per_slab=16),
+                                    workspace=_ws(ws)))
+        except L.RadonError as exc:   # a working band wider than one TMA box is refused, never run
+            assert exc.status == L.RADON_ERR_UNSUPPORTED and "TMA box" in str(exc) and v == 1
+    assert len(outs) >= 3
+    assert L.radon_get_device_error(torch.cuda.current_stream().cuda_stream) == L.RADON_OK
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    ref = O.forward(og, to_np(xs))
+    got = to_np(outs[-1])
+    if dtype == torch.float32:
+        assert rel_l2(got, ref) <= TOL_F32
+    else:
+        assert rel_l2(got, ref) <= TOL_16
+
+
 def test_forward_tiled_refuses_sparse_wide_views_auto_serves():
     """Every 30th view of the 512^2 fan set (15 degrees apart): no CTA shape keeps the working band
     inside one TMA box, so TILED refuses and AUTO serves the request with the plain kernel."""
