@@ -197,7 +197,20 @@ __device__ __forceinline__ void plan_forward_tile(const Unit& u, int tile, const
     const int G = u.cfg, Dt = kPlanThreads / G;
     const int n_dr = (u.D + Dt - 1) / Dt;
     const int vg = tile / n_dr, dr = tile - (tile / n_dr) * n_dr;
-    const int v = vg * G + (int)threadIdx.x / Dt, d = dr * Dt + (int)threadIdx.x % Dt;
+    // With two or more views per tile each group of eight lanes takes views 2m, 2m + 1 x four
+    // consecutive detectors: their quads' cache lines overlap more than those of eight detectors of
+    // one view (1-4 % faster from 60 to 1024 views; lane pairs still hold neighbouring detectors).
+    const int tid = (int)threadIdx.x;
+    int vl, dl;
+    if (G >= 2) {
+        const int per = Dt >> 2, P = tid >> 3;
+        vl = (P / per) * 2 + ((tid >> 2) & 1);
+        dl = (P - (P / per) * per) * 4 + (tid & 3);
+    } else {
+        vl = tid / Dt;
+        dl = tid - vl * Dt;
+    }
+    const int v = vg * G + vl, d = dr * Dt + dl;
     if (v < u.V && d < u.D) {
         const float y = plan_ray<T>(u, quads, v, d);
         const long long idx = (long long)v * u.D + d;
