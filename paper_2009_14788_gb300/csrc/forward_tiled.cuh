@@ -20,6 +20,8 @@
 // buffers of (R+2) x wc texels.
 #pragma once
 
+#include <type_traits>
+
 #include "device_error.cuh"
 #include "dtype.cuh"
 #include "epilogue.cuh"
@@ -398,6 +400,13 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
                     const int kleft = nk - k;
                     int i = 0;
                     float kk = 0.0f;
+                    // FP32 texels (4 images per load): a sample one row below the previous one in the
+                    // same column takes its upper row from the previous sample's lower row instead of
+                    // loading it (same values: same bits; 2-5 % faster in FP32; the 16-bit paths, with
+                    // twice the FMAs per load, measured 2-11 % slower and load every texel)
+                    constexpr bool kReuseRow = std::is_same<T, float>::value;
+                    unsigned pidx = 0xffffffffu;
+                    uint4 r10 = make_uint4(0u, 0u, 0u, 0u), r11 = r10;
                     for (; i < kleft; ++i, kk += 1.0f) {
                         const float fym = fmaf(kk, dY, sYm);
                         if (fym >= ylim_m) break;
@@ -405,7 +414,20 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
                         const float tx = fxm + M, ty = fym + M;
                         const unsigned idx = __float_as_uint(ty) * wcu + __float_as_uint(tx) + base;
                         const uint4* p = comp + idx;
-                        const uint4 q00 = p[0], q01 = p[1], q10 = p[wcu], q11 = p[wcu + 1];
+                        uint4 q00, q01;
+                        if (kReuseRow && idx == pidx + wcu) {
+                            q00 = r10;
+                            q01 = r11;
+                        } else {
+                            q00 = p[0];
+                            q01 = p[1];
+                        }
+                        const uint4 q10 = p[wcu], q11 = p[wcu + 1];
+                        if (kReuseRow) {
+                            r10 = q10;
+                            r11 = q11;
+                            pidx = idx;
+                        }
                         const float ax = fxm - (tx - M), ay = fym - (ty - M);   // in [-1/2, 1/2]
                         const float wx1 = 0.5f + ax, wx0 = 0.5f - ax, wy1 = 0.5f + ay, wy0 = 0.5f - ay;
                         using TX = Texel<T, MIXED>;
