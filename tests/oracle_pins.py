@@ -272,7 +272,10 @@ def pin_dense_transpose():
     for g in _small_geoms():
         A = O.dense_matrix(g)
         At = O.dense_matrix_adjoint(g)
-        worst = max(worst, float(np.max(np.abs(A - At.T)) / np.max(np.abs(A))))
+        scale = float(np.max(np.abs(A)))
+        if not scale > 0.0:
+            return math.inf   # an empty (or non-finite) system matrix fails the pin
+        worst = max(worst, float(np.max(np.abs(A - At.T))) / scale)
     return worst
 
 
