@@ -36,6 +36,12 @@ from synth import gaussian_blob, random_ellipses, rasterize_ellipses, uniform_an
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
+def _worse(worst, val):
+    """The larger of two errors; NaN wins (a broken oracle must not pass as a zero error)."""
+    val = float(val)
+    return val if not val <= worst else worst
+
+
 def _rel(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
@@ -275,7 +281,7 @@ def pin_dense_transpose():
         scale = float(np.max(np.abs(A)))
         if not scale > 0.0:
             return math.inf   # an empty (or non-finite) system matrix fails the pin
-        worst = max(worst, float(np.max(np.abs(A - At.T))) / scale)
+        worst = _worse(worst, float(np.max(np.abs(A - At.T))) / scale)
     return worst
 
 
@@ -289,7 +295,7 @@ def pin_dot_product():
         y = rng.standard_normal((2,) + g.sino_shape)
         a = float(np.vdot(O.forward(g, x), y))
         b = float(np.vdot(x, O.adjoint(g, y)))
-        worst = max(worst, abs(a - b) / max(abs(a), abs(b)))
+        worst = _worse(worst, abs(a - b) / max(abs(a), abs(b)))
     return worst
 
 

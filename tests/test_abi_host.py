@@ -297,6 +297,7 @@ def test_ray_table_positions_match_oracle(name):
             km = np.arange(-margin, nk + margin)
             for hpart in (dxh, dyh):
                 assert np.all(np.float32(km * np.float32(hpart)) == km * hpart)
+            assert np.all(np.isfinite(got))
             worst = max(worst, float(np.max(np.abs(got - ref))))
     assert worst < 1e-6
 
