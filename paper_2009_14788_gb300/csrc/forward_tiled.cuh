@@ -405,7 +405,7 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
                     // loading it (same values: same bits; 2-5 % faster in FP32; the 16-bit paths, with
                     // twice the FMAs per load, measured 2-11 % slower and load every texel)
                     constexpr bool kReuseRow = std::is_same<T, float>::value;
-                    unsigned pidx = 0xffffffffu;
+                    unsigned pidx = 0x80000000u;   // no texel index of a band lies within a row of it
                     uint4 r10 = make_uint4(0u, 0u, 0u, 0u), r11 = r10;
                     for (; i < kleft; ++i, kk += 1.0f) {
                         const float fym = fmaf(kk, dY, sYm);
