@@ -442,10 +442,11 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
         }
         mbar_arrive(&empty[buf]);   // this thread's reads of the buffer are done
     }
-    // Stores: consecutive lanes hold consecutive detectors of one view (coalesced).  With vec_store
-    // (D even and the output aligned to two elements, so every even detector's index is even) and the
-    // whole warp present, each even lane also takes its odd neighbour's value and writes both as one
-    // two-element vector.
+    // Stores: consecutive lanes hold runs of consecutive detectors of one view (a warp's 32 with one
+    // view per load phase, runs of 4 with two), so each image's stores coalesce per run.  With
+    // vec_store (D even and the output aligned to two elements, so every even detector's index is
+    // even) and the whole warp present, each even lane also takes its odd neighbour's value and writes
+    // both as one two-element vector.
     T* out = reinterpret_cast<T*>(a.sino);
     const long long vd = (long long)a.V * a.D;
     const long long o = (long long)(v0 + vl) * a.D + d;
