@@ -587,7 +587,7 @@ std::vector<Work> build_work(const radon_plan* p, const std::vector<int>& sel) {
     return w;
 }
 
-radon_status upload_work(radon_plan* p, const std::vector<Work>& w, Work** dst) {
+radon_status upload_work(const std::vector<Work>& w, Work** dst) {
     cudaFree(*dst);
     *dst = nullptr;
     if (w.empty()) return RADON_OK;
@@ -680,7 +680,7 @@ radon_status occupancy(radon_plan* p) {
 radon_status time_subset(radon_plan* p, const std::vector<int>& sel, float* ms) {
     const std::vector<Work> w = build_work(p, sel);
     Work* d = nullptr;
-    radon_status st = upload_work(p, w, &d);
+    radon_status st = upload_work(w, &d);
     if (st != RADON_OK) return st;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -859,7 +859,7 @@ extern "C" RADON_API radon_status radon_batch_plan_create(const radon_item* item
         std::vector<int> all(nu);
         for (size_t k = 0; k < nu; ++k) all[k] = (int)k;
         p->work = build_work(p, all);
-        st = upload_work(p, p->work, &p->d_work);
+        st = upload_work(p->work, &p->d_work);
     }
     if (st != RADON_OK) {
         free_plan(p);
