@@ -8,7 +8,7 @@ import pytest
 import torch
 
 import oracle as O
-from gpu_cases import CASES, TOL_F32, make, rel_l2, to_dev, to_np, within_16
+from gpu_cases import TOL_F32, make, rel_l2, to_dev, to_np, within_16
 from paper_2009_14788_gb300 import backproject_interpolating, backward_raw
 from synth import gaussian_blob
 

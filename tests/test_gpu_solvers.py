@@ -17,7 +17,7 @@ import torch
 
 import oracle as O
 from gpu_cases import phantoms, rel_l2, to_dev, to_np
-from paper_2009_14788_gb300 import Geometry, _lib as L, backward_fused, cg, cgne, forward_raw
+from paper_2009_14788_gb300 import Geometry, backward_fused, cg, cgne, forward_raw
 from paper_2009_14788_gb300.solvers import _Vec
 from synth import uniform_angles
 
