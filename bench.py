@@ -147,18 +147,26 @@ def whole_job_value(units_per_rank_step, world, ms_per_step):
     return units_per_rank_step * world / (ms_per_step * 1e-3)
 
 
-def workload_config(workload, storage, algo, geom=None):
-    """The ``config`` object of the JSON line (both arms): the workload and its geometry."""
-    from paper_2009_14788_gb300 import Geometry
+def workload_config(workload, storage, algo, geom):
+    """The ``config`` object of the GPU arm's JSON line: the workload and its library geometry."""
     w = WORKLOADS[workload]
-    if geom is None:
-        gargs = workload_geometry_args(w)
-        kind = gargs.pop("kind")
-        geom = Geometry(kind, host_only=True, **gargs)
     return {"workload": workload, "geometry": geom.kind, "batch": w.batch, "n": geom.n, "views": geom.n_angles,
             "det_count": geom.det_count, "det_spacing": geom.det_spacing, "source_distance": geom.source_distance,
             "det_distance": geom.det_distance, "storage": storage, "algo": algo,
             "samples_per_image": geom.sample_count,
+            "parallelism": "replica per GPU (batch sharding, no exchange)"}
+
+
+def oracle_workload_config(workload, storage, algo):
+    """The same ``config`` object built from the oracle's geometry alone (the reference arm never
+    loads the library): defaults resolved and samples counted by ``oracle``."""
+    import oracle as O
+    w = WORKLOADS[workload]
+    og = O.Geometry.from_args(workload_geometry_args(w))
+    return {"workload": workload, "geometry": og.kind, "batch": w.batch, "n": og.n, "views": og.n_angles,
+            "det_count": int(og.det_count), "det_spacing": float(og.det_spacing),
+            "source_distance": float(og.source_distance), "det_distance": float(og.det_distance),
+            "storage": storage, "algo": algo, "samples_per_image": O.sample_count(og),
             "parallelism": "replica per GPU (batch sharding, no exchange)"}
 
 
@@ -779,7 +787,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": dict(workload_config(args.workload, args.storage, args.algo),
+            "config": dict(oracle_workload_config(args.workload, args.storage, args.algo),
                            sample="every %d-th view" % stride),
             "cpu_baseline": {"value": value, "unit": "samples/s", "cores": O.num_threads(), "cpu": cpu_model(),
                              "kind": "oracle",

@@ -197,14 +197,19 @@ RADON_API radon_status radon_backward(const radon_geometry* geometry, const void
  * adjoint at 512^2.  Larger batches, or explicit parameters, run the batch-interleaved kernels.
  *
  * `weights` selects the forward projection's bilinear-weight precision for FP16 storage (Section
- * 3.3's half-precision path): 0 (default) rounds each sample's four weights to FP16 and forms every
- * product of a weight and a texel value exactly in one mixed-precision FMA accumulated in FP32 --
- * nothing converts the texel values, which makes the inner loop bound by the shared-memory load pipe;
- * the weight rounding (relative <= 2^-12 per weight) shifts a ray sum by at most ~1e-4 of its size,
- * below FP16's own output rounding.  1 keeps FP32 weights (texel values converted to FP32, FP32 FMAs),
- * the paper's all-single-precision arithmetic.  BF16 and FP32 storage always use FP32 weights, and so
- * does every fused call whose epilogue has an addend (the Landweber residual keeps its own precision).
+ * 3.3's half-precision path stores in FP16 and computes in single precision):
+ *   RADON_WEIGHTS_DEFAULT (0) and RADON_WEIGHTS_F32 (1): FP32 weights, texel values converted to
+ *     FP32, FP32 FMAs -- the paper's all-single-precision arithmetic, used by every storage type;
+ *   RADON_WEIGHTS_F16 (2, opt-in, FP16 storage only): each sample's four weights are rounded to FP16
+ *     and every product of a weight and a texel value is formed exactly in one mixed-precision FMA
+ *     accumulated in FP32.  Nothing converts the texel values, so the inner loop runs at the
+ *     shared-memory load pipe's rate; the weight rounding (relative <= 2^-12 per weight) shifts a ray
+ *     sum by at most 2^-12 of its size, below FP16's own output rounding.  BF16 and FP32 storage, and
+ *     every fused call whose epilogue has an addend, keep FP32 weights whatever this field says.
+ * Any other value is RADON_ERR_INVALID_ARG.
  */
+enum { RADON_WEIGHTS_DEFAULT = 0, RADON_WEIGHTS_F32 = 1, RADON_WEIGHTS_F16 = 2 };
+
 typedef struct {
     int algo;            /* radon_algo */
     int views_per_cta;   /* TILED forward: views per CTA (0 = default) */
@@ -213,7 +218,7 @@ typedef struct {
                             adjoint takes 8, 16 or 32, the staged one 4, 8 or 16) */
     int tile;            /* TILED backward: pixel tile side (0 = default) */
     int threads;         /* threads per CTA (0 = default) */
-    int weights;         /* forward, FP16 storage: 0 = FP16 weights (default), 1 = FP32 weights */
+    int weights;         /* forward, FP16 storage: RADON_WEIGHTS_* (0 = default = FP32 weights) */
 } radon_launch_config;
 
 RADON_API radon_status radon_forward_ex(const radon_geometry* geometry, const void* img, void* sino, radon_dtype dtype,
@@ -263,18 +268,21 @@ RADON_API radon_status radon_backward_ws(const radon_geometry* geometry, const v
 
 /*
  * Forward projection that allocates nothing (the paper has no counterpart: this serves callers that
- * cannot allocate device memory -- code being captured into a CUDA graph, real-time loops that forbid
- * allocation after start-up, plain C hosts without a device allocator).  It runs the packed path of
- * radon_forward_ws with its scratch in a fixed 32 MiB device array inside the library instead of a
- * caller workspace.
- *   - Same arguments and results as radon_forward.  A batch that needs more scratch than 32 MiB
- *     (radon_forward_workspace_size) is rejected with RADON_ERR_INVALID_ARG: split it.
+ * cannot allocate device memory -- real-time loops that forbid allocation after start-up, code that
+ * must not let an allocation synchronise the device, plain C hosts without a device allocator).  It
+ * runs the packed path of radon_forward_ws with its scratch in a fixed 32 MiB device array inside
+ * the library instead of a caller workspace.
+ *   - Same arguments and results as radon_forward_ws with a workspace.  The limit is the packed
+ *     batch, 2 * ceil(batch / BG) * N^2 * 16 bytes (BG = 4 images for FP32 storage, 8 for 16-bit; a
+ *     batch of one is one group): a batch that needs more than 32 MiB is rejected with
+ *     RADON_ERR_INVALID_ARG -- split it.
  *   - Every GPU that loads the library holds the 32 MiB until the process exits.
  *   - All calls share the array: each call overwrites what the previous one left there (nothing in
  *     it needs to start at zero), and calls whose kernels overlap on the GPU (e.g. on two streams)
  *     race on it -- order them.
- *   - The first call on each device looks up the array's address with that device current; make
- *     that first call before any stream capture begins.
+ *   - The first call on each device looks up the array's address with that device current and keeps
+ *     it for the life of the process; make that first call before any stream capture begins.  The
+ *     kept address does not survive a reset of the device's primary context (cudaDeviceReset).
  */
 RADON_API radon_status radon_forward_static_scratch(const radon_geometry* geometry, const void* img, void* sino,
                                                     radon_dtype dtype, int batch, void* stream);
@@ -522,10 +530,14 @@ RADON_API void radon_batch_plan_destroy(radon_plan* plan);
  * Measures the achievable rate of the forward projection's inner loop on the current GPU: a kernel
  * that marches straight rays through a shared-memory-resident tile of batch-interleaved texels (four
  * 16-byte loads, one floor / weight evaluation and FP32 accumulation for every image of the texel per
- * sample, no geometry, no TMA) on every SM.  *samples_per_second receives image-samples per second
- * (one probe sample serves the 8 (F16; BF16 costs the same) or 4 (F32) images of a texel), the
- * ceiling the forward's measured rate is compared with.  Synchronises the device; not capturable.
+ * sample, no geometry, no TMA) on every SM, with the forward's own accumulation code for `dtype`
+ * storage and the `weights` setting of radon_launch_config (RADON_WEIGHTS_F16 for FP16 storage only).
+ * *samples_per_second receives image-samples per second (one probe sample serves the 8 (16-bit) or
+ * 4 (F32) images of a texel), the ceiling the forward's measured rate is compared with.
+ * Synchronises the device; not capturable.  radon_probe_gather_ceiling(dtype, out) is
+ * radon_probe_gather_ceiling_ex(dtype, RADON_WEIGHTS_DEFAULT, out).
  */
+RADON_API radon_status radon_probe_gather_ceiling_ex(radon_dtype dtype, int weights, double* samples_per_second);
 RADON_API radon_status radon_probe_gather_ceiling(radon_dtype dtype, double* samples_per_second);
 
 /*

@@ -30,6 +30,10 @@ RADON_ALGO_AUTO = 0
 RADON_ALGO_PLAIN = 1
 RADON_ALGO_TILED = 2
 
+RADON_WEIGHTS_DEFAULT = 0   # FP32 bilinear weights
+RADON_WEIGHTS_F32 = 1
+RADON_WEIGHTS_F16 = 2       # FP16 storage only: FP16 weights in mixed-precision FMAs (opt-in)
+
 
 class RadonError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
@@ -175,6 +179,7 @@ _SIGNATURES = [
     ("radon_batch_plan_item_config", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("radon_batch_plan_destroy", None, [ctypes.c_void_p]),
     ("radon_probe_gather_ceiling", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    ("radon_probe_gather_ceiling_ex", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     ("radon_filter_sinogram", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     ("radon_dot_batched_workspace_size", ctypes.c_size_t, [ctypes.c_int]),
@@ -360,6 +365,10 @@ def radon_batch_plan_destroy(plan):
 
 def radon_probe_gather_ceiling(dtype, out_ptr):
     return _call("radon_probe_gather_ceiling", dtype, out_ptr)
+
+
+def radon_probe_gather_ceiling_ex(dtype, weights, out_ptr):
+    return _call("radon_probe_gather_ceiling_ex", dtype, weights, out_ptr)
 
 
 def radon_filter_sinogram(geom, sino, out, dtype, batch, filter_kind, stream):

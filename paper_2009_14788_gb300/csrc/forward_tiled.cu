@@ -10,16 +10,16 @@ namespace {
 
 constexpr uint32_t kSpinLimit = 1u << 22;   // bounded mbarrier polls (~seconds) before giving up
 
-// FP16 storage takes FP16 weights in mixed-precision FMAs unless the config asks for FP32 weights or
-// the epilogue adds to the projection (a fused residual keeps its own precision).
+// FP16 storage takes FP16 weights in mixed-precision FMAs only when the config asks for them and the
+// epilogue adds nothing to the projection (a fused residual keeps FP32 weights); the default is FP32.
 bool fp16_weights(const radon_launch_config* cfg, const Epilogue& ep) {
-    return !(cfg != nullptr && cfg->weights == 1) && ep.add == nullptr;
+    return cfg != nullptr && cfg->weights == RADON_WEIGHTS_F16 && ep.add == nullptr;
 }
 
-template <typename T, bool MIXED>
+template <typename T, int MODE>
 cudaError_t launch_t(const CUtensorMap& mv, const CUtensorMap& mh, const FwdTiledArgs& a, dim3 grid, size_t smem,
                      cudaStream_t s) {
-    auto kern = forward_tiled_kernel<T, MIXED>;
+    auto kern = forward_tiled_kernel<T, MODE>;
     static size_t attr_bytes = 0;
     if (smem > attr_bytes) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -126,11 +126,11 @@ radon_status launch_forward_tiled(radon_geometry* g, const void* img, void* sino
     cudaError_t e;
     switch (dt) {
         case RADON_F16:
-            e = fp16_weights(cfg, ep) ? launch_t<__half, true>(mv, mh, a, grid, smem, s)
-                                      : launch_t<__half, false>(mv, mh, a, grid, smem, s);
+            e = fp16_weights(cfg, ep) ? launch_t<__half, kMathF16W>(mv, mh, a, grid, smem, s)
+                                      : launch_t<__half, kMathScalar>(mv, mh, a, grid, smem, s);
             break;
-        case RADON_BF16: e = launch_t<__nv_bfloat16, false>(mv, mh, a, grid, smem, s); break;
-        default: e = launch_t<float, false>(mv, mh, a, grid, smem, s); break;
+        case RADON_BF16: e = launch_t<__nv_bfloat16, kMathScalar>(mv, mh, a, grid, smem, s); break;
+        default: e = launch_t<float, kMathScalar>(mv, mh, a, grid, smem, s); break;
     }
     if (e != cudaSuccess) {
         *why = std::string("tiled forward launch: ") + cudaGetErrorString(e);
@@ -145,10 +145,10 @@ namespace radon {
 
 namespace {
 
-template <typename T, bool MIXED>
+template <typename T, int MODE>
 cudaError_t launch_packed_t(const CUtensorMap& mr, const CUtensorMap& mc, const FwdTiledArgs& a, dim3 grid,
                             size_t smem, cudaStream_t s) {
-    auto kern = forward_packed_kernel<T, MIXED>;
+    auto kern = forward_packed_kernel<T, MODE>;
     static size_t attr_bytes = 0;
     if (smem > attr_bytes) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -250,11 +250,11 @@ radon_status launch_forward_packed(radon_geometry* g, const void* packed, void* 
     cudaError_t e;
     switch (dt) {
         case RADON_F16:
-            e = fp16_weights(cfg, ep) ? launch_packed_t<__half, true>(mr, mc, a, grid, smem, s)
-                                      : launch_packed_t<__half, false>(mr, mc, a, grid, smem, s);
+            e = fp16_weights(cfg, ep) ? launch_packed_t<__half, kMathF16W>(mr, mc, a, grid, smem, s)
+                                      : launch_packed_t<__half, kMathScalar>(mr, mc, a, grid, smem, s);
             break;
-        case RADON_BF16: e = launch_packed_t<__nv_bfloat16, false>(mr, mc, a, grid, smem, s); break;
-        default: e = launch_packed_t<float, false>(mr, mc, a, grid, smem, s); break;
+        case RADON_BF16: e = launch_packed_t<__nv_bfloat16, kMathScalar>(mr, mc, a, grid, smem, s); break;
+        default: e = launch_packed_t<float, kMathScalar>(mr, mc, a, grid, smem, s); break;
     }
     if (e != cudaSuccess) {
         *why = std::string("packed forward launch: ") + cudaGetErrorString(e);

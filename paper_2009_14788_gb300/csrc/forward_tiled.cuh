@@ -87,31 +87,49 @@ __host__ __device__ inline size_t fwd_smem_bytes(int stage_bytes, int R, int wc)
     return 128 + 128 + (size_t)(stage_bytes + 127) / 128 * 128 + 2 * ((fwd_comp_bytes(R, wc) + 127) / 128 * 128);
 }
 
-// 16-byte texel: BG values of one pixel (element b = image b), accumulated with weight w.
-// MIXED (FP16 storage only): the weight is rounded once to FP16 and each product of two FP16 values
-// is formed exactly and added in FP32 by one mixed-precision FMA (fma.rn.f32.f16), so nothing converts
-// the texel values and the inner loop is bound by the shared-memory load pipe; the weight's rounding
-// (relative <= 2^-12) is the only change.  Otherwise FP32 weights and FP32 FMAs on converted values.
-template <typename T, bool MIXED = false>
+// 16-byte texel: BG values of one pixel (element b = image b), accumulated with weight w into Acc.
+// Arithmetic modes (both accumulate in FP32):
+//   kMathScalar  FP32 weights, texel values converted to FP32, one FP32 FMA per image (the default
+//                for every storage type: the paper's single-precision arithmetic);
+//   kMathF16W    FP16 storage only, opt-in: the weight is rounded once to FP16 and each product of two
+//                FP16 values is formed exactly and added in FP32 by one mixed-precision FMA
+//                (fma.rn.f32.f16), so nothing converts the texel values; the weight's rounding
+//                (relative <= 2^-12) is the only change.
+constexpr int kMathScalar = 0;
+constexpr int kMathF16W = 1;
+
+template <int BG>
+struct AccF {
+    float v[BG];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int b = 0; b < BG; ++b) v[b] = 0.0f;
+    }
+    __device__ __forceinline__ float get(int b) const { return v[b]; }
+};
+
+template <typename T, int MODE = kMathScalar>
 struct Texel;
 
 template <>
-struct Texel<float, false> {
+struct Texel<float, kMathScalar> {
     static constexpr int BG = 4;
     using W = float;
+    using Acc = AccF<BG>;
     __device__ __forceinline__ static W weight(float w) { return w; }
-    __device__ __forceinline__ static void fma(float* acc, W w, const uint4& t) {
-        acc[0] = fmaf(w, __uint_as_float(t.x), acc[0]);
-        acc[1] = fmaf(w, __uint_as_float(t.y), acc[1]);
-        acc[2] = fmaf(w, __uint_as_float(t.z), acc[2]);
-        acc[3] = fmaf(w, __uint_as_float(t.w), acc[3]);
+    __device__ __forceinline__ static void fma(Acc& acc, W w, const uint4& t) {
+        acc.v[0] = fmaf(w, __uint_as_float(t.x), acc.v[0]);
+        acc.v[1] = fmaf(w, __uint_as_float(t.y), acc.v[1]);
+        acc.v[2] = fmaf(w, __uint_as_float(t.z), acc.v[2]);
+        acc.v[3] = fmaf(w, __uint_as_float(t.w), acc.v[3]);
     }
 };
 
 template <>
-struct Texel<__half, false> {
+struct Texel<__half, kMathScalar> {
     static constexpr int BG = 8;
     using W = float;
+    using Acc = AccF<BG>;
     __device__ __forceinline__ static W weight(float w) { return w; }
     __device__ __forceinline__ static void fma2(float* acc, W w, unsigned u) {
         __half2 h2;
@@ -120,11 +138,11 @@ struct Texel<__half, false> {
         acc[0] = fmaf(w, f.x, acc[0]);
         acc[1] = fmaf(w, f.y, acc[1]);
     }
-    __device__ __forceinline__ static void fma(float* acc, W w, const uint4& t) {
-        fma2(acc, w, t.x);
-        fma2(acc + 2, w, t.y);
-        fma2(acc + 4, w, t.z);
-        fma2(acc + 6, w, t.w);
+    __device__ __forceinline__ static void fma(Acc& acc, W w, const uint4& t) {
+        fma2(acc.v, w, t.x);
+        fma2(acc.v + 2, w, t.y);
+        fma2(acc.v + 4, w, t.z);
+        fma2(acc.v + 6, w, t.w);
     }
 };
 
@@ -135,36 +153,38 @@ __device__ __forceinline__ float mixed_fma_f16(unsigned short w, unsigned short 
 }
 
 template <>
-struct Texel<__half, true> {
+struct Texel<__half, kMathF16W> {
     static constexpr int BG = 8;
     using W = unsigned short;
+    using Acc = AccF<BG>;
     __device__ __forceinline__ static W weight(float w) { return __half_as_ushort(__float2half_rn(w)); }
     __device__ __forceinline__ static void fma2(float* acc, W w, unsigned u) {
         acc[0] = mixed_fma_f16(w, (unsigned short)(u & 0xffffu), acc[0]);
         acc[1] = mixed_fma_f16(w, (unsigned short)(u >> 16), acc[1]);
     }
-    __device__ __forceinline__ static void fma(float* acc, W w, const uint4& t) {
-        fma2(acc, w, t.x);
-        fma2(acc + 2, w, t.y);
-        fma2(acc + 4, w, t.z);
-        fma2(acc + 6, w, t.w);
+    __device__ __forceinline__ static void fma(Acc& acc, W w, const uint4& t) {
+        fma2(acc.v, w, t.x);
+        fma2(acc.v + 2, w, t.y);
+        fma2(acc.v + 4, w, t.z);
+        fma2(acc.v + 6, w, t.w);
     }
 };
 
 template <>
-struct Texel<__nv_bfloat16, false> {
+struct Texel<__nv_bfloat16, kMathScalar> {
     static constexpr int BG = 8;
     using W = float;
+    using Acc = AccF<BG>;
     __device__ __forceinline__ static W weight(float w) { return w; }
     __device__ __forceinline__ static void fma2(float* acc, W w, unsigned u) {
         acc[0] = fmaf(w, __uint_as_float(u << 16), acc[0]);
         acc[1] = fmaf(w, __uint_as_float(u & 0xffff0000u), acc[1]);
     }
-    __device__ __forceinline__ static void fma(float* acc, W w, const uint4& t) {
-        fma2(acc, w, t.x);
-        fma2(acc + 2, w, t.y);
-        fma2(acc + 4, w, t.z);
-        fma2(acc + 6, w, t.w);
+    __device__ __forceinline__ static void fma(Acc& acc, W w, const uint4& t) {
+        fma2(acc.v, w, t.x);
+        fma2(acc.v + 2, w, t.y);
+        fma2(acc.v + 4, w, t.z);
+        fma2(acc.v + 6, w, t.w);
     }
 };
 
@@ -320,11 +340,12 @@ __device__ void fwd_repack(const FwdTiledArgs& a, int cls, int yoff, const unsig
 
 // Consumer warps: one ray per thread, marched slab by slab through the double-buffered compute
 // buffers (texels [row][col][image], row pitch wc), released through `empty` after each slab.
-template <typename T, bool MIXED>
+template <typename T, int MODE>
 __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int d0, int b0, uint64_t* full,
                             uint64_t* empty, const int* band_xc0, const int* band_bad, volatile int* abort_flag,
                             const unsigned char* comp_base, size_t comp_stride, int wc) {
-    constexpr int BG = Texel<T, false>::BG;
+    using TX = Texel<T, MODE>;
+    constexpr int BG = TX::BG;
     const int tid = threadIdx.x;
     // Thread -> (view, detector) of the CTA.  By default consecutive threads take consecutive detectors
     // of one view; with pair_views each 8-lane phase of a 16-byte shared load takes views 2m, 2m + 1 x
@@ -354,9 +375,8 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
     }
     const float dX = dXh + dXl, dY = dYh + dYl;
     int k = 0;
-    float acc[BG];
-#pragma unroll
-    for (int b = 0; b < BG; ++b) acc[b] = 0.0f;
+    typename TX::Acc acc;
+    acc.zero();
 
     for (int s = 0; s < a.n_slabs; ++s) {
         const int buf = s % a.stages;
@@ -430,7 +450,6 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
                         }
                         const float ax = fxm - (tx - M), ay = fym - (ty - M);   // in [-1/2, 1/2]
                         const float wx1 = 0.5f + ax, wx0 = 0.5f - ax, wy1 = 0.5f + ay, wy0 = 0.5f - ay;
-                        using TX = Texel<T, MIXED>;
                         TX::fma(acc, TX::weight(wx0 * wy0), q00);
                         TX::fma(acc, TX::weight(wx1 * wy0), q01);
                         TX::fma(acc, TX::weight(wx0 * wy1), q10);
@@ -455,7 +474,7 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
     for (int b = 0; b < BG; ++b) {
         const bool mine = active && b0 + b < a.B;
         const long long idx = (long long)(b0 + b) * vd + o;
-        const float val = mine ? epilogue_value<T>(a.ep, a.h * acc[b], idx) : 0.0f;
+        const float val = mine ? epilogue_value<T>(a.ep, a.h * acc.get(b), idx) : 0.0f;
         if (pairs) {
             const float nval = __shfl_xor_sync(0xffffffffu, val, 1);
             const bool nmine = __shfl_xor_sync(0xffffffffu, mine ? 1 : 0, 1) != 0;
@@ -470,11 +489,11 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
     }
 }
 
-template <typename T, bool MIXED>
+template <typename T, int MODE>
 __global__ void __launch_bounds__(kFwdThreads, 3) forward_tiled_kernel(const __grid_constant__ CUtensorMap map_v,
                                                                       const __grid_constant__ CUtensorMap map_h,
                                                                       const FwdTiledArgs a) {
-    constexpr int BG = Texel<T, false>::BG;
+    constexpr int BG = Texel<T>::BG;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
     uint64_t* tma_bar = reinterpret_cast<uint64_t*>(smem);
@@ -542,14 +561,14 @@ __global__ void __launch_bounds__(kFwdThreads, 3) forward_tiled_kernel(const __g
         return;
     }
 
-    fwd_consume<T, MIXED>(a, cls, v0, cnt, d0, b0, full, empty, band_xc0, band_bad, abort_flag, comp_base, comp_stride,
+    fwd_consume<T, MODE>(a, cls, v0, cnt, d0, b0, full, empty, band_xc0, band_bad, abort_flag, comp_base, comp_stride,
                    a.wc);
 }
 
 // Packed variant: the image batch was packed once into 16-byte texels (rows / cols copies, see
 // pack.cu), so the producer warp only bounds each band and copies it with one 4-D TMA load straight
 // into the compute buffer it will become (row pitch = band width); no staging, no repack.
-template <typename T, bool MIXED>
+template <typename T, int MODE>
 __global__ void __launch_bounds__(kFwdThreads, 3) forward_packed_kernel(const __grid_constant__ CUtensorMap map_rows,
                                                                        const __grid_constant__ CUtensorMap map_cols,
                                                                        const FwdTiledArgs a) {
@@ -569,7 +588,7 @@ __global__ void __launch_bounds__(kFwdThreads, 3) forward_packed_kernel(const __
     const Int2 grp = a.groups[grp_idx];
     const int v0 = grp.x, cnt = grp.y & 0xffff, cls = grp.y >> 16;
     const int d0 = dr * a.Dt;
-    const int b0 = blockIdx.y * Texel<T, false>::BG;
+    const int b0 = blockIdx.y * Texel<T>::BG;
 
     if (tid < a.stages) {
         mbar_init(&full[tid], 1);
@@ -609,7 +628,7 @@ __global__ void __launch_bounds__(kFwdThreads, 3) forward_packed_kernel(const __
         }
         return;
     }
-    fwd_consume<T, MIXED>(a, cls, v0, cnt, d0, b0, full, empty, band_xc0, band_bad, abort_flag, comp_base, comp_stride,
+    fwd_consume<T, MODE>(a, cls, v0, cnt, d0, b0, full, empty, band_xc0, band_bad, abort_flag, comp_base, comp_stride,
                    a.wbox);
 }
 

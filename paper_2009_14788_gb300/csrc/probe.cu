@@ -23,9 +23,9 @@ constexpr int kProbeTile = 64;          // texels per row
 constexpr int kProbeRows = 40;          // rows (40 KB of texels)
 constexpr int kProbeSamples = 4096;     // samples per thread
 
-template <typename T>
+template <typename T, int MODE>
 __global__ void __launch_bounds__(kProbeThreads) probe_kernel(float* sink) {
-    using TX = Texel<T, std::is_same<T, __half>::value>;   // the forward's default per storage type
+    using TX = Texel<T, MODE>;
     constexpr int BG = TX::BG;
     __shared__ uint4 tile[kProbeTile * kProbeRows];
     for (int e = threadIdx.x; e < kProbeTile * kProbeRows; e += kProbeThreads) {
@@ -39,9 +39,8 @@ __global__ void __launch_bounds__(kProbeThreads) probe_kernel(float* sink) {
     const float ang = 0.7853982f * (float)((warp * 37 + blockIdx.x * 11) & 63) / 64.0f;
     const float dx = sinf(ang) * 0.55f, dy = cosf(ang) * 0.55f;   // x < 2.3 + 31 + 21.4 + 1 < 64, y < 2.2 + 30.3 + 1 < 40
     const float x0 = 2.3f + (float)lane, y0 = 2.2f;
-    float acc[BG];
-#pragma unroll
-    for (int b = 0; b < BG; ++b) acc[b] = 0.0f;
+    typename TX::Acc acc;
+    acc.zero();
     for (int k = 0; k < kProbeSamples; ++k) {
         // positions wrap inside the tile interior every 56 samples (no geometry, no bounds checks)
         const float kk = (float)(k % 56);
@@ -59,7 +58,7 @@ __global__ void __launch_bounds__(kProbeThreads) probe_kernel(float* sink) {
     }
     float s = 0.0f;
 #pragma unroll
-    for (int b = 0; b < BG; ++b) s += acc[b];
+    for (int b = 0; b < BG; ++b) s += acc.get(b);
     if (s == 1234.5f) sink[0] = s;   // keeps the loop live; never true for these inputs in practice
 }
 
@@ -69,17 +68,15 @@ __global__ void __launch_bounds__(kProbeThreads) probe_kernel(float* sink) {
 
 using namespace radon;
 
-extern "C" RADON_API radon_status radon_probe_gather_ceiling(radon_dtype dtype, double* samples_per_second) {
-    if (samples_per_second == nullptr) return fail(RADON_ERR_INVALID_ARG, "samples_per_second is NULL");
-    if (dtype != RADON_F32 && dtype != RADON_F16)
-        return fail(RADON_ERR_INVALID_ARG, "the probe takes RADON_F32 or RADON_F16 (BF16 has the F16 cost)");
+namespace {
+
+using ProbeKernel = void (*)(float*);
+
+radon_status run_probe(ProbeKernel kern, double images_per_sample, double* samples_per_second) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = dtype == RADON_F16
-                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, probe_kernel<__half>, kProbeThreads, 0)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, probe_kernel<float>, kProbeThreads, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kProbeThreads, 0);
     if (e != cudaSuccess) return cuda_fail(e, "probe setup");
     const int blocks = sms * (per_sm > 0 ? per_sm : 1) * 4;
     float* sink = nullptr;
@@ -91,8 +88,7 @@ extern "C" RADON_API radon_status radon_probe_gather_ceiling(radon_dtype dtype, 
     float best = 3.0e38f;
     for (int rep = 0; rep < 4; ++rep) {
         cudaEventRecord(e0, 0);
-        if (dtype == RADON_F16) probe_kernel<__half><<<blocks, kProbeThreads>>>(sink);
-        else probe_kernel<float><<<blocks, kProbeThreads>>>(sink);
+        kern<<<blocks, kProbeThreads>>>(sink);
         cudaEventRecord(e1, 0);
         e = cudaEventSynchronize(e1);
         if (e != cudaSuccess) break;
@@ -105,8 +101,31 @@ extern "C" RADON_API radon_status radon_probe_gather_ceiling(radon_dtype dtype, 
     cudaEventDestroy(e1);
     cudaFree(sink);
     if (e != cudaSuccess) return cuda_fail(e, "probe run");
-    // one probe sample covers BG images of the texel, as one forward sample per image does
-    const double bg = dtype == RADON_F16 ? 8.0 : 4.0;
-    *samples_per_second = (double)blocks * kProbeThreads * kProbeSamples * bg / (best * 1e-3);
+    // one probe sample covers the BG images of the texel, as one forward sample per image does
+    *samples_per_second = (double)blocks * kProbeThreads * kProbeSamples * images_per_sample / (best * 1e-3);
     return RADON_OK;
+}
+
+}  // namespace
+
+extern "C" RADON_API radon_status radon_probe_gather_ceiling_ex(radon_dtype dtype, int weights,
+                                                               double* samples_per_second) {
+    if (samples_per_second == nullptr) return fail(RADON_ERR_INVALID_ARG, "samples_per_second is NULL");
+    if (dtype != RADON_F32 && dtype != RADON_F16 && dtype != RADON_BF16)
+        return fail(RADON_ERR_INVALID_ARG, "unknown dtype");
+    if (weights != RADON_WEIGHTS_DEFAULT && weights != RADON_WEIGHTS_F32 && weights != RADON_WEIGHTS_F16)
+        return fail(RADON_ERR_INVALID_ARG, "weights must be 0, 1 or 2");
+    if (weights == RADON_WEIGHTS_F16 && dtype != RADON_F16)
+        return fail(RADON_ERR_INVALID_ARG, "FP16 weights apply to FP16 storage only");
+    switch (dtype) {
+        case RADON_F16:
+            return weights == RADON_WEIGHTS_F16 ? run_probe(probe_kernel<__half, kMathF16W>, 8.0, samples_per_second)
+                                                : run_probe(probe_kernel<__half, kMathScalar>, 8.0, samples_per_second);
+        case RADON_BF16: return run_probe(probe_kernel<__nv_bfloat16, kMathScalar>, 8.0, samples_per_second);
+        default: return run_probe(probe_kernel<float, kMathScalar>, 4.0, samples_per_second);
+    }
+}
+
+extern "C" RADON_API radon_status radon_probe_gather_ceiling(radon_dtype dtype, double* samples_per_second) {
+    return radon_probe_gather_ceiling_ex(dtype, RADON_WEIGHTS_DEFAULT, samples_per_second);
 }

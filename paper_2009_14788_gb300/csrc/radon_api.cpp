@@ -210,8 +210,10 @@ radon_status project(const radon_geometry* g, const void* in, void* out, radon_d
     const int algo = cfg ? cfg->algo : RADON_ALGO_AUTO;
     if (algo != RADON_ALGO_AUTO && algo != RADON_ALGO_PLAIN && algo != RADON_ALGO_TILED)
         return fail(RADON_ERR_INVALID_ARG, "unknown algo");
-    if (cfg != nullptr && cfg->weights != 0 && cfg->weights != 1)
-        return fail(RADON_ERR_INVALID_ARG, "weights must be 0 (FP16 weights for FP16 storage) or 1 (FP32 weights)");
+    if (cfg != nullptr && cfg->weights != RADON_WEIGHTS_DEFAULT && cfg->weights != RADON_WEIGHTS_F32 &&
+        cfg->weights != RADON_WEIGHTS_F16)
+        return fail(RADON_ERR_INVALID_ARG,
+                    "weights must be 0 or 1 (FP32 weights) or 2 (FP16 weights, FP16 storage only)");
     const int threads = cfg ? cfg->threads : 0;
     if (threads < 0 || threads > 1024 || (threads % 32) != 0)
         return fail(RADON_ERR_INVALID_ARG, "threads must be 0 or a multiple of 32 up to 1024");

@@ -1,24 +1,27 @@
 // Forward projection for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc at all, or not at the moment they project: a program that
-// is being captured into a CUDA graph (an allocation is not a capturable operation), a real-time
-// or safety-certified loop that forbids allocation after start-up, or a plain C host that has no
-// device allocator and no caching pool to borrow a workspace from.  radon_forward_static_scratch
+// Some callers cannot call cudaMalloc at all, or not at the moment they project: a real-time or
+// safety-certified loop that forbids allocation after start-up, code that must not let an
+// allocation synchronise the device in the middle of its stream work, or a plain C host that has
+// no device allocator and no caching pool to borrow a workspace from.  radon_forward_static_scratch
 // gives them the packed forward path -- the one that needs a scratch workspace for the packed
 // image batch -- with that scratch in a fixed, file-scope device array instead: nothing is
 // allocated, by this library or by anyone else, at any call.
 //
 // Costs and rules of the shared array (kStaticScratchBytes, 32 MiB):
 //   * every GPU that loads the library holds the array until the process exits;
-//   * a call needs radon_forward_workspace_size(geometry, dtype, batch) bytes; larger requests are
-//     rejected with RADON_ERR_INVALID_ARG (split the batch);
+//   * a call needs the packed batch, 2 * ceil(batch / BG) * N^2 * 16 bytes (BG = 4 images per texel
+//     for FP32 storage, 8 for 16-bit; a batch of one is one group); larger requests are rejected
+//     with RADON_ERR_INVALID_ARG (split the batch);
 //   * every call packs its whole batch into the array and so overwrites what the previous call left
 //     there; nothing in it has to start at zero (the packing writes every texel the kernel reads,
 //     padding included);
 //   * calls whose work overlaps on the GPU (two streams, or a second call before the first one's
 //     kernels have run on another stream) race on the array and must be ordered by the caller;
 //   * the first call on each device looks up the array's device address with that device current
-//     (cudaGetSymbolAddress); make that first call before any stream capture starts.
+//     (cudaGetSymbolAddress) and keeps it for the life of the process; make that first call before
+//     any stream capture starts.  The kept address is not valid across a reset of the device's
+//     primary context (cudaDeviceReset): do not call this entry point after one.
 #include <mutex>
 
 #include "radon_internal.h"

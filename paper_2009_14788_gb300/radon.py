@@ -25,7 +25,9 @@ ALGOS = {"auto": L.RADON_ALGO_AUTO, "plain": L.RADON_ALGO_PLAIN, "tiled": L.RADO
 def launch_config(algo="auto", views_per_cta=0, rows_per_slab=0, images_per_cta=0, tile=0, threads=0, weights=0):
     """A ``radon_launch_config`` (kernel family and tile parameters; 0 = library default).
 
-    ``weights=1`` keeps FP32 bilinear weights in the FP16 forward (see include/radon.h)."""
+    ``weights``: 0 / 1 keep FP32 bilinear weights (the default, single-precision arithmetic in every
+    storage type); 2 rounds them to FP16 inside exact mixed-precision products in the FP16 forward
+    (opt-in, see include/radon.h)."""
     return L.radon_launch_config(ALGOS[algo] if isinstance(algo, str) else int(algo), views_per_cta, rows_per_slab,
                                  images_per_cta, tile, threads, weights)
 

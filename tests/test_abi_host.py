@@ -115,7 +115,7 @@ def test_launch_argument_checks_without_gpu():
     cfg.threads = 48
     assert L.radon_forward_ex(h, p, p + 4, 0, 1, ctypes.byref(cfg), None) == L.RADON_ERR_INVALID_ARG
     cfg.threads = 0
-    cfg.weights = 2
+    cfg.weights = 3
     assert L.radon_forward_ex(h, p, p + 4, 0, 1, ctypes.byref(cfg), None) == L.RADON_ERR_INVALID_ARG
     assert "weights" in L.radon_last_error_message()
     cfg.weights = 0

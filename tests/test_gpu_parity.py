@@ -418,16 +418,18 @@ def test_forward_packed_any_image_size(case, dtype):
 @pytest.mark.parametrize("ws", WS)
 @pytest.mark.parametrize("case", FWD_TILED_CASES)
 def test_fp16_weight_modes(case, ws):
-    """FP16 storage: FP16 bilinear weights in mixed-precision FMAs (the default) and FP32 weights
-    (weights=1) both meet the 16-bit gate, and per ray they differ by no more than the weights'
-    rounding (relative <= 2^-12 each, so <= 2^-12 of the ray sum for non-negative images) plus one
-    FP16 output rounding of each result (2^-11 each)."""
+    """FP16 storage: FP32 bilinear weights (the default) and FP16 weights in mixed-precision FMAs
+    (weights=2, opt-in) both meet the 16-bit gate, and per ray they differ by no more than the
+    weights' rounding (relative <= 2^-12 each, so <= 2^-12 of the ray sum for non-negative images)
+    plus one FP16 output rounding of each result (2^-11 each).  weights=1 names the default."""
     g, og = make(case)
     x = phantoms(g.n, 3)
     xs = to_dev(x, torch.float16)
     ref = O.forward(og, to_np(xs))
-    fast = to_np(forward_raw(g, xs, launch_config("tiled"), workspace=_ws(ws)))
-    exact = to_np(forward_raw(g, xs, launch_config("tiled", weights=1), workspace=_ws(ws)))
+    fast = to_np(forward_raw(g, xs, launch_config("tiled", weights=2), workspace=_ws(ws)))
+    exact = to_np(forward_raw(g, xs, launch_config("tiled"), workspace=_ws(ws)))
+    named = to_np(forward_raw(g, xs, launch_config("tiled", weights=1), workspace=_ws(ws)))
+    assert np.array_equal(exact, named)
     assert rel_l2(fast, ref) <= TOL_16 and rel_l2(exact, ref) <= TOL_16
     bound = (2.0 ** -12 + 2 * 2.0 ** -11) * np.abs(ref) + 1e-6 * np.abs(ref).max()
     assert np.all(np.abs(fast - exact) <= bound)

@@ -78,3 +78,27 @@ def test_reference_arm_under_torchrun_prints_once(tmp_path):
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["unit"] == "samples/s"
     assert line["config"]["workload"] == "parallel_b1_n64_v64_d91" and line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["value"] > 0
+
+
+def test_reference_arm_never_loads_the_library():
+    """The reference arm is the FP64 oracle alone: its config and sample counts come from ``oracle``,
+    so the process neither imports the package nor maps libradon.so."""
+    code = (
+        "import sys\n"
+        "sys.path.insert(0, %r)\n"
+        "import bench\n"
+        "sys.argv = ['bench.py', '--impl', 'reference', '--steps', '1', '--warmup', '0',\n"
+        "            '--workload', 'parallel_b1_n64_v64_d91']\n"
+        "bench.main()\n"
+        "maps = open('/proc/self/maps').read()\n"
+        "assert 'libradon' not in maps, 'libradon.so mapped'\n"
+        "assert 'paper_2009_14788_gb300' not in sys.modules, 'package imported'\n"
+        "assert 'liboracle' in maps\n"
+        "print('REF_OK')\n"
+    ) % ROOT
+    res = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=dict(os.environ, OMP_NUM_THREADS="2"),
+                         capture_output=True, text=True, timeout=300)
+    assert res.returncode == 0, res.stderr[-2000:]
+    assert "REF_OK" in res.stdout
+    line = json.loads([l for l in res.stdout.splitlines() if l.startswith("{")][0])
+    assert line["config"]["samples_per_image"] > 0 and line["config"]["det_count"] == 91
