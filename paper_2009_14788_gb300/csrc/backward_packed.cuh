@@ -1,0 +1,503 @@
+// Packed gather adjoint (the exact transpose of the forward projection, computed pixel by pixel with
+// no atomics) and, with KW = 0, the interpolating backprojector.
+//
+// The sinogram batch is packed once (pack.cu) into rows of BG images per detector,
+// [group][view][det][BG] in the storage type (FP32 rows carry four padding words).  One CTA owns a
+// 16 x 16 pixel tile of BG images and loops over every view in chunks of kBwdPViews views, through a
+// ring of `stages` TMA destinations:
+//   * the producer warp computes each view's detector window for the tile (and checks that it holds
+//     every pixel's candidate rays), then issues per view one TMA copy of the window's rows
+//     [det][BG] and one of the window's rows of the ray table, up to the ring's depth ahead;
+//   * the 256 consumer threads (one pixel each), once a chunk has landed, convert 16-bit windows to
+//     FP32 rows of pitch (BG + 4) words in a double buffer (FP32 windows land in that layout
+//     directly), re-base each landed ray on the tile in place -- reference sample, step and the
+//     window constant C of its candidate samples -- meet at a named barrier and gather: for every
+//     candidate ray of the pixel, the KW sample weights once for all BG images, then BG FP32 FMAs
+//     issued as f32x2 pairs.
+// The row pitch of (BG + 4) words is an odd number of 16-byte units, so the 16-byte loads of eight
+// lanes that read eight consecutive detectors fall in eight different bank groups.
+#pragma once
+
+#include <string>
+
+#include "backward_tiled.cuh"
+#include "dtype.cuh"
+#include "epilogue.cuh"
+#include "f32x2.cuh"
+#include "radon_internal.h"
+#include "tensor_map.h"
+#include "tma.cuh"
+
+namespace radon {
+
+constexpr int kBwdPViews = 4;            // views per chunk
+constexpr int kBwdPMaxStages = 4;        // ring depth limit (mbarrier slots in the header)
+// Pixels per consumer thread: a vertical pair of neighbours shares its candidate rays, so every ray
+// record and window row loaded from shared memory serves both pixels' accumulators (16-image groups);
+// 32-image groups keep one pixel per thread (their accumulators already fill the registers).
+template <int BG>
+struct BwdPShape {
+    static constexpr int PX = BG <= 16 ? 2 : 1;
+    static constexpr int kConsumers = kBwdThreads / PX;
+    static constexpr int kThreads = kConsumers + 32;
+    static constexpr int kCtasPerSm = PX == 2 ? 4 : 2;   // resident CTAs the launch bounds ask for
+};
+constexpr size_t kBwdPHeader = 1024;     // barriers, flags, windows and view maps of the ring
+
+template <typename T, int BG>
+struct BwdPLayout {
+    static constexpr bool kConv = sizeof(T) == 2;              // 16-bit windows are converted in smem
+    static constexpr int kRowElems = kConv ? BG : BG + 4;      // elements per detector in the workspace
+    static constexpr int kPitch = (BG + 4) * 4;                // bytes per detector of an FP32 window row
+    static_assert(((BG + 4) / 4) % 2 == 1, "the FP32 row pitch must be an odd number of 16-byte units");
+};
+
+__host__ __device__ inline size_t bwdp_round128(size_t x) { return (x + 127) / 128 * 128; }
+
+// Shared-memory plan of one CTA, identical on host and device.
+struct BwdPSmem {
+    size_t yst_view;   // TMA'd window rows of one view
+    size_t rst_view;   // TMA'd ray rows of one view (re-based in place)
+    size_t stage;      // one ring slot (kBwdPViews views)
+    size_t yf_view;    // converted FP32 window of one view (16-bit storage only)
+    size_t yf_buf;     // one of the two converted buffers
+    size_t total;      // dynamic shared memory of the launch (with 128 B of alignment slack)
+};
+
+template <typename T, int BG>
+__host__ __device__ inline BwdPSmem bwdp_smem(int wd, int stages, bool rays) {
+    using L = BwdPLayout<T, BG>;
+    BwdPSmem m;
+    m.yst_view = bwdp_round128((size_t)wd * L::kRowElems * sizeof(T));
+    m.rst_view = rays ? bwdp_round128((size_t)wd * 32) : 0;
+    m.stage = (size_t)kBwdPViews * (m.yst_view + m.rst_view);
+    m.yf_view = L::kConv ? bwdp_round128((size_t)wd * L::kPitch) : 0;
+    m.yf_buf = (size_t)kBwdPViews * m.yf_view;
+    m.total = 128 + kBwdPHeader + (size_t)stages * m.stage + 2 * m.yf_buf;
+    return m;
+}
+
+struct BwdPArgs {
+    const ViewF* views;
+    void* img;
+    int n, V, D, B;
+    float h;           // output scale (the step; 1 for the interpolating backprojector)
+    float ih2;         // 1 / step^2 (every ray's step has length h)
+    int wd;            // detector window per view (rows copied per view)
+    int stages;        // ring depth (2..kBwdPMaxStages)
+    int tiles_x;
+    int out_dtype;     // radon_dtype of the output image
+    int* err;
+    uint32_t spin_limit;
+    Epilogue ep;
+};
+
+// Detector window of a tile for one view (bwd_view_window) and the largest detector coordinate of
+// its pixels, from the tile's four corners (a linear-fractional map takes its extremes over a
+// convex tile at the corners).
+__device__ __forceinline__ float bwdp_tile_tmax(const ViewF vf, int ti, int tj, int n) {
+    const float x0 = (float)tj, x1 = (float)min(tj + kBwdTile - 1, n - 1);
+    const float y0 = (float)ti, y1 = (float)min(ti + kBwdTile - 1, n - 1);
+    return fmaxf(fmaxf(bwd_det_coord(vf, x0, y0), bwd_det_coord(vf, x1, y0)),
+                 fmaxf(bwd_det_coord(vf, x0, y1), bwd_det_coord(vf, x1, y1)));
+}
+
+// Re-based ray record: A = (reference sample relative to the tile origin, step), Bc = (step / h^2,
+// C, 0) with C = -A.b - kr, so that the first of a pixel's KW candidate samples is
+// ceil(p.b + C) samples past the reference (kr = (|dx| + |dy|) / h^2 + 1e-4 half-widths the window:
+// every sample within the pixel's 2 x 2 support lies within kr of the pixel's projection).  A ray
+// outside the detector gets a far-away sentinel with step zero (weight zero everywhere).
+__device__ __forceinline__ void bwdp_rebase(const RayT ray, bool valid, int ti, int tj, float ih2, float4* A,
+                                            float4* Bc) {
+    *A = bwd_ray_pos_rec(ray, valid, ti, tj, ih2);
+    const float bx = A->z * ih2, by = A->w * ih2;
+    const float kr = fmaf(fabsf(A->z) + fabsf(A->w), ih2, 1e-4f);
+    *Bc = make_float4(bx, by, -fmaf(A->x, bx, A->y * by) - kr, 0.0f);
+}
+
+// Bilinear weight of the pixel at p2 (tile-local) on one ray: the sum over its KW consecutive
+// samples from the window start of tent(dx) * tent(dy), tent(v) = max(0, 1 - |v|) evaluated as one
+// saturating add (1 - |v| <= 1, so clamping to [0, 1] only clamps at 0).
+template <int KW>
+__device__ __forceinline__ float bwdp_weight(f32x2 p2, float px, float py, f32x2 a2, f32x2 d2, float bx, float by,
+                                             float C) {
+    const float ka = ceilf(fmaf(px, bx, fmaf(py, by, C)));
+    f32x2 r2 = f2_fma(f2_pack(ka, ka), d2, f2_sub(a2, p2));   // sample ka relative to the pixel
+    float w = 0.0f;
+#pragma unroll
+    for (int k = 0; k < KW; ++k) {
+        float rx, ry;
+        f2_unpack(r2, &rx, &ry);
+        w = fmaf(__saturatef(1.0f - fabsf(rx)), __saturatef(1.0f - fabsf(ry)), w);
+        if (k + 1 < KW) r2 = f2_add(r2, d2);
+    }
+    return w;
+}
+
+// 16-bit row segment of 8 images (one 16-byte load) -> 8 FP32 words (two 16-byte stores).
+template <typename T>
+__device__ __forceinline__ void bwdp_widen8(const uint4 u, float4* out);
+
+template <>
+__device__ __forceinline__ void bwdp_widen8<__half>(const uint4 u, float4* out) {
+    __half2 h[4];
+    memcpy(h, &u, 16);
+    const float2 a = __half22float2(h[0]), b = __half22float2(h[1]), c = __half22float2(h[2]),
+                 d = __half22float2(h[3]);
+    out[0] = make_float4(a.x, a.y, b.x, b.y);
+    out[1] = make_float4(c.x, c.y, d.x, d.y);
+}
+
+template <>
+__device__ __forceinline__ void bwdp_widen8<__nv_bfloat16>(const uint4 u, float4* out) {
+    out[0] = make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u), __uint_as_float(u.y << 16),
+                         __uint_as_float(u.y & 0xffff0000u));
+    out[1] = make_float4(__uint_as_float(u.z << 16), __uint_as_float(u.z & 0xffff0000u), __uint_as_float(u.w << 16),
+                         __uint_as_float(u.w & 0xffff0000u));
+}
+
+template <typename T, int BG, int KW>
+__global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasPerSm)
+    backward_packed_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap rmap,
+                           const BwdPArgs a) {
+    using L = BwdPLayout<T, BG>;
+    constexpr int NQ = BG / 4;
+    constexpr int PITCH = L::kPitch;
+    constexpr int PX = BwdPShape<BG>::PX;
+    constexpr int NC = BwdPShape<BG>::kConsumers;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    uint64_t* tma_bar = reinterpret_cast<uint64_t*>(smem);        // [stages]: a slot's copies landed
+    uint64_t* empty = reinterpret_cast<uint64_t*>(smem + 64);     // [stages]: consumers released a slot
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 128);
+    int* dlo_c = reinterpret_cast<int*>(smem + 192);              // [stages][views]
+    float* r_c = reinterpret_cast<float*>(smem + 256);            // [stages][views]
+    ViewF* view_c = reinterpret_cast<ViewF*>(smem + 512);         // [stages][views]
+    static_assert(kBwdPMaxStages * kBwdPViews * 4 <= 64 && 512 + kBwdPMaxStages * kBwdPViews * 32 <= kBwdPHeader,
+                  "ring header overflows its slots");
+    const int S = a.stages;
+    const BwdPSmem m = bwdp_smem<T, BG>(a.wd, S, KW > 0);
+    unsigned char* ring = smem + kBwdPHeader;
+    unsigned char* yf = ring + (size_t)S * m.stage;   // [2][views] converted windows (16-bit storage)
+
+    const int tid = threadIdx.x;
+    const int tile = blockIdx.x;
+    const int ti = (tile / a.tiles_x) * kBwdTile, tj = (tile - (tile / a.tiles_x) * a.tiles_x) * kBwdTile;
+    const int nchunks = (a.V + kBwdPViews - 1) / kBwdPViews;
+
+    if (tid < S) {
+        mbar_init(&tma_bar[tid], 1);
+        mbar_init(&empty[tid], NC);
+    }
+    if (tid == 0) *abort_flag = 0;
+    fence_mbar_init();
+    __syncthreads();
+
+    if (tid >= NC) {
+        // ------------------------------------------------------------------ producer warp
+        const int lane = tid & 31;
+        int c = 0;
+        for (; c < nchunks; ++c) {
+            const int st = c % S;
+            bool ok = true;
+            if (c >= S && lane == 0) ok = mbar_wait_bounded(&empty[st], (uint32_t)((c / S - 1) & 1), a.spin_limit);
+            if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
+            const int v0 = c * kBwdPViews;
+            const int nv = min(kBwdPViews, a.V - v0);
+            if (lane < nv) {
+                const ViewF vf = a.views[v0 + lane];
+                int dlo;
+                float r;
+                bwd_view_window(vf, ti, tj, a.n, &dlo, &r);
+                // every pixel's candidates [ceil(t - r), floor(t + r)] within the detector must lie in
+                // the copied window; the consumers clamp to it, so a miss is recorded, not overrun
+                const float thi = floorf(bwdp_tile_tmax(vf, ti, tj, a.n) + r);
+                if (fminf(thi, (float)(a.D - 1)) > (float)(dlo + a.wd - 1)) record_device_error(a.err, RADON_ERR_DEVICE_BOUNDS);
+                dlo_c[st * kBwdPViews + lane] = dlo;
+                r_c[st * kBwdPViews + lane] = r;
+                view_c[st * kBwdPViews + lane] = vf;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                unsigned char* slot = ring + (size_t)st * m.stage;
+                fence_proxy_async_shared();
+                mbar_arrive_expect_tx(&tma_bar[st],
+                                      (uint32_t)(nv * a.wd * (L::kRowElems * (int)sizeof(T) + (KW > 0 ? 32 : 0))));
+                for (int vl = 0; vl < nv; ++vl) {
+                    const int dlo = dlo_c[st * kBwdPViews + vl];
+                    tma_load_4d(slot + (size_t)vl * m.yst_view, &map, &tma_bar[st], 0, dlo, v0 + vl, blockIdx.y);
+                    if (KW > 0)   // the interpolating backprojector needs no rays
+                        tma_load_2d(slot + (size_t)kBwdPViews * m.yst_view + (size_t)vl * m.rst_view, &rmap,
+                                    &tma_bar[st], 0, (v0 + vl) * a.D + dlo);
+                }
+            }
+            __syncwarp();
+        }
+        if (c < nchunks && lane == 0) {
+            // The consumers stopped releasing slots: record it, let the copies still in flight land
+            // (bounded), then complete chunk c's phase without data so any consumer still waiting
+            // sees the abort.
+            record_device_error(a.err, RADON_ERR_TIMEOUT);
+            *abort_flag = 1;
+            for (int cc = max(0, c - S + 1); cc < c; ++cc)
+                mbar_wait_bounded(&tma_bar[cc % S], (uint32_t)((cc / S) & 1), a.spin_limit);
+            mbar_arrive(&tma_bar[c % S]);
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------------- consumer warps
+    // each warp takes an (4 PX) x 8 block of the tile, lanes on a 4 x 8 grid of pixels (PX = 1) or
+    // vertical pixel pairs (PX = 2): a block's detector footprints overlap more than those of a strip,
+    // so the gather's shared loads touch fewer distinct addresses.  A 16-byte shared load is served
+    // eight lanes at a time, so each group of eight lanes covers a compact block -- 4 x 2 pixels, or
+    // 2 x 4 pairs (4 x 4 pixels) -- whose detector span stays within the eight bank groups
+    const int warp = tid >> 5, lane = tid & 31;
+    const int grp = lane >> 3, e8 = lane & 7;
+    const int pi0 = PX == 2 ? (warp >> 1) * 8 + ((grp >> 1) * 2 + (e8 >> 2)) * 2 : (warp >> 1) * 4 + (e8 >> 1);
+    const int pj = PX == 2 ? (warp & 1) * 8 + (grp & 1) * 4 + (e8 & 3) : (warp & 1) * 8 + grp * 2 + (e8 & 1);
+    const float px = (float)pj;
+    f32x2 p2[PX];
+    bool inside[PX];
+#pragma unroll
+    for (int x = 0; x < PX; ++x) {
+        p2[x] = f2_pack(px, (float)(pi0 + x));
+        inside[x] = (ti + pi0 + x) < a.n && (tj + pj) < a.n;
+    }
+    const float gx = (float)(tj + pj), gy0 = (float)(ti + pi0);
+    f32x2 acc[PX][BG / 2];   // per pixel, image pairs (2b, 2b + 1)
+#pragma unroll
+    for (int x = 0; x < PX; ++x)
+#pragma unroll
+        for (int b = 0; b < BG / 2; ++b) acc[x][b] = 0ull;
+    for (int c = 0; c < nchunks; ++c) {
+        const int st = c % S;
+        const int v0 = c * kBwdPViews;
+        const int nv = min(kBwdPViews, a.V - v0);
+        bool bad = !mbar_wait_bounded(&tma_bar[st], (uint32_t)((c / S) & 1), a.spin_limit);
+        bad = bad || *abort_flag != 0;
+        unsigned char* slot = ring + (size_t)st * m.stage;
+        unsigned char* rst = slot + (size_t)kBwdPViews * m.yst_view;
+        unsigned char* ybuf = L::kConv ? yf + (size_t)(c & 1) * m.yf_buf : slot;
+        const size_t yview = L::kConv ? m.yf_view : m.yst_view;
+        if (!bad) {
+            if constexpr (L::kConv) {
+                // 16-bit window rows -> FP32 rows of pitch PITCH (8 images per 16-byte load)
+                constexpr int OCT = BG / 8;
+                for (int e = tid; e < nv * a.wd * OCT; e += NC) {
+                    const int vl = e / (a.wd * OCT), rest = e - vl * (a.wd * OCT);
+                    const int dl = rest / OCT, o = rest - dl * OCT;
+                    const uint4 u = *reinterpret_cast<const uint4*>(slot + (size_t)vl * m.yst_view + (size_t)dl * BG * 2 +
+                                                                    (size_t)o * 16);
+                    float4 f[2];
+                    bwdp_widen8<T>(u, f);
+                    float4* dst = reinterpret_cast<float4*>(ybuf + (size_t)vl * yview + (size_t)dl * PITCH + (size_t)o * 32);
+                    dst[0] = f[0];
+                    dst[1] = f[1];
+                }
+            }
+            if constexpr (KW > 0) {
+                // re-base the landed rays on this tile, in place: one ray per thread
+                for (int e = tid; e < nv * a.wd; e += NC) {
+                    const int vl = e / a.wd, dl = e - vl * a.wd;
+                    const int d = dlo_c[st * kBwdPViews + vl] + dl;
+                    float4* rec = reinterpret_cast<float4*>(rst + (size_t)vl * m.rst_view + (size_t)dl * 32);
+                    const RayT ray = *reinterpret_cast<const RayT*>(rec);
+                    float4 A, Bc;
+                    bwdp_rebase(ray, d >= 0 && d < a.D, ti, tj, a.ih2, &A, &Bc);
+                    rec[0] = A;
+                    rec[1] = Bc;
+                }
+            }
+        }
+        // all consumers: windows and records written (the converted buffer alternates, so the
+        // previous chunk's readers have all passed this barrier before it is overwritten) -- and
+        // one shared abort decision
+        if (named_barrier_or(1, NC, bad)) {
+            if (tid == 0) record_device_error(a.err, RADON_ERR_TIMEOUT);
+            return;
+        }
+        for (int vl = 0; vl < nv; ++vl) {
+            const ViewF vf = view_c[st * kBwdPViews + vl];
+            const int dlo = dlo_c[st * kBwdPViews + vl];
+            const unsigned char* yv = ybuf + (size_t)vl * yview;
+            if constexpr (KW == 0) {
+                // interpolating backprojector: the sinogram linearly interpolated at the pixel's detector
+                // coordinate t (IEEE division: the weights need t to ~1e-5 bins), weighted by the ray
+                // density |grad t|; both taps lie in the copied window by construction of its bounds
+                const int lo = max(dlo, 0), hi = min(a.D - 1, dlo + a.wd - 1);
+#pragma unroll
+                for (int x = 0; x < PX; ++x) {
+                    const float gy = gy0 + (float)x;
+                    const float den = fmaf(vf.bx, gx, fmaf(vf.by, gy, vf.b0));
+                    const float t = fmaf(vf.ax, gx, fmaf(vf.ay, gy, vf.a0)) / den;
+                    const float ga = fmaf(-t, vf.bx, vf.ax), gb = fmaf(-t, vf.by, vf.ay);
+                    const float w = sqrtf(fmaf(ga, ga, gb * gb)) / fabsf(den);
+                    const float fl = floorf(t);
+                    const int k = (int)fl;
+                    const float f = t - fl;
+                    const f32x2 w0 = f2_pack(w * (1.0f - f), w * (1.0f - f)), w1 = f2_pack(w * f, w * f);
+                    const bool in0 = k >= lo && k <= hi, in1 = k + 1 >= lo && k + 1 <= hi;
+                    const ulonglong2* y0 = reinterpret_cast<const ulonglong2*>(yv + (long long)(k - dlo) * PITCH);
+                    const ulonglong2* y1 = reinterpret_cast<const ulonglong2*>(yv + (long long)(k + 1 - dlo) * PITCH);
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) {
+                        if (in0) {
+                            const ulonglong2 y4 = y0[q];
+                            acc[x][2 * q + 0] = f2_fma(w0, y4.x, acc[x][2 * q + 0]);
+                            acc[x][2 * q + 1] = f2_fma(w0, y4.y, acc[x][2 * q + 1]);
+                        }
+                        if (in1) {
+                            const ulonglong2 y4 = y1[q];
+                            acc[x][2 * q + 0] = f2_fma(w1, y4.x, acc[x][2 * q + 0]);
+                            acc[x][2 * q + 1] = f2_fma(w1, y4.y, acc[x][2 * q + 1]);
+                        }
+                    }
+                }
+            } else {
+                const float r = r_c[st * kBwdPViews + vl];
+                // the union of the pixels' candidate ranges [t - r, t + r] (approximate divide: the
+                // windows carry margins far above its error); a candidate outside a pixel's own range
+                // has zero weight there.  Candidates outside the detector are sentinel rays over
+                // zero-filled rows, so only the copied window bounds the loop (the producer checked
+                // that it holds them all)
+                int la = 0x7fffffff, lb = -0x7fffffff;
+#pragma unroll
+                for (int x = 0; x < PX; ++x) {
+                    const float gy = gy0 + (float)x;
+                    const float t = __fdividef(fmaf(vf.ax, gx, fmaf(vf.ay, gy, vf.a0)),
+                                               fmaf(vf.bx, gx, fmaf(vf.by, gy, vf.b0)));
+                    la = min(la, (int)ceilf(t - r));
+                    lb = max(lb, (int)floorf(t + r));
+                }
+                la = max(la - dlo, 0);
+                lb = min(lb - dlo, a.wd - 1);
+                const unsigned char* rv = rst + (size_t)vl * m.rst_view;
+                for (int dl = la; dl <= lb; ++dl) {
+                    const ulonglong2* rec = reinterpret_cast<const ulonglong2*>(rv + (size_t)dl * 32);
+                    const ulonglong2 A = rec[0];
+                    const float4 Bc = *reinterpret_cast<const float4*>(rec + 1);
+                    f32x2 w2[PX];
+#pragma unroll
+                    for (int x = 0; x < PX; ++x) {
+                        float pxx, pyx;
+                        f2_unpack(p2[x], &pxx, &pyx);
+                        const float w = bwdp_weight<KW>(p2[x], pxx, pyx, A.x, A.y, Bc.x, Bc.y, Bc.z);
+                        w2[x] = f2_pack(w, w);
+                    }
+                    const ulonglong2* y = reinterpret_cast<const ulonglong2*>(yv + (size_t)dl * PITCH);
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) {
+                        const ulonglong2 y4 = y[q];
+#pragma unroll
+                        for (int x = 0; x < PX; ++x) {
+                            acc[x][2 * q + 0] = f2_fma(w2[x], y4.x, acc[x][2 * q + 0]);
+                            acc[x][2 * q + 1] = f2_fma(w2[x], y4.y, acc[x][2 * q + 1]);
+                        }
+                    }
+                }
+            }
+        }
+        mbar_arrive(&empty[st]);
+    }
+    const long long npix = (long long)a.n * a.n;
+    const int b0 = blockIdx.y * BG;
+#pragma unroll
+    for (int x = 0; x < PX; ++x) {
+        if (!inside[x]) continue;
+        float accf[BG];
+#pragma unroll
+        for (int b = 0; b < BG / 2; ++b) f2_unpack(acc[x][b], &accf[2 * b], &accf[2 * b + 1]);
+        const long long p = (long long)(ti + pi0 + x) * a.n + (tj + pj);
+#pragma unroll
+        for (int b = 0; b < BG; ++b)
+            if (b0 + b < a.B)
+                epilogue_store_rt(a.ep, a.out_dtype, a.img, a.h * accf[b], (long long)(b0 + b) * npix + p);
+    }
+}
+
+// Ring depth of a packed-adjoint CTA: the deepest ring (up to kBwdPMaxStages) that keeps the launch
+// bounds' CTAs resident per SM (228 KB of shared memory, 1 KB reserved per CTA), else two stages;
+// returns the dynamic shared memory.
+template <typename T, int BG>
+inline size_t bwdp_plan(int wd, bool rays, int* stages) {
+    const size_t budget = (size_t)228 * 1024 / BwdPShape<BG>::kCtasPerSm - 1024;
+    int S = kBwdPMaxStages;
+    while (S > 2 && bwdp_smem<T, BG>(wd, S, rays).total > budget) --S;
+    *stages = S;
+    return bwdp_smem<T, BG>(wd, S, rays).total;
+}
+
+template <typename T, int BG, int KW>
+cudaError_t bwdp_launch(const CUtensorMap& map, const CUtensorMap& rmap, const BwdPArgs& a, dim3 grid, size_t smem,
+                        cudaStream_t s) {
+    auto kern = backward_packed_kernel<T, BG, KW>;
+    static size_t attr_bytes = 0;
+    if (smem > attr_bytes) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_bytes = smem;
+    }
+    kern<<<grid, BwdPShape<BG>::kThreads, smem, s>>>(map, rmap, a);
+    return cudaGetLastError();
+}
+
+// Host launcher for storage type T and BG images per CTA (backward_packed_{f32,f16,bf16}.cu
+// instantiate it): `packed` holds pack_sino's rows for this batch; kw = 0 runs the interpolating
+// backprojector, 3 or 6 the exact adjoint with that many samples per candidate window.
+template <typename T, int BG>
+radon_status launch_backward_packed_t(const radon_geometry* g, const void* packed, void* img, radon_dtype dt,
+                                      int batch, int kw, const Epilogue& ep, cudaStream_t s, std::string* why,
+                                      const CUtensorMap& rmap, uint32_t spin_limit, int* err) {
+    using L = BwdPLayout<T, BG>;
+    const int wd = g->bwd_window + 2;
+    if (wd > 256) {
+        *why = "detector window wider than a TMA box";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    int stages = 2;
+    const size_t smem = bwdp_plan<T, BG>(wd, kw > 0, &stages);
+    if (smem > 227 * 1024) {
+        *why = "shared memory budget exceeded";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    const int groups = (batch + BG - 1) / BG;
+    const uint64_t row = (uint64_t)L::kRowElems * sizeof(T);
+    const uint64_t dims[4] = {(uint64_t)L::kRowElems, (uint64_t)g->D, (uint64_t)g->V, (uint64_t)groups};
+    const uint64_t strides[3] = {row, row * (uint64_t)g->D, row * (uint64_t)g->D * (uint64_t)g->V};
+    const uint32_t box[4] = {(uint32_t)L::kRowElems, (uint32_t)wd, 1, 1};
+    CUtensorMap map;
+    const int rc = encode_tiled(&map, tma_dtype(dt), 4, const_cast<void*>(packed), dims, strides, box,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
+    if (rc != 0) {
+        *why = "cuTensorMapEncodeTiled rejected the packed-sinogram descriptor (CUresult " + std::to_string(rc) + ")";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    BwdPArgs a;
+    a.views = g->d_view;
+    a.img = img;
+    a.n = g->n;
+    a.V = g->V;
+    a.D = g->D;
+    a.B = batch;
+    a.h = kw == 0 ? 1.0f : (float)g->h;   // the interpolating backprojector's sum carries no step factor
+    a.ih2 = (float)(1.0 / (g->h * g->h));
+    a.wd = wd;
+    a.stages = stages;
+    a.tiles_x = (g->n + kBwdTile - 1) / kBwdTile;
+    a.out_dtype = dt;
+    a.err = err;
+    a.spin_limit = spin_limit;
+    a.ep = ep;
+    const dim3 grid((unsigned)(a.tiles_x * a.tiles_x), (unsigned)groups);
+    const cudaError_t e = kw == 0   ? bwdp_launch<T, BG, 0>(map, rmap, a, grid, smem, s)
+                          : kw == 3 ? bwdp_launch<T, BG, 3>(map, rmap, a, grid, smem, s)
+                                    : bwdp_launch<T, BG, 6>(map, rmap, a, grid, smem, s);
+    if (e != cudaSuccess) {
+        *why = std::string("packed adjoint launch: ") + cudaGetErrorString(e);
+        return RADON_ERR_CUDA;
+    }
+    return RADON_OK;
+}
+
+}  // namespace radon

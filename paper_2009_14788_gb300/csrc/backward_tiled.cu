@@ -139,131 +139,3 @@ radon_status launch_backward_tiled(const radon_geometry* g, const void* sino, vo
 }
 
 }  // namespace radon
-
-namespace radon {
-
-namespace {
-
-template <int BG, int KW>
-cudaError_t launch_packed_bg(const CUtensorMap& map, const CUtensorMap& rmap, const BwdTiledArgs& a, dim3 grid,
-                             size_t smem, cudaStream_t s) {
-    auto kern = backward_packed_kernel<BG, KW>;
-    static size_t attr_bytes = 0;
-    if (smem > attr_bytes) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_bytes = smem;
-    }
-    kern<<<grid, kBwdPackedThreads, smem, s>>>(map, rmap, a);
-    return cudaGetLastError();
-}
-
-}  // namespace
-
-int backward_packed_images_per_cta(const radon_geometry* g, int batch, const radon_launch_config* cfg) {
-    if (cfg != nullptr && cfg->images_per_cta != 0) return cfg->images_per_cta;
-    if (batch <= 8) return 8;
-    if (batch <= 16) return 16;
-    // A 32-image CTA costs ~1.56x a 16-image one (each weight serves twice the images; 96 registers,
-    // 2 CTAs/SM): take it when its groups cost less and its staging fits one CTA's shared memory.
-    const long long g32 = (batch + 31) / 32, g16 = (batch + 15) / 16;
-    if (25 * g32 < 16 * g16 && bwd_packed_smem_bytes(32, g->bwd_window + 2) <= 227 * 1024) return 32;
-    return 16;
-}
-
-radon_status launch_backward_packed(const radon_geometry* g, const void* packed, void* img, radon_dtype dt, int batch,
-                                    int bg, const Epilogue& ep, cudaStream_t s, std::string* why, bool interpolating) {
-    if (bg != 8 && bg != 16 && bg != 32) {
-        *why = "images_per_cta must be 8, 16 or 32 for the packed adjoint";
-        return RADON_ERR_UNSUPPORTED;
-    }
-    const double span = 2.0 * std::sqrt(2.0) / g->h + 2e-4;
-    const int kw_needed = (int)std::floor(span) + 1;
-    if (!interpolating && kw_needed > 6) {
-        *why = "sampling step too small for the tiled adjoint";
-        return RADON_ERR_UNSUPPORTED;
-    }
-    // KW = 0 selects the interpolating backprojector (two taps per view, no rays)
-    const int kw = interpolating ? 0 : (kw_needed <= 3 ? 3 : 6);
-    const int wd = g->bwd_window + 2;
-    if (wd > 256) {
-        *why = "detector window wider than a TMA box";
-        return RADON_ERR_UNSUPPORTED;
-    }
-    const size_t smem = bwd_packed_smem_bytes(bg, wd);
-    if (smem > 227 * 1024) {
-        *why = "shared memory budget exceeded";
-        return RADON_ERR_UNSUPPORTED;
-    }
-    const int groups = (batch + bg - 1) / bg;
-    const uint64_t dims[5] = {4, (uint64_t)g->D, (uint64_t)(bg / 4), (uint64_t)g->V, (uint64_t)groups};
-    const uint64_t strides[4] = {16, (uint64_t)g->D * 16, (uint64_t)g->D * 16 * (bg / 4),
-                                 (uint64_t)g->D * 16 * (bg / 4) * g->V};
-    const uint32_t box[5] = {4, (uint32_t)wd, (uint32_t)(bg / 4), 1, 1};
-    CUtensorMap map;
-    const int rc = encode_tiled(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void*>(packed), dims, strides, box,
-                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
-    if (rc != 0) {
-        *why = "cuTensorMapEncodeTiled rejected the packed-sinogram descriptor (CUresult " + std::to_string(rc) + ")";
-        return RADON_ERR_UNSUPPORTED;
-    }
-    // the ray table as rows of 8 words (bit copies), one row per ray, rays of view v at v * D
-    CUtensorMap rmap;
-    const uint64_t rdims[2] = {8, (uint64_t)g->V * g->D};
-    const uint64_t rstrides[1] = {32};
-    const uint32_t rbox[2] = {8, (uint32_t)wd};
-    const int rc2 = encode_tiled(&rmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, g->d_ray, rdims, rstrides, rbox,
-                                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
-    if (rc2 != 0) {
-        *why = "cuTensorMapEncodeTiled rejected the ray-table descriptor (CUresult " + std::to_string(rc2) + ")";
-        return RADON_ERR_UNSUPPORTED;
-    }
-    BwdTiledArgs a;
-    a.rays = g->d_ray;
-    a.nks = g->d_nk;
-    a.views = g->d_view;
-    a.img = img;
-    a.n = g->n;
-    a.V = g->V;
-    a.D = g->D;
-    a.B = batch;
-    a.h = (float)g->h;
-    a.ep = ep;
-    a.ih2 = (float)(1.0 / (g->h * g->h));
-    a.wd = wd;
-    a.wdb = wd;
-    a.align = 1;
-    a.stage_stride = 0;
-    a.tiles_x = (g->n + kBwdTile - 1) / kBwdTile;
-    a.err = device_error_word();
-    if (a.err == nullptr) {
-        *why = "device error word unavailable";
-        return RADON_ERR_CUDA;
-    }
-    a.stall_test = 0;
-    a.spin_limit = kSpinLimit;
-    a.tma_rank = 5;
-    a.out_dtype = dt;
-    dim3 grid((unsigned)(a.tiles_x * a.tiles_x), (unsigned)groups);
-    cudaError_t e;
-    if (interpolating) a.h = 1.0f;   // the interpolating backprojector's sum carries no step factor
-    if (bg == 32)
-        e = kw == 0 ? launch_packed_bg<32, 0>(map, rmap, a, grid, smem, s)
-                    : kw == 3 ? launch_packed_bg<32, 3>(map, rmap, a, grid, smem, s)
-                              : launch_packed_bg<32, 6>(map, rmap, a, grid, smem, s);
-    else if (bg == 16)
-        e = kw == 0 ? launch_packed_bg<16, 0>(map, rmap, a, grid, smem, s)
-                    : kw == 3 ? launch_packed_bg<16, 3>(map, rmap, a, grid, smem, s)
-                              : launch_packed_bg<16, 6>(map, rmap, a, grid, smem, s);
-    else
-        e = kw == 0 ? launch_packed_bg<8, 0>(map, rmap, a, grid, smem, s)
-                    : kw == 3 ? launch_packed_bg<8, 3>(map, rmap, a, grid, smem, s)
-                              : launch_packed_bg<8, 6>(map, rmap, a, grid, smem, s);
-    if (e != cudaSuccess) {
-        *why = std::string("packed adjoint launch: ") + cudaGetErrorString(e);
-        return RADON_ERR_CUDA;
-    }
-    return RADON_OK;
-}
-
-}  // namespace radon

@@ -155,36 +155,7 @@ __device__ __forceinline__ float4 bwd_ray_pos_rec(const RayT ray, bool valid, in
     return A;
 }
 
-// Bilinear weight of the pixel at p2 = (px, py) (tile-local) on the ray with tile-relative
-// position a0 = (rx, ry) and step d2 = (dx, dy): the sum over the KW samples whose index window
-// [ka, ka + KW) holds every sample within the pixel's 2 x 2 support square.  Steps have length h,
-// so step / |step|^2 = step * ih2.  The x and y halves run as f32x2 pairs.
-template <int KW>
-__device__ __forceinline__ float bwd_ray_weight_pair(f32x2 p2, f32x2 a0, f32x2 d2, f32x2 ih2_2, float ih2) {
-    const f32x2 e2 = f2_sub(a0, p2);   // A - p = -(p - A)
-    const f32x2 b2 = f2_mul(d2, ih2_2);
-    float ex, ey, bx, by, dx, dy;
-    f2_unpack(e2, &ex, &ey);
-    f2_unpack(b2, &bx, &by);
-    f2_unpack(d2, &dx, &dy);
-    const float kap = -fmaf(ex, bx, ey * by);
-    const float kr = fmaf(fabsf(dx) + fabsf(dy), ih2, 1e-4f);
-    const float ka = ceilf(kap - kr);
-    f32x2 r2 = f2_fma(f2_pack(ka, ka), d2, e2);   // ka * step - (p - A)
-    float w = 0.0f;
-#pragma unroll
-    for (int k = 0; k < KW; ++k) {
-        float rx, ry;
-        f2_unpack(r2, &rx, &ry);
-        const float wx = fmaxf(0.0f, 1.0f - fabsf(rx));
-        const float wy = fmaxf(0.0f, 1.0f - fabsf(ry));
-        w = fmaf(wx, wy, w);
-        if (k + 1 < KW) r2 = f2_add(r2, d2);
-    }
-    return w;
-}
-
-// The ray-dependent part of bwd_ray_weight_pair's window start, hoisted out of the per-pixel work:
+// The ray-dependent part of a candidate window's start, hoisted out of the per-pixel work:
 // kap - kr = (p - A).b - kr = p.b + C with b = step / |step|^2 and C = -A.b - kr (a sentinel ray
 // has step zero, so C = -1e-4 and every weight stays zero).
 __device__ __forceinline__ float bwd_ray_window_c(const float4 A, float ih2) {
@@ -193,8 +164,9 @@ __device__ __forceinline__ float bwd_ray_window_c(const float4 A, float ih2) {
     return -fmaf(A.x, bx, A.y * by) - kr;
 }
 
-// bwd_ray_weight_pair with the window constant C of bwd_ray_window_c: the same samples and tent
-// products (the window start may round differently, which only moves a zero-weight sample).
+// Bilinear weight of the pixel at p2 (tile-local) on the ray with tile-relative reference sample a0
+// and step d2: the sum over the KW samples from the window start ceil(p.b + C) (C from
+// bwd_ray_window_c), each a product of two tents.  The x and y halves run as f32x2 pairs.
 template <int KW>
 __device__ __forceinline__ float bwd_ray_weight_c(f32x2 p2, float px, float py, f32x2 a0, f32x2 d2, f32x2 ih2_2,
                                                   float C) {
@@ -407,231 +379,5 @@ __global__ void __launch_bounds__(kBwdThreads, 2) backward_tiled_kernel(const __
     }
 }
 
-
-// ---------------------------------------------------------------------------------------------
-// Packed variant: the sinogram batch was packed once into FP32 image quads laid out
-// [group][view][quad][det][4] (pack.cu), so one 5-D TMA box per view lands the tile's detector
-// window directly in the gather's [quad][det] layout, and one 2-D box copies the matching rows of the
-// ray table.  Warp-specialised over a ring of kBwdPackedStages chunks (kBwdPackedViews views each):
-// a producer warp computes each view's window and issues both copies, up to the ring's depth ahead;
-// the 256 consumer threads (one pixel each) re-base the landed rays on the tile, one ray per thread,
-// meet at a named barrier, and gather.  No global load sits on the consumers' path.
-constexpr int kBwdPackedViews = 4;
-constexpr int kBwdPackedStages = 4;
-constexpr int kBwdPackedThreads = kBwdThreads + 32;
-static_assert(sizeof(ViewF) == 32, "view maps are staged as 32-byte records");
-
-// Per-view slice of a staged window: padded so every TMA destination starts on 128 bytes.
-__host__ __device__ inline size_t bwd_packed_view_bytes(int bg, int wd) { return ((size_t)wd * bg * 4 + 127) / 128 * 128; }
-__host__ __device__ inline size_t bwd_packed_ray_bytes(int wd) { return ((size_t)wd * 32 + 127) / 128 * 128; }
-__host__ __device__ inline size_t bwd_packed_rp_bytes(int wd) { return ((size_t)kBwdPackedViews * wd * 16 + 127) / 128 * 128; }
-constexpr size_t kBwdPackedHeader = 1024;   // barriers, flags, windows and view maps of the ring
-
-__host__ __device__ inline size_t bwd_packed_smem_bytes(int bg, int wd) {
-    const size_t ystage = (size_t)kBwdPackedViews * bwd_packed_view_bytes(bg, wd);   // per stage
-    const size_t rstage = (size_t)kBwdPackedViews * bwd_packed_ray_bytes(wd);        // per stage
-    return 128 + kBwdPackedHeader + kBwdPackedStages * (ystage + rstage) + 2 * bwd_packed_rp_bytes(wd);
-}
-
-template <int BG, int KW>
-__global__ void __launch_bounds__(kBwdPackedThreads, BG >= 32 ? 2 : 3) backward_packed_kernel(const __grid_constant__ CUtensorMap map,
-                                                                              const __grid_constant__ CUtensorMap rmap,
-                                                                              const BwdTiledArgs a) {
-    constexpr int NQ = BG / 4;
-    constexpr int S = kBwdPackedStages;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
-    uint64_t* tma_bar = reinterpret_cast<uint64_t*>(smem);        // [S]: a stage's copies landed
-    uint64_t* empty = reinterpret_cast<uint64_t*>(smem + 64);     // [S]: consumers released a stage
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 128);
-    int* dlo_c = reinterpret_cast<int*>(smem + 192);              // [S][views]
-    float* r_c = reinterpret_cast<float*>(smem + 256);            // [S][views]
-    ViewF* view_c = reinterpret_cast<ViewF*>(smem + 512);         // [S][views]
-    static_assert(S * kBwdPackedViews * 4 <= 64 && 512 + S * kBwdPackedViews * 32 <= kBwdPackedHeader,
-                  "ring header overflows its slots");
-    const size_t yv_bytes = bwd_packed_view_bytes(BG, a.wd);
-    const size_t ys_bytes = (size_t)kBwdPackedViews * yv_bytes;
-    const size_t rv_bytes = bwd_packed_ray_bytes(a.wd);
-    const size_t rs_bytes = (size_t)kBwdPackedViews * rv_bytes;
-    const size_t rp_bytes = bwd_packed_rp_bytes(a.wd);
-    unsigned char* ystage = smem + kBwdPackedHeader;
-    unsigned char* rstage = ystage + S * ys_bytes;
-    unsigned char* rpbuf = rstage + S * rs_bytes;
-
-    const int tid = threadIdx.x;
-    const int tile = blockIdx.x;
-    const int ti = (tile / a.tiles_x) * kBwdTile, tj = (tile - (tile / a.tiles_x) * a.tiles_x) * kBwdTile;
-    const int nchunks = (a.V + kBwdPackedViews - 1) / kBwdPackedViews;
-
-    if (tid < S) {
-        mbar_init(&tma_bar[tid], 1);
-        mbar_init(&empty[tid], kBwdThreads);
-    }
-    if (tid == 0) *abort_flag = 0;
-    fence_mbar_init();
-    __syncthreads();
-
-    if (tid >= kBwdThreads) {
-        // ------------------------------------------------------------------ producer warp
-        const int lane = tid & 31;
-        int c = 0;
-        for (; c < nchunks; ++c) {
-            const int st = c % S;
-            bool ok = true;
-            if (c >= S && lane == 0) ok = mbar_wait_bounded(&empty[st], (uint32_t)((c / S - 1) & 1), a.spin_limit);
-            if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
-            const int v0 = c * kBwdPackedViews;
-            const int nv = min(kBwdPackedViews, a.V - v0);
-            if (lane < nv) {
-                const ViewF vf = a.views[v0 + lane];
-                int dlo;
-                float r;
-                bwd_view_window(vf, ti, tj, a.n, &dlo, &r);
-                dlo_c[st * kBwdPackedViews + lane] = dlo;
-                r_c[st * kBwdPackedViews + lane] = r;
-                view_c[st * kBwdPackedViews + lane] = vf;
-            }
-            __syncwarp();
-            if (lane == 0) {
-                fence_proxy_async_shared();
-                mbar_arrive_expect_tx(&tma_bar[st], (uint32_t)(nv * a.wd * (BG * 4 + (KW > 0 ? 32 : 0))));
-                for (int vl = 0; vl < nv; ++vl) {
-                    const int dlo = dlo_c[st * kBwdPackedViews + vl];
-                    tma_load_5d(ystage + st * ys_bytes + (size_t)vl * yv_bytes, &map, &tma_bar[st], 0, dlo, 0, v0 + vl,
-                                blockIdx.y);
-                    if (KW > 0)   // the interpolating backprojector needs no rays
-                        tma_load_2d(rstage + st * rs_bytes + (size_t)vl * rv_bytes, &rmap, &tma_bar[st], 0,
-                                    (v0 + vl) * a.D + dlo);
-                }
-            }
-            __syncwarp();
-        }
-        if (c < nchunks && lane == 0) {
-            // The consumers stopped releasing stages: record it, let the copies still in flight land
-            // (bounded), then complete chunk c's phase without data so any consumer still waiting
-            // sees the abort.
-            record_device_error(a.err, RADON_ERR_TIMEOUT);
-            *abort_flag = 1;
-            for (int cc = max(0, c - S + 1); cc < c; ++cc)
-                mbar_wait_bounded(&tma_bar[cc % S], (uint32_t)((cc / S) & 1), a.spin_limit);
-            mbar_arrive(&tma_bar[c % S]);
-        }
-        return;
-    }
-
-    // ---------------------------------------------------------------------- consumer warps
-    // each warp takes a 4 x 8 block of the tile: its pixels' detector footprints overlap more than
-    // those of a 2 x 16 strip, so the gather's shared loads touch fewer distinct addresses.  A
-    // 16-byte shared load is served eight lanes at a time, so each group of eight lanes is a 4 x 2
-    // sub-block (narrower on the detector than a row of 8: 2.6 % faster on the fan workload)
-    const int warp = tid >> 5, lane = tid & 31;
-    const int pi = (warp >> 1) * 4 + ((lane & 7) >> 1), pj = (warp & 1) * 8 + (lane >> 3) * 2 + (lane & 1);
-    const f32x2 p2 = f2_pack((float)pj, (float)pi);
-    const f32x2 ih2_2 = f2_pack(a.ih2, a.ih2);
-    const float gx = (float)(tj + pj), gy = (float)(ti + pi);
-    const bool inside = (ti + pi) < a.n && (tj + pj) < a.n;
-    f32x2 acc[BG / 2];   // image pairs (2b, 2b + 1)
-#pragma unroll
-    for (int b = 0; b < BG / 2; ++b) acc[b] = 0ull;
-    for (int c = 0; c < nchunks; ++c) {
-        const int st = c % S;
-        const int v0 = c * kBwdPackedViews;
-        const int nv = min(kBwdPackedViews, a.V - v0);
-        bool bad = !mbar_wait_bounded(&tma_bar[st], (uint32_t)((c / S) & 1), a.spin_limit);
-        bad = bad || *abort_flag != 0;
-        float4* rp = reinterpret_cast<float4*>(rpbuf + (c & 1) * rp_bytes);
-        if (KW > 0 && !bad) {
-            // re-base the landed rays on this tile: one ray per thread
-            for (int e = tid; e < nv * a.wd; e += kBwdThreads) {
-                const int vl = e / a.wd, dl = e - (e / a.wd) * a.wd;
-                const int d = dlo_c[st * kBwdPackedViews + vl] + dl;
-                const RayT ray = *reinterpret_cast<const RayT*>(rstage + st * rs_bytes + (size_t)vl * rv_bytes +
-                                                                (size_t)dl * 32);
-                rp[e] = bwd_ray_pos_rec(ray, d >= 0 && d < a.D, ti, tj, a.ih2);
-            }
-        }
-        // all consumers: parameters written (the buffer alternates, so the previous chunk's readers
-        // have all passed this barrier before it is overwritten) -- and one shared abort decision
-        if (named_barrier_or(1, kBwdThreads, bad)) {
-            if (tid == 0) record_device_error(a.err, RADON_ERR_TIMEOUT);
-            return;
-        }
-        if constexpr (KW == 0) {
-            // interpolating backprojector: the sinogram linearly interpolated at the pixel's detector
-            // coordinate t (IEEE division: the weights need t to ~1e-5 bins), weighted by the ray
-            // density |grad t|; both taps lie in the staged window by construction of its bounds
-            for (int vl = 0; vl < nv; ++vl) {
-                const ViewF vf = view_c[st * kBwdPackedViews + vl];
-                const int dlo = dlo_c[st * kBwdPackedViews + vl];
-                const float den = fmaf(vf.bx, gx, fmaf(vf.by, gy, vf.b0));
-                const float t = fmaf(vf.ax, gx, fmaf(vf.ay, gy, vf.a0)) / den;
-                const float ga = fmaf(-t, vf.bx, vf.ax), gb = fmaf(-t, vf.by, vf.ay);
-                const float w = sqrtf(fmaf(ga, ga, gb * gb)) / fabsf(den);
-                const float fl = floorf(t);
-                const int k = (int)fl;
-                const float f = t - fl;
-                const int lo = max(dlo, 0), hi = min(a.D - 1, dlo + a.wd - 1);
-                if (inside && ((k < dlo && k >= 0) || (k + 1 > dlo + a.wd - 1 && k + 1 <= a.D - 1)))
-                    record_device_error(a.err, RADON_ERR_DEVICE_BOUNDS);
-                const ulonglong2* yq = reinterpret_cast<const ulonglong2*>(ystage + st * ys_bytes + (size_t)vl * yv_bytes);
-                const f32x2 w0 = f2_pack(w * (1.0f - f), w * (1.0f - f)), w1 = f2_pack(w * f, w * f);
-                const bool in0 = k >= lo && k <= hi, in1 = k + 1 >= lo && k + 1 <= hi;
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) {
-                    if (in0) {
-                        const ulonglong2 y4 = yq[q * a.wd + (k - dlo)];
-                        acc[2 * q + 0] = f2_fma(w0, y4.x, acc[2 * q + 0]);
-                        acc[2 * q + 1] = f2_fma(w0, y4.y, acc[2 * q + 1]);
-                    }
-                    if (in1) {
-                        const ulonglong2 y4 = yq[q * a.wd + (k + 1 - dlo)];
-                        acc[2 * q + 0] = f2_fma(w1, y4.x, acc[2 * q + 0]);
-                        acc[2 * q + 1] = f2_fma(w1, y4.y, acc[2 * q + 1]);
-                    }
-                }
-            }
-        } else {
-        for (int vl = 0; vl < nv; ++vl) {
-            const ViewF vf = view_c[st * kBwdPackedViews + vl];
-            const int dlo = dlo_c[st * kBwdPackedViews + vl];
-            const float r = r_c[st * kBwdPackedViews + vl];
-            // approximate divide: the window [t - r, t + r] carries margins far above its error
-            const float t = __fdividef(fmaf(vf.ax, gx, fmaf(vf.ay, gy, vf.a0)), fmaf(vf.bx, gx, fmaf(vf.by, gy, vf.b0)));
-            const float flo = ceilf(t - r), fhi = floorf(t + r);
-            const int da = (int)fmaxf(flo, (float)max(dlo, 0));
-            const int db = (int)fminf(fhi, (float)min(a.D - 1, dlo + a.wd - 1));
-            if (inside && ((flo < (float)dlo && flo >= 0.0f) || (fhi > (float)(dlo + a.wd - 1) && fhi <= (float)(a.D - 1))))
-                record_device_error(a.err, RADON_ERR_DEVICE_BOUNDS);
-            const ulonglong2* rpv = reinterpret_cast<const ulonglong2*>(rp) + vl * a.wd;
-            const ulonglong2* yq = reinterpret_cast<const ulonglong2*>(ystage + st * ys_bytes + (size_t)vl * yv_bytes);
-            for (int d = da; d <= db; ++d) {
-                const int dl = d - dlo;
-                const ulonglong2 rr = rpv[dl];
-                const float w = bwd_ray_weight_pair<KW>(p2, rr.x, rr.y, ih2_2, a.ih2);
-                const f32x2 w2 = f2_pack(w, w);
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) {
-                    const ulonglong2 y4 = yq[q * a.wd + dl];
-                    acc[2 * q + 0] = f2_fma(w2, y4.x, acc[2 * q + 0]);
-                    acc[2 * q + 1] = f2_fma(w2, y4.y, acc[2 * q + 1]);
-                }
-            }
-        }
-        }
-        mbar_arrive(&empty[st]);
-    }
-    if (inside) {
-        float accf[BG];
-#pragma unroll
-        for (int b = 0; b < BG / 2; ++b) f2_unpack(acc[b], &accf[2 * b], &accf[2 * b + 1]);
-        const long long npix = (long long)a.n * a.n;
-        const long long p = (long long)(ti + pi) * a.n + (tj + pj);
-        const int b0 = blockIdx.y * BG;
-#pragma unroll
-        for (int b = 0; b < BG; ++b)
-            if (b0 + b < a.B)
-                epilogue_store_rt(a.ep, a.out_dtype, a.img, a.h * accf[b], (long long)(b0 + b) * npix + p);
-    }
-}
 
 }  // namespace radon

@@ -108,8 +108,8 @@ extern "C" RADON_API radon_status radon_backproject_interpolating_ws(const radon
     if (batch == 0) return RADON_OK;
     st = check_device(g);
     if (st != RADON_OK) return st;
-    const int bg = backward_packed_images_per_cta(g, batch, nullptr);
-    if (workspace != nullptr && workspace_bytes >= packed_sino_bytes(g->V, g->D, batch, bg)) {
+    const int bg = backward_packed_images_per_cta(g, batch, dtype, nullptr);
+    if (workspace != nullptr && workspace_bytes >= packed_sino_bytes(g->V, g->D, batch, bg, dtype)) {
         cudaStream_t s = (cudaStream_t)stream;
         cudaError_t e = launch_pack_sino(sino, workspace, g->V, g->D, batch, bg, dtype, s);
         if (e != cudaSuccess) return cuda_fail(e, "sinogram pack launch");

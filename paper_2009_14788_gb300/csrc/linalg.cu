@@ -201,7 +201,7 @@ PowerLayout power_layout(const radon_geometry* g) {
     L.fws = align_up(L.t + sino, 256);
     L.fws_bytes = packed_image_bytes(g->n, 1, RADON_F32);
     L.bws = align_up(L.fws + L.fws_bytes, 256);
-    L.bws_bytes = packed_sino_bytes(g->V, g->D, 1, backward_packed_images_per_cta(g, 1, nullptr));
+    L.bws_bytes = packed_sino_bytes(g->V, g->D, 1, backward_packed_images_per_cta(g, 1, RADON_F32, nullptr), RADON_F32);
     L.partial = align_up(L.bws + L.bws_bytes, 256);
     L.scal = align_up(L.partial + kDotBlocks * sizeof(double), 256);
     L.total = align_up(L.scal + 4 * sizeof(float), 256);
@@ -384,7 +384,7 @@ CgneLayout cgne_layout(const radon_geometry* g, int batch) {
     L.fws = align_up(L.p + img, 256);
     L.fws_bytes = packed_image_bytes(g->n, batch, RADON_F32);
     L.bws = align_up(L.fws + L.fws_bytes, 256);
-    L.bws_bytes = packed_sino_bytes(g->V, g->D, batch, backward_packed_images_per_cta(g, batch, nullptr));
+    L.bws_bytes = packed_sino_bytes(g->V, g->D, batch, backward_packed_images_per_cta(g, batch, RADON_F32, nullptr), RADON_F32);
     L.partial = align_up(L.bws + L.bws_bytes, 256);
     L.scal = align_up(L.partial + (size_t)batch * dot_blocks(batch) * sizeof(double), 256);
     L.total = align_up(L.scal + 5 * (size_t)batch * sizeof(float), 256);

@@ -71,53 +71,59 @@ __global__ void __launch_bounds__(256) pack_interleaved_kernel(const T* __restri
     }
 }
 
-// Sinogram batch -> FP32 image quads [group][view][quad][det][4] (group = bg images, quad = 4 of
-// them).  One thread per output quad; consecutive threads walk detectors (coalesced both ways).
+// Sinogram batch -> rows of bg images per detector, [group][view][det][row] in the storage type, row =
+// bg elements (16-bit) or bg + 4 (FP32: four padding words, never read, keep the row pitch an odd
+// number of 16-byte units).  One thread per row; consecutive threads walk detectors, so the reads of
+// each image coalesce and the rows are written contiguously.
 template <typename T>
-__global__ void __launch_bounds__(256) pack_sino_kernel(const T* __restrict__ y, float4* __restrict__ out, int V,
-                                                        int D, int B, int bg, long long total) {
+__global__ void __launch_bounds__(256) pack_sino_kernel(const T* __restrict__ y, unsigned char* __restrict__ out,
+                                                        int V, int D, int B, int bg, int row_bytes, long long rows) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= total) return;
-    const int nq = bg / 4;
+    if (idx >= rows) return;
     const int d = (int)(idx % D);
-    long long rest = idx / D;
-    const int q = (int)(rest % nq);
-    rest /= nq;
+    const long long rest = idx / D;
     const int v = (int)(rest % V);
     const int g = (int)(rest / V);
-    float vals[4];
+    constexpr int PER = 16 / sizeof(T);   // elements per 16-byte store
+    uint4* dst = reinterpret_cast<uint4*>(out + idx * row_bytes);
+    for (int c = 0; c < bg / PER; ++c) {
+        T v16[PER];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int b = g * bg + 4 * q + u;
-        vals[u] = b < B ? to_f32(y[((long long)b * V + v) * D + d]) : 0.0f;
+        for (int u = 0; u < PER; ++u) {
+            const int b = g * bg + c * PER + u;
+            v16[u] = b < B ? y[((long long)b * V + v) * D + d] : from_f32<T>(0.0f);
+        }
+        dst[c] = pack16<T>(v16);
     }
-    out[idx] = make_float4(vals[0], vals[1], vals[2], vals[3]);
 }
 
 }  // namespace
 
-size_t packed_sino_bytes(int V, int D, int batch, int bg) {
+int packed_sino_row_bytes(int bg, radon_dtype dt) { return dt == RADON_F32 ? (bg + 4) * 4 : bg * 2; }
+
+size_t packed_sino_bytes(int V, int D, int batch, int bg, radon_dtype dt) {
     const long long groups = (batch + bg - 1) / bg;
-    return (size_t)(groups * (long long)V * D * bg * 4);
+    return (size_t)(groups * (long long)V * D * packed_sino_row_bytes(bg, dt));
 }
 
 cudaError_t launch_pack_sino(const void* sino, void* workspace, int V, int D, int batch, int bg, radon_dtype dt,
                              cudaStream_t s) {
     const long long groups = (batch + bg - 1) / bg;
-    const long long total = groups * (long long)V * (bg / 4) * D;
-    if (total == 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((total + 255) / 256);
-    float4* out = reinterpret_cast<float4*>(workspace);
+    const long long rows = groups * (long long)V * D;
+    if (rows == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((rows + 255) / 256);
+    unsigned char* out = reinterpret_cast<unsigned char*>(workspace);
+    const int rb = packed_sino_row_bytes(bg, dt);
     switch (dt) {
         case RADON_F16:
-            pack_sino_kernel<__half><<<blocks, 256, 0, s>>>((const __half*)sino, out, V, D, batch, bg, total);
+            pack_sino_kernel<__half><<<blocks, 256, 0, s>>>((const __half*)sino, out, V, D, batch, bg, rb, rows);
             break;
         case RADON_BF16:
             pack_sino_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>((const __nv_bfloat16*)sino, out, V, D, batch, bg,
-                                                                   total);
+                                                                   rb, rows);
             break;
         default:
-            pack_sino_kernel<float><<<blocks, 256, 0, s>>>((const float*)sino, out, V, D, batch, bg, total);
+            pack_sino_kernel<float><<<blocks, 256, 0, s>>>((const float*)sino, out, V, D, batch, bg, rb, rows);
             break;
     }
     return cudaGetLastError();

@@ -243,8 +243,8 @@ radon_status project(const radon_geometry* g, const void* in, void* out, radon_d
     if (!forward && algo != RADON_ALGO_PLAIN && ws != nullptr) {
         // Packed path: pack the sinogram batch once, then copy detector windows straight into
         // shared memory.  A too small workspace or a geometry the kernel refuses continues below.
-        const int bg = backward_packed_images_per_cta(g, batch, cfg);
-        if (ws_bytes >= packed_sino_bytes(g->V, g->D, batch, bg)) {
+        const int bg = backward_packed_images_per_cta(g, batch, dt, cfg);
+        if (ws_bytes >= packed_sino_bytes(g->V, g->D, batch, bg, dt)) {
             cudaError_t e = launch_pack_sino(in, ws, g->V, g->D, batch, bg, dt, s);
             if (e != cudaSuccess) return cuda_fail(e, "sinogram pack launch");
             std::string why;
@@ -436,7 +436,7 @@ size_t radon_backward_workspace_size(const radon_geometry* g, radon_dtype dtype,
     if (validate_geometry(g) != RADON_OK) return 0;
     if (dtype != RADON_F32 && dtype != RADON_F16 && dtype != RADON_BF16) return 0;
     if (batch < 0) return 0;
-    return packed_sino_bytes(g->V, g->D, batch, backward_packed_images_per_cta(g, batch, nullptr));
+    return packed_sino_bytes(g->V, g->D, batch, backward_packed_images_per_cta(g, batch, dtype, nullptr), dtype);
 }
 
 radon_status radon_backward_ws(const radon_geometry* g, const void* sino, void* img, radon_dtype dtype, int batch,

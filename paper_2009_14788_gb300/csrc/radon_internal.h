@@ -141,12 +141,12 @@ radon_status launch_backward_single(const radon_geometry* g, const void* sino, v
 // pack.cu
 size_t packed_image_bytes(int n, int batch, radon_dtype dt);
 cudaError_t launch_pack_images(const void* img, void* workspace, int n, int batch, radon_dtype dt, cudaStream_t s);
-size_t packed_sino_bytes(int V, int D, int batch, int bg);
+size_t packed_sino_bytes(int V, int D, int batch, int bg, radon_dtype dt);
 cudaError_t launch_pack_sino(const void* sino, void* workspace, int V, int D, int batch, int bg, radon_dtype dt,
                              cudaStream_t s);
 
-// backward_tiled.cu: the packed-sinogram adjoint (the workspace already holds pack_sino's output)
-int backward_packed_images_per_cta(const radon_geometry* g, int batch, const radon_launch_config* cfg);
+// backward_packed.cu: the packed-sinogram adjoint (the workspace already holds pack_sino's output)
+int backward_packed_images_per_cta(const radon_geometry* g, int batch, radon_dtype dt, const radon_launch_config* cfg);
 radon_status launch_backward_packed(const radon_geometry* g, const void* packed, void* img, radon_dtype dt, int batch,
                                     int images_per_cta, const Epilogue& ep, cudaStream_t s, std::string* why,
                                     bool interpolating = false);

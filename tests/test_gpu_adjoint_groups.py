@@ -17,8 +17,9 @@ pytestmark = pytest.mark.gpu
 
 
 def _ws(og, batch):
-    """A workspace for groups of up to 32 images (the automatic one is sized for the default group)."""
-    return torch.empty((batch + 31) // 32 * 32 * og.sino_shape[0] * og.sino_shape[1] * 4, dtype=torch.uint8,
+    """A workspace for groups of 8, 16 or 32 images (the automatic one is sized for the default group):
+    FP32 rows of a group of bg images take bg + 4 words, at most 1.5 words per image slot."""
+    return torch.empty((batch + 31) // 32 * 32 * og.sino_shape[0] * og.sino_shape[1] * 6, dtype=torch.uint8,
                        device="cuda")
 
 
@@ -53,10 +54,13 @@ def test_fan_group_of_32_matches_16():
 @pytest.mark.parametrize("batch", [17, 32, 33, 64])
 def test_workspace_holds_the_chosen_groups(batch):
     """The workspace size follows the group the default picks: whole groups of 8, 16 or 32 images,
-    FP32 quads, every view and detector."""
+    every view and detector, rows of the storage type (16-bit rows hold the group's values as they
+    are; FP32 rows carry four padding words)."""
     g, og = make("fan_ragged")
-    need = int(L.radon_backward_workspace_size(g.handle, L.RADON_F16, batch))
-    per_image = og.sino_shape[0] * og.sino_shape[1] * 4
-    assert need % per_image == 0
-    slots = need // per_image
+    vd = og.sino_shape[0] * og.sino_shape[1]
+    need16 = int(L.radon_backward_workspace_size(g.handle, L.RADON_F16, batch))
+    assert need16 % (vd * 2) == 0
+    slots = need16 // (vd * 2)
     assert slots >= batch and any(slots % bg == 0 and slots - batch < bg for bg in (8, 16, 32))
+    need32 = int(L.radon_backward_workspace_size(g.handle, L.RADON_F32, batch))
+    assert any(need32 == -(-batch // bg) * vd * (bg + 4) * 4 for bg in (8, 16, 32))
