@@ -11,9 +11,11 @@
 //   * the 256 consumer threads (one pixel each), once a chunk has landed, convert 16-bit windows to
 //     FP32 rows of pitch (BG + 4) words in a double buffer (FP32 windows land in that layout
 //     directly), re-base each landed ray on the tile in place -- reference sample, step and the
-//     window constant C of its candidate samples -- meet at a named barrier and gather: for every
-//     candidate ray of the pixel, the KW sample weights once for all BG images, then BG FP32 FMAs
-//     issued as f32x2 pairs.
+//     window constant C of its candidate samples -- meet at a named barrier and gather: each thread
+//     owns two vertically neighbouring pixels (one for 32-image groups); for every candidate ray of
+//     either pixel, each pixel's KW sample weights once for all BG images, then one FP32 FMA per
+//     image and pixel from one row of loads.
+// Shared-memory addresses stay 32-bit (explicit ld/st.shared), and no index needs a division.
 // The row pitch of (BG + 4) words is an odd number of 16-byte units, so the 16-byte loads of eight
 // lanes that read eight consecutive detectors fall in eight different bank groups.
 #pragma once
@@ -23,7 +25,6 @@
 #include "backward_tiled.cuh"
 #include "dtype.cuh"
 #include "epilogue.cuh"
-#include "f32x2.cuh"
 #include "radon_internal.h"
 #include "tensor_map.h"
 #include "tma.cuh"
@@ -115,21 +116,36 @@ __device__ __forceinline__ void bwdp_rebase(const RayT ray, bool valid, int ti, 
     *Bc = make_float4(bx, by, -fmaf(A->x, bx, A->y * by) - kr, 0.0f);
 }
 
-// Bilinear weight of the pixel at p2 (tile-local) on one ray: the sum over its KW consecutive
-// samples from the window start of tent(dx) * tent(dy), tent(v) = max(0, 1 - |v|) evaluated as one
-// saturating add (1 - |v| <= 1, so clamping to [0, 1] only clamps at 0).
+// Shared-memory loads and stores at 32-bit shared addresses (the CTA's offsets stay 32-bit).
+__device__ __forceinline__ float4 lds4(uint32_t a) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint4 lds4u(uint32_t a) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts4(uint32_t a, float4 v) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+// Bilinear weight of the pixel at (px, py) (tile-local) on one ray with record A = (reference sample
+// relative to the tile origin, step) and Bc = (step / h^2, C): the sum over KW consecutive samples
+// from the window start ceil(p.b + C) of tent(dx) * tent(dy), tent(v) = max(0, 1 - |v|) evaluated
+// as one saturating add (1 - |v| <= 1, so clamping to [0, 1] only clamps at 0).  `s` is p.b + C.
 template <int KW>
-__device__ __forceinline__ float bwdp_weight(f32x2 p2, float px, float py, f32x2 a2, f32x2 d2, float bx, float by,
-                                             float C) {
-    const float ka = ceilf(fmaf(px, bx, fmaf(py, by, C)));
-    f32x2 r2 = f2_fma(f2_pack(ka, ka), d2, f2_sub(a2, p2));   // sample ka relative to the pixel
-    float w = 0.0f;
+__device__ __forceinline__ float bwdp_weight(float px, float py, float s, const float4 A) {
+    const float ka = ceilf(s);
+    float rx = fmaf(ka, A.z, A.x - px), ry = fmaf(ka, A.w, A.y - py);   // sample ka relative to the pixel
+    float w = __saturatef(1.0f - fabsf(rx)) * __saturatef(1.0f - fabsf(ry));
 #pragma unroll
-    for (int k = 0; k < KW; ++k) {
-        float rx, ry;
-        f2_unpack(r2, &rx, &ry);
+    for (int k = 1; k < KW; ++k) {
+        rx += A.z;
+        ry += A.w;
         w = fmaf(__saturatef(1.0f - fabsf(rx)), __saturatef(1.0f - fabsf(ry)), w);
-        if (k + 1 < KW) r2 = f2_add(r2, d2);
     }
     return w;
 }
@@ -256,57 +272,67 @@ __global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasP
     const int grp = lane >> 3, e8 = lane & 7;
     const int pi0 = PX == 2 ? (warp >> 1) * 8 + ((grp >> 1) * 2 + (e8 >> 2)) * 2 : (warp >> 1) * 4 + (e8 >> 1);
     const int pj = PX == 2 ? (warp & 1) * 8 + (grp & 1) * 4 + (e8 & 3) : (warp & 1) * 8 + grp * 2 + (e8 & 1);
-    const float px = (float)pj;
-    f32x2 p2[PX];
-    bool inside[PX];
-#pragma unroll
-    for (int x = 0; x < PX; ++x) {
-        p2[x] = f2_pack(px, (float)(pi0 + x));
-        inside[x] = (ti + pi0 + x) < a.n && (tj + pj) < a.n;
-    }
+    const float px = (float)pj, py0 = (float)pi0;
     const float gx = (float)(tj + pj), gy0 = (float)(ti + pi0);
-    f32x2 acc[PX][BG / 2];   // per pixel, image pairs (2b, 2b + 1)
+    float acc[PX][BG];
 #pragma unroll
     for (int x = 0; x < PX; ++x)
 #pragma unroll
-        for (int b = 0; b < BG / 2; ++b) acc[x][b] = 0ull;
+        for (int b = 0; b < BG; ++b) acc[x][b] = 0.0f;
+    constexpr int OCT = BG / 8;                 // 16-byte segments of a 16-bit window row
+    constexpr int LOG_OCT = OCT == 1 ? 0 : OCT == 2 ? 1 : 2;
+    const uint32_t ring_a = smem_u32(ring), yf_a = smem_u32(yf);
+    const uint32_t win_a = smem_u32(view_c);
+    const uint32_t yview = L::kConv ? (uint32_t)m.yf_view : (uint32_t)m.yst_view;
+    const uint32_t ystv = (uint32_t)m.yst_view, rstv = (uint32_t)m.rst_view;
     for (int c = 0; c < nchunks; ++c) {
         const int st = c % S;
         const int v0 = c * kBwdPViews;
         const int nv = min(kBwdPViews, a.V - v0);
         bool bad = !mbar_wait_bounded(&tma_bar[st], (uint32_t)((c / S) & 1), a.spin_limit);
         bad = bad || *abort_flag != 0;
-        unsigned char* slot = ring + (size_t)st * m.stage;
-        unsigned char* rst = slot + (size_t)kBwdPViews * m.yst_view;
-        unsigned char* ybuf = L::kConv ? yf + (size_t)(c & 1) * m.yf_buf : slot;
-        const size_t yview = L::kConv ? m.yf_view : m.yst_view;
+        const uint32_t slot_a = ring_a + (uint32_t)st * (uint32_t)m.stage;
+        const uint32_t rst_a = slot_a + kBwdPViews * ystv;
+        const uint32_t ybuf_a = L::kConv ? yf_a + (uint32_t)(c & 1) * (uint32_t)m.yf_buf : slot_a;
         if (!bad) {
             if constexpr (L::kConv) {
-                // 16-bit window rows -> FP32 rows of pitch PITCH (8 images per 16-byte load)
-                constexpr int OCT = BG / 8;
-                for (int e = tid; e < nv * a.wd * OCT; e += NC) {
-                    const int vl = e / (a.wd * OCT), rest = e - vl * (a.wd * OCT);
-                    const int dl = rest / OCT, o = rest - dl * OCT;
-                    const uint4 u = *reinterpret_cast<const uint4*>(slot + (size_t)vl * m.yst_view + (size_t)dl * BG * 2 +
-                                                                    (size_t)o * 16);
+                // 16-bit window rows -> FP32 rows of pitch PITCH (8 images per 16-byte load); the
+                // view of item e is found by comparison (no division)
+                const int W = a.wd * OCT;
+                for (int e = tid; e < nv * W; e += NC) {
+                    const int vl = (e >= W) + (e >= 2 * W) + (e >= 3 * W);
+                    const int rest = e - vl * W;
+                    const int dl = rest >> LOG_OCT, o = rest & (OCT - 1);
+                    const uint4 u = lds4u(slot_a + (uint32_t)vl * ystv + (uint32_t)(dl * BG * 2 + o * 16));
                     float4 f[2];
                     bwdp_widen8<T>(u, f);
-                    float4* dst = reinterpret_cast<float4*>(ybuf + (size_t)vl * yview + (size_t)dl * PITCH + (size_t)o * 32);
-                    dst[0] = f[0];
-                    dst[1] = f[1];
+                    const uint32_t dst = ybuf_a + (uint32_t)vl * yview + (uint32_t)(dl * PITCH + o * 32);
+                    sts4(dst, f[0]);
+                    sts4(dst + 16, f[1]);
                 }
             }
             if constexpr (KW > 0) {
                 // re-base the landed rays on this tile, in place: one ray per thread
-                for (int e = tid; e < nv * a.wd; e += NC) {
-                    const int vl = e / a.wd, dl = e - vl * a.wd;
+                const int W = a.wd;
+                for (int e = tid; e < nv * W; e += NC) {
+                    const int vl = (e >= W) + (e >= 2 * W) + (e >= 3 * W);
+                    const int dl = e - vl * W;
                     const int d = dlo_c[st * kBwdPViews + vl] + dl;
-                    float4* rec = reinterpret_cast<float4*>(rst + (size_t)vl * m.rst_view + (size_t)dl * 32);
-                    const RayT ray = *reinterpret_cast<const RayT*>(rec);
+                    const uint32_t rec = rst_a + (uint32_t)vl * rstv + (uint32_t)dl * 32u;
+                    const float4 lo = lds4(rec), hi = lds4(rec + 16);
+                    RayT ray;
+                    ray.J0 = __float_as_int(lo.x);
+                    ray.I0 = __float_as_int(lo.y);
+                    ray.fx0 = lo.z;
+                    ray.fy0 = lo.w;
+                    ray.dxh = hi.x;
+                    ray.dyh = hi.y;
+                    ray.dxl = hi.z;
+                    ray.dyl = hi.w;
                     float4 A, Bc;
                     bwdp_rebase(ray, d >= 0 && d < a.D, ti, tj, a.ih2, &A, &Bc);
-                    rec[0] = A;
-                    rec[1] = Bc;
+                    sts4(rec, A);
+                    sts4(rec + 16, Bc);
                 }
             }
         }
@@ -318,39 +344,46 @@ __global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasP
             return;
         }
         for (int vl = 0; vl < nv; ++vl) {
-            const ViewF vf = view_c[st * kBwdPViews + vl];
+            const uint32_t va = win_a + (uint32_t)(st * kBwdPViews + vl) * 32u;
+            const float4 v01 = lds4(va), v23 = lds4(va + 16);   // ax, ay, a0, bx | by, b0, -, -
             const int dlo = dlo_c[st * kBwdPViews + vl];
-            const unsigned char* yv = ybuf + (size_t)vl * yview;
+            const uint32_t yv = ybuf_a + (uint32_t)vl * yview;
+            // detector coordinate of the first pixel; the second (one row down) adds (ay, by)
+            const float num0 = fmaf(v01.x, gx, fmaf(v01.y, gy0, v01.z));
+            const float den0 = fmaf(v01.w, gx, fmaf(v23.x, gy0, v23.y));
             if constexpr (KW == 0) {
                 // interpolating backprojector: the sinogram linearly interpolated at the pixel's detector
                 // coordinate t (IEEE division: the weights need t to ~1e-5 bins), weighted by the ray
                 // density |grad t|; both taps lie in the copied window by construction of its bounds
-                const int lo = max(dlo, 0), hi = min(a.D - 1, dlo + a.wd - 1);
+                const int lo = max(dlo, 0) - dlo, hi = min(a.D - 1, dlo + a.wd - 1) - dlo;
 #pragma unroll
                 for (int x = 0; x < PX; ++x) {
                     const float gy = gy0 + (float)x;
-                    const float den = fmaf(vf.bx, gx, fmaf(vf.by, gy, vf.b0));
-                    const float t = fmaf(vf.ax, gx, fmaf(vf.ay, gy, vf.a0)) / den;
-                    const float ga = fmaf(-t, vf.bx, vf.ax), gb = fmaf(-t, vf.by, vf.ay);
+                    const float den = fmaf(v01.w, gx, fmaf(v23.x, gy, v23.y));
+                    const float t = fmaf(v01.x, gx, fmaf(v01.y, gy, v01.z)) / den;
+                    const float ga = fmaf(-t, v01.w, v01.x), gb = fmaf(-t, v23.x, v01.y);
                     const float w = sqrtf(fmaf(ga, ga, gb * gb)) / fabsf(den);
                     const float fl = floorf(t);
-                    const int k = (int)fl;
+                    const int k = (int)fl - dlo;
                     const float f = t - fl;
-                    const f32x2 w0 = f2_pack(w * (1.0f - f), w * (1.0f - f)), w1 = f2_pack(w * f, w * f);
+                    const float w0 = w * (1.0f - f), w1 = w * f;
                     const bool in0 = k >= lo && k <= hi, in1 = k + 1 >= lo && k + 1 <= hi;
-                    const ulonglong2* y0 = reinterpret_cast<const ulonglong2*>(yv + (long long)(k - dlo) * PITCH);
-                    const ulonglong2* y1 = reinterpret_cast<const ulonglong2*>(yv + (long long)(k + 1 - dlo) * PITCH);
+                    const uint32_t y0 = yv + (uint32_t)k * PITCH;
 #pragma unroll
                     for (int q = 0; q < NQ; ++q) {
                         if (in0) {
-                            const ulonglong2 y4 = y0[q];
-                            acc[x][2 * q + 0] = f2_fma(w0, y4.x, acc[x][2 * q + 0]);
-                            acc[x][2 * q + 1] = f2_fma(w0, y4.y, acc[x][2 * q + 1]);
+                            const float4 y4 = lds4(y0 + 16 * q);
+                            acc[x][4 * q + 0] = fmaf(w0, y4.x, acc[x][4 * q + 0]);
+                            acc[x][4 * q + 1] = fmaf(w0, y4.y, acc[x][4 * q + 1]);
+                            acc[x][4 * q + 2] = fmaf(w0, y4.z, acc[x][4 * q + 2]);
+                            acc[x][4 * q + 3] = fmaf(w0, y4.w, acc[x][4 * q + 3]);
                         }
                         if (in1) {
-                            const ulonglong2 y4 = y1[q];
-                            acc[x][2 * q + 0] = f2_fma(w1, y4.x, acc[x][2 * q + 0]);
-                            acc[x][2 * q + 1] = f2_fma(w1, y4.y, acc[x][2 * q + 1]);
+                            const float4 y4 = lds4(y0 + PITCH + 16 * q);
+                            acc[x][4 * q + 0] = fmaf(w1, y4.x, acc[x][4 * q + 0]);
+                            acc[x][4 * q + 1] = fmaf(w1, y4.y, acc[x][4 * q + 1]);
+                            acc[x][4 * q + 2] = fmaf(w1, y4.z, acc[x][4 * q + 2]);
+                            acc[x][4 * q + 3] = fmaf(w1, y4.w, acc[x][4 * q + 3]);
                         }
                     }
                 }
@@ -360,39 +393,34 @@ __global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasP
                 // windows carry margins far above its error); a candidate outside a pixel's own range
                 // has zero weight there.  Candidates outside the detector are sentinel rays over
                 // zero-filled rows, so only the copied window bounds the loop (the producer checked
-                // that it holds them all)
-                int la = 0x7fffffff, lb = -0x7fffffff;
-#pragma unroll
-                for (int x = 0; x < PX; ++x) {
-                    const float gy = gy0 + (float)x;
-                    const float t = __fdividef(fmaf(vf.ax, gx, fmaf(vf.ay, gy, vf.a0)),
-                                               fmaf(vf.bx, gx, fmaf(vf.by, gy, vf.b0)));
-                    la = min(la, (int)ceilf(t - r));
-                    lb = max(lb, (int)floorf(t + r));
+                // that it holds them all); the bounds are clamped in FP32, so a non-finite coordinate
+                // still gives a loop inside the window
+                float tlo = __fdividef(num0, den0), thi = tlo;
+                if constexpr (PX == 2) {
+                    const float t1 = __fdividef(num0 + v01.y, den0 + v23.x);
+                    tlo = fminf(tlo, t1);
+                    thi = fmaxf(thi, t1);
                 }
-                la = max(la - dlo, 0);
-                lb = min(lb - dlo, a.wd - 1);
-                const unsigned char* rv = rst + (size_t)vl * m.rst_view;
-                for (int dl = la; dl <= lb; ++dl) {
-                    const ulonglong2* rec = reinterpret_cast<const ulonglong2*>(rv + (size_t)dl * 32);
-                    const ulonglong2 A = rec[0];
-                    const float4 Bc = *reinterpret_cast<const float4*>(rec + 1);
-                    f32x2 w2[PX];
-#pragma unroll
-                    for (int x = 0; x < PX; ++x) {
-                        float pxx, pyx;
-                        f2_unpack(p2[x], &pxx, &pyx);
-                        const float w = bwdp_weight<KW>(p2[x], pxx, pyx, A.x, A.y, Bc.x, Bc.y, Bc.z);
-                        w2[x] = f2_pack(w, w);
-                    }
-                    const ulonglong2* y = reinterpret_cast<const ulonglong2*>(yv + (size_t)dl * PITCH);
+                const float fd = (float)dlo;
+                const int la = __float2int_ru(fmaxf((tlo - r) - fd, 0.0f));
+                const int lb = __float2int_rd(fminf((thi + r) - fd, (float)(a.wd - 1)));
+                uint32_t ra = rst_a + (uint32_t)vl * rstv + (uint32_t)la * 32u;
+                uint32_t ya = yv + (uint32_t)la * PITCH;
+                for (int dl = la; dl <= lb; ++dl, ra += 32u, ya += PITCH) {
+                    const float4 A = lds4(ra), Bc = lds4(ra + 16);
+                    const float s0 = fmaf(px, Bc.x, fmaf(py0, Bc.y, Bc.z));
+                    float w[PX];
+                    w[0] = bwdp_weight<KW>(px, py0, s0, A);
+                    if constexpr (PX == 2) w[1] = bwdp_weight<KW>(px, py0 + 1.0f, s0 + Bc.y, A);
 #pragma unroll
                     for (int q = 0; q < NQ; ++q) {
-                        const ulonglong2 y4 = y[q];
+                        const float4 y4 = lds4(ya + 16 * q);
 #pragma unroll
                         for (int x = 0; x < PX; ++x) {
-                            acc[x][2 * q + 0] = f2_fma(w2[x], y4.x, acc[x][2 * q + 0]);
-                            acc[x][2 * q + 1] = f2_fma(w2[x], y4.y, acc[x][2 * q + 1]);
+                            acc[x][4 * q + 0] = fmaf(w[x], y4.x, acc[x][4 * q + 0]);
+                            acc[x][4 * q + 1] = fmaf(w[x], y4.y, acc[x][4 * q + 1]);
+                            acc[x][4 * q + 2] = fmaf(w[x], y4.z, acc[x][4 * q + 2]);
+                            acc[x][4 * q + 3] = fmaf(w[x], y4.w, acc[x][4 * q + 3]);
                         }
                     }
                 }
@@ -404,15 +432,12 @@ __global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasP
     const int b0 = blockIdx.y * BG;
 #pragma unroll
     for (int x = 0; x < PX; ++x) {
-        if (!inside[x]) continue;
-        float accf[BG];
-#pragma unroll
-        for (int b = 0; b < BG / 2; ++b) f2_unpack(acc[x][b], &accf[2 * b], &accf[2 * b + 1]);
+        if ((ti + pi0 + x) >= a.n || (tj + pj) >= a.n) continue;
         const long long p = (long long)(ti + pi0 + x) * a.n + (tj + pj);
 #pragma unroll
         for (int b = 0; b < BG; ++b)
             if (b0 + b < a.B)
-                epilogue_store_rt(a.ep, a.out_dtype, a.img, a.h * accf[b], (long long)(b0 + b) * npix + p);
+                epilogue_store_rt(a.ep, a.out_dtype, a.img, a.h * acc[x][b], (long long)(b0 + b) * npix + p);
     }
 }
 
