@@ -263,8 +263,36 @@ def run_ours(args):
     p_steps = max(2, min(5, args.steps))
     p_total, p_fwd, p_adj = timed(plain, p_steps, 1, sets32)
     plain_ms = p_total / p_steps
+    # supplementary: the same tuned kernels with FP32 storage (Section 3.3 compares 16-bit with FP32
+    # storage in one design)
+    t_steps = max(3, min(20, args.steps))
+    t_total, t_fwd, t_adj = timed(chosen, t_steps, 3, sets32)
+    tuned32_ms = t_total / t_steps
     del sets32, x32, y32
     torch.cuda.empty_cache()
+    # supplementary: the FP16 forward with FP16 weights in mixed-precision FMAs (opt-in), timed alone,
+    # and its departure from the FP32-weight forward on the same input
+    f16w = None
+    if args.storage == "f16":
+        cfg_w2 = launch_config(args.algo, weights=2)
+        for i in range(3):
+            forward_raw(geom, xs[i % n_sets], cfg_w2, out=outs_y[i % n_sets])
+        torch.cuda.synchronize()
+        wev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(t_steps)]
+        for i in range(t_steps):
+            wev[i][0].record(stream)
+            forward_raw(geom, xs[i % n_sets], cfg_w2, out=outs_y[i % n_sets])
+            wev[i][1].record(stream)
+        torch.cuda.synchronize()
+        w2_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in wev)
+        y_w2 = forward_raw(geom, xs[0], cfg_w2).double()
+        y_w0 = forward_raw(geom, xs[0], chosen).double()
+        f16w = {"fwd_ms": w2_ms, "samples_per_s": B * S / (w2_ms * 1e-3),
+                "max_abs_diff_rel_to_max": float((y_w2 - y_w0).abs().max() / y_w0.abs().max()),
+                "rel_l2_vs_fp32_weights": float(torch.linalg.vector_norm(y_w2 - y_w0) / torch.linalg.vector_norm(y_w0)),
+                "weights": "FP16 (each weight rounded once, relative error <= 2^-12), exact FP16 x FP16 products "
+                           "accumulated in FP32 (fma.rn.f32.f16)"}
+        del y_w2, y_w0
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -351,8 +379,8 @@ def run_ours(args):
         except (OSError, ValueError):
             traffic_tab = {}
     probe = ctypes.c_double(0.0)
-    L.check(L.radon_probe_gather_ceiling(L.RADON_F32 if args.storage == "f32" else L.RADON_F16, ctypes.byref(probe)),
-            "radon_probe_gather_ceiling")
+    dt_code = {"f32": L.RADON_F32, "f16": L.RADON_F16, "bf16": L.RADON_BF16}[args.storage]
+    L.check(L.radon_probe_gather_ceiling_ex(dt_code, 0, ctypes.byref(probe)), "radon_probe_gather_ceiling_ex")
     rooflines = {
         # forward: 4 texels per sample through the shared-memory / L1 load pipe, 128 B/clk/SM
         "forward": roofline(B * S, mean_fwd, sm_count, 128.0 / (4.0 * bytes_per_texel), clk_mhz,
@@ -368,6 +396,21 @@ def run_ours(args):
 
     rooflines["forward"]["probe_ceiling"] = probe.value / 1e9
     rooflines["forward"]["frac_of_probe"] = rooflines["forward"]["achieved"] / (probe.value / 1e9)
+    if f16w is not None:
+        probe2 = ctypes.c_double(0.0)
+        L.check(L.radon_probe_gather_ceiling_ex(L.RADON_F16, 2, ctypes.byref(probe2)), "radon_probe_gather_ceiling_ex")
+        f16w["roofline"] = roofline(B * S, f16w["fwd_ms"], sm_count, 128.0 / (4.0 * bytes_per_texel), clk_mhz,
+                                    rooflines["forward"]["peak_basis"].split(" (")[0], None)
+        f16w["roofline"]["probe_ceiling"] = probe2.value / 1e9
+        f16w["roofline"]["frac_of_probe"] = f16w["samples_per_s"] / probe2.value
+    tuned32 = {"ms_per_step": tuned32_ms, "samples_per_s": samples_per_step / (tuned32_ms * 1e-3),
+               "images_per_s": B / (tuned32_ms * 1e-3), "fwd_ms": statistics.mean(t_fwd),
+               "adj_ms": statistics.mean(t_adj),
+               "roofline_forward": roofline(B * S, statistics.mean(t_fwd), sm_count, 128.0 / 16.0, clk_mhz,
+                                            "%d SMs x 8 samples/clk/SM (128 B/clk/SM load pipe / 4 texels x 4 B) x %.0f MHz"
+                                            % (sm_count, clk_mhz), None),
+               "roofline_backward": roofline(B * S, statistics.mean(t_adj), sm_count, 128.0 / ADJ_OPS_PER_SAMPLE,
+                                             clk_mhz, rooflines["backward"]["peak_basis"].split(" (")[0], None)}
     secondary = None
     if rank == 0 and world == 1 and not args.no_secondary:
         secondary = run_secondary(args)
@@ -391,6 +434,7 @@ def run_ours(args):
             "dtype": "f32",
             "data": "synthetic",
             "config": dict(workload_config(args.workload, args.storage, args.algo, geom),
+                           arithmetic="FP32 (FP32 bilinear weights, FP32 accumulation; storage %s)" % args.storage,
                            l2="rotating %d input/output sets, %.0f MB total (> 2x L2)" % (
                                n_sets, n_sets * bytes_per_set / 2**20)),
             "images_per_s": B * world / (ms_per_step * 1e-3),
@@ -399,6 +443,9 @@ def run_ours(args):
             "plain_f32": {"ms_per_step": plain_ms, "samples_per_s": samples_per_step / (plain_ms * 1e-3),
                           "fwd_ms": statistics.mean(p_fwd), "adj_ms": statistics.mean(p_adj)},
             "speedup_vs_plain_f32": plain_ms / ms_per_step,
+            "tuned_f32": tuned32,
+            "speedup_16bit_storage_vs_tuned_f32": tuned32_ms / ms_per_step,
+            "fp16_weights_forward": f16w,
             "roofline": dict(rooflines[dom], kernel=dom),
             "roofline_forward": rooflines["forward"],
             "roofline_backward": rooflines["backward"],
@@ -506,6 +553,7 @@ def run_secondary(args):
     res = {"workload": "parallel_b32_n512_v512_d512", "samples_per_image": S,
            "l2": "flushed (2x L2 write) before each timed step"}
     for label, dt, cfg in (("chosen_f16", torch.float16, launch_config("auto")),
+                           ("tuned_f32", torch.float32, launch_config("auto")),
                            ("plain_f32", torch.float32, launch_config("plain"))):
         x = torch.from_numpy(xs).to("cuda", dt)
         yb = forward_raw(g, x, cfg)
@@ -518,6 +566,7 @@ def run_secondary(args):
         res[label] = {"ms_per_step": ms, "samples_per_s": 2 * B * S / (ms * 1e-3), "images_per_s": B / (ms * 1e-3)}
         del x, yb, oy, ox
     res["speedup_chosen_vs_plain_f32"] = res["plain_f32"]["ms_per_step"] / res["chosen_f16"]["ms_per_step"]
+    res["speedup_chosen_vs_tuned_f32"] = res["tuned_f32"]["ms_per_step"] / res["chosen_f16"]["ms_per_step"]
     out["paper_batch"] = res
     del xs
     # the uneven batch: 64 images of 128^2..1024^2, each with its own geometry, in one persistent

@@ -116,22 +116,6 @@ __device__ __forceinline__ void bwdp_rebase(const RayT ray, bool valid, int ti, 
     *Bc = make_float4(bx, by, -fmaf(A->x, bx, A->y * by) - kr, 0.0f);
 }
 
-// Shared-memory loads and stores at 32-bit shared addresses (the CTA's offsets stay 32-bit).
-__device__ __forceinline__ float4 lds4(uint32_t a) {
-    float4 v;
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
-    return v;
-}
-__device__ __forceinline__ uint4 lds4u(uint32_t a) {
-    uint4 v;
-    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
-    return v;
-}
-__device__ __forceinline__ void sts4(uint32_t a, float4 v) {
-    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
-                 : "memory");
-}
-
 // Bilinear weight of the pixel at (px, py) (tile-local) on one ray with record A = (reference sample
 // relative to the tile origin, step) and Bc = (step / h^2, C): the sum over KW consecutive samples
 // from the window start ceil(p.b + C) of tent(dx) * tent(dy), tent(v) = max(0, 1 - |v|) evaluated

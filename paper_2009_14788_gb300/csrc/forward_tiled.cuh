@@ -415,8 +415,11 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
                     const float M = 12582912.0f;
                     const unsigned magic = 0x4B400000u;
                     const float sXm = sX - 0.5f, sYm = sY - 0.5f, ylim_m = ylim - 0.5f;
-                    const unsigned base = (unsigned)(IB * wc + JB) - magic * (unsigned)(wc + 1);
-                    const unsigned wcu = (unsigned)wc;
+                    const unsigned comp_a = smem_u32(comp);
+                    // shared address of texel (row, col) = comp + 16 (row * wc + col): the magic-biased
+                    // bit patterns of the floors enter modulo 2^32, so the biases cancel exactly
+                    const unsigned wc16 = 16u * (unsigned)wc;
+                    const unsigned base16 = comp_a + 16u * ((unsigned)(IB * wc + JB) - magic * (unsigned)(wc + 1));
                     const int kleft = nk - k;
                     int i = 0;
                     float kk = 0.0f;
@@ -425,28 +428,27 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
                     // loading it (same values: same bits; 2-5 % faster in FP32; the 16-bit paths, with
                     // twice the FMAs per load, measured 2-11 % slower and load every texel)
                     constexpr bool kReuseRow = std::is_same<T, float>::value;
-                    unsigned pidx = 0x80000000u;   // no texel index of a band lies within a row of it
+                    unsigned pa = 0x80000000u;   // no texel address of a band lies within a row of it
                     uint4 r10 = make_uint4(0u, 0u, 0u, 0u), r11 = r10;
                     for (; i < kleft; ++i, kk += 1.0f) {
                         const float fym = fmaf(kk, dY, sYm);
                         if (fym >= ylim_m) break;
                         const float fxm = fmaf(kk, dX, sXm);
                         const float tx = fxm + M, ty = fym + M;
-                        const unsigned idx = __float_as_uint(ty) * wcu + __float_as_uint(tx) + base;
-                        const uint4* p = comp + idx;
+                        const unsigned ad = __float_as_uint(ty) * wc16 + __float_as_uint(tx) * 16u + base16;
                         uint4 q00, q01;
-                        if (kReuseRow && idx == pidx + wcu) {
+                        if (kReuseRow && ad == pa + wc16) {
                             q00 = r10;
                             q01 = r11;
                         } else {
-                            q00 = p[0];
-                            q01 = p[1];
+                            q00 = lds4u(ad);
+                            q01 = lds4u(ad + 16u);
                         }
-                        const uint4 q10 = p[wcu], q11 = p[wcu + 1];
+                        const uint4 q10 = lds4u(ad + wc16), q11 = lds4u(ad + wc16 + 16u);
                         if (kReuseRow) {
                             r10 = q10;
                             r11 = q11;
-                            pidx = idx;
+                            pa = ad;
                         }
                         const float ax = fxm - (tx - M), ay = fym - (ty - M);   // in [-1/2, 1/2]
                         const float wx1 = 0.5f + ax, wx0 = 0.5f - ax, wy1 = 0.5f + ay, wy0 = 0.5f - ay;
