@@ -602,21 +602,32 @@ def run_secondary(args):
     ms_graph = time_it(graph.replay, 5)
     ms_fwd = time_it(pf.launch, 5)
     ms_adj = time_it(pa.launch, 5)
+    # the library defaults without the autotuner (forward: 8 views x 1 lane per ray block; adjoint:
+    # chunks of 32 views where they fit), on the same buffers
+    df = BatchPlan(list(zip(geoms, xs16, oy)), "forward", autotune=False)
+    da = BatchPlan(list(zip(geoms, ys16, ox)), "adjoint", autotune=False)
+    ms_fwd_default = time_it(df.launch, 5)
+    ms_adj_default = time_it(da.launch, 5)
+    df.close()
+    da.close()
 
     def per_item():
         for g, x, y, a_, b_ in zip(geoms, xs16, ys16, oy, ox):
             forward_raw(g, x, out=a_)
             backward_raw(g, y, out=b_)
     ms_loop = time_it(per_item, 3, warm=1)
-    cfg_f = sorted({(items[k]["n"], pf.item_config(k)) for k in range(len(items))})
+    cfg_f = sorted({(items[k]["n"],) + pf.item_shape(k) for k in range(len(items))})
     cfg_a = sorted({(items[k]["n"], pa.item_config(k)) for k in range(len(items))})
     out["uneven"] = {
         "workload": w.name, "storage": "f16", "images": len(items), "samples_per_pass": S_tot,
         "ms_graph_fwd_adj": ms_graph, "ms_plan_fwd": ms_fwd, "ms_plan_adj": ms_adj,
         "samples_per_s": 2 * S_tot / (ms_graph * 1e-3), "images_per_s": len(items) / (ms_graph * 1e-3),
         "per_image_calls_ms": ms_loop, "speedup_vs_per_image_calls": ms_loop / ms_graph,
-        "plan_create_s": t_plan, "autotuned_forward_views_by_size": cfg_f,
-        "autotuned_adjoint_views_by_size": cfg_a, "work_items": [pf.info["work_items"], pa.info["work_items"]],
+        "plan_create_s": t_plan, "autotuned_forward_n_views_lanes": cfg_f,
+        "autotuned_adjoint_n_views": cfg_a,
+        "default_shapes_ms_plan_fwd": ms_fwd_default, "default_shapes_ms_plan_adj": ms_adj_default,
+        "autotuned_speedup_vs_default_shapes": (ms_fwd_default + ms_adj_default) / (ms_fwd + ms_adj),
+        "work_items": [pf.info["work_items"], pa.info["work_items"]],
         "ctas": [pf.info["ctas"], pa.info["ctas"]],
         "l2": "flushed (2x L2 write) before each timed launch",
     }

@@ -474,11 +474,15 @@ RADON_API radon_status radon_filter_sinogram(const radon_geometry* geometry, con
  *   - Forward: the plan keeps a packed copy of every image (each pixel's 2 x 2 bilinear neighbourhood
  *     in one 8-byte texel, FP32: 16 bytes, in the image frame and transposed), refreshed by a pack
  *     kernel at every launch; each sample is one texel load.
- *   - Adjoint: per chunk of views the CTA re-bases the rays crossing its tile and stages their
- *     sinogram values in shared memory, then every thread gathers its pixel.
- *   - Tile shapes (forward: views x detectors per ray block; adjoint: views per chunk) are picked per
- *     image size by a built-in autotuner that times each candidate on the plan's own buffers at
- *     creation (and writes the outputs while doing so), unless options fix them.
+ *   - Adjoint: per chunk of views the CTA stages the sinogram values of the rays crossing its tile in
+ *     shared memory (re-basing one ray per parallel-beam view, whose rays share one sample lattice,
+ *     or every ray of a fan-beam window), then every thread gathers its pixel.
+ *   - Tile shapes (forward: views per ray block x lanes per ray, 8 candidates; adjoint: views per
+ *     chunk, 4 candidates) are picked per image size and geometry kind by a built-in autotuner that
+ *     times each candidate on the plan's own buffers at creation (and writes the outputs while doing
+ *     so), unless options fix them.  With the environment variable RADON_TUNE_CACHE naming a file,
+ *     picks are appended to it and later plans reuse them for the same direction, storage type, image
+ *     size and geometry kind instead of timing.
  * The caller keeps the geometries and buffers alive until radon_batch_plan_destroy; the buffer
  * addresses are baked into the plan.
  */
@@ -493,9 +497,11 @@ typedef struct radon_plan radon_plan;
 
 typedef struct radon_plan_options {
     int autotune;            /* 1: time the candidates (default); 0: library defaults */
-    int forward_views;       /* > 0: views per forward ray block (1, 2, 4 or 8; detectors = 256 / views) */
+    int forward_views;       /* > 0: views per forward ray block (1, 2, 4 or 8; detectors = 256 / (views x lanes)) */
     int adjoint_views;       /* > 0: views per adjoint chunk (4, 8, 16 or 32; RADON_ERR_UNSUPPORTED if 32
                                 views of the widest detector window do not fit one CTA's shared memory) */
+    int forward_lanes;       /* > 0: lanes per forward ray (1, or 4: the ray's samples interleaved over four
+                                lanes whose partial sums meet in a fixed shuffle tree) */
 } radon_plan_options;
 
 /*
@@ -523,6 +529,9 @@ typedef struct radon_plan_info {
 } radon_plan_info;
 RADON_API radon_status radon_batch_plan_get_info(const radon_plan* plan, radon_plan_info* info);
 RADON_API radon_status radon_batch_plan_item_config(const radon_plan* plan, int item, int* views);
+/* The shape item i runs with: views per forward ray block or adjoint chunk, and lanes per forward ray
+ * (1 for the adjoint). */
+RADON_API radon_status radon_batch_plan_item_shape(const radon_plan* plan, int item, int* views, int* lanes);
 
 RADON_API void radon_batch_plan_destroy(radon_plan* plan);
 

@@ -106,6 +106,7 @@ class radon_plan_options(ctypes.Structure):
         ("autotune", ctypes.c_int),
         ("forward_views", ctypes.c_int),
         ("adjoint_views", ctypes.c_int),
+        ("forward_lanes", ctypes.c_int),
     ]
 
 
@@ -177,6 +178,8 @@ _SIGNATURES = [
     ("radon_batch_plan_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("radon_batch_plan_get_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(radon_plan_info)]),
     ("radon_batch_plan_item_config", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("radon_batch_plan_item_shape", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("radon_batch_plan_destroy", None, [ctypes.c_void_p]),
     ("radon_probe_gather_ceiling", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     ("radon_probe_gather_ceiling_ex", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
@@ -357,6 +360,10 @@ def radon_batch_plan_get_info(plan, info_ptr):
 
 def radon_batch_plan_item_config(plan, item, views_ptr):
     return _call("radon_batch_plan_item_config", plan, item, views_ptr)
+
+
+def radon_batch_plan_item_shape(plan, item, views_ptr, lanes_ptr):
+    return _call("radon_batch_plan_item_shape", plan, item, views_ptr, lanes_ptr)
 
 
 def radon_batch_plan_destroy(plan):

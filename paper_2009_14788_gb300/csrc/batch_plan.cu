@@ -9,16 +9,21 @@
 // amortised across images as in the batch-interleaved kernels; instead:
 //   * forward: a pack kernel stores each pixel's 2 x 2 bilinear neighbourhood as one texel (four
 //     16-bit values in 8 bytes, or four FP32 in 16), once in the image frame and once transposed;
-//     every sample is one texel load through L1.  A warp holds 32 neighbouring detectors of one view,
-//     whose samples at a given step lie along the detector direction; the frame whose rows run along
-//     that direction keeps them within a few cache lines;
-//   * adjoint: per chunk of views the CTA computes each view's detector window for its tile,
-//     re-bases every ray of the windows on the tile (one ray per thread) and stages the rays'
-//     sinogram values in shared memory; then every thread gathers its pixel from shared memory.
+//     every sample is one texel load through L1.  Four lanes share a ray (interleaved samples,
+//     partial sums joined by a fixed shuffle tree) and a warp holds eight neighbouring detectors of
+//     one view, whose samples at a given step lie along the detector direction; the frame whose rows
+//     run along that direction keeps them within a few cache lines;
+//   * adjoint: per chunk of views the CTA computes each view's detector window for its tile and
+//     stages the window's sinogram values in shared memory; then every thread gathers its pixel
+//     from shared memory.  For a parallel-beam view every ray shares one sample lattice, so the CTA
+//     re-bases one ray per view and each pixel steps from one candidate ray's samples to the
+//     next; a fan-beam view re-bases every ray of its window (one ray per thread).
 // Tile shapes (forward: views x detectors per ray block; adjoint: views per chunk) are chosen per
 // image size by timing each candidate on the plan's own buffers when the plan is created.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <map>
 #include <new>
 #include <string>
@@ -29,6 +34,7 @@
 #include "dtype.cuh"
 #include "epilogue.cuh"
 #include "radon_internal.h"
+#include "tma.cuh"
 
 namespace radon {
 
@@ -49,6 +55,7 @@ struct Unit {
     float h, ih2;
     int wd;            // adjoint: detector window of a 16 x 16 tile
     int cfg;           // forward: views per ray block; adjoint: views per chunk
+    int lanes;         // forward: lanes per ray (1 or 4)
     int fan;           // 1: fan beam (detector coordinate a ratio); 0: parallel (affine)
 };
 
@@ -145,10 +152,18 @@ __global__ void __launch_bounds__(256) plan_pack_kernel(const Unit* __restrict__
 
 // ------------------------------------------------------------------------------------- forward
 
-// Ray (v, d) of unit u: h * sum_k bilinear(sample k), every sample one texel load.  Positions are
-// re-based from the split-precision table every 32 samples (as in the plain kernel).
+// Lanes per ray of the forward work items (a tuned shape: 1 or 4).  With four, the lanes of a ray take
+// its samples k = sub, sub + 4, ... (spatially neighbouring texels, so a warp's loads stay within a
+// few cache lines), which gives the SM four times the independent loads in flight -- the shape for
+// images whose rays alone do not fill the GPU -- and sum their partial sums in a fixed shuffle tree
+// (the same bits on every call).
+constexpr int kPlanMaxLanes = 4;
+
+// Ray (v, d) of unit u, lane `sub` of its group: the partial sum over its samples (without the factor
+// h), every sample one texel load.  Positions are re-based from the split-precision table every 32 samples.
 template <typename T>
-__device__ float plan_ray(const Unit& u, const typename Quad<T>::type* __restrict__ quads, int v, int d) {
+__device__ float plan_ray(const Unit& u, const typename Quad<T>::type* __restrict__ quads, int v, int d, int sub,
+                          int lanes) {
     const long long r = (long long)v * u.D + d;
     const int nk = u.nks[r];
     if (nk == 0) return 0.0f;
@@ -172,7 +187,7 @@ __device__ float plan_ray(const Unit& u, const typename Quad<T>::type* __restric
         const float sY = fmaf(kbf, dYl, fY0 + (qy - QY));
         const int jb = J0 + (int)QX, ib = I0 + (int)QY;
         const int kend = min(nk - kb, 32);
-        for (int kk = 0; kk < kend; ++kk) {
+        for (int kk = sub; kk < kend; kk += lanes) {
             const float lx = fmaf((float)kk, dX, sX), ly = fmaf((float)kk, dY, sY);
             const float flx = floorf(lx), fly = floorf(ly);
             // samples lie strictly inside the support box, so j, i are in [-1, n-1]; the clamps only
@@ -187,23 +202,30 @@ __device__ float plan_ray(const Unit& u, const typename Quad<T>::type* __restric
             acc += fmaf(b, bot - top, top);
         }
     }
-    return u.h * acc;
+    return acc;
 }
 
-// Work item `tile` of unit u (a block of G views x 256 / G detectors, one ray per thread), stored
-// through the epilogue (the identity for plans).
+// Work item `tile` of unit u (a block of G views x 256 / (G lanes) detectors, `lanes` lanes per ray),
+// stored through the epilogue (the identity for plans).  Every thread of the CTA calls it (the lanes
+// of a ray meet in shuffles).
 template <typename T>
 __device__ __forceinline__ void plan_forward_tile(const Unit& u, int tile, const typename Quad<T>::type* __restrict__ quads,
                                                   const Epilogue& ep) {
-    const int G = u.cfg, Dt = kPlanThreads / G;
+    const int lanes = u.lanes;
+    const int G = u.cfg, Dt = kPlanThreads / (lanes * G);
     const int n_dr = (u.D + Dt - 1) / Dt;
     const int vg = tile / n_dr, dr = tile - (tile / n_dr) * n_dr;
-    // With two or more views per tile each group of eight lanes takes views 2m, 2m + 1 x four
-    // consecutive detectors: their quads' cache lines overlap more than those of eight detectors of
-    // one view (1-4 % faster from 60 to 1024 views; lane pairs still hold neighbouring detectors).
     const int tid = (int)threadIdx.x;
-    int vl, dl;
-    if (G >= 2) {
+    int vl, dl, sub = 0;
+    if (lanes == kPlanMaxLanes) {
+        const int ray = tid >> 2;
+        sub = tid & 3;
+        vl = ray / Dt;
+        dl = ray - vl * Dt;
+    } else if (G >= 2) {
+        // one lane per ray: each group of eight lanes takes views 2m, 2m + 1 x four consecutive
+        // detectors, whose quads' cache lines overlap more than those of eight detectors of one view
+        // (1-4 % faster from 60 to 1024 views; lane pairs still hold neighbouring detectors)
         const int per = Dt >> 2, P = tid >> 3;
         vl = (P / per) * 2 + ((tid >> 2) & 1);
         dl = (P - (P / per) * per) * 4 + (tid & 3);
@@ -212,10 +234,15 @@ __device__ __forceinline__ void plan_forward_tile(const Unit& u, int tile, const
         dl = tid - vl * Dt;
     }
     const int v = vg * G + vl, d = dr * Dt + dl;
-    if (v < u.V && d < u.D) {
-        const float y = plan_ray<T>(u, quads, v, d);
+    const bool live = v < u.V && d < u.D;
+    float y = live ? plan_ray<T>(u, quads, v, d, sub, lanes) : 0.0f;
+    if (lanes == kPlanMaxLanes) {   // uniform over the CTA: one work item at a time
+        y += __shfl_xor_sync(0xffffffffu, y, 1);
+        y += __shfl_xor_sync(0xffffffffu, y, 2);
+    }
+    if (live && sub == 0) {
         const long long idx = (long long)v * u.D + d;
-        static_cast<T*>(u.out)[idx] = from_f32<T>(epilogue_value<T>(ep, y, idx));
+        static_cast<T*>(u.out)[idx] = from_f32<T>(epilogue_value<T>(ep, u.h * y, idx));
     }
 }
 
@@ -267,6 +294,12 @@ struct AdjShared {
     ViewF view[kMaxChunkViews];
     int dlo[kMaxChunkViews];
     float r[kMaxChunkViews];
+    // parallel beams: the window's first ray's sample nearest the tile centre (tile-relative) and
+    // step, the offset between neighbouring rays' samples of one lattice index, and the window
+    // constants (step / h^2, C) of the candidate samples
+    float4 ref[kMaxChunkViews];
+    float4 bc[kMaxChunkViews];   // (bx, by, C, -)
+    float2 dn[kMaxChunkViews];
     int w;
 };
 
@@ -360,6 +393,111 @@ __device__ void plan_adjoint_tile(const Unit& u, int tile, const AdjBuffers& b, 
     }
 }
 
+// Parallel beams: every ray of a view has the same direction and the rays' sample lattices line up
+// (sample k of ray d sits at m_d + k h u with m_d = s_d n, so sample k of ray d + 1 is sample k of
+// ray d moved by det_spacing * n).  So the CTA re-bases one ray per view -- the window's first --
+// and stages only the window's sinogram values; each pixel finds its first candidate sample ka once
+// per view (the same lattice index on every ray) and steps from one candidate ray to the next by
+// det_spacing * n.  Every lattice point within a pixel's 2 x 2 support lies inside the support box,
+// so it is a sample of its ray whenever the ray exists; rays outside the detector have zero values.
+template <typename T, int KW>
+__device__ void plan_adjoint_tile_parallel(const Unit& u, int tile, const AdjBuffers& b, const Epilogue& ep,
+                                           int* err) {
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    // 4 x 8 pixels per warp, each group of eight lanes (one shared-load phase) a 4 x 2 block
+    const int pi = (warp >> 1) * 4 + ((lane & 7) >> 1), pj = (warp & 1) * 8 + (lane >> 3) * 2 + (lane & 1);
+    const float px = (float)pj, py = (float)pi;
+    const int tiles_x = (u.n + kBwdTile - 1) / kBwdTile;
+    const int ti = (tile / tiles_x) * kBwdTile, tj = (tile - (tile / tiles_x) * tiles_x) * kBwdTile;
+    const float gx = (float)(tj + pj), gy = (float)(ti + pi);
+    const T* y = static_cast<const T*>(u.in);
+    const int CV = u.cfg, wd = u.wd;
+    const float inv_wd = 1.0f / (float)wd, wd_last = (float)(wd - 1);
+    const uint32_t ys_a = smem_u32(b.ys);
+    float acc = 0.0f;
+    for (int c0 = 0; c0 < u.V; c0 += CV) {
+        const int nv = min(CV, u.V - c0);
+        if (tid < nv) {
+            ViewF vf = u.views[c0 + tid];
+            int dlo;
+            float r;
+            bwd_view_window(vf, ti, tj, u.n, &dlo, &r);
+            // every pixel's candidates [ceil(t - r), floor(t + r)] within the detector must lie in the
+            // staged window (the tile's largest t is at a corner); the loop clamps to it, so a miss is
+            // recorded, not overrun
+            const float x1 = (float)min(tj + kBwdTile - 1, u.n - 1), y1 = (float)min(ti + kBwdTile - 1, u.n - 1);
+            const float tmax = fmaxf(fmaxf(bwd_det_coord(vf, (float)tj, (float)ti), bwd_det_coord(vf, x1, (float)ti)),
+                                     fmaxf(bwd_det_coord(vf, (float)tj, y1), bwd_det_coord(vf, x1, y1)));
+            if (fminf(floorf(tmax + r), (float)(u.D - 1)) > (float)(dlo + wd - 1)) record_device_error(err, RADON_ERR_DEVICE_BOUNDS);
+            // every ray keeps its line in the table (a ray missing the image included)
+            const int dref = min(max(dlo, 0), u.D - 1);
+            const float4 A = bwd_ray_pos_rec(u.rays[(long long)(c0 + tid) * u.D + dref], true, ti, tj, u.ih2);
+            // det_spacing * n = (ax, ay) / (ax^2 + ay^2): the map t = (n.P) / det_spacing + const
+            const float q = 1.0f / fmaf(vf.ax, vf.ax, vf.ay * vf.ay);
+            const float2 dn = make_float2(vf.ax * q, vf.ay * q);
+            const float bx = A.z * u.ih2, by = A.w * u.ih2;
+            const float kr = fmaf(fabsf(A.z) + fabsf(A.w), u.ih2, 1e-4f);
+            const float sh = (float)(dlo - dref);
+            vf.a0 -= (float)dlo;   // window-relative detector coordinate
+            b.sh->view[tid] = vf;
+            b.sh->dlo[tid] = dlo;
+            b.sh->r[tid] = r;
+            b.sh->ref[tid] = make_float4(fmaf(sh, dn.x, A.x), fmaf(sh, dn.y, A.y), A.z, A.w);
+            b.sh->bc[tid] = make_float4(bx, by, -fmaf(A.x, bx, A.y * by) - kr, 0.0f);
+            b.sh->dn[tid] = dn;
+        }
+        __syncthreads();
+        for (int e = tid; e < nv * wd; e += kPlanThreads) {
+            int vl = (int)((float)e * inv_wd);   // e / wd, corrected for the quotient's rounding
+            vl -= vl * wd > e;
+            vl += (vl + 1) * wd <= e;
+            const int d = b.sh->dlo[vl] + (e - vl * wd);
+            b.ys[e] = (d >= 0 && d < u.D) ? to_f32(y[(long long)(c0 + vl) * u.D + d]) : 0.0f;
+        }
+        __syncthreads();
+        for (int vl = 0; vl < nv; ++vl) {
+            const float4 vf0 = *reinterpret_cast<const float4*>(&b.sh->view[vl]);   // ax, ay, a0 - dlo, -
+            const float r = b.sh->r[vl];
+            const float t = fmaf(vf0.x, gx, fmaf(vf0.y, gy, vf0.z));
+            // window-relative candidate range, clamped in FP32 (a non-finite coordinate still gives a
+            // loop inside the window)
+            const int la = __float2int_ru(fmaxf(t - r, 0.0f)), lb = __float2int_rd(fminf(t + r, wd_last));
+            const float4 A = b.sh->ref[vl];
+            const float4 bc = b.sh->bc[vl];
+            const float2 dn = b.sh->dn[vl];
+            const float ka = ceilf(fmaf(px, bc.x, fmaf(py, bc.y, bc.z)));
+            const float fla = (float)la;
+            // sample ka of the first candidate ray, relative to the pixel
+            // (x, y) pairs advance as f32x2 (one instruction per pair); the tents stay scalar
+            f32x2 r2 = f2_pack(fmaf(ka, A.z, fmaf(fla, dn.x, A.x) - px), fmaf(ka, A.w, fmaf(fla, dn.y, A.y) - py));
+            const f32x2 st2 = f2_pack(A.z, A.w), dn2 = f2_pack(dn.x, dn.y);
+            uint32_t ya = ys_a + (uint32_t)(vl * wd + la) * 4u;
+            for (int l = la; l <= lb; ++l, ya += 4u) {
+                f32x2 s2 = r2;
+                float sx, sy;
+                f2_unpack(s2, &sx, &sy);
+                float w = __saturatef(1.0f - fabsf(sx)) * __saturatef(1.0f - fabsf(sy));
+#pragma unroll
+                for (int k = 1; k < KW; ++k) {
+                    s2 = f2_add(s2, st2);
+                    f2_unpack(s2, &sx, &sy);
+                    w = fmaf(__saturatef(1.0f - fabsf(sx)), __saturatef(1.0f - fabsf(sy)), w);
+                }
+                float yv;
+                asm volatile("ld.shared.f32 %0, [%1];" : "=f"(yv) : "r"(ya));
+                acc = fmaf(w, yv, acc);
+                r2 = f2_add(r2, dn2);
+            }
+        }
+        __syncthreads();
+    }
+    if ((ti + pi) < u.n && (tj + pj) < u.n) {
+        const long long idx = (long long)(ti + pi) * u.n + (tj + pj);
+        static_cast<T*>(u.out)[idx] = from_f32<T>(epilogue_value<T>(ep, u.h * acc, idx));
+    }
+}
+
 // Four CTAs per SM: with both geometry kinds in one kernel the register allocation would otherwise
 // drop it to three (8.6 % slower on the uneven batch; 1.4 % faster than one generic path at four).
 template <typename T, int KW>
@@ -379,7 +517,7 @@ __global__ void __launch_bounds__(kPlanThreads, 4) plan_adjoint_kernel(const Uni
         if (u.fan)
             plan_adjoint_tile<T, KW, true>(u, w.tile, b, Epilogue{1.0f, nullptr, 0.0f, nullptr}, err);
         else
-            plan_adjoint_tile<T, KW, false>(u, w.tile, b, Epilogue{1.0f, nullptr, 0.0f, nullptr}, err);
+            plan_adjoint_tile_parallel<T, KW>(u, w.tile, b, Epilogue{1.0f, nullptr, 0.0f, nullptr}, err);
     }
 }
 
@@ -387,7 +525,10 @@ __global__ void __launch_bounds__(kPlanThreads, 4) plan_adjoint_kernel(const Uni
 template <typename T, int KW, bool FAN>
 __global__ void __launch_bounds__(kPlanThreads) single_adjoint_kernel(const Unit u, const Epilogue ep, int* err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    plan_adjoint_tile<T, KW, FAN>(u, (int)blockIdx.x, adj_buffers(smem_raw, u.wd, u.cfg), ep, err);
+    if constexpr (FAN)
+        plan_adjoint_tile<T, KW, true>(u, (int)blockIdx.x, adj_buffers(smem_raw, u.wd, u.cfg), ep, err);
+    else
+        plan_adjoint_tile_parallel<T, KW>(u, (int)blockIdx.x, adj_buffers(smem_raw, u.wd, u.cfg), ep, err);
 }
 
 size_t adj_smem_bytes(int max_wd, int cap) {
@@ -409,6 +550,7 @@ size_t texel_bytes(radon_dtype dt) { return dt == RADON_F32 ? 16 : 8; }
 // One image through the plan's kernels, without a plan: the unit is a kernel argument and every
 // work item is its own CTA, so a call allocates nothing and can be captured.
 constexpr int kSingleForwardViews = 8;    // views per ray block (the plan's default)
+constexpr int kSingleForwardLanes = 4;    // lanes per ray: one image's rays alone do not fill the GPU
 constexpr int kSingleAdjointViews = 32;   // views per staged chunk (the autotuner's pick at every size)
 
 Unit single_unit(const radon_geometry* g, const void* in, void* out, int cfg) {
@@ -426,6 +568,7 @@ Unit single_unit(const radon_geometry* g, const void* in, void* out, int cfg) {
     u.ih2 = (float)(1.0 / (g->h * g->h));
     u.wd = g->bwd_window + 2;
     u.cfg = cfg;
+    u.lanes = kSingleForwardLanes;
     u.fan = g->fan;
     return u;
 }
@@ -441,7 +584,7 @@ radon_status single_forward_t(const radon_geometry* g, const void* img, void* si
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "single-image pack launch");
     count_launches(1);
-    const int Dt = kPlanThreads / kSingleForwardViews;
+    const int Dt = kPlanThreads / (kSingleForwardLanes * kSingleForwardViews);
     const long long blocks = (long long)((g->V + kSingleForwardViews - 1) / kSingleForwardViews) * ((g->D + Dt - 1) / Dt);
     single_forward_kernel<T><<<(unsigned)blocks, kPlanThreads, 0, s>>>(u, static_cast<const Q*>(ws), ep);
     e = cudaGetLastError();
@@ -538,6 +681,7 @@ struct radon_plan {
     std::vector<Unit> units;
     std::vector<int> unit_item;
     std::vector<int> item_cfg;
+    std::vector<int> item_lanes;
     std::vector<Work> work;
     std::vector<long long> prefix;   // forward: texel offsets, n_units + 1
     Unit* d_units = nullptr;
@@ -576,7 +720,7 @@ std::vector<Work> build_work(const radon_plan* p, const std::vector<int>& sel) {
         const Unit& u = p->units[ui];
         int tiles;
         if (p->direction == 0) {
-            const int G = u.cfg, Dt = kPlanThreads / G;
+            const int G = u.cfg, Dt = kPlanThreads / (u.lanes * G);
             tiles = ((u.V + G - 1) / G) * ((u.D + Dt - 1) / Dt);
         } else {
             const int t = (u.n + kBwdTile - 1) / kBwdTile;
@@ -676,6 +820,39 @@ radon_status occupancy(radon_plan* p) {
     }
 }
 
+// Tuning cache: when RADON_TUNE_CACHE names a file, every tuned group's pick is appended to it as
+// one line "<key> <views> <lanes>" and later plans take a group's pick from the file (the last line
+// of a key wins) instead of timing its candidates.  The key is the direction, storage type, image
+// size and geometry kind -- the group the tuner times together.
+using TuneCache = std::map<std::string, std::pair<int, int>>;
+
+std::string tune_key(int direction, radon_dtype dt, int n, int fan) {
+    return "plan" + std::to_string(direction) + "_dt" + std::to_string((int)dt) + "_n" + std::to_string(n) +
+           (fan ? "_fan" : "_par");
+}
+
+TuneCache load_tune_cache() {
+    TuneCache c;
+    const char* path = std::getenv("RADON_TUNE_CACHE");
+    if (path == nullptr || path[0] == 0) return c;
+    std::FILE* f = std::fopen(path, "r");
+    if (f == nullptr) return c;
+    char key[128];
+    int v = 0, l = 0;
+    while (std::fscanf(f, "%127s %d %d", key, &v, &l) == 3) c[key] = {v, l};
+    std::fclose(f);
+    return c;
+}
+
+void store_tune_cache(const std::string& key, std::pair<int, int> pick) {
+    const char* path = std::getenv("RADON_TUNE_CACHE");
+    if (path == nullptr || path[0] == 0) return;
+    std::FILE* f = std::fopen(path, "a");   // one short line per append
+    if (f == nullptr) return;
+    std::fprintf(f, "%s %d %d\n", key.c_str(), pick.first, pick.second);
+    std::fclose(f);
+}
+
 // Times `reps` launches of the plan restricted to units `sel`; returns the median in ms.
 radon_status time_subset(radon_plan* p, const std::vector<int>& sel, float* ms) {
     const std::vector<Work> w = build_work(p, sel);
@@ -721,8 +898,10 @@ extern "C" RADON_API radon_status radon_batch_plan_create(const radon_item* item
     if (dtype != RADON_F32 && dtype != RADON_F16 && dtype != RADON_BF16)
         return fail(RADON_ERR_INVALID_ARG, "dtype must be RADON_F32, RADON_F16 or RADON_BF16");
     const int fv = options ? options->forward_views : 0, av = options ? options->adjoint_views : 0;
+    const int fl = options ? options->forward_lanes : 0;
     if (fv < 0 || (fv > 0 && fv != 1 && fv != 2 && fv != 4 && fv != 8))
         return fail(RADON_ERR_INVALID_ARG, "forward_views must be 0, 1, 2, 4 or 8");
+    if (fl != 0 && fl != 1 && fl != kPlanMaxLanes) return fail(RADON_ERR_INVALID_ARG, "forward_lanes must be 0, 1 or 4");
     if (av < 0 || (av > 0 && av != 4 && av != 8 && av != 16 && av != 32))
         return fail(RADON_ERR_INVALID_ARG, "adjoint_views must be 0, 4, 8, 16 or 32");
     const bool autotune = options == nullptr || options->autotune != 0;
@@ -751,6 +930,7 @@ extern "C" RADON_API radon_status radon_batch_plan_create(const radon_item* item
     p->dtype = dtype;
     p->device = dev;
     p->item_cfg.assign(n, 0);
+    p->item_lanes.assign(n, 0);
     for (int i = 0; i < n; ++i) {
         const radon_item& it = items[i];
         const radon_geometry* g = it.geometry;
@@ -771,7 +951,8 @@ extern "C" RADON_API radon_status radon_batch_plan_create(const radon_item* item
             u.ih2 = (float)(1.0 / (g->h * g->h));
             u.wd = g->bwd_window + 2;
             u.fan = g->fan;
-            u.cfg = direction == 0 ? (fv > 0 ? fv : 8) : (av > 0 ? av : 8);
+            u.cfg = direction == 0 ? (fv > 0 ? fv : 8) : (av > 0 ? av : kMaxChunkViews);
+            u.lanes = direction == 0 && fl > 0 ? fl : 1;
             p->units.push_back(u);
             p->unit_item.push_back(i);
             p->max_wd = std::max(p->max_wd, u.wd);
@@ -809,6 +990,7 @@ extern "C" RADON_API radon_status radon_batch_plan_create(const radon_item* item
                                                    " exceeds the shared memory of these detector windows");
         }
         p->smem = adj_smem_bytes(std::max(p->max_wd, 1), p->cap);
+        for (Unit& u : p->units) u.cfg = std::min(u.cfg, p->cap);   // the default chunk where it fits
     }
     if (nu > 0) {
         if (cudaMalloc(&p->d_units, nu * sizeof(Unit)) != cudaSuccess ||
@@ -828,29 +1010,51 @@ extern "C" RADON_API radon_status radon_batch_plan_create(const radon_item* item
         }
         st = occupancy(p);
         if (st == RADON_OK) st = upload_units(p);
-        // Autotuner: per image size, time each candidate tile shape on that size's units alone.
-        const bool fixed = direction == 0 ? fv > 0 : av > 0;
+        // Autotuner: per image size (and geometry kind), time each candidate shape on that group's
+        // units alone -- forward: views per ray block x lanes per ray, adjoint: views per chunk --
+        // unless the options fix it; a tuning cache (RADON_TUNE_CACHE) answers groups tuned before.
+        const bool fixed = direction == 0 ? (fv > 0 && fl > 0) : av > 0;
         if (st == RADON_OK && autotune && !fixed) {
-            static const int kFwdCand[4] = {8, 4, 2, 1};
-            static const int kAdjCand[4] = {4, 8, 16, 32};
-            const int* cand = direction == 0 ? kFwdCand : kAdjCand;
-            const int nc = direction == 0 ? 4 : (p->cap >= 32 ? 4 : 3);
-            std::map<int, std::vector<int>> by_size;
-            for (size_t k = 0; k < nu; ++k) by_size[p->units[k].n].push_back((int)k);
-            for (auto& kv : by_size) {
-                float best = 3.0e38f;
-                int best_c = cand[0];
-                for (int c = 0; c < nc && st == RADON_OK; ++c) {
-                    for (int k : kv.second) p->units[k].cfg = cand[c];
-                    st = upload_units(p);
-                    float ms = 0.f;
-                    if (st == RADON_OK) st = time_subset(p, kv.second, &ms);
-                    if (st == RADON_OK && ms < best) {
-                        best = ms;
-                        best_c = cand[c];
+            std::vector<std::pair<int, int>> cand;   // (views, lanes)
+            if (direction == 0) {
+                for (int G : {8, 4, 2, 1})
+                    for (int lanes : {1, kPlanMaxLanes})
+                        if ((fv == 0 || G == fv) && (fl == 0 || lanes == fl)) cand.emplace_back(G, lanes);
+            } else {
+                for (int cv : {4, 8, 16, 32})
+                    if (cv <= p->cap) cand.emplace_back(cv, 1);
+            }
+            std::map<std::pair<int, int>, std::vector<int>> groups;   // (n, fan) -> units
+            for (size_t k = 0; k < nu; ++k) groups[{p->units[k].n, p->units[k].fan}].push_back((int)k);
+            const TuneCache cache = load_tune_cache();
+            for (auto& kv : groups) {
+                const std::string key = tune_key(direction, dtype, kv.first.first, kv.first.second);
+                auto hit = cache.find(key);
+                std::pair<int, int> best_c = cand[0];
+                if (hit != cache.end() &&
+                    std::find(cand.begin(), cand.end(), hit->second) != cand.end()) {
+                    best_c = hit->second;
+                } else {
+                    float best = 3.0e38f;
+                    for (size_t c = 0; c < cand.size() && st == RADON_OK; ++c) {
+                        for (int k : kv.second) {
+                            p->units[k].cfg = cand[c].first;
+                            p->units[k].lanes = cand[c].second;
+                        }
+                        st = upload_units(p);
+                        float ms = 0.f;
+                        if (st == RADON_OK) st = time_subset(p, kv.second, &ms);
+                        if (st == RADON_OK && ms < best) {
+                            best = ms;
+                            best_c = cand[c];
+                        }
                     }
+                    if (st == RADON_OK) store_tune_cache(key, best_c);
                 }
-                for (int k : kv.second) p->units[k].cfg = best_c;
+                for (int k : kv.second) {
+                    p->units[k].cfg = best_c.first;
+                    p->units[k].lanes = best_c.second;
+                }
             }
             if (st == RADON_OK) st = upload_units(p);
         }
@@ -865,7 +1069,10 @@ extern "C" RADON_API radon_status radon_batch_plan_create(const radon_item* item
         free_plan(p);
         return st;
     }
-    for (size_t k = 0; k < nu; ++k) p->item_cfg[p->unit_item[k]] = p->units[k].cfg;
+    for (size_t k = 0; k < nu; ++k) {
+        p->item_cfg[p->unit_item[k]] = p->units[k].cfg;
+        p->item_lanes[p->unit_item[k]] = p->units[k].lanes;
+    }
     *out = p;
     return RADON_OK;
 }
@@ -895,6 +1102,15 @@ extern "C" RADON_API radon_status radon_batch_plan_item_config(const radon_plan*
     if (item < 0 || item >= (int)p->item_cfg.size() || views == nullptr)
         return fail(RADON_ERR_INVALID_ARG, "item out of range or views is NULL");
     *views = p->item_cfg[item];
+    return RADON_OK;
+}
+
+extern "C" RADON_API radon_status radon_batch_plan_item_shape(const radon_plan* p, int item, int* views, int* lanes) {
+    if (p == nullptr || p->magic != kPlanMagic) return fail(RADON_ERR_INVALID_ARG, "plan is not a live plan");
+    if (item < 0 || item >= (int)p->item_cfg.size() || views == nullptr || lanes == nullptr)
+        return fail(RADON_ERR_INVALID_ARG, "item out of range or NULL output");
+    *views = p->item_cfg[item];
+    *lanes = p->item_lanes[item];
     return RADON_OK;
 }
 

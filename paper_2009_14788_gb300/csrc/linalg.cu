@@ -1,6 +1,7 @@
 // Vector kernels of the iterative reconstruction (Section 4.2: Landweber iteration with its step
 // size from the power method): a deterministic inner product, a scaled add / cast, and the power
 // iteration itself, sequenced on the device so that the eigenvalue estimate never leaves it.
+#include <algorithm>
 #include <cmath>
 #include <string>
 
@@ -199,7 +200,7 @@ PowerLayout power_layout(const radon_geometry* g) {
     L.w = align_up(L.z + img, 256);
     L.t = align_up(L.w + img, 256);
     L.fws = align_up(L.t + sino, 256);
-    L.fws_bytes = packed_image_bytes(g->n, 1, RADON_F32);
+    L.fws_bytes = std::max(packed_image_bytes(g->n, 1, RADON_F32), single_forward_workspace_bytes(g, RADON_F32));
     L.bws = align_up(L.fws + L.fws_bytes, 256);
     L.bws_bytes = packed_sino_bytes(g->V, g->D, 1, backward_packed_images_per_cta(g, 1, RADON_F32, nullptr), RADON_F32);
     L.partial = align_up(L.bws + L.bws_bytes, 256);
@@ -382,7 +383,8 @@ CgneLayout cgne_layout(const radon_geometry* g, int batch) {
     L.s = align_up(L.q + sino, 256);
     L.p = align_up(L.s + img, 256);
     L.fws = align_up(L.p + img, 256);
-    L.fws_bytes = packed_image_bytes(g->n, batch, RADON_F32);
+    L.fws_bytes = batch == 1 ? std::max(packed_image_bytes(g->n, 1, RADON_F32), single_forward_workspace_bytes(g, RADON_F32))
+                             : packed_image_bytes(g->n, batch, RADON_F32);
     L.bws = align_up(L.fws + L.fws_bytes, 256);
     L.bws_bytes = packed_sino_bytes(g->V, g->D, batch, backward_packed_images_per_cta(g, batch, RADON_F32, nullptr), RADON_F32);
     L.partial = align_up(L.bws + L.bws_bytes, 256);

@@ -386,11 +386,13 @@ class BatchPlan:
     ``[N, N]``) for ``direction="forward"`` and sinograms ``[B, V, D]`` for ``"adjoint"``, outputs
     the matching results, all contiguous CUDA tensors of one dtype on one device.  The plan keeps
     references to the tensors (their addresses are baked in) and writes the outputs at every
-    ``launch()``; creation autotunes the tile shapes per image size unless ``autotune=False`` or a
-    shape is given.  ``launch()`` is capturable in a CUDA graph.
+    ``launch()``; creation autotunes the shapes per image size unless ``autotune=False`` or the
+    shapes are given (forward: ``forward_views`` and ``forward_lanes``; adjoint: ``adjoint_views``);
+    ``RADON_TUNE_CACHE`` names a file that keeps the picks across plans.  ``launch()`` is capturable
+    in a CUDA graph.
     """
 
-    def __init__(self, items, direction="forward", autotune=True, forward_views=0, adjoint_views=0):
+    def __init__(self, items, direction="forward", autotune=True, forward_views=0, adjoint_views=0, forward_lanes=0):
         if direction not in ("forward", "adjoint"):
             raise ValueError("direction must be 'forward' or 'adjoint'")
         self._h = None
@@ -416,7 +418,7 @@ class BatchPlan:
             arr[k] = L.radon_item(geom.handle, inp.data_ptr(), out.data_ptr(), inp.numel() // (ishape[0] * ishape[1]))
             self._keep += [geom, inp, out]
         self.dtype = dtype if dtype is not None else torch.float32
-        opts = L.radon_plan_options(1 if autotune else 0, int(forward_views), int(adjoint_views))
+        opts = L.radon_plan_options(1 if autotune else 0, int(forward_views), int(adjoint_views), int(forward_lanes))
         h = ctypes.c_void_p()
         with torch.cuda.device(device if device is not None else torch.cuda.current_device()):
             st = L.radon_batch_plan_create(arr, len(items), 0 if direction == "forward" else 1, _DTYPES[self.dtype],
@@ -442,6 +444,13 @@ class BatchPlan:
         v = ctypes.c_int()
         L.check(L.radon_batch_plan_item_config(self._h, int(item), ctypes.byref(v)), "radon_batch_plan_item_config")
         return v.value
+
+    def item_shape(self, item: int) -> tuple[int, int]:
+        """(views per forward ray block or adjoint chunk, lanes per forward ray) of item ``item``."""
+        v, l = ctypes.c_int(), ctypes.c_int()
+        L.check(L.radon_batch_plan_item_shape(self._h, int(item), ctypes.byref(v), ctypes.byref(l)),
+                "radon_batch_plan_item_shape")
+        return v.value, l.value
 
     def close(self):
         if self._h is not None:

@@ -192,6 +192,9 @@ def test_batch_plan_rejects_bad_arguments_without_gpu():
     assert L.radon_batch_plan_create(items, 2, 0, 0, ctypes.byref(opts), ctypes.byref(out)) == L.RADON_ERR_INVALID_ARG
     opts = L.radon_plan_options(1, 0, 5)
     assert L.radon_batch_plan_create(items, 2, 1, 0, ctypes.byref(opts), ctypes.byref(out)) == L.RADON_ERR_INVALID_ARG
+    opts = L.radon_plan_options(1, 0, 0, 2)
+    assert L.radon_batch_plan_create(items, 2, 0, 0, ctypes.byref(opts), ctypes.byref(out)) == L.RADON_ERR_INVALID_ARG
+    assert "forward_lanes" in L.radon_last_error_message()
     bad = (L.radon_item * 1)(L.radon_item(None, p, p + 64, 1))
     assert L.radon_batch_plan_create(bad, 1, 0, 0, None, ctypes.byref(out)) == L.RADON_ERR_INVALID_ARG
     # a dead handle is refused by every plan call
@@ -200,6 +203,7 @@ def test_batch_plan_rejects_bad_arguments_without_gpu():
     assert L.radon_batch_plan_launch(None, None) == L.RADON_ERR_INVALID_ARG
     assert L.radon_batch_plan_get_info(None, ctypes.byref(info)) == L.RADON_ERR_INVALID_ARG
     assert L.radon_batch_plan_item_config(None, 0, ctypes.byref(v)) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_batch_plan_item_shape(None, 0, ctypes.byref(v), ctypes.byref(v)) == L.RADON_ERR_INVALID_ARG
     L.radon_batch_plan_destroy(None)
     L.radon_geometry_destroy(h)
 

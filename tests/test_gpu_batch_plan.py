@@ -79,19 +79,57 @@ def test_plan_matches_oracle(direction, dtype):
 
 @pytest.mark.parametrize("direction", ["forward", "adjoint"])
 def test_tile_shapes_do_not_change_a_bit(direction):
-    """Every candidate the autotuner may pick computes each output in the same order."""
-    gs, ins, outs, _ = _mixed(torch.float32, direction, seed=3)
-    results = []
-    for v in ((1, 2, 4, 8) if direction == "forward" else (4, 8, 16, 32)):
-        kw = dict(forward_views=v) if direction == "forward" else dict(adjoint_views=v)
-        plan = BatchPlan(list(zip(gs, ins, outs)), direction, autotune=False, **kw)
-        assert all(plan.item_config(k) == v for k in range(len(gs)))
-        plan.launch()
-        torch.cuda.synchronize()
-        results.append([o.clone() for o in outs])
-    for other in results[1:]:
-        for a, b in zip(results[0], other):
-            assert torch.equal(a, b)
+    """Every views-per-block (or chunk) candidate computes each output in the same order; the forward's
+    lanes per ray change only the order of a ray's partial sums (FP32 rounding)."""
+    gs, ins, outs, refs = _mixed(torch.float32, direction, seed=3)
+    by_lanes = {}
+    for lanes in ((1, 4) if direction == "forward" else (0,)):
+        results = []
+        for v in ((1, 2, 4, 8) if direction == "forward" else (4, 8, 16, 32)):
+            kw = dict(forward_views=v, forward_lanes=lanes) if direction == "forward" else dict(adjoint_views=v)
+            plan = BatchPlan(list(zip(gs, ins, outs)), direction, autotune=False, **kw)
+            assert all(plan.item_config(k) == v for k in range(len(gs)))
+            assert all(plan.item_shape(k) == (v, lanes if direction == "forward" else 1) for k in range(len(gs)))
+            plan.launch()
+            torch.cuda.synchronize()
+            results.append([o.clone() for o in outs])
+        for other in results[1:]:
+            for a, b in zip(results[0], other):
+                assert torch.equal(a, b)
+        by_lanes[lanes] = results[0]
+    if direction == "forward":
+        for a, b, r in zip(by_lanes[1], by_lanes[4], refs):
+            assert rel_l2(to_np(a), to_np(b)) <= 1e-6
+            assert rel_l2(to_np(b), r) <= TOL_F32
+
+
+def test_tuning_cache_records_and_reuses_the_picks(tmp_path, monkeypatch):
+    """With RADON_TUNE_CACHE set, a plan appends one pick per (direction, storage, size, kind) group
+    and a later plan of the same groups takes its shapes from the file."""
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("RADON_TUNE_CACHE", str(cache))
+    gs, ins, outs, refs = _mixed(torch.float32, "forward", seed=7)
+    first = BatchPlan(list(zip(gs, ins, outs)), "forward")
+    lines = cache.read_text().split("\n")
+    groups = {(g.n, g.kind) for g in gs}
+    assert len([l for l in lines if l.strip()]) == len(groups)
+    picks = [first.item_shape(k) for k in range(len(gs))]
+    # rewrite the cache with other (valid) picks: a new plan must follow the file, not retime
+    alt = {}
+    with open(cache, "w") as f:
+        for l in lines:
+            if l.strip():
+                key, v, ln = l.split()
+                nv, nl = (1 if int(v) != 1 else 2), (4 if int(ln) == 1 else 1)
+                alt[key] = (nv, nl)
+                f.write("%s %d %d\n" % (key, nv, nl))
+    second = BatchPlan(list(zip(gs, ins, outs)), "forward")
+    got = [second.item_shape(k) for k in range(len(gs))]
+    assert sorted(set(got)) == sorted(set(alt.values())) and got != picks
+    second.launch()
+    torch.cuda.synchronize()
+    for o, r in zip(outs, refs):
+        assert rel_l2(to_np(o), r) <= TOL_F32
 
 
 @pytest.mark.parametrize("direction", ["forward", "adjoint"])

@@ -49,7 +49,7 @@ def test_batch_one_is_the_plan_kernel(case, direction):
     if direction == "forward":
         inp = to_dev(phantoms(g.n, 1, seed=3))
         out_plan = torch.empty((1,) + g.sino_shape, device="cuda")
-        plan = BatchPlan([(g, inp, out_plan)], "forward", autotune=False, forward_views=8)
+        plan = BatchPlan([(g, inp, out_plan)], "forward", autotune=False, forward_views=8, forward_lanes=4)
         got = forward_raw(g, inp)
     else:
         inp = to_dev(np.random.default_rng(4).normal(size=(1,) + og.sino_shape))
