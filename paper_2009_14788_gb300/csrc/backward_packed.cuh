@@ -284,7 +284,9 @@ __global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasP
                 // view of item e is found by comparison (no division)
                 const int W = a.wd * OCT;
                 for (int e = tid; e < nv * W; e += NC) {
-                    const int vl = (e >= W) + (e >= 2 * W) + (e >= 3 * W);
+                    int vl = 0;
+#pragma unroll
+                    for (int m = 1; m < kBwdPViews; ++m) vl += e >= m * W;
                     const int rest = e - vl * W;
                     const int dl = rest >> LOG_OCT, o = rest & (OCT - 1);
                     const uint4 u = lds4u(slot_a + (uint32_t)vl * ystv + (uint32_t)(dl * BG * 2 + o * 16));
@@ -299,7 +301,9 @@ __global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasP
                 // re-base the landed rays on this tile, in place: one ray per thread
                 const int W = a.wd;
                 for (int e = tid; e < nv * W; e += NC) {
-                    const int vl = (e >= W) + (e >= 2 * W) + (e >= 3 * W);
+                    int vl = 0;
+#pragma unroll
+                    for (int m = 1; m < kBwdPViews; ++m) vl += e >= m * W;
                     const int dl = e - vl * W;
                     const int d = dlo_c[st * kBwdPViews + vl] + dl;
                     const uint32_t rec = rst_a + (uint32_t)vl * rstv + (uint32_t)dl * 32u;

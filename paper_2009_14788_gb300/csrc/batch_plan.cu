@@ -178,26 +178,33 @@ __device__ float plan_ray(const Unit& u, const typename Quad<T>::type* __restric
     const float dX = dXh + dXl, dY = dYh + dYl;
     const int p = u.n + 1;
     const typename Quad<T>::type* q = quads + u.q_off + (tr ? (long long)p * p : 0ll);
+    const unsigned last = (unsigned)p * (unsigned)p - 1u;
+    const float M = 12582912.0f;          // 1.5 * 2^23: x + M rounds x to the nearest integer
+    const unsigned magic = 0x4B400000u;   // the bit pattern of M
     float acc = 0.0f;
     for (int kb = 0; kb < nk; kb += 32) {
         const float kbf = (float)kb;
         const float qx = kbf * dXh, qy = kbf * dYh;   // exact products
         const float QX = floorf(qx), QY = floorf(qy);
-        const float sX = fmaf(kbf, dXl, fX0 + (qx - QX));
-        const float sY = fmaf(kbf, dYl, fY0 + (qy - QY));
+        const float sXm = fmaf(kbf, dXl, fX0 + (qx - QX)) - 0.5f;
+        const float sYm = fmaf(kbf, dYl, fY0 + (qy - QY)) - 0.5f;
         const int jb = J0 + (int)QX, ib = I0 + (int)QY;
+        // texel index of a sample: (ib + floor(ly) + 1) p + (jb + floor(lx) + 1), each floor taken as
+        // the nearest integer to (l - 1/2) through the magic constant, whose bias cancels modulo 2^32
+        // (at an exact integer either neighbour gives the same bilinear value)
+        const unsigned base = (unsigned)((ib + 1) * p + (jb + 1)) - magic * (unsigned)(p + 1);
         const int kend = min(nk - kb, 32);
+#pragma unroll 1   // unrolled loops measured slower (registers)
         for (int kk = sub; kk < kend; kk += lanes) {
-            const float lx = fmaf((float)kk, dX, sX), ly = fmaf((float)kk, dY, sY);
-            const float flx = floorf(lx), fly = floorf(ly);
-            // samples lie strictly inside the support box, so j, i are in [-1, n-1]; the clamps only
-            // absorb FP32 rounding at the box edge, where the far texel values are zero
-            const int j = min(max(jb + (int)flx, -1), u.n - 1), i = min(max(ib + (int)fly, -1), u.n - 1);
-            const float a = fminf(fmaxf(lx - (float)(j - jb), 0.0f), 1.0f);
-            const float b = fminf(fmaxf(ly - (float)(i - ib), 0.0f), 1.0f);
+            const float fxm = fmaf((float)kk, dX, sXm), fym = fmaf((float)kk, dY, sYm);
+            const float tx = fxm + M, ty = fym + M;
+            // samples lie strictly inside the support box, so every texel index is in range; FP32
+            // rounding within ~1e-5 px of the box edge may step one texel past the border, where the
+            // weight is ~0: the clamp keeps every read inside the texel array
+            const unsigned idx = min(__float_as_uint(ty) * (unsigned)p + __float_as_uint(tx) + base, last);
+            const float a = (fxm - (tx - M)) + 0.5f, b = (fym - (ty - M)) + 0.5f;   // fractions in [0, 1]
             float t[4];
-            const typename Quad<T>::type tex = __ldg(q + (long long)(i + 1) * p + (j + 1));   // one 8/16-byte load
-            Quad<T>::unpack(tex, t);
+            Quad<T>::unpack(__ldg(q + idx), t);   // one 8/16-byte load
             const float top = fmaf(a, t[1] - t[0], t[0]), bot = fmaf(a, t[3] - t[2], t[2]);
             acc += fmaf(b, bot - top, top);
         }
