@@ -57,6 +57,7 @@ struct Unit {
     int cfg;           // forward: views per ray block; adjoint: views per chunk
     int lanes;         // forward: lanes per ray (1 or 4)
     int fan;           // 1: fan beam (detector coordinate a ratio); 0: parallel (affine)
+    int cand3;         // adjoint, parallel beam: every pixel's candidate window holds at most 3 rays
 };
 
 struct Work {
@@ -407,7 +408,11 @@ __device__ void plan_adjoint_tile(const Unit& u, int tile, const AdjBuffers& b, 
 // per view (the same lattice index on every ray) and steps from one candidate ray to the next by
 // det_spacing * n.  Every lattice point within a pixel's 2 x 2 support lies inside the support box,
 // so it is a sample of its ray whenever the ray exists; rays outside the detector have zero values.
-template <typename T, int KW>
+// NC > 0: every candidate window [t - r, t + r] is shorter than NC rays and the staged window holds
+// at least NC, so each pixel steps through exactly NC rays from its first candidate (moved back
+// inside the window at its end), unrolled; rays beyond the pixel's support square carry weight zero
+// and add nothing.  NC = 0: a loop over the pixel's candidates.
+template <typename T, int KW, int NC>
 __device__ void plan_adjoint_tile_parallel(const Unit& u, int tile, const AdjBuffers& b, const Epilogue& ep,
                                            int* err) {
     const int tid = threadIdx.x;
@@ -469,7 +474,8 @@ __device__ void plan_adjoint_tile_parallel(const Unit& u, int tile, const AdjBuf
             const float t = fmaf(vf0.x, gx, fmaf(vf0.y, gy, vf0.z));
             // window-relative candidate range, clamped in FP32 (a non-finite coordinate still gives a
             // loop inside the window)
-            const int la = __float2int_ru(fmaxf(t - r, 0.0f)), lb = __float2int_rd(fminf(t + r, wd_last));
+            const int la0 = __float2int_ru(fmaxf(t - r, 0.0f));
+            const int la = NC > 0 ? min(la0, wd - NC) : la0;
             const float4 A = b.sh->ref[vl];
             const float4 bc = b.sh->bc[vl];
             const float2 dn = b.sh->dn[vl];
@@ -480,7 +486,8 @@ __device__ void plan_adjoint_tile_parallel(const Unit& u, int tile, const AdjBuf
             f32x2 r2 = f2_pack(fmaf(ka, A.z, fmaf(fla, dn.x, A.x) - px), fmaf(ka, A.w, fmaf(fla, dn.y, A.y) - py));
             const f32x2 st2 = f2_pack(A.z, A.w), dn2 = f2_pack(dn.x, dn.y);
             uint32_t ya = ys_a + (uint32_t)(vl * wd + la) * 4u;
-            for (int l = la; l <= lb; ++l, ya += 4u) {
+            // one candidate ray: its KW samples' weights against the pixel, times the ray's value
+            auto candidate = [&]() {
                 f32x2 s2 = r2;
                 float sx, sy;
                 f2_unpack(s2, &sx, &sy);
@@ -495,6 +502,14 @@ __device__ void plan_adjoint_tile_parallel(const Unit& u, int tile, const AdjBuf
                 asm volatile("ld.shared.f32 %0, [%1];" : "=f"(yv) : "r"(ya));
                 acc = fmaf(w, yv, acc);
                 r2 = f2_add(r2, dn2);
+                ya += 4u;
+            };
+            if constexpr (NC > 0) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) candidate();
+            } else {
+                const int lb = __float2int_rd(fminf(t + r, wd_last));
+                for (int l = la; l <= lb; ++l) candidate();
             }
         }
         __syncthreads();
@@ -523,19 +538,21 @@ __global__ void __launch_bounds__(kPlanThreads, 4) plan_adjoint_kernel(const Uni
         const Unit& u = units[w.unit];
         if (u.fan)
             plan_adjoint_tile<T, KW, true>(u, w.tile, b, Epilogue{1.0f, nullptr, 0.0f, nullptr}, err);
+        else if (u.cand3)
+            plan_adjoint_tile_parallel<T, KW, 3>(u, w.tile, b, Epilogue{1.0f, nullptr, 0.0f, nullptr}, err);
         else
-            plan_adjoint_tile_parallel<T, KW>(u, w.tile, b, Epilogue{1.0f, nullptr, 0.0f, nullptr}, err);
+            plan_adjoint_tile_parallel<T, KW, 0>(u, w.tile, b, Epilogue{1.0f, nullptr, 0.0f, nullptr}, err);
     }
 }
 
-// Single image (a batch-1 call): one CTA per tile, the unit passed by value.
-template <typename T, int KW, bool FAN>
+// Single image (a batch-1 call): one CTA per tile, the unit passed by value.  NC < 0: fan beam.
+template <typename T, int KW, int NC>
 __global__ void __launch_bounds__(kPlanThreads) single_adjoint_kernel(const Unit u, const Epilogue ep, int* err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    if constexpr (FAN)
+    if constexpr (NC < 0)
         plan_adjoint_tile<T, KW, true>(u, (int)blockIdx.x, adj_buffers(smem_raw, u.wd, u.cfg), ep, err);
     else
-        plan_adjoint_tile_parallel<T, KW>(u, (int)blockIdx.x, adj_buffers(smem_raw, u.wd, u.cfg), ep, err);
+        plan_adjoint_tile_parallel<T, KW, NC>(u, (int)blockIdx.x, adj_buffers(smem_raw, u.wd, u.cfg), ep, err);
 }
 
 size_t adj_smem_bytes(int max_wd, int cap) {
@@ -560,6 +577,18 @@ constexpr int kSingleForwardViews = 8;    // views per ray block (the plan's def
 constexpr int kSingleForwardLanes = 4;    // lanes per ray: one image's rays alone do not fill the GPU
 constexpr int kSingleAdjointViews = 32;   // views per staged chunk (the autotuner's pick at every size)
 
+// Parallel beam: whether every pixel's candidate window holds at most three rays, from the same
+// FP32 half width r = (|ax| + |ay|) / b0 + 0.01 the kernel computes (a window shorter than 3
+// holds at most 3 integers; 1.49 leaves room for its rounding), and the staged window at least 3.
+int three_candidates(const radon_geometry* g) {
+    if (g->fan || g->bwd_window + 2 < 3) return 0;
+    for (const ViewF& v : g->h_view) {
+        const float r = (std::fabs(v.ax) + std::fabs(v.ay)) / v.b0 + 0.01f;
+        if (!(r < 1.49f)) return 0;
+    }
+    return 1;
+}
+
 Unit single_unit(const radon_geometry* g, const void* in, void* out, int cfg) {
     Unit u;
     u.in = in;
@@ -577,6 +606,7 @@ Unit single_unit(const radon_geometry* g, const void* in, void* out, int cfg) {
     u.cfg = cfg;
     u.lanes = kSingleForwardLanes;
     u.fan = g->fan;
+    u.cand3 = three_candidates(g);
     return u;
 }
 
@@ -600,10 +630,10 @@ radon_status single_forward_t(const radon_geometry* g, const void* img, void* si
     return RADON_OK;
 }
 
-template <typename T, int KW, bool FAN>
+template <typename T, int KW, int NC>
 radon_status single_backward_tk(const Unit& u, long long tiles, size_t smem, const Epilogue& ep, int* err,
                                 cudaStream_t s) {
-    auto kern = single_adjoint_kernel<T, KW, FAN>;
+    auto kern = single_adjoint_kernel<T, KW, NC>;
     static size_t attr_bytes = 0;
     if (smem > attr_bytes) {
         const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -640,10 +670,13 @@ radon_status single_backward_t(const radon_geometry* g, const void* sino, void* 
     const long long tiles_x = (g->n + kBwdTile - 1) / kBwdTile;
     const long long tiles = tiles_x * tiles_x;
     if (g->fan)
-        return kw_needed <= 3 ? single_backward_tk<T, 3, true>(u, tiles, smem, ep, err, s)
-                              : single_backward_tk<T, 6, true>(u, tiles, smem, ep, err, s);
-    return kw_needed <= 3 ? single_backward_tk<T, 3, false>(u, tiles, smem, ep, err, s)
-                          : single_backward_tk<T, 6, false>(u, tiles, smem, ep, err, s);
+        return kw_needed <= 3 ? single_backward_tk<T, 3, -1>(u, tiles, smem, ep, err, s)
+                              : single_backward_tk<T, 6, -1>(u, tiles, smem, ep, err, s);
+    if (u.cand3)
+        return kw_needed <= 3 ? single_backward_tk<T, 3, 3>(u, tiles, smem, ep, err, s)
+                              : single_backward_tk<T, 6, 3>(u, tiles, smem, ep, err, s);
+    return kw_needed <= 3 ? single_backward_tk<T, 3, 0>(u, tiles, smem, ep, err, s)
+                          : single_backward_tk<T, 6, 0>(u, tiles, smem, ep, err, s);
 }
 
 }  // namespace
@@ -958,6 +991,7 @@ extern "C" RADON_API radon_status radon_batch_plan_create(const radon_item* item
             u.ih2 = (float)(1.0 / (g->h * g->h));
             u.wd = g->bwd_window + 2;
             u.fan = g->fan;
+            u.cand3 = direction == 1 ? three_candidates(g) : 0;
             u.cfg = direction == 0 ? (fv > 0 ? fv : 8) : (av > 0 ? av : kMaxChunkViews);
             u.lanes = direction == 0 && fl > 0 ? fl : 1;
             p->units.push_back(u);
