@@ -516,7 +516,9 @@ RADON_API radon_status radon_batch_plan_create(const radon_item* items, int n, i
 /*
  * Runs the plan on `stream`: resets the work counter, packs (forward), then one persistent kernel.
  * Allocates nothing, never synchronises; can be captured in a CUDA graph (replays read the items'
- * input buffers as they are at replay time).
+ * input buffers as they are at replay time).  A plan owns one work counter and (forward) one packed
+ * texel buffer, so launches of the same plan must be ordered on the GPU (one stream, or events
+ * between streams; graph replays of it likewise); concurrent use needs one plan per launch.
  */
 RADON_API radon_status radon_batch_plan_launch(radon_plan* plan, void* stream);
 

@@ -55,6 +55,11 @@ CASES = {
                           det_spacing=0.3, step=0.5),
     "parallel_coarse": dict(kind="parallel", n=60, angles=uniform_angles(9, math.pi) + 0.1, det_count=25,
                             det_spacing=3.1, step=1.9),
+    # a pixel's candidate window just under three rays wide at the diagonal views (2 sqrt(2) / 0.955
+    # = 2.96): the widest windows that the single-image adjoint's three-candidate stepping takes
+    "parallel_three_rays": dict(kind="parallel", n=50, angles=np.array([0.1, math.pi / 4, 0.9, 3 * math.pi / 4,
+                                                                         2.0, 2.6]),
+                                det_count=80, det_spacing=0.955),
 }
 
 
