@@ -502,6 +502,10 @@ typedef struct radon_plan_options {
                                 views of the widest detector window do not fit one CTA's shared memory) */
     int forward_lanes;       /* > 0: lanes per forward ray (1, or 4: the ray's samples interleaved over four
                                 lanes whose partial sums meet in a fixed shuffle tree) */
+    int forward_rows;        /* > 0: texel rows per slab of the staged forward (8, 16 or 32) */
+    int forward_kernel;      /* 0: the staged forward (image slabs copied into shared memory by bulk copies)
+                                where its bands fit, else the L1 gather; 1: staged (RADON_ERR_UNSUPPORTED if
+                                the bands do not fit); -1: the L1 gather (one texel load per sample) */
 } radon_plan_options;
 
 /*
@@ -534,6 +538,9 @@ RADON_API radon_status radon_batch_plan_item_config(const radon_plan* plan, int 
 /* The shape item i runs with: views per forward ray block or adjoint chunk, and lanes per forward ray
  * (1 for the adjoint). */
 RADON_API radon_status radon_batch_plan_item_shape(const radon_plan* plan, int item, int* views, int* lanes);
+
+/* Texel rows per slab of item i's staged forward (0 for the L1 gather and for adjoint plans). */
+RADON_API radon_status radon_batch_plan_item_rows(const radon_plan* plan, int item, int* rows);
 
 RADON_API void radon_batch_plan_destroy(radon_plan* plan);
 

@@ -107,6 +107,8 @@ class radon_plan_options(ctypes.Structure):
         ("forward_views", ctypes.c_int),
         ("adjoint_views", ctypes.c_int),
         ("forward_lanes", ctypes.c_int),
+        ("forward_rows", ctypes.c_int),
+        ("forward_kernel", ctypes.c_int),
     ]
 
 
@@ -180,6 +182,7 @@ _SIGNATURES = [
     ("radon_batch_plan_item_config", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("radon_batch_plan_item_shape", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    ("radon_batch_plan_item_rows", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("radon_batch_plan_destroy", None, [ctypes.c_void_p]),
     ("radon_probe_gather_ceiling", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     ("radon_probe_gather_ceiling_ex", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
@@ -364,6 +367,10 @@ def radon_batch_plan_item_config(plan, item, views_ptr):
 
 def radon_batch_plan_item_shape(plan, item, views_ptr, lanes_ptr):
     return _call("radon_batch_plan_item_shape", plan, item, views_ptr, lanes_ptr)
+
+
+def radon_batch_plan_item_rows(plan, item, rows_ptr):
+    return _call("radon_batch_plan_item_rows", plan, item, rows_ptr)
 
 
 def radon_batch_plan_destroy(plan):

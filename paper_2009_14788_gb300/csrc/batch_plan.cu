@@ -58,6 +58,10 @@ struct Unit {
     int lanes;         // forward: lanes per ray (1 or 4)
     int fan;           // 1: fan beam (detector coordinate a ratio); 0: parallel (affine)
     int cand3;         // adjoint, parallel beam: every pixel's candidate window holds at most 3 rays
+    const Int2* groups;   // forward, staged: view groups of one orientation class for G = cfg
+    int n_groups;
+    int R;                // forward, staged: texel rows per slab
+    int staged;           // forward: 1 = the staged kernel, 0 = the L1 gather
 };
 
 struct Work {
@@ -124,32 +128,13 @@ __device__ __forceinline__ T pix(const T* x, int n, int i, int j) {
     return (i >= 0 && i < n && j >= 0 && j < n) ? x[(long long)i * n + j] : from_f32<T>(0.0f);
 }
 
-// One thread per texel of every unit (both frames); `prefix[u]` = first texel of unit u.
-template <typename T>
-__global__ void __launch_bounds__(256) plan_pack_kernel(const Unit* __restrict__ units, const long long* __restrict__ prefix,
-                                                        int n_units, long long total,
-                                                        typename Quad<T>::type* __restrict__ quads) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
-        int lo = 0, hi = n_units - 1;   // last unit with prefix <= g
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (prefix[mid] <= g) lo = mid;
-            else hi = mid - 1;
-        }
-        const Unit& u = units[lo];
-        const T* x = static_cast<const T*>(u.in);
-        const long long p = (long long)u.n + 1;
-        long long e = g - prefix[lo];
-        const int frame = e >= p * p ? 1 : 0;
-        if (frame) e -= p * p;
-        const int i = (int)(e / p) - 1, j = (int)(e - (e / p) * p) - 1;
-        quads[g] = frame == 0 ? Quad<T>::make(pix(x, u.n, i, j), pix(x, u.n, i, j + 1), pix(x, u.n, i + 1, j),
-                                              pix(x, u.n, i + 1, j + 1))
-                              : Quad<T>::make(pix(x, u.n, j, i), pix(x, u.n, j + 1, i), pix(x, u.n, j, i + 1),
-                                              pix(x, u.n, j + 1, i + 1));
-    }
-}
+}  // namespace
+}  // namespace radon
+
+#include "staged_forward.cuh"
+
+namespace radon {
+namespace {
 
 // ------------------------------------------------------------------------------------- forward
 
@@ -177,9 +162,9 @@ __device__ float plan_ray(const Unit& u, const typename Quad<T>::type* __restric
     const float dXh = tr ? ray.dyh : ray.dxh, dYh = tr ? ray.dxh : ray.dyh;
     const float dXl = tr ? ray.dyl : ray.dxl, dYl = tr ? ray.dxl : ray.dyl;
     const float dX = dXh + dXl, dY = dYh + dYl;
-    const int p = u.n + 1;
-    const typename Quad<T>::type* q = quads + u.q_off + (tr ? (long long)p * p : 0ll);
-    const unsigned last = (unsigned)p * (unsigned)p - 1u;
+    const int p = sq_pitch(u.n);
+    const typename Quad<T>::type* q = quads + u.q_off + (tr ? sq_frame(u.n) : 0ll);
+    const unsigned last = (unsigned)sq_frame(u.n) - 1u;
     const float M = 12582912.0f;          // 1.5 * 2^23: x + M rounds x to the nearest integer
     const unsigned magic = 0x4B400000u;   // the bit pattern of M
     float acc = 0.0f;
@@ -190,10 +175,10 @@ __device__ float plan_ray(const Unit& u, const typename Quad<T>::type* __restric
         const float sXm = fmaf(kbf, dXl, fX0 + (qx - QX)) - 0.5f;
         const float sYm = fmaf(kbf, dYl, fY0 + (qy - QY)) - 0.5f;
         const int jb = J0 + (int)QX, ib = I0 + (int)QY;
-        // texel index of a sample: (ib + floor(ly) + 1) p + (jb + floor(lx) + 1), each floor taken as
+        // texel index of a sample: (ib + floor(ly) + 2) p + (jb + floor(lx) + 2), each floor taken as
         // the nearest integer to (l - 1/2) through the magic constant, whose bias cancels modulo 2^32
         // (at an exact integer either neighbour gives the same bilinear value)
-        const unsigned base = (unsigned)((ib + 1) * p + (jb + 1)) - magic * (unsigned)(p + 1);
+        const unsigned base = (unsigned)((ib + 2) * p + (jb + 2)) - magic * (unsigned)(p + 1);
         const int kend = min(nk - kb, 32);
 #pragma unroll 1   // unrolled loops measured slower (registers)
         for (int kk = sub; kk < kend; kk += lanes) {
@@ -272,23 +257,6 @@ __global__ void __launch_bounds__(kPlanThreads) plan_forward_kernel(const Unit* 
 }
 
 // Single image (a batch-1 call): the same work items, one CTA each, the unit passed by value.
-template <typename T>
-__global__ void __launch_bounds__(256) single_pack_kernel(const Unit u, typename Quad<T>::type* __restrict__ quads) {
-    const T* x = static_cast<const T*>(u.in);
-    const long long p = (long long)u.n + 1, total = 2 * p * p;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
-        long long e = g;
-        const int frame = e >= p * p ? 1 : 0;
-        if (frame) e -= p * p;
-        const int i = (int)(e / p) - 1, j = (int)(e - (e / p) * p) - 1;
-        quads[g] = frame == 0 ? Quad<T>::make(pix(x, u.n, i, j), pix(x, u.n, i, j + 1), pix(x, u.n, i + 1, j),
-                                              pix(x, u.n, i + 1, j + 1))
-                              : Quad<T>::make(pix(x, u.n, j, i), pix(x, u.n, j + 1, i), pix(x, u.n, j, i + 1),
-                                              pix(x, u.n, j + 1, i + 1));
-    }
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kPlanThreads) single_forward_kernel(const Unit u,
                                                                       const typename Quad<T>::type* __restrict__ quads,
@@ -589,6 +557,114 @@ int three_candidates(const radon_geometry* g) {
     return 1;
 }
 
+// ---- staged forward: view groups, band bounds, ring shape
+
+constexpr uint32_t kSfSpinLimit = 1u << 22;   // bounded mbarrier polls (~seconds) before giving up
+
+int group_index(int G) { return G >= 8 ? 3 : G >= 4 ? 2 : G >= 2 ? 1 : 0; }
+
+// The unit's view groups for G views per work item (groups of one orientation class).
+void set_groups(Unit& u, const radon_geometry* g, int G) {
+    const int gi = group_index(G);
+    u.groups = g->d_groups + g->group_offset[gi];
+    u.n_groups = g->group_count[gi];
+}
+
+// Upper bound of the staged forward's band width (texel columns) over every work item and slab of
+// geometry g with G views x Dt detectors per item and R rows per slab.  Within one slab's rows
+// [y0, y1] the band spans max_l x_l - min_l x_l over the item's extreme-ray lines l; the spread
+// max_l x_l(y) - min_l x_l(y) is convex in y, so it is largest at the first or last row any slab
+// reaches, and moving within the slab adds at most max |slope| (y1 - y0).  Adds the kernel's margins
+// (2 columns each side, floor / ceil, alignment) and slack for its FP32 line evaluation; lines that
+// run nearly along the rows count as the whole support.  Cached per geometry and shape.
+int staged_band_bound(const radon_geometry* gc, int G, int Dt, int R) {
+    radon_geometry* g = const_cast<radon_geometry*>(gc);   // the cache is guarded by band_mu
+    const long long key = (1LL << 62) | ((long long)G << 40) | ((long long)Dt << 20) | (long long)R;
+    std::lock_guard<std::mutex> lock(g->band_mu);
+    auto it = g->band_width.find(key);
+    if (it != g->band_width.end()) return it->second;
+    const int gi = group_index(G);
+    const int n_slabs = (g->n + 3 + R - 1) / R;
+    const double y_top = -3.0, y_bot = -2.0 + (double)n_slabs * R + 1.0;
+    const int n_dr = (g->D + Dt - 1) / Dt;
+    const double cap = g->n + 14.0;
+    double maxw = 0.0;
+    for (int q = 0; q < g->group_count[gi] && maxw < cap; ++q) {
+        const Int2 grp = g->h_groups[g->group_offset[gi] + q];
+        const int v0 = grp.x, cnt = grp.y & 0xffff, cls = grp.y >> 16;
+        for (int dr = 0; dr < n_dr && maxw < cap; ++dr) {
+            const int d0 = dr * Dt, d1 = std::min(d0 + Dt - 1, g->D - 1);
+            double lo_t = 1e300, hi_t = -1e300, lo_b = 1e300, hi_b = -1e300, maxsl = 0.0;
+            bool flat = false;
+            for (int vl = 0; vl < cnt && !flat; ++vl) {
+                for (int e = 0; e < 2; ++e) {
+                    const RayT& r = g->h_ray[(size_t)(v0 + vl) * g->D + (e ? d1 : d0)];
+                    const double X0 = cls ? (double)r.I0 + r.fy0 : (double)r.J0 + r.fx0;
+                    const double Y0 = cls ? (double)r.J0 + r.fx0 : (double)r.I0 + r.fy0;
+                    const double dX = cls ? (double)r.dyh + r.dyl : (double)r.dxh + r.dxl;
+                    const double dY = cls ? (double)r.dxh + r.dxl : (double)r.dyh + r.dyl;
+                    if (std::fabs(dY) <= 1e-4 * std::fabs(dX)) {
+                        flat = true;
+                        break;
+                    }
+                    const double sl = dX / dY;
+                    const double xt = X0 + (y_top - Y0) * sl, xb = X0 + (y_bot - Y0) * sl;
+                    lo_t = std::min(lo_t, xt);
+                    hi_t = std::max(hi_t, xt);
+                    lo_b = std::min(lo_b, xb);
+                    hi_b = std::max(hi_b, xb);
+                    maxsl = std::max(maxsl, std::fabs(sl));
+                }
+            }
+            const double w = flat ? cap : std::max(hi_t - lo_t, hi_b - lo_b) + maxsl * (R + 2) + 12.0;
+            maxw = std::max(maxw, std::min(w, cap));
+        }
+    }
+    int w = (int)std::ceil(maxw);
+    w += w & 1;   // even: whole 16-byte blocks of 8-byte texels
+    g->band_width[key] = w;
+    return w;
+}
+
+// Ring of the staged forward for bands of `wbox` texels and `rmax` rows: the most stages (2..4)
+// that keep 3 CTAs per SM, else 2 CTAs, else 1; ok = false when not even 2 stages fit one CTA.
+struct StagedRing {
+    bool ok;
+    int stages;
+    size_t smem;
+};
+
+StagedRing staged_ring(int wbox, int rmax, int qb) {
+    constexpr size_t kSmPool = 228 * 1024, kPerCta = 1024, kCtaMax = 227 * 1024;
+    for (int ctas : {3, 2, 1})
+        for (int st = kSfMaxStages; st >= 2; --st) {
+            const size_t smem = sf_smem_bytes(rmax, wbox, qb, st);
+            if (smem <= kCtaMax && (size_t)ctas * (smem + kPerCta) <= kSmPool) return StagedRing{true, st, smem};
+        }
+    return StagedRing{false, 0, 0};
+}
+
+// Raises kernel K's dynamic shared memory limit on the current device to `smem`, never lowering it:
+// plans of different shapes and the batch-1 calls share the kernels, and a launch needs the limit at
+// least as large as its own request.  Not thread-safe, like the other attribute caches here.
+template <auto K>
+cudaError_t raise_smem_attr(size_t smem) {
+    static size_t attr_bytes[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    size_t& cur = attr_bytes[dev & 63];
+    if (smem <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) cur = smem;
+    return e;
+}
+
+template <typename T>
+cudaError_t staged_smem_attr(size_t smem) {
+    return raise_smem_attr<staged_forward_kernel<T>>(smem);
+}
+
 Unit single_unit(const radon_geometry* g, const void* in, void* out, int cfg) {
     Unit u;
     u.in = in;
@@ -607,6 +683,9 @@ Unit single_unit(const radon_geometry* g, const void* in, void* out, int cfg) {
     u.lanes = kSingleForwardLanes;
     u.fan = g->fan;
     u.cand3 = three_candidates(g);
+    u.R = 0;
+    u.staged = 0;
+    set_groups(u, g, cfg);
     return u;
 }
 
@@ -615,14 +694,16 @@ radon_status single_forward_t(const radon_geometry* g, const void* img, void* si
                               cudaStream_t s) {
     using Q = typename Quad<T>::type;
     const Unit u = single_unit(g, img, sino, kSingleForwardViews);
-    const long long texels = 2LL * (g->n + 1) * (g->n + 1);
+    const long long texels = 2 * sq_frame(g->n);
     const unsigned pack_blocks = (unsigned)std::min<long long>((texels + 255) / 256, 152LL * 64);
-    single_pack_kernel<T><<<pack_blocks, 256, 0, s>>>(u, static_cast<Q*>(ws));
+    sq_pack_single_kernel<T><<<pack_blocks, 256, 0, s>>>(static_cast<const T*>(img), g->n, static_cast<Q*>(ws));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "single-image pack launch");
     count_launches(1);
-    const int Dt = kPlanThreads / (kSingleForwardLanes * kSingleForwardViews);
-    const long long blocks = (long long)((g->V + kSingleForwardViews - 1) / kSingleForwardViews) * ((g->D + Dt - 1) / Dt);
+    // every sample one texel load through L1, four lanes per ray: a single image's rays alone fill
+    // the GPU only thinly, and the staged kernel measured slower here (512^2, 60 views: 0.39 vs 0.09 ms)
+    const int Dl = kPlanThreads / (kSingleForwardLanes * kSingleForwardViews);
+    const long long blocks = (long long)((g->V + kSingleForwardViews - 1) / kSingleForwardViews) * ((g->D + Dl - 1) / Dl);
     single_forward_kernel<T><<<(unsigned)blocks, kPlanThreads, 0, s>>>(u, static_cast<const Q*>(ws), ep);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "single-image forward launch");
@@ -634,12 +715,8 @@ template <typename T, int KW, int NC>
 radon_status single_backward_tk(const Unit& u, long long tiles, size_t smem, const Epilogue& ep, int* err,
                                 cudaStream_t s) {
     auto kern = single_adjoint_kernel<T, KW, NC>;
-    static size_t attr_bytes = 0;
-    if (smem > attr_bytes) {
-        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "single-image adjoint shared memory");
-        attr_bytes = smem;
-    }
+    const cudaError_t ea = raise_smem_attr<single_adjoint_kernel<T, KW, NC>>(smem);
+    if (ea != cudaSuccess) return cuda_fail(ea, "single-image adjoint shared memory");
     kern<<<(unsigned)tiles, kPlanThreads, smem, s>>>(u, ep, err);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "single-image adjoint launch");
@@ -682,8 +759,7 @@ radon_status single_backward_t(const radon_geometry* g, const void* sino, void* 
 }  // namespace
 
 size_t single_forward_workspace_bytes(const radon_geometry* g, radon_dtype dt) {
-    const size_t p = (size_t)g->n + 1;
-    return 2 * p * p * texel_bytes(dt);
+    return 2 * (size_t)sq_frame(g->n) * texel_bytes(dt);
 }
 
 radon_status launch_forward_single(const radon_geometry* g, const void* img, void* sino, radon_dtype dt, void* ws,
@@ -722,6 +798,11 @@ struct radon_plan {
     std::vector<int> unit_item;
     std::vector<int> item_cfg;
     std::vector<int> item_lanes;
+    std::vector<int> item_rows;
+    std::vector<const radon_geometry*> unit_geom;
+    bool staged_ok = false;     // forward: the staged kernel may serve units (its ring fits)
+    int wbox = 0, rmax = 0, stages = 0, ctas_staged = 0;
+    int n_work_staged = 0;      // forward: the work list's first n_work_staged items run the staged kernel
     std::vector<Work> work;
     std::vector<long long> prefix;   // forward: texel offsets, n_units + 1
     Unit* d_units = nullptr;
@@ -747,19 +828,29 @@ void free_plan(radon_plan* p) {
     delete p;
 }
 
-// Work list for `cfg` over the units in `sel`, largest work items first.
-std::vector<Work> build_work(const radon_plan* p, const std::vector<int>& sel) {
+// Work list over the units in `sel`, largest work items first: the staged kernel's units first (their
+// count in *n_staged), then the others.
+std::vector<Work> build_work(const radon_plan* p, const std::vector<int>& sel, int* n_staged) {
     std::vector<int> order(sel);
     auto cost = [&](int ui) -> double {
         const Unit& u = p->units[ui];
         return p->direction == 0 ? (double)u.n : (double)u.V;   // per work item
     };
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    auto staged = [&](int ui) { return p->direction == 0 && p->units[ui].staged != 0; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (staged(a) != staged(b)) return staged(a);
+        return cost(a) > cost(b);
+    });
     std::vector<Work> w;
+    *n_staged = 0;
     for (int ui : order) {
         const Unit& u = p->units[ui];
         int tiles;
-        if (p->direction == 0) {
+        if (staged(ui)) {
+            const int Dt = kSfConsumers / (u.lanes * u.cfg);
+            tiles = u.n_groups * ((u.D + Dt - 1) / Dt);
+            *n_staged += tiles;
+        } else if (p->direction == 0) {
             const int G = u.cfg, Dt = kPlanThreads / (u.lanes * G);
             tiles = ((u.V + G - 1) / G) * ((u.D + Dt - 1) / Dt);
         } else {
@@ -789,22 +880,36 @@ radon_status upload_units(radon_plan* p) {
 }
 
 template <typename T>
-radon_status launch_t(const radon_plan* p, const Work* d_work, int n_work, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned), s);
+// Runs the plan over the work list d_work (n_work items, the first n_staged of them staged-kernel
+// items): forward = pack, then the staged kernel and the L1 gather, each persistent over its items
+// with its own counter; adjoint = one persistent kernel.
+radon_status launch_t(const radon_plan* p, const Work* d_work, int n_work, int n_staged, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(p->d_counter, 0, 2 * sizeof(unsigned), s);
     if (e != cudaSuccess) return cuda_fail(e, "work counter reset");
     if (n_work == 0) return RADON_OK;
     using Q = typename Quad<T>::type;
     if (p->direction == 0) {
         const unsigned blocks = (unsigned)std::min<long long>((p->total_texels + 255) / 256, 152LL * 64);
-        plan_pack_kernel<T><<<blocks, 256, 0, s>>>(p->d_units, p->d_prefix, (int)p->units.size(), p->total_texels,
-                                                   static_cast<Q*>(p->d_quads));
+        sq_pack_kernel<T><<<blocks, 256, 0, s>>>(p->d_units, p->d_prefix, (int)p->units.size(), p->total_texels,
+                                                 static_cast<Q*>(p->d_quads));
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "plan pack launch");
-        plan_forward_kernel<T><<<p->ctas, kPlanThreads, 0, s>>>(p->d_units, d_work, n_work, p->d_counter,
-                                                               static_cast<const Q*>(p->d_quads));
+        if (n_staged > 0) {
+            int* err = device_error_word();
+            if (err == nullptr) return fail(RADON_ERR_CUDA, "device error word unavailable");
+            const SfArgs a{p->d_units, d_work, n_staged, p->d_counter, p->d_quads, p->wbox,
+                           sf_pitch(p->wbox, (int)sizeof(Q)), p->rmax, p->stages, err, kSfSpinLimit, identity_epilogue()};
+            staged_forward_kernel<T><<<p->ctas_staged, kSfThreads, p->smem, s>>>(a);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(e, "plan staged forward launch");
+            count_launches(1);
+        }
+        if (n_work > n_staged)
+            plan_forward_kernel<T><<<p->ctas, kPlanThreads, 0, s>>>(p->d_units, d_work + n_staged, n_work - n_staged,
+                                                                   p->d_counter + 1, static_cast<const Q*>(p->d_quads));
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "plan forward launch");
-        count_launches(2);
+        count_launches(n_work > n_staged ? 2 : 1);
     } else {
         int* err = device_error_word();
         if (err == nullptr) return fail(RADON_ERR_CUDA, "device error word unavailable");
@@ -821,11 +926,11 @@ radon_status launch_t(const radon_plan* p, const Work* d_work, int n_work, cudaS
     return RADON_OK;
 }
 
-radon_status launch_plan(const radon_plan* p, const Work* d_work, int n_work, cudaStream_t s) {
+radon_status launch_plan(const radon_plan* p, const Work* d_work, int n_work, int n_staged, cudaStream_t s) {
     switch (p->dtype) {
-        case RADON_F16: return launch_t<__half>(p, d_work, n_work, s);
-        case RADON_BF16: return launch_t<__nv_bfloat16>(p, d_work, n_work, s);
-        default: return launch_t<float>(p, d_work, n_work, s);
+        case RADON_F16: return launch_t<__half>(p, d_work, n_work, n_staged, s);
+        case RADON_BF16: return launch_t<__nv_bfloat16>(p, d_work, n_work, n_staged, s);
+        default: return launch_t<float>(p, d_work, n_work, n_staged, s);
     }
 }
 
@@ -833,21 +938,29 @@ template <typename T>
 radon_status occupancy_t(radon_plan* p) {
     int per_sm = 0;
     cudaError_t e;
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    if (p->direction == 0 && p->staged_ok && p->smem > 0) {   // the staged kernel at the current ring
+        int per_sm_s = 0;
+        e = staged_smem_attr<T>(p->smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, staged_forward_kernel<T>, kSfThreads, p->smem);
+        if (e != cudaSuccess) return cuda_fail(e, "plan occupancy query");
+        p->ctas_staged = std::max(1, per_sm_s) * sms;
+    }
     if (p->direction == 0) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_forward_kernel<T>, kPlanThreads, 0);
     } else if (p->kw == 3) {
-        e = cudaFuncSetAttribute(plan_adjoint_kernel<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
+        e = raise_smem_attr<plan_adjoint_kernel<T, 3>>(p->smem);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_adjoint_kernel<T, 3>, kPlanThreads, p->smem);
     } else {
-        e = cudaFuncSetAttribute(plan_adjoint_kernel<T, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
+        e = raise_smem_attr<plan_adjoint_kernel<T, 6>>(p->smem);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_adjoint_kernel<T, 6>, kPlanThreads, p->smem);
     }
     if (e != cudaSuccess) return cuda_fail(e, "plan occupancy query");
-    int sms = 0;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     p->ctas = std::max(1, per_sm) * sms;
     return RADON_OK;
 }
@@ -860,15 +973,23 @@ radon_status occupancy(radon_plan* p) {
     }
 }
 
-// Tuning cache: when RADON_TUNE_CACHE names a file, every tuned group's pick is appended to it as
-// one line "<key> <views> <lanes>" and later plans take a group's pick from the file (the last line
-// of a key wins) instead of timing its candidates.  The key is the direction, storage type, image
-// size and geometry kind -- the group the tuner times together.
-using TuneCache = std::map<std::string, std::pair<int, int>>;
+// A tuned shape: views per forward work item or adjoint chunk, lanes per forward ray, texel rows per
+// staged forward slab (0 for the L1 gather and the adjoint; rows > 0 selects the staged kernel).
+struct Shape {
+    int views, lanes, rows;
+    bool operator==(const Shape& o) const { return views == o.views && lanes == o.lanes && rows == o.rows; }
+};
 
-std::string tune_key(int direction, radon_dtype dt, int n, int fan) {
+// Tuning cache: when RADON_TUNE_CACHE names a file, every tuned group's pick is appended to it as
+// one line "<key> <views> <lanes> <rows>" and later plans take a group's pick from the file (the last
+// line of a key wins) instead of timing its candidates.  The key is the direction, storage type,
+// image size, geometry kind and forward kernel -- the group the tuner times together.
+using TuneCache = std::map<std::string, Shape>;
+
+std::string tune_key(int direction, radon_dtype dt, int n, int fan, int kernels) {
+    static const char* const names[3] = {"_gather", "_any", "_staged"};
     return "plan" + std::to_string(direction) + "_dt" + std::to_string((int)dt) + "_n" + std::to_string(n) +
-           (fan ? "_fan" : "_par");
+           (fan ? "_fan" : "_par") + (direction == 0 ? names[kernels + 1] : "");
 }
 
 TuneCache load_tune_cache() {
@@ -878,24 +999,67 @@ TuneCache load_tune_cache() {
     std::FILE* f = std::fopen(path, "r");
     if (f == nullptr) return c;
     char key[128];
-    int v = 0, l = 0;
-    while (std::fscanf(f, "%127s %d %d", key, &v, &l) == 3) c[key] = {v, l};
+    int v = 0, l = 0, r = 0;
+    while (std::fscanf(f, "%127s %d %d %d", key, &v, &l, &r) == 4) c[key] = Shape{v, l, r};
     std::fclose(f);
     return c;
 }
 
-void store_tune_cache(const std::string& key, std::pair<int, int> pick) {
+void store_tune_cache(const std::string& key, const Shape& pick) {
     const char* path = std::getenv("RADON_TUNE_CACHE");
     if (path == nullptr || path[0] == 0) return;
     std::FILE* f = std::fopen(path, "a");   // one short line per append
     if (f == nullptr) return;
-    std::fprintf(f, "%s %d %d\n", key.c_str(), pick.first, pick.second);
+    std::fprintf(f, "%s %d %d %d\n", key.c_str(), pick.views, pick.lanes, pick.rows);
     std::fclose(f);
 }
 
-// Times `reps` launches of the plan restricted to units `sel`; returns the median in ms.
+constexpr int kPlanForwardRows = 16;   // texel rows per staged slab by default
+
+// Forward shape of unit k (views per work item, lanes per ray; rows per slab > 0 = the staged kernel)
+// and its view groups.
+void set_forward_shape(radon_plan* p, int k, const Shape& sh) {
+    Unit& u = p->units[k];
+    u.cfg = sh.views;
+    u.lanes = sh.lanes;
+    u.staged = sh.rows > 0 ? 1 : 0;
+    u.R = sh.rows > 0 ? sh.rows : kPlanForwardRows;
+    set_groups(u, p->unit_geom[k], u.cfg);
+}
+
+// Staged forward over units `sel`: widest band, most rows and the ring they need (the plan's launch
+// shape); false when the ring does not fit one CTA's shared memory.
+bool staged_fit(radon_plan* p, const std::vector<int>& sel) {
+    int wbox = 2, rmax = 1;
+    for (int k : sel) {
+        const Unit& u = p->units[k];
+        if (!u.staged) continue;
+        const int Dt = kSfConsumers / (u.lanes * u.cfg);
+        wbox = std::max(wbox, staged_band_bound(p->unit_geom[k], u.cfg, Dt, u.R));
+        rmax = std::max(rmax, u.R);
+    }
+    const StagedRing ring = staged_ring(wbox, rmax, (int)texel_bytes(p->dtype));
+    if (!ring.ok) return false;
+    p->wbox = wbox;
+    p->rmax = rmax;
+    p->stages = ring.stages;
+    p->smem = ring.smem;
+    return true;
+}
+
+// Times `reps` launches of the plan restricted to units `sel`; returns the median in ms (3e38 for a
+// staged shape whose ring does not fit).
 radon_status time_subset(radon_plan* p, const std::vector<int>& sel, float* ms) {
-    const std::vector<Work> w = build_work(p, sel);
+    if (p->direction == 0 && p->staged_ok) {
+        if (!staged_fit(p, sel)) {
+            *ms = 3.0e38f;
+            return RADON_OK;
+        }
+        const radon_status so = occupancy(p);
+        if (so != RADON_OK) return so;
+    }
+    int n_staged = 0;
+    const std::vector<Work> w = build_work(p, sel, &n_staged);
     Work* d = nullptr;
     radon_status st = upload_work(w, &d);
     if (st != RADON_OK) return st;
@@ -905,7 +1069,7 @@ radon_status time_subset(radon_plan* p, const std::vector<int>& sel, float* ms) 
     std::vector<float> t;
     for (int r = 0; r < 4 && st == RADON_OK; ++r) {
         cudaEventRecord(e0, 0);
-        st = launch_plan(p, d, (int)w.size(), 0);
+        st = launch_plan(p, d, (int)w.size(), n_staged, 0);
         cudaEventRecord(e1, 0);
         if (st == RADON_OK && cudaEventSynchronize(e1) == cudaSuccess) {
             float x = 0.f;
@@ -939,9 +1103,13 @@ extern "C" RADON_API radon_status radon_batch_plan_create(const radon_item* item
         return fail(RADON_ERR_INVALID_ARG, "dtype must be RADON_F32, RADON_F16 or RADON_BF16");
     const int fv = options ? options->forward_views : 0, av = options ? options->adjoint_views : 0;
     const int fl = options ? options->forward_lanes : 0;
+    const int fr = options ? options->forward_rows : 0;
+    const int fk = options ? options->forward_kernel : 0;
     if (fv < 0 || (fv > 0 && fv != 1 && fv != 2 && fv != 4 && fv != 8))
         return fail(RADON_ERR_INVALID_ARG, "forward_views must be 0, 1, 2, 4 or 8");
     if (fl != 0 && fl != 1 && fl != kPlanMaxLanes) return fail(RADON_ERR_INVALID_ARG, "forward_lanes must be 0, 1 or 4");
+    if (fr != 0 && fr != 8 && fr != 16 && fr != 32) return fail(RADON_ERR_INVALID_ARG, "forward_rows must be 0, 8, 16 or 32");
+    if (fk < -1 || fk > 1) return fail(RADON_ERR_INVALID_ARG, "forward_kernel must be -1, 0 or 1");
     if (av < 0 || (av > 0 && av != 4 && av != 8 && av != 16 && av != 32))
         return fail(RADON_ERR_INVALID_ARG, "adjoint_views must be 0, 4, 8, 16 or 32");
     const bool autotune = options == nullptr || options->autotune != 0;
@@ -971,6 +1139,7 @@ extern "C" RADON_API radon_status radon_batch_plan_create(const radon_item* item
     p->device = dev;
     p->item_cfg.assign(n, 0);
     p->item_lanes.assign(n, 0);
+    p->item_rows.assign(n, 0);
     for (int i = 0; i < n; ++i) {
         const radon_item& it = items[i];
         const radon_geometry* g = it.geometry;
@@ -994,8 +1163,13 @@ extern "C" RADON_API radon_status radon_batch_plan_create(const radon_item* item
             u.cand3 = direction == 1 ? three_candidates(g) : 0;
             u.cfg = direction == 0 ? (fv > 0 ? fv : 8) : (av > 0 ? av : kMaxChunkViews);
             u.lanes = direction == 0 && fl > 0 ? fl : 1;
+            u.R = fr > 0 ? fr : kPlanForwardRows;
+            // the kernel before tuning: staged when asked for (or rows given), else the L1 gather
+            u.staged = direction == 0 && (fk == 1 || (fk == 0 && fr > 0)) ? 1 : 0;
+            set_groups(u, g, u.cfg);
             p->units.push_back(u);
             p->unit_item.push_back(i);
+            p->unit_geom.push_back(g);
             p->max_wd = std::max(p->max_wd, u.wd);
             if (direction == 1) {
                 // samples per candidate window: the window spans 2 (|dx|+|dy|)/h^2 <= 2 sqrt(2) / h
@@ -1014,11 +1188,21 @@ extern "C" RADON_API radon_status radon_batch_plan_create(const radon_item* item
     if (direction == 0) {
         p->prefix.assign(nu + 1, 0);
         for (size_t k = 0; k < nu; ++k) {
-            const long long q = (long long)(p->units[k].n + 1) * (p->units[k].n + 1);
             p->units[k].q_off = p->prefix[k];
-            p->prefix[k + 1] = p->prefix[k] + 2 * q;
+            p->prefix[k + 1] = p->prefix[k] + 2 * sq_frame(p->units[k].n);
         }
         p->total_texels = p->prefix[nu];
+        // the staged kernel may serve units unless refused; its ring must fit the units that start on it
+        std::vector<int> all(nu);
+        for (size_t k = 0; k < nu; ++k) all[k] = (int)k;
+        p->staged_ok = fk >= 0;
+        if (p->staged_ok && nu > 0 && !staged_fit(p, all)) {
+            if (fk == 1 || fr > 0) {
+                free_plan(p);
+                return fail(RADON_ERR_UNSUPPORTED, "the staged forward's bands do not fit shared memory");
+            }
+            p->staged_ok = false;
+        }
     } else {
         p->cap = adj_chunk_cap(std::max(p->max_wd, 1));
         if (p->cap == 0) {
@@ -1035,7 +1219,7 @@ extern "C" RADON_API radon_status radon_batch_plan_create(const radon_item* item
     }
     if (nu > 0) {
         if (cudaMalloc(&p->d_units, nu * sizeof(Unit)) != cudaSuccess ||
-            cudaMalloc(&p->d_counter, sizeof(unsigned)) != cudaSuccess ||
+            cudaMalloc(&p->d_counter, 2 * sizeof(unsigned)) != cudaSuccess ||
             (direction == 0 && (cudaMalloc(&p->d_prefix, (nu + 1) * sizeof(long long)) != cudaSuccess ||
                                 cudaMalloc(&p->d_quads, (size_t)p->total_texels * texel_bytes(dtype)) != cudaSuccess))) {
             cudaGetLastError();
@@ -1052,36 +1236,48 @@ extern "C" RADON_API radon_status radon_batch_plan_create(const radon_item* item
         st = occupancy(p);
         if (st == RADON_OK) st = upload_units(p);
         // Autotuner: per image size (and geometry kind), time each candidate shape on that group's
-        // units alone -- forward: views per ray block x lanes per ray, adjoint: views per chunk --
-        // unless the options fix it; a tuning cache (RADON_TUNE_CACHE) answers groups tuned before.
-        const bool fixed = direction == 0 ? (fv > 0 && fl > 0) : av > 0;
+        // units alone -- forward: views per work item x lanes per ray (x texel rows per slab for the
+        // staged kernel), adjoint: views per chunk -- unless the options fix it; a tuning cache
+        // (RADON_TUNE_CACHE) answers groups tuned before.
+        const bool fixed = direction == 0 ? (fv > 0 && fl > 0 && (fk != 1 || fr > 0)) : av > 0;
         if (st == RADON_OK && autotune && !fixed) {
-            std::vector<std::pair<int, int>> cand;   // (views, lanes)
+            std::vector<Shape> cand;
             if (direction == 0) {
-                for (int G : {8, 4, 2, 1})
-                    for (int lanes : {1, kPlanMaxLanes})
-                        if ((fv == 0 || G == fv) && (fl == 0 || lanes == fl)) cand.emplace_back(G, lanes);
+                // the L1 gather: views per ray block x lanes per ray
+                if (fk <= 0 && fr == 0)
+                    for (int G : {8, 4, 2, 1})
+                        for (int lanes : {1, kPlanMaxLanes})
+                            if ((fv == 0 || G == fv) && (fl == 0 || lanes == fl)) cand.push_back(Shape{G, lanes, 0});
+                // the staged kernel: views per item x rows per slab (one lane per ray unless asked: four
+                // lanes measured slower at every size)
+                if (p->staged_ok)
+                    for (int G : {8, 4, 2})
+                        for (int R : {16, 32})
+                            if ((fv == 0 || G == fv) && (fr == 0 || R == fr))
+                                cand.push_back(Shape{G, fl > 0 ? fl : 1, R});
             } else {
                 for (int cv : {4, 8, 16, 32})
-                    if (cv <= p->cap) cand.emplace_back(cv, 1);
+                    if (cv <= p->cap) cand.push_back(Shape{cv, 1, 0});
             }
             std::map<std::pair<int, int>, std::vector<int>> groups;   // (n, fan) -> units
             for (size_t k = 0; k < nu; ++k) groups[{p->units[k].n, p->units[k].fan}].push_back((int)k);
             const TuneCache cache = load_tune_cache();
+            auto apply = [&](const std::vector<int>& ks, const Shape& sh) {
+                for (int k : ks) {
+                    if (direction == 0) set_forward_shape(p, k, sh);
+                    else p->units[k].cfg = sh.views;
+                }
+            };
             for (auto& kv : groups) {
-                const std::string key = tune_key(direction, dtype, kv.first.first, kv.first.second);
+                const std::string key = tune_key(direction, dtype, kv.first.first, kv.first.second, fk);
                 auto hit = cache.find(key);
-                std::pair<int, int> best_c = cand[0];
-                if (hit != cache.end() &&
-                    std::find(cand.begin(), cand.end(), hit->second) != cand.end()) {
+                Shape best_c = cand[0];
+                if (hit != cache.end() && std::find(cand.begin(), cand.end(), hit->second) != cand.end()) {
                     best_c = hit->second;
                 } else {
                     float best = 3.0e38f;
                     for (size_t c = 0; c < cand.size() && st == RADON_OK; ++c) {
-                        for (int k : kv.second) {
-                            p->units[k].cfg = cand[c].first;
-                            p->units[k].lanes = cand[c].second;
-                        }
+                        apply(kv.second, cand[c]);
                         st = upload_units(p);
                         float ms = 0.f;
                         if (st == RADON_OK) st = time_subset(p, kv.second, &ms);
@@ -1092,18 +1288,31 @@ extern "C" RADON_API radon_status radon_batch_plan_create(const radon_item* item
                     }
                     if (st == RADON_OK) store_tune_cache(key, best_c);
                 }
-                for (int k : kv.second) {
-                    p->units[k].cfg = best_c.first;
-                    p->units[k].lanes = best_c.second;
-                }
+                apply(kv.second, best_c);
             }
             if (st == RADON_OK) st = upload_units(p);
+        }
+        if (st == RADON_OK && direction == 0 && p->staged_ok) {   // the staged launch of the whole plan
+            std::vector<int> all(nu);
+            for (size_t k = 0; k < nu; ++k) all[k] = (int)k;
+            if (!staged_fit(p, all)) {
+                // the size groups' picks together need more shared memory than one CTA has: the staged
+                // units fall back to the gather's default shape, unless the staged kernel was required
+                if (fk == 1) {
+                    st = fail(RADON_ERR_UNSUPPORTED, "the staged forward's bands do not fit shared memory");
+                } else {
+                    for (size_t k = 0; k < nu; ++k)
+                        if (p->units[k].staged) set_forward_shape(p, (int)k, Shape{8, 1, 0});
+                    st = upload_units(p);
+                }
+            }
+            if (st == RADON_OK) st = occupancy(p);
         }
     }
     if (st == RADON_OK) {
         std::vector<int> all(nu);
         for (size_t k = 0; k < nu; ++k) all[k] = (int)k;
-        p->work = build_work(p, all);
+        p->work = build_work(p, all, &p->n_work_staged);
         st = upload_work(p->work, &p->d_work);
     }
     if (st != RADON_OK) {
@@ -1113,6 +1322,7 @@ extern "C" RADON_API radon_status radon_batch_plan_create(const radon_item* item
     for (size_t k = 0; k < nu; ++k) {
         p->item_cfg[p->unit_item[k]] = p->units[k].cfg;
         p->item_lanes[p->unit_item[k]] = p->units[k].lanes;
+        p->item_rows[p->unit_item[k]] = direction == 0 && p->units[k].staged ? p->units[k].R : 0;
     }
     *out = p;
     return RADON_OK;
@@ -1125,7 +1335,7 @@ extern "C" RADON_API radon_status radon_batch_plan_launch(radon_plan* p, void* s
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev != p->device) return fail(RADON_ERR_INVALID_ARG, "plan lives on another device");
     if (p->units.empty()) return RADON_OK;
-    return launch_plan(p, p->d_work, (int)p->work.size(), (cudaStream_t)stream);
+    return launch_plan(p, p->d_work, (int)p->work.size(), p->n_work_staged, (cudaStream_t)stream);
 }
 
 extern "C" RADON_API radon_status radon_batch_plan_get_info(const radon_plan* p, radon_plan_info* info) {
@@ -1152,6 +1362,14 @@ extern "C" RADON_API radon_status radon_batch_plan_item_shape(const radon_plan* 
         return fail(RADON_ERR_INVALID_ARG, "item out of range or NULL output");
     *views = p->item_cfg[item];
     *lanes = p->item_lanes[item];
+    return RADON_OK;
+}
+
+extern "C" RADON_API radon_status radon_batch_plan_item_rows(const radon_plan* p, int item, int* rows) {
+    if (p == nullptr || p->magic != kPlanMagic) return fail(RADON_ERR_INVALID_ARG, "plan is not a live plan");
+    if (item < 0 || item >= (int)p->item_rows.size() || rows == nullptr)
+        return fail(RADON_ERR_INVALID_ARG, "item out of range or rows is NULL");
+    *rows = p->item_rows[item];
     return RADON_OK;
 }
 

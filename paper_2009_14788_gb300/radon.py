@@ -387,12 +387,15 @@ class BatchPlan:
     the matching results, all contiguous CUDA tensors of one dtype on one device.  The plan keeps
     references to the tensors (their addresses are baked in) and writes the outputs at every
     ``launch()``; creation autotunes the shapes per image size unless ``autotune=False`` or the
-    shapes are given (forward: ``forward_views`` and ``forward_lanes``; adjoint: ``adjoint_views``);
+    shapes are given (forward: ``forward_views``, ``forward_lanes`` and, for the staged kernel,
+    ``forward_rows``; adjoint: ``adjoint_views``).  ``forward_kernel``: ``"auto"`` (the staged kernel
+    where its bands fit shared memory, else the L1 gather), ``"staged"`` or ``"gather"``.
     ``RADON_TUNE_CACHE`` names a file that keeps the picks across plans.  ``launch()`` is capturable
     in a CUDA graph.
     """
 
-    def __init__(self, items, direction="forward", autotune=True, forward_views=0, adjoint_views=0, forward_lanes=0):
+    def __init__(self, items, direction="forward", autotune=True, forward_views=0, adjoint_views=0, forward_lanes=0,
+                 forward_rows=0, forward_kernel="auto"):
         if direction not in ("forward", "adjoint"):
             raise ValueError("direction must be 'forward' or 'adjoint'")
         self._h = None
@@ -418,7 +421,11 @@ class BatchPlan:
             arr[k] = L.radon_item(geom.handle, inp.data_ptr(), out.data_ptr(), inp.numel() // (ishape[0] * ishape[1]))
             self._keep += [geom, inp, out]
         self.dtype = dtype if dtype is not None else torch.float32
-        opts = L.radon_plan_options(1 if autotune else 0, int(forward_views), int(adjoint_views), int(forward_lanes))
+        kernels = {"auto": 0, "staged": 1, "gather": -1}
+        if forward_kernel not in kernels:
+            raise ValueError("forward_kernel must be 'auto', 'staged' or 'gather'")
+        opts = L.radon_plan_options(1 if autotune else 0, int(forward_views), int(adjoint_views), int(forward_lanes),
+                                    int(forward_rows), kernels[forward_kernel])
         h = ctypes.c_void_p()
         with torch.cuda.device(device if device is not None else torch.cuda.current_device()):
             st = L.radon_batch_plan_create(arr, len(items), 0 if direction == "forward" else 1, _DTYPES[self.dtype],
@@ -451,6 +458,12 @@ class BatchPlan:
         L.check(L.radon_batch_plan_item_shape(self._h, int(item), ctypes.byref(v), ctypes.byref(l)),
                 "radon_batch_plan_item_shape")
         return v.value, l.value
+
+    def item_rows(self, item: int) -> int:
+        """Texel rows per slab of item ``item`` (staged forward; 0 for the L1 gather and the adjoint)."""
+        r = ctypes.c_int()
+        L.check(L.radon_batch_plan_item_rows(self._h, int(item), ctypes.byref(r)), "radon_batch_plan_item_rows")
+        return r.value
 
     def close(self):
         if self._h is not None:

@@ -318,13 +318,14 @@ def test_orientation_major_axis_step_is_nonnegative():
 
 
 def test_forward_workspace_covers_the_single_image_texels():
-    """A batch-1 forward packs the image's 2 x 2 quad texels (both frames, one-pixel border) into the
-    workspace: (N + 1)^2 texels twice, 16 bytes each for FP32, 8 for 16-bit storage; larger batches
-    keep the batch-interleaved size."""
+    """A batch-1 forward packs the image's 2 x 2 quad texels (both frames, two texels of border, an
+    even row pitch of at least N + 4) into the workspace: (N + 3) rows of that pitch twice, 16 bytes
+    each for FP32, 8 for 16-bit storage; larger batches keep the batch-interleaved size."""
     for n in (1, 40, 97):
         g = Geometry("parallel", n, uniform_angles(5, math.pi), host_only=True)
         for dt, texel in ((L.RADON_F32, 16), (L.RADON_F16, 8), (L.RADON_BF16, 8)):
             one = int(L.radon_forward_workspace_size(g.handle, dt, 1))
-            assert one >= 2 * (n + 1) ** 2 * texel
+            pitch = n + 4 + (n % 2)
+            assert one >= 2 * (n + 3) * pitch * texel
             two = int(L.radon_forward_workspace_size(g.handle, dt, 2))
             assert two > 0 and int(L.radon_forward_workspace_size(g.handle, dt, 0)) == 0

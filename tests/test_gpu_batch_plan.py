@@ -1,7 +1,8 @@
 """Uneven batches in one persistent launch (Section 4.1, mixed sizes and geometries) against the
-FP64 oracle: every item of a plan, in both directions, in FP32 (rel-L2 1e-5) and 16-bit storage
-(2e-3); tile shapes that do not change a single bit; CUDA-graph replay; and the full 64-image
-mixed workload with one complete item per image size checked against the oracle."""
+FP64 oracle: every item of a plan, in both directions and with both forward kernels (the staged one
+and the L1 gather), in FP32 (rel-L2 1e-5) and 16-bit storage (2e-3); tile shapes that do not change
+a single bit; CUDA-graph replay; and the full 64-image mixed workload with one complete item per image
+size checked against the oracle."""
 
 from __future__ import annotations
 
@@ -58,11 +59,19 @@ def _mixed(dtype, direction, seed=0):
     return gs, ins, outs, refs
 
 
-@pytest.mark.parametrize("direction", ["forward", "adjoint"])
+# plan kinds: the staged forward, the L1-gather forward, the adjoint
+KINDS = [("forward", "staged"), ("forward", "gather"), ("adjoint", "auto")]
+# the shapes a tuned plan may pick: views per item (or chunk) and rows per staged slab (0: the gather)
+PICKS = {("forward", "staged"): ((2, 4, 8), (16, 32)), ("forward", "gather"): ((1, 2, 4, 8), (0,)),
+         ("forward", "auto"): ((1, 2, 4, 8), (0, 16, 32)), ("adjoint", "auto"): ((4, 8, 16, 32), (0,))}
+
+
+@pytest.mark.parametrize("direction,kernel", KINDS + [("forward", "auto")],
+                         ids=["fwd_staged", "fwd_gather", "adjoint", "fwd_auto"])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float16, torch.bfloat16], ids=["f32", "f16", "bf16"])
-def test_plan_matches_oracle(direction, dtype):
+def test_plan_matches_oracle(direction, kernel, dtype):
     gs, ins, outs, refs = _mixed(dtype, direction)
-    plan = BatchPlan(list(zip(gs, ins, outs)), direction)
+    plan = BatchPlan(list(zip(gs, ins, outs)), direction, forward_kernel=kernel)
     plan.launch()
     torch.cuda.synchronize()
     for k, (o, r) in enumerate(zip(outs, refs)):
@@ -73,58 +82,86 @@ def test_plan_matches_oracle(direction, dtype):
     info = plan.info
     assert info["units"] == sum(BATCH) and info["work_items"] > 0 and info["direction"] == direction
     assert info["ctas"] % torch.cuda.get_device_properties(0).multi_processor_count == 0
-    cands = (1, 2, 4, 8) if direction == "forward" else (4, 8, 16, 32)
-    assert all(plan.item_config(k) in cands for k in range(len(gs)))
+    views, rows = PICKS[(direction, kernel)]
+    assert all(plan.item_config(k) in views for k in range(len(gs)))
+    assert all(plan.item_rows(k) in rows for k in range(len(gs)))
 
 
-@pytest.mark.parametrize("direction", ["forward", "adjoint"])
-def test_tile_shapes_do_not_change_a_bit(direction):
-    """Every views-per-block (or chunk) candidate computes each output in the same order; the forward's
-    lanes per ray change only the order of a ray's partial sums (FP32 rounding)."""
+@pytest.mark.parametrize("direction,kernel", KINDS, ids=["fwd_staged", "fwd_gather", "adjoint"])
+def test_tile_shapes_do_not_change_a_bit(direction, kernel):
+    """Every views-per-item (or chunk) candidate computes each output in the same order: the same bits.
+    The forward's lanes per ray change only the order of a ray's partial sums, and the staged
+    forward's rows per slab only where each ray's positions are re-based (FP32 rounding)."""
     gs, ins, outs, refs = _mixed(torch.float32, direction, seed=3)
-    by_lanes = {}
-    for lanes in ((1, 4) if direction == "forward" else (0,)):
+    if direction == "forward":
+        views = (1, 2, 4, 8)
+        shapes = [(lanes, rows) for lanes in (1, 4) for rows in ((8, 16, 32) if kernel == "staged" else (0,))]
+    else:
+        views, shapes = (4, 8, 16, 32), [(0, 0)]
+    firsts = []
+    for lanes, rows in shapes:
         results = []
-        for v in ((1, 2, 4, 8) if direction == "forward" else (4, 8, 16, 32)):
-            kw = dict(forward_views=v, forward_lanes=lanes) if direction == "forward" else dict(adjoint_views=v)
+        for v in views:
+            if direction == "forward":
+                kw = dict(forward_views=v, forward_lanes=lanes, forward_rows=rows, forward_kernel=kernel)
+            else:
+                kw = dict(adjoint_views=v)
             plan = BatchPlan(list(zip(gs, ins, outs)), direction, autotune=False, **kw)
             assert all(plan.item_config(k) == v for k in range(len(gs)))
             assert all(plan.item_shape(k) == (v, lanes if direction == "forward" else 1) for k in range(len(gs)))
+            assert all(plan.item_rows(k) == rows for k in range(len(gs)))
             plan.launch()
             torch.cuda.synchronize()
             results.append([o.clone() for o in outs])
         for other in results[1:]:
             for a, b in zip(results[0], other):
                 assert torch.equal(a, b)
-        by_lanes[lanes] = results[0]
-    if direction == "forward":
-        for a, b, r in zip(by_lanes[1], by_lanes[4], refs):
+        firsts.append(results[0])
+    for res in firsts[1:]:
+        for a, b, r in zip(firsts[0], res, refs):
             assert rel_l2(to_np(a), to_np(b)) <= 1e-6
             assert rel_l2(to_np(b), r) <= TOL_F32
 
 
+@pytest.mark.parametrize("kernel", ["staged", "gather"])
+def test_staged_and_gather_forwards_agree(kernel):
+    """The two forward kernels sample the same points with the same bilinear arithmetic; they differ
+    only where positions are re-based (FP32 rounding)."""
+    gs, ins, outs, refs = _mixed(torch.float32, "forward", seed=9)
+    BatchPlan(list(zip(gs, ins, outs)), "forward", forward_kernel=kernel).launch()
+    torch.cuda.synchronize()
+    mine = [o.clone() for o in outs]
+    other = "gather" if kernel == "staged" else "staged"
+    BatchPlan(list(zip(gs, ins, outs)), "forward", forward_kernel=other).launch()
+    torch.cuda.synchronize()
+    for a, b, r in zip(mine, outs, refs):
+        assert rel_l2(to_np(a), to_np(b)) <= 1e-6
+        assert rel_l2(to_np(a), r) <= TOL_F32
+
+
 def test_tuning_cache_records_and_reuses_the_picks(tmp_path, monkeypatch):
-    """With RADON_TUNE_CACHE set, a plan appends one pick per (direction, storage, size, kind) group
-    and a later plan of the same groups takes its shapes from the file."""
+    """With RADON_TUNE_CACHE set, a plan appends one pick per (direction, storage, size, kind, kernel)
+    group and a later plan of the same groups takes its shapes from the file."""
     cache = tmp_path / "tune.txt"
     monkeypatch.setenv("RADON_TUNE_CACHE", str(cache))
     gs, ins, outs, refs = _mixed(torch.float32, "forward", seed=7)
-    first = BatchPlan(list(zip(gs, ins, outs)), "forward")
+    first = BatchPlan(list(zip(gs, ins, outs)), "forward", forward_kernel="staged")
     lines = cache.read_text().split("\n")
     groups = {(g.n, g.kind) for g in gs}
     assert len([l for l in lines if l.strip()]) == len(groups)
-    picks = [first.item_shape(k) for k in range(len(gs))]
+    picks = [(first.item_shape(k), first.item_rows(k)) for k in range(len(gs))]
     # rewrite the cache with other (valid) picks: a new plan must follow the file, not retime
     alt = {}
     with open(cache, "w") as f:
         for l in lines:
             if l.strip():
-                key, v, ln = l.split()
-                nv, nl = (1 if int(v) != 1 else 2), (4 if int(ln) == 1 else 1)
-                alt[key] = (nv, nl)
-                f.write("%s %d %d\n" % (key, nv, nl))
-    second = BatchPlan(list(zip(gs, ins, outs)), "forward")
-    got = [second.item_shape(k) for k in range(len(gs))]
+                key, v, ln, r = l.split()
+                assert key.endswith("_staged") and int(r) in (16, 32)
+                nv, nl, nr = (2 if int(v) != 2 else 4), int(ln), (32 if int(r) == 16 else 16)
+                alt[key] = ((nv, nl), nr)
+                f.write("%s %d %d %d\n" % (key, nv, nl, nr))
+    second = BatchPlan(list(zip(gs, ins, outs)), "forward", forward_kernel="staged")
+    got = [(second.item_shape(k), second.item_rows(k)) for k in range(len(gs))]
     assert sorted(set(got)) == sorted(set(alt.values())) and got != picks
     second.launch()
     torch.cuda.synchronize()
@@ -132,10 +169,10 @@ def test_tuning_cache_records_and_reuses_the_picks(tmp_path, monkeypatch):
         assert rel_l2(to_np(o), r) <= TOL_F32
 
 
-@pytest.mark.parametrize("direction", ["forward", "adjoint"])
-def test_plan_replays_in_a_cuda_graph(direction):
+@pytest.mark.parametrize("direction,kernel", KINDS, ids=["fwd_staged", "fwd_gather", "adjoint"])
+def test_plan_replays_in_a_cuda_graph(direction, kernel):
     gs, ins, outs, _ = _mixed(torch.float16, direction, seed=5)
-    plan = BatchPlan(list(zip(gs, ins, outs)), direction)
+    plan = BatchPlan(list(zip(gs, ins, outs)), direction, forward_kernel=kernel)
     stream = torch.cuda.Stream()
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.stream(stream):
