@@ -610,20 +610,29 @@ def run_secondary(args):
     ms_adj_default = time_it(da.launch, 5)
     df.close()
     da.close()
+    # the staged forward alone (image slabs copied into shared memory by bulk copies), its own shapes
+    # tuned: the alternative the autotuner weighs against the L1 gather at every image size
+    sf = BatchPlan(list(zip(geoms, xs16, oy)), "forward", forward_kernel="staged")
+    ms_fwd_staged = time_it(sf.launch, 5)
+    cfg_staged = sorted({(items[k]["n"],) + sf.item_shape(k) + (sf.item_rows(k),) for k in range(len(items))})
+    sf.close()
 
     def per_item():
         for g, x, y, a_, b_ in zip(geoms, xs16, ys16, oy, ox):
             forward_raw(g, x, out=a_)
             backward_raw(g, y, out=b_)
     ms_loop = time_it(per_item, 3, warm=1)
-    cfg_f = sorted({(items[k]["n"],) + pf.item_shape(k) for k in range(len(items))})
+    cfg_f = sorted({(items[k]["n"],) + pf.item_shape(k) + (pf.item_rows(k),) for k in range(len(items))})
     cfg_a = sorted({(items[k]["n"], pa.item_config(k)) for k in range(len(items))})
     out["uneven"] = {
         "workload": w.name, "storage": "f16", "images": len(items), "samples_per_pass": S_tot,
         "ms_graph_fwd_adj": ms_graph, "ms_plan_fwd": ms_fwd, "ms_plan_adj": ms_adj,
         "samples_per_s": 2 * S_tot / (ms_graph * 1e-3), "images_per_s": len(items) / (ms_graph * 1e-3),
         "per_image_calls_ms": ms_loop, "speedup_vs_per_image_calls": ms_loop / ms_graph,
-        "plan_create_s": t_plan, "autotuned_forward_n_views_lanes": cfg_f,
+        "plan_create_s": t_plan,
+        "autotuned_forward_n_views_lanes_rows": cfg_f,
+        "forward_kernel_note": "rows 0: the L1 gather; rows > 0: the staged kernel with that many texel rows per slab",
+        "staged_forward_ms_plan_fwd": ms_fwd_staged, "staged_forward_n_views_lanes_rows": cfg_staged,
         "autotuned_adjoint_n_views": cfg_a,
         "default_shapes_ms_plan_fwd": ms_fwd_default, "default_shapes_ms_plan_adj": ms_adj_default,
         "autotuned_speedup_vs_default_shapes": (ms_fwd_default + ms_adj_default) / (ms_fwd + ms_adj),

@@ -14,7 +14,7 @@ import torch
 
 import oracle as O
 from gpu_cases import TOL_16, TOL_F32, rel_l2, to_dev, to_np, within_16
-from paper_2009_14788_gb300 import BatchPlan, Geometry
+from paper_2009_14788_gb300 import BatchPlan, Geometry, _lib as L
 from synth import WORKLOADS, ellipse_phantom, uneven_items, uniform_angles, workload_geometry_args, workload_images
 
 pytestmark = pytest.mark.gpu
@@ -85,6 +85,7 @@ def test_plan_matches_oracle(direction, kernel, dtype):
     views, rows = PICKS[(direction, kernel)]
     assert all(plan.item_config(k) in views for k in range(len(gs)))
     assert all(plan.item_rows(k) in rows for k in range(len(gs)))
+    assert L.radon_get_device_error(torch.cuda.current_stream().cuda_stream) == L.RADON_OK
 
 
 @pytest.mark.parametrize("direction,kernel", KINDS, ids=["fwd_staged", "fwd_gather", "adjoint"])
@@ -113,6 +114,7 @@ def test_tile_shapes_do_not_change_a_bit(direction, kernel):
             plan.launch()
             torch.cuda.synchronize()
             results.append([o.clone() for o in outs])
+            assert L.radon_get_device_error(torch.cuda.current_stream().cuda_stream) == L.RADON_OK
         for other in results[1:]:
             for a, b in zip(results[0], other):
                 assert torch.equal(a, b)
@@ -223,6 +225,30 @@ def _full_uneven():
         kind = a.pop("kind")
         geoms.append(Geometry(kind, **a))
     return w, items, geoms
+
+
+def test_staged_shapes_leave_no_bounds_flag_on_the_uneven_images():
+    """One image of each size of the uneven workload (sparse to dense views, view groups across the
+    class boundaries and across 90 degrees) through every staged shape: the kernel's own bounds checks
+    never fire, and each result agrees with the L1 gather's."""
+    w, items, geoms = _full_uneven()
+    imgs = workload_images(w)
+    stream = torch.cuda.current_stream().cuda_stream
+    assert L.radon_get_device_error(stream) == L.RADON_OK
+    for n in w.extra["sizes"]:
+        k = [i for i in range(len(items)) if items[i]["n"] == n][1]
+        g = geoms[k]
+        x = to_dev(imgs[k][None], torch.float16)
+        ref = torch.empty((1,) + g.sino_shape, dtype=torch.float16, device="cuda")
+        BatchPlan([(g, x, ref)], "forward", forward_kernel="gather").launch()
+        y = torch.empty_like(ref)
+        for views in (2, 4, 8):
+            for lanes in (1, 4):
+                for rows in (8, 16, 32):
+                    BatchPlan([(g, x, y)], "forward", autotune=False, forward_views=views, forward_lanes=lanes,
+                              forward_rows=rows, forward_kernel="staged").launch()
+                    assert L.radon_get_device_error(stream) == L.RADON_OK, (n, views, lanes, rows)
+                    assert rel_l2(to_np(y), to_np(ref)) <= 1e-3, (n, views, lanes, rows)
 
 
 def test_full_uneven_workload_one_item_per_size_against_oracle():
