@@ -129,6 +129,7 @@ def _rel_l2(a, b):
 
 
 ADJ_OPS_PER_SAMPLE = 18
+ADJ_PRODUCTS_PER_SAMPLE = 2.5
 
 
 def max_over_ranks(values, device=None):
@@ -394,6 +395,16 @@ def run_ours(args):
                              traffic_tab.get("backward")),
     }
 
+    # the same adjoint against a products-only floor: one FP32 FMA per image, pixel and candidate ray
+    # that carries weight (~2.6 such rays per pixel and view, ~1.04 samples per pixel and view on the
+    # headline geometry: ~2.5 FMAs per image-sample), the weights shared by a group's images counted
+    # as free -- the ceiling a perfect use of the weight sharing would approach
+    floor = sm_count * (128.0 / ADJ_PRODUCTS_PER_SAMPLE) * clk_mhz * 1e6 / 1e9
+    rooflines["backward"]["products_floor"] = floor
+    rooflines["backward"]["frac_of_products_floor"] = rooflines["backward"]["achieved"] / floor
+    rooflines["backward"]["products_floor_basis"] = (
+        "%d SMs x %.1f samples/clk/SM (128 FP32 FMA lanes/clk/SM / %.1f products per image-sample) x %.0f MHz"
+        % (sm_count, 128.0 / ADJ_PRODUCTS_PER_SAMPLE, ADJ_PRODUCTS_PER_SAMPLE, clk_mhz))
     rooflines["forward"]["probe_ceiling"] = probe.value / 1e9
     rooflines["forward"]["frac_of_probe"] = rooflines["forward"]["achieved"] / (probe.value / 1e9)
     if f16w is not None:
