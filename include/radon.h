@@ -288,6 +288,33 @@ RADON_API radon_status radon_forward_static_scratch(const radon_geometry* geomet
                                                     radon_dtype dtype, int batch, void* stream);
 
 /*
+ * Weight table of the exact adjoint (a GB300 memory-for-compute trade; the paper computes every weight
+ * on the fly).  radon_geometry_build_adjoint_table precomputes, for every 16 x 16 pixel tile, view and
+ * vertical pixel pair, the first detector whose ray weighs on the pair and both pixels' bilinear weights
+ * on five consecutive rays from it -- the weights the packed adjoint (radon_backward_ws and the calls
+ * built on it) would compute, by the same arithmetic.  Pairs whose weighted rays span more than five
+ * detectors in a view (rays denser than a pixel, e.g. near a fan's source) are marked and keep
+ * computing their weights.  While a geometry holds its table, the packed adjoint of batches that run
+ * 8- or 16-image groups reads the weights instead of evaluating them: the same nonzero products added
+ * in the same order, so the same bits.
+ *   - radon_geometry_adjoint_table_size: the table's device bytes, tiles x views x (128 pairs x 44
+ *     + 4) (4.2 GB for 512^2 and 720 views); no allocation.
+ *   - radon_geometry_build_adjoint_table: allocates the table on the geometry's device (which must be
+ *     current) and fills it; synchronises the device; not capturable.  RADON_ERR_UNSUPPORTED (nothing
+ *     kept) where the packed adjoint cannot serve the geometry (a detector window wider than 256 or a
+ *     sampling step of sqrt(2) / 3 or less), RADON_ERR_OOM when the device memory runs out.  Building
+ *     again replaces the table.
+ *   - radon_geometry_adjoint_table_overflow: the fraction of (pair, view) records left to the
+ *     on-the-fly weights (0 without a table).
+ *   - radon_geometry_free_adjoint_table: frees it (radon_geometry_destroy does too); the adjoint then
+ *     computes its weights again.  Calls that may still read the table must have completed.
+ */
+RADON_API radon_status radon_geometry_adjoint_table_size(const radon_geometry* geometry, size_t* bytes);
+RADON_API radon_status radon_geometry_build_adjoint_table(radon_geometry* geometry);
+RADON_API radon_status radon_geometry_adjoint_table_overflow(const radon_geometry* geometry, double* fraction);
+RADON_API radon_status radon_geometry_free_adjoint_table(radon_geometry* geometry);
+
+/*
  * ---- Iterative reconstruction (Section 4.2: Landweber iteration, step size by power iteration) ----
  *
  * Output epilogue of the fused projections below.  Each output element is

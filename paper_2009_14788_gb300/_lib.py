@@ -137,6 +137,10 @@ _SIGNATURES = [
     ("radon_geometry_destroy", None, [ctypes.c_void_p]),
     ("radon_geometry_get_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(radon_geometry_info)]),
     ("radon_geometry_sample_count", ctypes.c_int64, [ctypes.c_void_p]),
+    ("radon_geometry_adjoint_table_size", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    ("radon_geometry_build_adjoint_table", ctypes.c_int, [ctypes.c_void_p]),
+    ("radon_geometry_free_adjoint_table", ctypes.c_int, [ctypes.c_void_p]),
+    ("radon_geometry_adjoint_table_overflow", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     ("radon_forward", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     ("radon_backward", ctypes.c_int,
@@ -280,6 +284,22 @@ def radon_geometry_get_info(geom, info_ptr):
 
 def radon_geometry_sample_count(geom):
     return _call("radon_geometry_sample_count", geom)
+
+
+def radon_geometry_adjoint_table_size(geom, bytes_ptr):
+    return _call("radon_geometry_adjoint_table_size", geom, bytes_ptr)
+
+
+def radon_geometry_build_adjoint_table(geom):
+    return _call("radon_geometry_build_adjoint_table", geom)
+
+
+def radon_geometry_adjoint_table_overflow(geom, fraction_ptr):
+    return _call("radon_geometry_adjoint_table_overflow", geom, fraction_ptr)
+
+
+def radon_geometry_free_adjoint_table(geom):
+    return _call("radon_geometry_free_adjoint_table", geom)
 
 
 def radon_forward(geom, img, sino, dtype, batch, stream):

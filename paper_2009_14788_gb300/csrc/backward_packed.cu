@@ -1,5 +1,7 @@
 // Host dispatch of the packed adjoint (backward_packed.cuh): image-group size, ring descriptor of
 // the ray table, and the launcher instantiated for the storage type.
+#include <cmath>
+
 #include "backward_packed.cuh"
 
 namespace radon {
@@ -101,6 +103,99 @@ radon_status launch_backward_packed(const radon_geometry* g, const void* packed,
         case RADON_BF16: return launch_bg<__nv_bfloat16>(g, packed, img, dt, batch, bg, kw, ep, s, why, rmap, err);
         default: return launch_bg<float>(g, packed, img, dt, batch, bg, kw, ep, s, why, rmap, err);
     }
+}
+
+size_t adjoint_table_bytes(const radon_geometry* g) {
+    const size_t tiles_x = (size_t)(g->n + kBwdTile - 1) / kBwdTile;
+    return tiles_x * tiles_x * (size_t)g->V * (kBwdTabPairs * (2 * sizeof(float4) + sizeof(float2) + sizeof(int)) + sizeof(int));
+}
+
+void free_adjoint_table(radon_geometry* g) {
+    if (g->d_tab_w) cudaFree(g->d_tab_w);
+    if (g->d_tab_w5) cudaFree(g->d_tab_w5);
+    if (g->d_tab_la) cudaFree(g->d_tab_la);
+    if (g->d_tab_vflag) cudaFree(g->d_tab_vflag);
+    g->d_tab_vflag = nullptr;
+    g->d_tab_w = nullptr;
+    g->d_tab_w5 = nullptr;
+    g->d_tab_la = nullptr;
+    g->tab_kw = 0;
+    g->tab_wd = 0;
+    g->tab_bytes = 0;
+    g->tab_overflow = 0.0;
+}
+
+// Builds the geometry's weight table on the current device (the geometry's), synchronising it.
+radon_status build_adjoint_table(radon_geometry* g, std::string* why) {
+    const double span = 2.0 * std::sqrt(2.0) / g->h + 2e-4;
+    const int kw_needed = (int)std::floor(span) + 1;
+    if (kw_needed > 6) {
+        *why = "sampling step too small for the packed adjoint";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    const int kw = kw_needed <= 3 ? 3 : 6;
+    const int wd = g->bwd_window + 2;
+    if (wd > 256) {
+        *why = "detector window wider than a TMA box";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    free_adjoint_table(g);
+    const int tiles_x = (g->n + kBwdTile - 1) / kBwdTile;
+    const size_t recs = (size_t)tiles_x * tiles_x * (size_t)g->V * kBwdTabPairs;
+    float4* w = nullptr;
+    float2* w5 = nullptr;
+    int* la = nullptr;
+    int* vflag = nullptr;
+    unsigned long long* over = nullptr;
+    const size_t tv = (size_t)tiles_x * tiles_x * (size_t)g->V;
+    if (cudaMalloc(&w, recs * 2 * sizeof(float4)) != cudaSuccess || cudaMalloc(&w5, recs * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&la, recs * sizeof(int)) != cudaSuccess || cudaMalloc(&vflag, tv * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&over, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(w);
+        cudaFree(w5);
+        cudaFree(la);
+        cudaFree(vflag);
+        cudaFree(over);
+        *why = "device allocation of the weight table failed";
+        return RADON_ERR_OOM;
+    }
+    constexpr int kViewsPerBlock = 16;
+    cudaError_t e = cudaMemset(over, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(vflag, 0, tv * sizeof(int));
+    if (e == cudaSuccess) {
+        const dim3 grid((unsigned)(tiles_x * tiles_x), (unsigned)((g->V + kViewsPerBlock - 1) / kViewsPerBlock));
+        const float ih2 = (float)(1.0 / (g->h * g->h));
+        if (kw == 3)
+            bwdp_table_kernel<3><<<grid, kBwdTabPairs>>>(g->d_ray, g->d_view, g->n, g->V, g->D, ih2, wd, tiles_x,
+                                                         kViewsPerBlock, w, w5, la, vflag, over);
+        else
+            bwdp_table_kernel<6><<<grid, kBwdTabPairs>>>(g->d_ray, g->d_view, g->n, g->V, g->D, ih2, wd, tiles_x,
+                                                         kViewsPerBlock, w, w5, la, vflag, over);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    unsigned long long n_over = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&n_over, over, sizeof(n_over), cudaMemcpyDeviceToHost);
+    cudaFree(over);
+    if (e != cudaSuccess) {
+        cudaFree(w);
+        cudaFree(w5);
+        cudaFree(la);
+        cudaFree(vflag);
+        *why = std::string("weight table build: ") + cudaGetErrorString(e);
+        return RADON_ERR_CUDA;
+    }
+    count_launches(1);
+    g->d_tab_w = w;
+    g->d_tab_w5 = w5;
+    g->d_tab_la = la;
+    g->d_tab_vflag = vflag;
+    g->tab_kw = kw;
+    g->tab_wd = wd;
+    g->tab_bytes = adjoint_table_bytes(g);
+    g->tab_overflow = (double)n_over / (double)recs;
+    return RADON_OK;
 }
 
 }  // namespace radon

@@ -91,7 +91,33 @@ struct BwdPArgs {
     int* err;
     uint32_t spin_limit;
     Epilogue ep;
+    const float4* tab_w;   // weight table (TAB kernels): [tile][view][pair] two float4s, see bwdp_table_kernel
+    const float2* tab_w5;  // [tile][view][pair] the fifth ray's weights of both pixels
+    const int* tab_la;     // [tile][view][pair] the first of the pair's five table rays (detector index)
+    const int* tab_vflag;  // [tile][view] nonzero where some pair of the tile overflows in that view
 };
+
+// Weight table of the exact adjoint (the TAB mode of the packed kernel): per 16 x 16 tile, view and
+// consumer thread (a vertical pixel pair, the PX = 2 layout) the detector index la of the first ray
+// that weighs on either pixel and both pixels' weights on rays la .. la + 4 (zero past the pair's
+// candidates), or la = kBwdTabOverflow where the pair's weighted rays span more than five detectors
+// (rays much denser than a pixel) -- such pairs compute their weights as without a table.  (On the
+// 512^2 fan with 720 views and 1024 detectors a pair's weighted rays span 2-5 detectors: five
+// covers all but ~0.1 % of the pairs and views, four left ~1.4 % to the slower path, spread over a
+// third of the warps.)  The weights are the gather's own: the same re-based ray records and the same
+// bwdp_weight arithmetic, so the table adjoint adds the same nonzero products in the same order.
+constexpr int kBwdTabRays = 5;
+constexpr int kBwdTabOverflow = (int)0x80000000;
+constexpr int kBwdTabPairs = kBwdThreads / 2;   // consumer threads of a 16-image CTA
+
+// Pixel pair of consumer thread `tid` in a 16 x 16 tile (PX = 2): rows pi0, pi0 + 1 of column pj.
+// Each warp takes an 8 x 8 block, each group of eight lanes a 4 x 4 block (2 x 4 pairs).
+__host__ __device__ inline void bwdp_pair_of(int tid, int* pi0, int* pj) {
+    const int warp = tid >> 5, lane = tid & 31;
+    const int grp = lane >> 3, e8 = lane & 7;
+    *pi0 = (warp >> 1) * 8 + ((grp >> 1) * 2 + (e8 >> 2)) * 2;
+    *pj = (warp & 1) * 8 + (grp & 1) * 4 + (e8 & 3);
+}
 
 // Detector window of a tile for one view (bwd_view_window) and the largest detector coordinate of
 // its pixels, from the tile's four corners (a linear-fractional map takes its extremes over a
@@ -156,10 +182,16 @@ __device__ __forceinline__ void bwdp_widen8<__nv_bfloat16>(const uint4 u, float4
                          __uint_as_float(u.w & 0xffff0000u));
 }
 
-template <typename T, int BG, int KW>
+// TAB (exact adjoint, PX = 2 only): a pair's weights come from the geometry's weight table instead of
+// being evaluated from re-based ray records; ray rows are copied and re-based only for chunks with a
+// view in which some pair of the tile overflows the table (the table's per-view flags).  The producer
+// prefetches the table's rows for the chunk that will next reuse its ring slot into L2.
+template <typename T, int BG, int KW, bool TAB = false>
 __global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasPerSm)
     backward_packed_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap rmap,
                            const BwdPArgs a) {
+    static_assert(!TAB || (KW > 0 && BwdPShape<BG>::PX == 2), "the weight table serves the exact adjoint's pairs");
+    constexpr bool kRays = KW > 0;   // ray rows copied and re-based per chunk
     using L = BwdPLayout<T, BG>;
     constexpr int NQ = BG / 4;
     constexpr int PITCH = L::kPitch;
@@ -173,10 +205,11 @@ __global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasP
     int* dlo_c = reinterpret_cast<int*>(smem + 192);              // [stages][views]
     float* r_c = reinterpret_cast<float*>(smem + 256);            // [stages][views]
     ViewF* view_c = reinterpret_cast<ViewF*>(smem + 512);         // [stages][views]
+    int* rays_c = reinterpret_cast<int*>(smem + 320);             // [stages]: the chunk's ray rows were copied
     static_assert(kBwdPMaxStages * kBwdPViews * 4 <= 64 && 512 + kBwdPMaxStages * kBwdPViews * 32 <= kBwdPHeader,
                   "ring header overflows its slots");
     const int S = a.stages;
-    const BwdPSmem m = bwdp_smem<T, BG>(a.wd, S, KW > 0);
+    const BwdPSmem m = bwdp_smem<T, BG>(a.wd, S, kRays);
     unsigned char* ring = smem + kBwdPHeader;
     unsigned char* yf = ring + (size_t)S * m.stage;   // [2][views] converted windows (16-bit storage)
 
@@ -217,18 +250,37 @@ __global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasP
                 r_c[st * kBwdPViews + lane] = r;
                 view_c[st * kBwdPViews + lane] = vf;
             }
+            // ray rows: always for the on-the-fly weights; with a table only where some pair overflows
+            bool rays = kRays;
+            if constexpr (TAB) {
+                const int fl = lane < nv ? __ldg(a.tab_vflag + (size_t)tile * a.V + v0 + lane) : 0;
+                rays = __any_sync(0xffffffffu, fl != 0);
+            }
             __syncwarp();
             if (lane == 0) {
                 unsigned char* slot = ring + (size_t)st * m.stage;
+                rays_c[st] = rays ? 1 : 0;
                 fence_proxy_async_shared();
                 mbar_arrive_expect_tx(&tma_bar[st],
-                                      (uint32_t)(nv * a.wd * (L::kRowElems * (int)sizeof(T) + (KW > 0 ? 32 : 0))));
+                                      (uint32_t)(nv * a.wd * (L::kRowElems * (int)sizeof(T) + (rays ? 32 : 0))));
                 for (int vl = 0; vl < nv; ++vl) {
                     const int dlo = dlo_c[st * kBwdPViews + vl];
                     tma_load_4d(slot + (size_t)vl * m.yst_view, &map, &tma_bar[st], 0, dlo, v0 + vl, blockIdx.y);
-                    if (KW > 0)   // the interpolating backprojector needs no rays
+                    if (rays)   // the interpolating backprojector needs no rays
                         tma_load_2d(slot + (size_t)kBwdPViews * m.yst_view + (size_t)vl * m.rst_view, &rmap,
                                     &tma_bar[st], 0, (v0 + vl) * a.D + dlo);
+                }
+                if constexpr (TAB) {
+                    // the table rows of the chunk that will next use this slot, into L2 (a hint: no
+                    // completion to wait for); 16-byte aligned multiples of 16 bytes by construction
+                    const int cn = c + S;
+                    if (cn < nchunks) {
+                        const int vn = cn * kBwdPViews, nvn = min(kBwdPViews, a.V - vn);
+                        const size_t rec = ((size_t)tile * a.V + vn) * kBwdTabPairs;
+                        bulk_prefetch_l2(a.tab_w + 2 * rec, (uint32_t)(nvn * kBwdTabPairs * 32));
+                        bulk_prefetch_l2(a.tab_w5 + rec, (uint32_t)(nvn * kBwdTabPairs * 8));
+                        bulk_prefetch_l2(a.tab_la + rec, (uint32_t)(nvn * kBwdTabPairs * 4));
+                    }
                 }
             }
             __syncwarp();
@@ -254,8 +306,8 @@ __global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasP
     // 2 x 4 pairs (4 x 4 pixels) -- whose detector span stays within the eight bank groups
     const int warp = tid >> 5, lane = tid & 31;
     const int grp = lane >> 3, e8 = lane & 7;
-    const int pi0 = PX == 2 ? (warp >> 1) * 8 + ((grp >> 1) * 2 + (e8 >> 2)) * 2 : (warp >> 1) * 4 + (e8 >> 1);
-    const int pj = PX == 2 ? (warp & 1) * 8 + (grp & 1) * 4 + (e8 & 3) : (warp & 1) * 8 + grp * 2 + (e8 & 1);
+    int pi0 = (warp >> 1) * 4 + (e8 >> 1), pj = (warp & 1) * 8 + grp * 2 + (e8 & 1);
+    if constexpr (PX == 2) bwdp_pair_of(tid, &pi0, &pj);
     const float px = (float)pj, py0 = (float)pi0;
     const float gx = (float)(tj + pj), gy0 = (float)(ti + pi0);
     float acc[PX][BG];
@@ -269,6 +321,17 @@ __global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasP
     const uint32_t win_a = smem_u32(view_c);
     const uint32_t yview = L::kConv ? (uint32_t)m.yf_view : (uint32_t)m.yst_view;
     const uint32_t ystv = (uint32_t)m.yst_view, rstv = (uint32_t)m.rst_view;
+    // TAB: this thread's table record of the next view, loaded one view ahead of its use
+    [[maybe_unused]] float4 tw0 = make_float4(0.f, 0.f, 0.f, 0.f), tw1 = tw0;
+    [[maybe_unused]] float2 tw5 = make_float2(0.f, 0.f);
+    [[maybe_unused]] int tla = 0;
+    [[maybe_unused]] const size_t trec0 = (size_t)tile * a.V * kBwdTabPairs + (size_t)tid;
+    if constexpr (TAB) {
+        tw0 = __ldg(a.tab_w + 2 * trec0);
+        tw1 = __ldg(a.tab_w + 2 * trec0 + 1);
+        tw5 = __ldg(a.tab_w5 + trec0);
+        tla = __ldg(a.tab_la + trec0);
+    }
     for (int c = 0; c < nchunks; ++c) {
         const int st = c % S;
         const int v0 = c * kBwdPViews;
@@ -297,7 +360,7 @@ __global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasP
                     sts4(dst + 16, f[1]);
                 }
             }
-            if constexpr (KW > 0) {
+            if (kRays && rays_c[st]) {
                 // re-base the landed rays on this tile, in place: one ray per thread
                 const int W = a.wd;
                 for (int e = tid; e < nv * W; e += NC) {
@@ -376,39 +439,80 @@ __global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasP
                     }
                 }
             } else {
-                const float r = r_c[st * kBwdPViews + vl];
-                // the union of the pixels' candidate ranges [t - r, t + r] (approximate divide: the
-                // windows carry margins far above its error); a candidate outside a pixel's own range
-                // has zero weight there.  Candidates outside the detector are sentinel rays over
-                // zero-filled rows, so only the copied window bounds the loop (the producer checked
-                // that it holds them all); the bounds are clamped in FP32, so a non-finite coordinate
-                // still gives a loop inside the window
-                float tlo = __fdividef(num0, den0), thi = tlo;
-                if constexpr (PX == 2) {
-                    const float t1 = __fdividef(num0 + v01.y, den0 + v23.x);
-                    tlo = fminf(tlo, t1);
-                    thi = fmaxf(thi, t1);
+                bool tabbed = false;
+                if constexpr (TAB) {
+                    // the pair's four table rays from la: rows clamped into the window (a clamped row
+                    // has weight zero); the same nonzero products, in the same order, as the gather
+                    const float4 w0 = tw0, w1 = tw1;
+                    const float2 w5 = tw5;
+                    const int la_t = tla;
+                    const int vnext = v0 + vl + 1;
+                    if (vnext < a.V) {
+                        const size_t nr = trec0 + (size_t)vnext * kBwdTabPairs;
+                        tw0 = __ldg(a.tab_w + 2 * nr);
+                        tw1 = __ldg(a.tab_w + 2 * nr + 1);
+                        tw5 = __ldg(a.tab_w5 + nr);
+                        tla = __ldg(a.tab_la + nr);
+                    }
+                    if (la_t != kBwdTabOverflow) {
+                        tabbed = true;
+                        const int rel0 = la_t - dlo;
+                        const float wa[kBwdTabRays] = {w0.x, w0.y, w0.z, w0.w, w5.x};
+                        const float wb[kBwdTabRays] = {w1.x, w1.y, w1.z, w1.w, w5.y};
+#pragma unroll
+                        for (int cr = 0; cr < kBwdTabRays; ++cr) {
+                            const int rel = min(max(rel0 + cr, 0), a.wd - 1);
+                            const uint32_t ya = yv + (uint32_t)rel * PITCH;
+#pragma unroll
+                            for (int q = 0; q < NQ; ++q) {
+                                const float4 y4 = lds4(ya + 16 * q);
+                                acc[0][4 * q + 0] = fmaf(wa[cr], y4.x, acc[0][4 * q + 0]);
+                                acc[0][4 * q + 1] = fmaf(wa[cr], y4.y, acc[0][4 * q + 1]);
+                                acc[0][4 * q + 2] = fmaf(wa[cr], y4.z, acc[0][4 * q + 2]);
+                                acc[0][4 * q + 3] = fmaf(wa[cr], y4.w, acc[0][4 * q + 3]);
+                                acc[PX - 1][4 * q + 0] = fmaf(wb[cr], y4.x, acc[PX - 1][4 * q + 0]);
+                                acc[PX - 1][4 * q + 1] = fmaf(wb[cr], y4.y, acc[PX - 1][4 * q + 1]);
+                                acc[PX - 1][4 * q + 2] = fmaf(wb[cr], y4.z, acc[PX - 1][4 * q + 2]);
+                                acc[PX - 1][4 * q + 3] = fmaf(wb[cr], y4.w, acc[PX - 1][4 * q + 3]);
+                            }
+                        }
+                    }
                 }
-                const float fd = (float)dlo;
-                const int la = __float2int_ru(fmaxf((tlo - r) - fd, 0.0f));
-                const int lb = __float2int_rd(fminf((thi + r) - fd, (float)(a.wd - 1)));
-                uint32_t ra = rst_a + (uint32_t)vl * rstv + (uint32_t)la * 32u;
-                uint32_t ya = yv + (uint32_t)la * PITCH;
-                for (int dl = la; dl <= lb; ++dl, ra += 32u, ya += PITCH) {
-                    const float4 A = lds4(ra), Bc = lds4(ra + 16);
-                    const float s0 = fmaf(px, Bc.x, fmaf(py0, Bc.y, Bc.z));
-                    float w[PX];
-                    w[0] = bwdp_weight<KW>(px, py0, s0, A);
-                    if constexpr (PX == 2) w[1] = bwdp_weight<KW>(px, py0 + 1.0f, s0 + Bc.y, A);
+                if (!tabbed) {
+                    const float r = r_c[st * kBwdPViews + vl];
+                    // the union of the pixels' candidate ranges [t - r, t + r] (approximate divide: the
+                    // windows carry margins far above its error); a candidate outside a pixel's own range
+                    // has zero weight there.  Candidates outside the detector are sentinel rays over
+                    // zero-filled rows, so only the copied window bounds the loop (the producer checked
+                    // that it holds them all); the bounds are clamped in FP32, so a non-finite coordinate
+                    // still gives a loop inside the window
+                    float tlo = __fdividef(num0, den0), thi = tlo;
+                    if constexpr (PX == 2) {
+                        const float t1 = __fdividef(num0 + v01.y, den0 + v23.x);
+                        tlo = fminf(tlo, t1);
+                        thi = fmaxf(thi, t1);
+                    }
+                    const float fd = (float)dlo;
+                    const int la = __float2int_ru(fmaxf((tlo - r) - fd, 0.0f));
+                    const int lb = __float2int_rd(fminf((thi + r) - fd, (float)(a.wd - 1)));
+                    uint32_t ra = rst_a + (uint32_t)vl * rstv + (uint32_t)la * 32u;
+                    uint32_t ya = yv + (uint32_t)la * PITCH;
+                    for (int dl = la; dl <= lb; ++dl, ra += 32u, ya += PITCH) {
+                        const float4 A = lds4(ra), Bc = lds4(ra + 16);
+                        const float s0 = fmaf(px, Bc.x, fmaf(py0, Bc.y, Bc.z));
+                        float w[PX];
+                        w[0] = bwdp_weight<KW>(px, py0, s0, A);
+                        if constexpr (PX == 2) w[1] = bwdp_weight<KW>(px, py0 + 1.0f, s0 + Bc.y, A);
 #pragma unroll
-                    for (int q = 0; q < NQ; ++q) {
-                        const float4 y4 = lds4(ya + 16 * q);
+                        for (int q = 0; q < NQ; ++q) {
+                            const float4 y4 = lds4(ya + 16 * q);
 #pragma unroll
-                        for (int x = 0; x < PX; ++x) {
-                            acc[x][4 * q + 0] = fmaf(w[x], y4.x, acc[x][4 * q + 0]);
-                            acc[x][4 * q + 1] = fmaf(w[x], y4.y, acc[x][4 * q + 1]);
-                            acc[x][4 * q + 2] = fmaf(w[x], y4.z, acc[x][4 * q + 2]);
-                            acc[x][4 * q + 3] = fmaf(w[x], y4.w, acc[x][4 * q + 3]);
+                            for (int x = 0; x < PX; ++x) {
+                                acc[x][4 * q + 0] = fmaf(w[x], y4.x, acc[x][4 * q + 0]);
+                                acc[x][4 * q + 1] = fmaf(w[x], y4.y, acc[x][4 * q + 1]);
+                                acc[x][4 * q + 2] = fmaf(w[x], y4.z, acc[x][4 * q + 2]);
+                                acc[x][4 * q + 3] = fmaf(w[x], y4.w, acc[x][4 * q + 3]);
+                            }
                         }
                     }
                 }
@@ -429,6 +533,83 @@ __global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasP
     }
 }
 
+// Builds the weight table of the exact adjoint: one CTA per (tile, block of views), one thread per
+// consumer pixel pair (bwdp_pair_of).  For each view the thread takes the pair's candidate rays as the
+// gather does (the tile's window, the union of the pixels' ranges [t - r, t + r] clamped to it),
+// re-bases each on the tile and evaluates both pixels' weights with bwdp_weight; it stores the first
+// ray that weighs on either pixel (la) and the weights on rays la .. la + 4, or kBwdTabOverflow where
+// the weighted rays span more than five (counted in *overflow, and flagged for the tile and view in
+// tab_vflag, which must start at zero).
+template <int KW>
+__global__ void __launch_bounds__(kBwdTabPairs) bwdp_table_kernel(const RayT* __restrict__ rays,
+                                                                 const ViewF* __restrict__ views, int n, int V, int D,
+                                                                 float ih2, int wd, int tiles_x, int views_per_block,
+                                                                 float4* __restrict__ tab_w, float2* __restrict__ tab_w5,
+                                                                 int* __restrict__ tab_la, int* __restrict__ tab_vflag,
+                                                                 unsigned long long* overflow) {
+    const int tile = blockIdx.x, tid = threadIdx.x;
+    const int ti = (tile / tiles_x) * kBwdTile, tj = (tile - (tile / tiles_x) * tiles_x) * kBwdTile;
+    int pi0, pj;
+    bwdp_pair_of(tid, &pi0, &pj);
+    const float px = (float)pj, py0 = (float)pi0;
+    const float gx = (float)(tj + pj), gy0 = (float)(ti + pi0);
+    const int vb = blockIdx.y * views_per_block, ve = min(vb + views_per_block, V);
+    for (int v = vb; v < ve; ++v) {
+        const ViewF vf = views[v];
+        int dlo;
+        float r;
+        bwd_view_window(vf, ti, tj, n, &dlo, &r);
+        const float num0 = fmaf(vf.ax, gx, fmaf(vf.ay, gy0, vf.a0));
+        const float den0 = fmaf(vf.bx, gx, fmaf(vf.by, gy0, vf.b0));
+        float tlo = __fdividef(num0, den0), thi = tlo;
+        const float t1 = __fdividef(num0 + vf.ay, den0 + vf.by);
+        tlo = fminf(tlo, t1);
+        thi = fmaxf(thi, t1);
+        const float fd = (float)dlo;
+        const int la = __float2int_ru(fmaxf((tlo - r) - fd, 0.0f));
+        const int lb = __float2int_rd(fminf((thi + r) - fd, (float)(wd - 1)));
+        auto weights = [&](int dl, float* w0, float* w1) {
+            const int d = dlo + dl;
+            const bool valid = d >= 0 && d < D;
+            RayT ray{0, 0, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            if (valid) ray = rays[(long long)v * D + d];
+            float4 A, Bc;
+            bwdp_rebase(ray, valid, ti, tj, ih2, &A, &Bc);
+            const float s0 = fmaf(px, Bc.x, fmaf(py0, Bc.y, Bc.z));
+            *w0 = bwdp_weight<KW>(px, py0, s0, A);
+            *w1 = bwdp_weight<KW>(px, py0 + 1.0f, s0 + Bc.y, A);
+        };
+        int f = -1, l = -1;
+        for (int dl = la; dl <= lb; ++dl) {
+            float w0, w1;
+            weights(dl, &w0, &w1);
+            if (w0 != 0.0f || w1 != 0.0f) {
+                if (f < 0) f = dl;
+                l = dl;
+            }
+        }
+        const bool over = f >= 0 && l - f >= kBwdTabRays;
+        if (over) {
+            atomicAdd(overflow, 1ull);
+            atomicOr(tab_vflag + (size_t)tile * V + v, 1);
+        }
+        const int first = f >= 0 ? f : la;
+        float wa[kBwdTabRays], wb[kBwdTabRays];
+#pragma unroll
+        for (int cr = 0; cr < kBwdTabRays; ++cr) {
+            wa[cr] = 0.0f;
+            wb[cr] = 0.0f;
+            const int dl = first + cr;
+            if (!over && dl >= la && dl <= lb) weights(dl, &wa[cr], &wb[cr]);
+        }
+        const size_t rec = ((size_t)tile * V + v) * kBwdTabPairs + tid;
+        tab_w[2 * rec] = make_float4(wa[0], wa[1], wa[2], wa[3]);
+        tab_w[2 * rec + 1] = make_float4(wb[0], wb[1], wb[2], wb[3]);
+        tab_w5[rec] = make_float2(wa[4], wb[4]);
+        tab_la[rec] = over ? kBwdTabOverflow : dlo + first;
+    }
+}
+
 // Ring depth of a packed-adjoint CTA: the deepest ring (up to kBwdPMaxStages) that keeps the launch
 // bounds' CTAs resident per SM (228 KB of shared memory, 1 KB reserved per CTA), else two stages;
 // returns the dynamic shared memory.
@@ -441,10 +622,10 @@ inline size_t bwdp_plan(int wd, bool rays, int* stages) {
     return bwdp_smem<T, BG>(wd, S, rays).total;
 }
 
-template <typename T, int BG, int KW>
+template <typename T, int BG, int KW, bool TAB = false>
 cudaError_t bwdp_launch(const CUtensorMap& map, const CUtensorMap& rmap, const BwdPArgs& a, dim3 grid, size_t smem,
                         cudaStream_t s) {
-    auto kern = backward_packed_kernel<T, BG, KW>;
+    auto kern = backward_packed_kernel<T, BG, KW, TAB>;
     static size_t attr_bytes = 0;
     if (smem > attr_bytes) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -468,7 +649,10 @@ radon_status launch_backward_packed_t(const radon_geometry* g, const void* packe
         *why = "detector window wider than a TMA box";
         return RADON_ERR_UNSUPPORTED;
     }
+    // the geometry's weight table serves the exact adjoint's pixel pairs (16-bit or smaller groups)
+    const bool tab = kw > 0 && BwdPShape<BG>::PX == 2 && g->d_tab_w != nullptr && g->tab_kw == kw && g->tab_wd == wd;
     int stages = 2;
+    // the table kernel stages ray rows too (for the pairs its table marks as overflowing)
     const size_t smem = bwdp_plan<T, BG>(wd, kw > 0, &stages);
     if (smem > 227 * 1024) {
         *why = "shared memory budget exceeded";
@@ -502,10 +686,26 @@ radon_status launch_backward_packed_t(const radon_geometry* g, const void* packe
     a.err = err;
     a.spin_limit = spin_limit;
     a.ep = ep;
+    a.tab_w = static_cast<const float4*>(g->d_tab_w);
+    a.tab_w5 = static_cast<const float2*>(g->d_tab_w5);
+    a.tab_vflag = g->d_tab_vflag;
+    a.tab_la = g->d_tab_la;
     const dim3 grid((unsigned)(a.tiles_x * a.tiles_x), (unsigned)groups);
-    const cudaError_t e = kw == 0   ? bwdp_launch<T, BG, 0>(map, rmap, a, grid, smem, s)
-                          : kw == 3 ? bwdp_launch<T, BG, 3>(map, rmap, a, grid, smem, s)
-                                    : bwdp_launch<T, BG, 6>(map, rmap, a, grid, smem, s);
+    cudaError_t e;
+    if constexpr (BwdPShape<BG>::PX == 2) {
+        if (tab) {
+            e = kw == 3 ? bwdp_launch<T, BG, 3, true>(map, rmap, a, grid, smem, s)
+                        : bwdp_launch<T, BG, 6, true>(map, rmap, a, grid, smem, s);
+        } else {
+            e = kw == 0   ? bwdp_launch<T, BG, 0>(map, rmap, a, grid, smem, s)
+                : kw == 3 ? bwdp_launch<T, BG, 3>(map, rmap, a, grid, smem, s)
+                          : bwdp_launch<T, BG, 6>(map, rmap, a, grid, smem, s);
+        }
+    } else {
+        e = kw == 0   ? bwdp_launch<T, BG, 0>(map, rmap, a, grid, smem, s)
+            : kw == 3 ? bwdp_launch<T, BG, 3>(map, rmap, a, grid, smem, s)
+                      : bwdp_launch<T, BG, 6>(map, rmap, a, grid, smem, s);
+    }
     if (e != cudaSuccess) {
         *why = std::string("packed adjoint launch: ") + cudaGetErrorString(e);
         return RADON_ERR_CUDA;

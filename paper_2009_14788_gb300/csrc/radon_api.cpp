@@ -104,6 +104,7 @@ void release(radon_geometry* g) {
     if (g->d_view) cudaFree(g->d_view);
     if (g->d_groups) cudaFree(g->d_groups);
     if (g->d_filter_taps) cudaFree(g->d_filter_taps);
+    free_adjoint_table(g);
     g->magic = 0;
     delete g;
 }
@@ -371,6 +372,41 @@ radon_status radon_geometry_copy_rays(const radon_geometry* g, float* rays, int3
 void radon_geometry_destroy(radon_geometry* geometry) {
     if (geometry == nullptr || geometry->magic != kGeometryMagic) return;
     release(geometry);
+}
+
+radon_status radon_geometry_adjoint_table_size(const radon_geometry* g, size_t* bytes) {
+    radon_status st = validate_geometry(g);
+    if (st != RADON_OK) return st;
+    if (bytes == nullptr) return fail(RADON_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = adjoint_table_bytes(g);
+    return RADON_OK;
+}
+
+radon_status radon_geometry_build_adjoint_table(radon_geometry* g) {
+    radon_status st = validate_geometry(g);
+    if (st != RADON_OK) return st;
+    if (g->host_only) return fail(RADON_ERR_INVALID_ARG, "host-only geometry");
+    st = check_device(g);
+    if (st != RADON_OK) return st;
+    std::string why;
+    st = build_adjoint_table(g, &why);
+    if (st != RADON_OK) return fail(st, why);
+    return RADON_OK;
+}
+
+radon_status radon_geometry_adjoint_table_overflow(const radon_geometry* g, double* fraction) {
+    radon_status st = validate_geometry(g);
+    if (st != RADON_OK) return st;
+    if (fraction == nullptr) return fail(RADON_ERR_INVALID_ARG, "fraction is NULL");
+    *fraction = g->d_tab_w != nullptr ? g->tab_overflow : 0.0;
+    return RADON_OK;
+}
+
+radon_status radon_geometry_free_adjoint_table(radon_geometry* g) {
+    radon_status st = validate_geometry(g);
+    if (st != RADON_OK) return st;
+    free_adjoint_table(g);
+    return RADON_OK;
 }
 
 radon_status radon_geometry_get_info(const radon_geometry* g, radon_geometry_info* out) {

@@ -86,6 +86,16 @@ struct radon_geometry {
     // FBP filter taps, (pi / V) k[m] for m = -(D-1) .. D-1 as (hi, lo) FP32 pairs, one row of 2D - 1
     // per radon_filter kind
     float2* d_filter_taps = nullptr;
+    // Weight table of the exact adjoint (built on request, radon_geometry_build_adjoint_table):
+    // [tile][view][pair] two float4 and one float2 of weights and an int32 first ray; NULL when absent
+    void* d_tab_w = nullptr;
+    void* d_tab_w5 = nullptr;
+    int* d_tab_la = nullptr;
+    int* d_tab_vflag = nullptr;   // [tile][view]: some pair of the tile overflows the table there
+    int tab_kw = 0;             // samples per candidate window it was built for
+    int tab_wd = 0;             // detector window it was built for
+    size_t tab_bytes = 0;
+    double tab_overflow = 0.0;  // fraction of (pair, view) records left to the on-the-fly weights
 };
 
 namespace radon {
@@ -147,6 +157,10 @@ cudaError_t launch_pack_sino(const void* sino, void* workspace, int V, int D, in
 
 // backward_packed.cu: the packed-sinogram adjoint (the workspace already holds pack_sino's output)
 int backward_packed_images_per_cta(const radon_geometry* g, int batch, radon_dtype dt, const radon_launch_config* cfg);
+// backward_packed.cu: the exact adjoint's weight table of a geometry (bytes it needs; build; free)
+size_t adjoint_table_bytes(const radon_geometry* g);
+radon_status build_adjoint_table(radon_geometry* g, std::string* why);
+void free_adjoint_table(radon_geometry* g);
 radon_status launch_backward_packed(const radon_geometry* g, const void* packed, void* img, radon_dtype dt, int batch,
                                     int images_per_cta, const Epilogue& ep, cudaStream_t s, std::string* why,
                                     bool interpolating = false);

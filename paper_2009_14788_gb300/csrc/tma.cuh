@@ -101,6 +101,11 @@ __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// Prefetch of `bytes` (a multiple of 16) from global `src` (16-byte aligned) into L2: a hint with no
+// completion to wait for.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 // Named barrier `id` over `nthreads` threads (a multiple of 32) that also ORs a predicate across
 // them: every participant gets true if any passed true.
 __device__ __forceinline__ bool named_barrier_or(int id, int nthreads, bool pred) {

@@ -92,6 +92,31 @@ class Geometry:
                 "radon_geometry_copy_rays")
         return rays, counts
 
+    def adjoint_table_bytes(self) -> int:
+        """Device bytes of the exact adjoint's weight table (see ``build_adjoint_table``)."""
+        b = ctypes.c_size_t()
+        L.check(L.radon_geometry_adjoint_table_size(self._h, ctypes.byref(b)), "radon_geometry_adjoint_table_size")
+        return int(b.value)
+
+    def build_adjoint_table(self) -> None:
+        """Precomputes the exact adjoint's bilinear weights on the geometry's device (tiles x views x 128
+        pixel pairs x 44 bytes, ``adjoint_table_bytes``); the packed adjoint then reads them instead of
+        computing them, with the same bits (pixel pairs whose weighted rays span more than five detectors
+        in a view keep computing theirs: ``adjoint_table_overflow``).  Raises ``RadonError``
+        (RADON_ERR_UNSUPPORTED) where the packed adjoint cannot serve the geometry."""
+        with torch.cuda.device(self.device):
+            L.check(L.radon_geometry_build_adjoint_table(self._h), "radon_geometry_build_adjoint_table")
+
+    def adjoint_table_overflow(self) -> float:
+        """Fraction of the table's (pixel pair, view) records left to the on-the-fly weights."""
+        f = ctypes.c_double()
+        L.check(L.radon_geometry_adjoint_table_overflow(self._h, ctypes.byref(f)),
+                "radon_geometry_adjoint_table_overflow")
+        return float(f.value)
+
+    def free_adjoint_table(self) -> None:
+        L.check(L.radon_geometry_free_adjoint_table(self._h), "radon_geometry_free_adjoint_table")
+
     def close(self):
         if self._h is not None and self._h.value:
             self._lib.radon_geometry_destroy(self._h)
