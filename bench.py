@@ -440,6 +440,21 @@ def run_ours(args):
     rooflines["backward"]["products_floor_basis"] = (
         "%d SMs x %.1f samples/clk/SM (128 FP32 FMA lanes/clk/SM / %.1f products per image-sample) x %.0f MHz"
         % (sm_count, 128.0 / ADJ_PRODUCTS_PER_SAMPLE, ADJ_PRODUCTS_PER_SAMPLE, clk_mhz))
+    if table is not None:
+        # with the weight table the adjoint no longer evaluates weights: its floor is the products (the
+        # per-sample weight-evaluation basis above stays as the table-free adjoint's), and it streams
+        # the table from HBM once per launch
+        weight_basis = dict(rooflines["backward"])
+        rooflines["backward"] = roofline(
+            B * S, mean_adj, sm_count, 128.0 / ADJ_PRODUCTS_PER_SAMPLE, clk_mhz,
+            "%d SMs x %.1f samples/clk/SM (128 FP32 FMA lanes/clk/SM / %.1f products per image-sample) x %.0f MHz"
+            % (sm_count, 128.0 / ADJ_PRODUCTS_PER_SAMPLE, ADJ_PRODUCTS_PER_SAMPLE, clk_mhz),
+            traffic_tab.get("backward_table"))
+        hbm = float(peaks.get("hbm_gbs", 6764.0))
+        rooflines["backward"]["table_hbm"] = {"achieved": table[0] / (mean_adj * 1e-3) / 1e9, "peak": hbm,
+                                              "unit": "GB/s", "frac": table[0] / (mean_adj * 1e-3) / 1e9 / hbm,
+                                              "bytes": table[0], "peak_basis": "hbm_gbs of MEASURED_PEAKS.json"}
+        rooflines["backward"]["frac_of_weight_evaluation_basis"] = weight_basis["frac"]
     rooflines["forward"]["probe_ceiling"] = probe.value / 1e9
     rooflines["forward"]["frac_of_probe"] = rooflines["forward"]["achieved"] / (probe.value / 1e9)
     if f16w is not None:

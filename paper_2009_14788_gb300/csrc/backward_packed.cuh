@@ -342,7 +342,9 @@ __global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasP
         const uint32_t rst_a = slot_a + kBwdPViews * ystv;
         const uint32_t ybuf_a = L::kConv ? yf_a + (uint32_t)(c & 1) * (uint32_t)m.yf_buf : slot_a;
         if (!bad) {
-            if constexpr (L::kConv) {
+            // (the table gather converts the 16-bit rows it reads itself: the widened rows serve only
+            // the on-the-fly weights, needed where the chunk's rays were copied)
+            if (L::kConv && (!TAB || rays_c[st])) {
                 // 16-bit window rows -> FP32 rows of pitch PITCH (8 images per 16-byte load); the
                 // view of item e is found by comparison (no division)
                 const int W = a.wd * OCT;
@@ -462,10 +464,25 @@ __global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasP
 #pragma unroll
                         for (int cr = 0; cr < kBwdTabRays; ++cr) {
                             const int rel = min(max(rel0 + cr, 0), a.wd - 1);
+                            // 16-bit storage: the landed row itself, converted in registers (half the
+                            // shared loads of the widened row, and no widening pass); FP32: the row
                             const uint32_t ya = yv + (uint32_t)rel * PITCH;
+                            const uint32_t yr = slot_a + (uint32_t)vl * ystv + (uint32_t)rel * (uint32_t)(BG * 2);
+                            float4 yw[NQ];
+                            if constexpr (L::kConv) {
+#pragma unroll
+                                for (int o = 0; o < NQ / 2; ++o) {
+                                    float4 f[2];
+                                    bwdp_widen8<T>(lds4u(yr + 16 * o), f);
+                                    yw[2 * o] = f[0];
+                                    yw[2 * o + 1] = f[1];
+                                }
+                            }
 #pragma unroll
                             for (int q = 0; q < NQ; ++q) {
-                                const float4 y4 = lds4(ya + 16 * q);
+                                float4 y4;
+                                if constexpr (L::kConv) y4 = yw[q];
+                                else y4 = lds4(ya + 16 * q);
                                 acc[0][4 * q + 0] = fmaf(wa[cr], y4.x, acc[0][4 * q + 0]);
                                 acc[0][4 * q + 1] = fmaf(wa[cr], y4.y, acc[0][4 * q + 1]);
                                 acc[0][4 * q + 2] = fmaf(wa[cr], y4.z, acc[0][4 * q + 2]);
