@@ -540,7 +540,8 @@ def run_secondary(args):
 
     * Landweber (8 x 512^2 parallel, 60 views in [0, pi), 725 detectors, bf16 storage): the step
       size by 20 power iterations, 10 Landweber iterations forward, and the reverse pass to the
-      gradients w.r.t. y and alpha (per-iteration checkpoints: 3 projections per iteration).
+      gradients w.r.t. y and alpha (per-iteration checkpoints: 3 projections per iteration); the
+      iterations again with the geometry's adjoint weight table.
     * The paper's batch benchmark shape (32 x 512^2 parallel, 512 views in [0, pi), 512
       detectors): forward + adjoint, chosen 16-bit form against the plain FP32 form.
     * The uneven batch (64 images, 16 each of 128^2 .. 1024^2, each with its own parallel geometry,
@@ -552,7 +553,7 @@ def run_secondary(args):
     """
     import torch
 
-    from paper_2009_14788_gb300 import Geometry, Landweber, backward_raw, forward_raw, launch_config
+    from paper_2009_14788_gb300 import Geometry, Landweber, _lib as L, backward_raw, forward_raw, launch_config
     from synth import power_start, uniform_angles, workload_noise
 
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
@@ -601,6 +602,12 @@ def run_secondary(args):
         loss = ((xk.float() - xt) ** 2).sum()
         loss.backward()
     ms_fb = time_it(fwd_bwd, 3)
+    # the same with the geometry's adjoint weight table (its 8-image groups read the weights)
+    tab = _try_adjoint_table(g, L)
+    ms_fwd_t = time_it(lambda: lw.run(x0, yg, ag, K), 3) if tab is not None else None
+    ms_fb_t = time_it(fwd_bwd, 3) if tab is not None else None
+    if tab is not None:
+        g.free_adjoint_table()
     proj_fwd = 2 * K * w.batch * S
     proj_bwd = 3 * K * w.batch * S
     out["landweber"] = {
@@ -610,6 +617,9 @@ def run_secondary(args):
         "samples_per_s_forward": proj_fwd / (ms_fwd * 1e-3),
         "samples_per_s_forward_backward": (proj_fwd + proj_bwd) / (ms_fb * 1e-3),
         "samples_per_s_power_iteration": 2 * P * S / (ms_power * 1e-3),
+        "with_adjoint_table": (None if tab is None else
+                               {"bytes": tab[0], "ms_forward": ms_fwd_t, "ms_forward_backward": ms_fb_t,
+                                "samples_per_s_forward_backward": (proj_fwd + proj_bwd) / (ms_fb_t * 1e-3)}),
         "l2": "flushed (2x L2 write) before each timed iteration",
     }
     del g, xt, y32, y, yg, ag, x0

@@ -580,6 +580,11 @@ class Radon:
 
     backward = backprojection
 
+    def build_adjoint_table(self) -> None:
+        """Precomputes the exact adjoint's weights for this geometry (``Geometry.build_adjoint_table``):
+        batched backprojections then read them, with the same bits."""
+        self.geometry.build_adjoint_table()
+
     def filter_sinogram(self, sino: torch.Tensor, filter_name: str = "ram-lak") -> torch.Tensor:
         """Section 3.1.3: the sinogram filtered for filtered backprojection (differentiable)."""
         return FilterSinogramFunction.apply(_autocast(sino), self.geometry, filter_name)
