@@ -329,3 +329,17 @@ def test_forward_workspace_covers_the_single_image_texels():
             assert one >= 2 * (n + 3) * pitch * texel
             two = int(L.radon_forward_workspace_size(g.handle, dt, 2))
             assert two > 0 and int(L.radon_forward_workspace_size(g.handle, dt, 0)) == 0
+
+
+def test_adjoint_table_size_and_refusals_on_the_host():
+    """The weight table's size is a closed form of the geometry (tiles x views x (128 pairs x 44 + 4)
+    bytes); a host-only geometry can be asked for it but cannot build one, and without a table the
+    overflow fraction is 0."""
+    for n, V in ((1, 3), (40, 7), (97, 13)):
+        g = Geometry("parallel", n, uniform_angles(V, math.pi), host_only=True)
+        tiles = ((n + 15) // 16) ** 2
+        assert g.adjoint_table_bytes() == tiles * V * (128 * 44 + 4)
+        assert g.adjoint_table_overflow() == 0.0
+        st = L.radon_geometry_build_adjoint_table(g.handle)
+        assert st == L.RADON_ERR_INVALID_ARG
+        assert L.radon_geometry_free_adjoint_table(g.handle) == L.RADON_OK
