@@ -543,7 +543,8 @@ def run_secondary(args):
       gradients w.r.t. y and alpha (per-iteration checkpoints: 3 projections per iteration); the
       iterations again with the geometry's adjoint weight table.
     * The paper's batch benchmark shape (32 x 512^2 parallel, 512 views in [0, pi), 512
-      detectors): forward + adjoint, chosen 16-bit form against the plain FP32 form.
+      detectors): forward + adjoint, chosen 16-bit form against the plain FP32 form, without and
+      with the geometry's adjoint weight table.
     * The uneven batch (64 images, 16 each of 128^2 .. 1024^2, each with its own parallel geometry,
       fp16): one forward plan and one adjoint plan (autotuned at creation) replayed as one CUDA
       graph, against one library call per image and direction.
@@ -646,6 +647,25 @@ def run_secondary(args):
         del x, yb, oy, ox
     res["speedup_chosen_vs_plain_f32"] = res["plain_f32"]["ms_per_step"] / res["chosen_f16"]["ms_per_step"]
     res["speedup_chosen_vs_tuned_f32"] = res["tuned_f32"]["ms_per_step"] / res["chosen_f16"]["ms_per_step"]
+    # the same two tuned forms with the geometry's adjoint weight table (16-image groups reading it)
+    tab = _try_adjoint_table(g, L)
+    if tab is not None:
+        res["adjoint_table_bytes"] = tab[0]
+        for label, dt in (("chosen_f16_table", torch.float16), ("tuned_f32_table", torch.float32)):
+            cfg = launch_config("auto")
+            x = torch.from_numpy(xs).to("cuda", dt)
+            yb = forward_raw(g, x, cfg)
+            oy, ox = torch.empty_like(yb), torch.empty_like(x)
+
+            def fa():
+                forward_raw(g, x, cfg, out=oy)
+                backward_raw(g, yb, cfg, out=ox)
+            ms = time_it(fa, 5, warm=1)
+            res[label] = {"ms_per_step": ms, "samples_per_s": 2 * B * S / (ms * 1e-3), "images_per_s": B / (ms * 1e-3)}
+            del x, yb, oy, ox
+        g.free_adjoint_table()
+        res["speedup_chosen_table_vs_plain_f32"] = (res["plain_f32"]["ms_per_step"] /
+                                                    res["chosen_f16_table"]["ms_per_step"])
     out["paper_batch"] = res
     del xs
     # the uneven batch: 64 images of 128^2..1024^2, each with its own geometry, in one persistent

@@ -52,6 +52,10 @@ int backward_packed_images_per_cta(const radon_geometry* g, int batch, radon_dty
     if (cfg != nullptr && cfg->images_per_cta != 0) return cfg->images_per_cta;
     if (batch <= 8) return 8;
     if (batch <= 16) return 16;
+    // with the geometry's weight table 16-bit 16-image groups read their weights, which measured faster
+    // than 32-image groups computing them (parallel 32 x 512^2, 512 views, FP16 adjoint: 1.84 vs 1.94
+    // ms; FP32 rows measured no faster: a step of 4.32 vs 4.27 ms)
+    if (g->d_tab_w != nullptr && dt != RADON_F32) return 16;
     // A 32-image CTA costs ~1.56x a 16-image one (each weight serves twice the images; two CTAs per
     // SM): take it when its groups cost less and its staging fits one CTA's shared memory.
     const long long g32 = (batch + 31) / 32, g16 = (batch + 15) / 16;

@@ -93,7 +93,8 @@ struct BwdPArgs {
     Epilogue ep;
     const float4* tab_w;   // weight table (TAB kernels): [tile][view][pair] two float4s, see bwdp_table_kernel
     const float2* tab_w5;  // [tile][view][pair] the fifth ray's weights of both pixels
-    const int* tab_la;     // [tile][view][pair] the first of the pair's five table rays (detector index)
+    const int* tab_la;     // [tile][view][pair] 8 la + n: the first of the pair's five table rays (detector
+                           // index la) and how many of them weigh (n <= 5), or kBwdTabOverflow
     const int* tab_vflag;  // [tile][view] nonzero where some pair of the tile overflows in that view
 };
 
@@ -443,11 +444,16 @@ __global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasP
             } else {
                 bool tabbed = false;
                 if constexpr (TAB) {
-                    // the pair's four table rays from la: rows clamped into the window (a clamped row
-                    // has weight zero); the same nonzero products, in the same order, as the gather
+                    // the pair's table rays from la: rows clamped into the window (a clamped row has
+                    // weight zero); the same nonzero products, in the same order, as the gather.  The
+                    // warp runs to the largest count of weighted rays among its pairs (the rest of a
+                    // pair's five carry zero weight)
                     const float4 w0 = tw0, w1 = tw1;
                     const float2 w5 = tw5;
-                    const int la_t = tla;
+                    const int pk = tla;
+                    const bool over_t = pk == kBwdTabOverflow;
+                    const int la_t = pk >> 3;
+                    const int nc = __reduce_max_sync(0xffffffffu, over_t ? 0 : (pk & 7));
                     const int vnext = v0 + vl + 1;
                     if (vnext < a.V) {
                         const size_t nr = trec0 + (size_t)vnext * kBwdTabPairs;
@@ -456,13 +462,14 @@ __global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasP
                         tw5 = __ldg(a.tab_w5 + nr);
                         tla = __ldg(a.tab_la + nr);
                     }
-                    if (la_t != kBwdTabOverflow) {
+                    if (!over_t) {
                         tabbed = true;
                         const int rel0 = la_t - dlo;
                         const float wa[kBwdTabRays] = {w0.x, w0.y, w0.z, w0.w, w5.x};
                         const float wb[kBwdTabRays] = {w1.x, w1.y, w1.z, w1.w, w5.y};
 #pragma unroll
                         for (int cr = 0; cr < kBwdTabRays; ++cr) {
+                            if (cr >= nc) break;
                             const int rel = min(max(rel0 + cr, 0), a.wd - 1);
                             // 16-bit storage: the landed row itself, converted in registers (half the
                             // shared loads of the widened row, and no widening pass); FP32: the row
@@ -554,7 +561,8 @@ __global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasP
 // consumer pixel pair (bwdp_pair_of).  For each view the thread takes the pair's candidate rays as the
 // gather does (the tile's window, the union of the pixels' ranges [t - r, t + r] clamped to it),
 // re-bases each on the tile and evaluates both pixels' weights with bwdp_weight; it stores the first
-// ray that weighs on either pixel (la) and the weights on rays la .. la + 4, or kBwdTabOverflow where
+// ray that weighs on either pixel (la), the count of weighted rays from it and the weights on rays
+// la .. la + 4 (record 8 la + count), or kBwdTabOverflow where
 // the weighted rays span more than five (counted in *overflow, and flagged for the tile and view in
 // tab_vflag, which must start at zero).
 template <int KW>
@@ -623,7 +631,7 @@ __global__ void __launch_bounds__(kBwdTabPairs) bwdp_table_kernel(const RayT* __
         tab_w[2 * rec] = make_float4(wa[0], wa[1], wa[2], wa[3]);
         tab_w[2 * rec + 1] = make_float4(wb[0], wb[1], wb[2], wb[3]);
         tab_w5[rec] = make_float2(wa[4], wb[4]);
-        tab_la[rec] = over ? kBwdTabOverflow : dlo + first;
+        tab_la[rec] = over ? kBwdTabOverflow : (dlo + first) * 8 + (f >= 0 ? l - f + 1 : 0);
     }
 }
 

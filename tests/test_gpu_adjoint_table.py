@@ -3,8 +3,8 @@
 The table holds, per 16 x 16 tile, view and pixel pair, the weights that the packed adjoint computes on
 the fly, computed by the same arithmetic; the adjoint that reads them adds the same nonzero products in
 the same order.  So its results must equal the table-free adjoint bit for bit (and meet the FP64
-oracle's gates), for every storage type and for the 8- and 16-image groups that it serves; larger
-groups keep computing their weights.  Geometries whose pixel pairs weigh on rays spanning more than
+oracle's gates), for every storage type and for the 8- and 16-image groups that it serves (batches
+of more than 16 images run 16-image groups while a table exists).  Geometries whose pixel pairs weigh on rays spanning more than
 five detectors in a view keep computing their weights for those views (the table marks them); only
 geometries the packed adjoint cannot serve are refused.
 """
@@ -53,9 +53,10 @@ def test_table_adjoint_equals_the_gather_bit_for_bit(case, dtype):
     assert torch.equal(backward_raw(g, ys[3]), want[3])
 
 
-def test_table_leaves_larger_groups_and_single_images_alone():
-    """32-image groups (one pixel per thread) and batch-1 calls run their own kernels with or without
-    a table: the same bits either way."""
+def test_table_serves_larger_batches_and_leaves_single_images_alone():
+    """With a table, batches of more than 16 images run 16-image groups that read it instead of
+    32-image groups that compute their weights (one pixel per thread); batch-1 calls keep their own
+    kernel.  The same bits either way."""
     g, og = make("fan_n512_sub")
     rng = np.random.default_rng(5)
     y40 = to_dev(rng.normal(size=(40,) + g.sino_shape), torch.float16)
