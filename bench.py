@@ -549,7 +549,8 @@ def run_secondary(args):
       fp16): one forward plan and one adjoint plan (autotuned at creation) replayed as one CUDA
       graph, against one library call per image and direction.
     * Filtered backprojection at the paper's FBP setting (512^2, 512 views, 725 detectors, Ram-Lak),
-      and CGNE (20 iterations) at the same setting.
+      and CGNE (20 iterations) at the same setting; the batched ones also with the geometry's adjoint
+      weight table.
     * The pixel-driven interpolating backprojector against the exact adjoint on the headline workload.
     """
     import torch
@@ -748,7 +749,9 @@ def run_secondary(args):
     g = Geometry("parallel", 512, uniform_angles(512, np.pi), det_count=D, det_spacing=1.0)
     res = {"workload": "parallel_n512_v512_d725_ramlak", "storage": "f32",
            "l2": "flushed (2x L2 write) before each timed call"}
-    for B in (1, 16):
+    for B, table in ((1, False), (16, False), (16, True)):
+        if table and _try_adjoint_table(g, L) is None:
+            continue
         x = torch.from_numpy(np.stack([ellipse_phantom(512, 10, 4242 + b) for b in range(B)])).to("cuda", torch.float32)
         y = forward_raw(g, x)
         q = torch.empty_like(y)
@@ -759,21 +762,26 @@ def run_secondary(args):
             filter_sinogram(g, y, "ram-lak", out=q)
             backward_raw(g, q, out=rec)
         ms_fbp = time_it(fbp, 5)
-        res["batch%d" % B] = {"ms_filter": ms_f, "ms_fbp": ms_fbp, "images_per_s": B / (ms_fbp * 1e-3)}
+        res["batch%d%s" % (B, "_table" if table else "")] = {"ms_filter": ms_f, "ms_fbp": ms_fbp,
+                                                            "images_per_s": B / (ms_fbp * 1e-3)}
         del x, y, q, rec
+    g.free_adjoint_table()
     out["fbp"] = res
     # CGNE at the same setting (Section 4.2 runs 500 iterations): 20 iterations, batch 1 and 8
     from paper_2009_14788_gb300 import cgne
     res = {"workload": "parallel_n512_v512_d725", "storage": "f32", "iterations": 20,
            "l2": "flushed (2x L2 write) before each timed call"}
-    for B in (1, 8):
+    for B, table in ((1, False), (8, False), (8, True)):
+        if table and _try_adjoint_table(g, L) is None:
+            continue
         x = torch.from_numpy(np.stack([ellipse_phantom(512, 10, 4242 + b) for b in range(B)])).to("cuda", torch.float32)
         y = forward_raw(g, x)
         x0 = torch.zeros_like(x)
         ms = time_it(lambda: cgne(g, x0, y, 20), 3, warm=1)
-        res["batch%d" % B] = {"ms": ms, "ms_per_iteration": ms / 20,
-                              "samples_per_s": 2 * 20 * B * g.sample_count / (ms * 1e-3)}
+        res["batch%d%s" % (B, "_table" if table else "")] = {
+            "ms": ms, "ms_per_iteration": ms / 20, "samples_per_s": 2 * 20 * B * g.sample_count / (ms * 1e-3)}
         del x, y, x0
+    g.free_adjoint_table()
     out["cgne"] = res
     # the pixel-driven interpolating backprojector against the exact adjoint, headline workload
     from paper_2009_14788_gb300 import backproject_interpolating
@@ -786,8 +794,11 @@ def run_secondary(args):
     ox = torch.empty_like(x)
     ms_i = time_it(lambda: backproject_interpolating(g, y, out=ox), 5)
     ms_a = time_it(lambda: backward_raw(g, y, out=ox), 5)
+    ms_t = time_it(lambda: backward_raw(g, y, out=ox), 5) if _try_adjoint_table(g, L) is not None else None
+    g.free_adjoint_table()
     out["interpolating_backprojection"] = {"workload": w.name, "storage": "f16", "ms": ms_i,
-                                           "exact_adjoint_ms": ms_a, "speedup_vs_exact_adjoint": ms_a / ms_i}
+                                           "exact_adjoint_ms": ms_a, "speedup_vs_exact_adjoint": ms_a / ms_i,
+                                           "exact_adjoint_with_table_ms": ms_t}
     del x, y, ox
     del flush
     torch.cuda.empty_cache()
