@@ -149,3 +149,51 @@ def test_full_size_headline_geometry_with_table_against_oracle_on_sampled_views(
         assert rel_l2(to_np(got), O.adjoint(og, to_np(ys))) <= TOL_16
     finally:
         gs.free_adjoint_table()
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
+def test_table_under_fused_epilogues_graphs_and_autograd(dtype):
+    """The table serves every caller of the packed adjoint: a fused epilogue (device step length and
+    addend, the Landweber update), a CUDA-graph replay, and the gradient of the forward projection
+    through autograd -- each equal, bit for bit, to the same call without a table."""
+    from paper_2009_14788_gb300 import Radon, backward_fused
+    from synth import uniform_angles
+    g, og = make("parallel_n256_sub")
+    rng = np.random.default_rng(12)
+    y = to_dev(rng.normal(size=(6,) + g.sino_shape), dtype)
+    add = to_dev(rng.normal(size=(6, g.n, g.n)), dtype)
+    s_dev = torch.tensor([0.37], device="cuda")
+
+    def fused():
+        return backward_fused(g, y, op_scale=-1.5, op_scale_dev=s_dev, add=add, add_scale=0.5)
+
+    radon = Radon(64, uniform_angles(33, np.pi), det_count=91)
+    x = torch.from_numpy(rng.uniform(0.0, 1.0, (6, 64, 64))).to("cuda", torch.float32)
+
+    def grad():
+        xg = x.clone().requires_grad_(True)
+        (radon.forward(xg) ** 2).sum().backward()
+        return xg.grad
+
+    want_f, want_g = fused(), grad()
+    stream = torch.cuda.Stream()
+    g.build_adjoint_table()
+    radon.build_adjoint_table()
+    try:
+        assert torch.equal(fused(), want_f)
+        assert torch.equal(grad(), want_g)
+        out = torch.empty_like(want_f)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
+            backward_fused(g, y, op_scale=-1.5, op_scale_dev=s_dev, add=add, add_scale=0.5, out=out)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(graph, stream=stream):
+                backward_fused(g, y, op_scale=-1.5, op_scale_dev=s_dev, add=add, add_scale=0.5, out=out)
+        out.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, want_f)
+        _clean()
+    finally:
+        g.free_adjoint_table()
+        radon.geometry.free_adjoint_table()
