@@ -195,6 +195,12 @@ def test_batch_plan_rejects_bad_arguments_without_gpu():
     opts = L.radon_plan_options(1, 0, 0, 2)
     assert L.radon_batch_plan_create(items, 2, 0, 0, ctypes.byref(opts), ctypes.byref(out)) == L.RADON_ERR_INVALID_ARG
     assert "forward_lanes" in L.radon_last_error_message()
+    opts = L.radon_plan_options(1, 0, 0, 0, 12)
+    assert L.radon_batch_plan_create(items, 2, 0, 0, ctypes.byref(opts), ctypes.byref(out)) == L.RADON_ERR_INVALID_ARG
+    assert "forward_rows" in L.radon_last_error_message()
+    opts = L.radon_plan_options(1, 0, 0, 0, 0, 2)
+    assert L.radon_batch_plan_create(items, 2, 0, 0, ctypes.byref(opts), ctypes.byref(out)) == L.RADON_ERR_INVALID_ARG
+    assert "forward_kernel" in L.radon_last_error_message()
     bad = (L.radon_item * 1)(L.radon_item(None, p, p + 64, 1))
     assert L.radon_batch_plan_create(bad, 1, 0, 0, None, ctypes.byref(out)) == L.RADON_ERR_INVALID_ARG
     # a dead handle is refused by every plan call
