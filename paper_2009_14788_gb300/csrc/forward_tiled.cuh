@@ -16,6 +16,9 @@
 //     loads fetch the 2x2 texels of every image -- and release the buffer.
 // Each ray re-bases its next sample on the band origin from the split-precision table at every
 // slab.  All waits are bounded; on expiry the kernel records RADON_ERR_TIMEOUT and unwinds.
+// The packed variant streams only the slabs between the first and the last in which one of the CTA's
+// rays has a sample (about half of all slabs on a fan whose detector is wider than the image; a CTA
+// whose rays all miss the image streams none), and hands its CTAs out centre-out along the detector.
 // Shared memory: header (mbarriers, band origins, abort flag), staging buffer, two compute
 // buffers of (R+2) x wc texels.
 #pragma once
@@ -343,7 +346,7 @@ __device__ void fwd_repack(const FwdTiledArgs& a, int cls, int yoff, const unsig
 template <typename T, int MODE>
 __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int d0, int b0, uint64_t* full,
                             uint64_t* empty, const int* band_xc0, const int* band_bad, volatile int* abort_flag,
-                            const unsigned char* comp_base, size_t comp_stride, int wc) {
+                            const unsigned char* comp_base, size_t comp_stride, int wc, int* slab_rng) {
     using TX = Texel<T, MODE>;
     constexpr int BG = TX::BG;
     const int tid = threadIdx.x;
@@ -374,13 +377,38 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
         }
     }
     const float dX = dXh + dXl, dY = dYh + dYl;
+    // Slabs [s_lo, s_hi] hold the CTA's samples: slab s takes a ray's samples whose compute-frame row
+    // Y (= I0 + fY0 + k dY, increasing with k) lies below R (s + 1) - 3, from the first slab on where
+    // that holds (the loop below), so sample Y falls in slab floor((Y + 3) / R).  With slab_rng the
+    // consumer warps reduce their rays' first and last slabs (a 0.01-row margin absorbs rounding)
+    // and the producer streams only that range; slabs outside it would give no ray a sample, so the
+    // sums are the same bits.  A CTA none of whose rays meets the image streams nothing.
+    int s_lo = 0, s_hi = a.n_slabs - 1;
+    if (slab_rng != nullptr) {
+        int lo = 0x7fffffff, hi = -1;
+        if (nk > 0) {
+            const float y0 = (float)I0 + fY0, y1 = fmaf((float)(nk - 1), dY, y0);
+            lo = max((int)floorf((fminf(y0, y1) + 2.99f) / (float)a.R), 0);
+            hi = min((int)floorf((fmaxf(y0, y1) + 3.01f) / (float)a.R), a.n_slabs - 1);
+        }
+        lo = __reduce_min_sync(0xffffffffu, lo);
+        hi = __reduce_max_sync(0xffffffffu, hi);
+        if ((tid & 31) == 0) {
+            atomicMin(&slab_rng[0], lo);
+            atomicMax(&slab_rng[1], hi);
+        }
+        named_barrier_sync(1, kFwdThreads);   // with the producer warp
+        s_lo = slab_rng[0];
+        s_hi = slab_rng[1];
+    }
     int k = 0;
     typename TX::Acc acc;
     acc.zero();
 
-    for (int s = 0; s < a.n_slabs; ++s) {
-        const int buf = s % a.stages;
-        if (!mbar_wait_bounded(&full[buf], (uint32_t)((s / a.stages) & 1), a.spin_limit)) {
+    for (int s = s_lo; s <= s_hi; ++s) {
+        const int j = s - s_lo;   // ring position
+        const int buf = j % a.stages;
+        if (!mbar_wait_bounded(&full[buf], (uint32_t)((j / a.stages) & 1), a.spin_limit)) {
             record_device_error(a.err, RADON_ERR_TIMEOUT);
             return;
         }
@@ -564,7 +592,7 @@ __global__ void __launch_bounds__(kFwdThreads, 3) forward_tiled_kernel(const __g
     }
 
     fwd_consume<T, MODE>(a, cls, v0, cnt, d0, b0, full, empty, band_xc0, band_bad, abort_flag, comp_base, comp_stride,
-                   a.wc);
+                   a.wc, nullptr);
 }
 
 // Packed variant: the image batch was packed once into 16-byte texels (rows / cols copies, see
@@ -581,12 +609,17 @@ __global__ void __launch_bounds__(kFwdThreads, 3) forward_packed_kernel(const __
     int* band_xc0 = reinterpret_cast<int*>(smem + 64);          // [stages]
     int* band_bad = reinterpret_cast<int*>(smem + 80);          // [stages]
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 96);
+    int* slab_rng = reinterpret_cast<int*>(smem + 104);         // [2]: first, last slab with samples
     const size_t comp_stride = (fwd_comp_bytes(a.R, a.wbox) + 127) / 128 * 128;
     unsigned char* comp_base = smem + 128;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
-    const int grp_idx = blockIdx.x / a.n_dr, dr = blockIdx.x - (blockIdx.x / a.n_dr) * a.n_dr;
+    // CTAs are handed out in index order, so the detector ranges run centre-out: the ranges whose rays
+    // cross the middle of the image (the longest) start first and the short outer ones fill the tail.
+    const int n_grp = gridDim.x / a.n_dr;
+    const int rank = blockIdx.x / n_grp, grp_idx = blockIdx.x - rank * n_grp;
+    const int dr = (rank & 1) ? ((a.n_dr + 1) / 2 + (rank >> 1)) : ((a.n_dr - 1) / 2 - (rank >> 1));
     const Int2 grp = a.groups[grp_idx];
     const int v0 = grp.x, cnt = grp.y & 0xffff, cls = grp.y >> 16;
     const int d0 = dr * a.Dt;
@@ -596,7 +629,11 @@ __global__ void __launch_bounds__(kFwdThreads, 3) forward_packed_kernel(const __
         mbar_init(&full[tid], 1);
         mbar_init(&empty[tid], kFwdRays);
     }
-    if (tid == 0) *abort_flag = 0;
+    if (tid == 0) {
+        *abort_flag = 0;
+        slab_rng[0] = 0x7fffffff;
+        slab_rng[1] = -1;
+    }
     fence_mbar_init();
     __syncthreads();
 
@@ -604,12 +641,15 @@ __global__ void __launch_bounds__(kFwdThreads, 3) forward_packed_kernel(const __
         const int lane = tid & 31;
         const CUtensorMap* map = cls ? &map_cols : &map_rows;
         const FwdEdge edge = fwd_edge(a, v0, cnt, cls, d0);
-        for (int s = 0; s < a.n_slabs; ++s) {
-            const int buf = s % a.stages;
+        named_barrier_sync(1, kFwdThreads);   // the consumers have reduced the slab range
+        const int s_lo = slab_rng[0], s_hi = slab_rng[1];
+        for (int s = s_lo; s <= s_hi; ++s) {
+            const int j = s - s_lo;
+            const int buf = j % a.stages;
             const FwdBand band = fwd_band(a, edge, s, 1);
             bool ok = true;
-            if (s >= a.stages && lane == 0)
-                ok = mbar_wait_bounded(&empty[buf], (uint32_t)((s / a.stages - 1) & 1), a.spin_limit);
+            if (j >= a.stages && lane == 0)
+                ok = mbar_wait_bounded(&empty[buf], (uint32_t)((j / a.stages - 1) & 1), a.spin_limit);
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (lane == 0) {
                 if (!ok) {
@@ -631,7 +671,7 @@ __global__ void __launch_bounds__(kFwdThreads, 3) forward_packed_kernel(const __
         return;
     }
     fwd_consume<T, MODE>(a, cls, v0, cnt, d0, b0, full, empty, band_xc0, band_bad, abort_flag, comp_base, comp_stride,
-                   a.wbox);
+                   a.wbox, slab_rng);
 }
 
 }  // namespace radon

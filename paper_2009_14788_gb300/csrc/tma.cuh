@@ -106,6 +106,10 @@ __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, u
 __device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
+// Named barrier `id` over `nthreads` threads (a multiple of 32).
+__device__ __forceinline__ void named_barrier_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
 // Named barrier `id` over `nthreads` threads (a multiple of 32) that also ORs a predicate across
 // them: every participant gets true if any passed true.
 __device__ __forceinline__ bool named_barrier_or(int id, int nthreads, bool pred) {
