@@ -196,7 +196,8 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2009_14788_gb300 import Geometry, _lib as L, backward_raw, forward_raw, launch_config
+    from paper_2009_14788_gb300 import (Geometry, _lib as L, backward_raw, forward_images_per_cta, forward_raw,
+                                        launch_config)
     from paper_2009_14788_gb300.build import build
 
     world, rank, local = _dist()
@@ -414,9 +415,13 @@ def run_ours(args):
                 traffic_tab = json.load(f).get(args.workload, {}).get(args.storage, {})
         except (OSError, ValueError):
             traffic_tab = {}
+    # the gather-ceiling probe over as many texel groups per sample as the chosen forward's CTAs take
     probe = ctypes.c_double(0.0)
     dt_code = {"f32": L.RADON_F32, "f16": L.RADON_F16, "bf16": L.RADON_BF16}[args.storage]
-    L.check(L.radon_probe_gather_ceiling_ex(dt_code, 0, ctypes.byref(probe)), "radon_probe_gather_ceiling_ex")
+    bg = 4 if args.storage == "f32" else 8
+    fwd_groups = max(1, forward_images_per_cta(geom, dt, B, chosen) // bg)
+    L.check(L.radon_probe_gather_ceiling_groups(dt_code, 0, fwd_groups, ctypes.byref(probe)),
+            "radon_probe_gather_ceiling_groups")
     rooflines = {
         # forward: 4 texels per sample through the shared-memory / L1 load pipe, 128 B/clk/SM
         "forward": roofline(B * S, mean_fwd, sm_count, 128.0 / (4.0 * bytes_per_texel), clk_mhz,
@@ -457,9 +462,12 @@ def run_ours(args):
         rooflines["backward"]["frac_of_weight_evaluation_basis"] = weight_basis["frac"]
     rooflines["forward"]["probe_ceiling"] = probe.value / 1e9
     rooflines["forward"]["frac_of_probe"] = rooflines["forward"]["achieved"] / (probe.value / 1e9)
+    rooflines["forward"]["images_per_cta"] = fwd_groups * bg
     if f16w is not None:
         probe2 = ctypes.c_double(0.0)
-        L.check(L.radon_probe_gather_ceiling_ex(L.RADON_F16, 2, ctypes.byref(probe2)), "radon_probe_gather_ceiling_ex")
+        w2_groups = max(1, forward_images_per_cta(geom, dt, B, launch_config(args.algo, weights=2)) // 8)
+        L.check(L.radon_probe_gather_ceiling_groups(L.RADON_F16, 2, w2_groups, ctypes.byref(probe2)),
+                "radon_probe_gather_ceiling_groups")
         f16w["roofline"] = roofline(B * S, f16w["fwd_ms"], sm_count, 128.0 / (4.0 * bytes_per_texel), clk_mhz,
                                     rooflines["forward"]["peak_basis"].split(" (")[0], None)
         f16w["roofline"]["probe_ceiling"] = probe2.value / 1e9

@@ -215,7 +215,9 @@ typedef struct {
     int views_per_cta;   /* TILED forward: views per CTA (0 = default) */
     int rows_per_slab;   /* TILED forward: image rows staged per step (0 = default) */
     int images_per_cta;  /* TILED: images sharing the geometry work in one CTA (0 = default; the packed
-                            adjoint takes 8, 16 or 32, the staged one 4, 8 or 16) */
+                            adjoint takes 8, 16 or 32, the staged one 4, 8 or 16; the packed forward one
+                            or two texel groups: 8 or 16 for 16-bit storage, 4 or 8 for FP32, other
+                            values leaving it at its default) */
     int tile;            /* TILED backward: pixel tile side (0 = default) */
     int threads;         /* threads per CTA (0 = default) */
     int weights;         /* forward, FP16 storage: RADON_WEIGHTS_* (0 = default = FP32 weights) */
@@ -236,6 +238,17 @@ RADON_API radon_status radon_backward_ex(const radon_geometry* geometry, const v
 RADON_API size_t radon_forward_workspace_size(const radon_geometry* geometry, radon_dtype dtype, int batch);
 
 /*
+ * Images per CTA of the packed forward that radon_forward_ws (with a large enough workspace) runs for
+ * this call: one texel group (8 for 16-bit storage, 4 for FP32) or two groups whose images share each
+ * sample's position, floor and weight evaluation (16 / 8).  By default 16-bit batches of more than 8
+ * images take two groups and FP32 one; `config`'s images_per_cta chooses where it holds one of those
+ * values.  *images = 0 when another kernel serves the call (one image under AUTO, the PLAIN algorithm,
+ * a geometry no packed shape takes).  Host only (host-only geometries are answered too); no launch.
+ */
+RADON_API radon_status radon_forward_images_per_cta(const radon_geometry* geometry, radon_dtype dtype, int batch,
+                                                    const radon_launch_config* config, int* images);
+
+/*
  * Forward projection with a caller-owned device workspace (>= radon_forward_workspace_size bytes,
  * 16-byte aligned, used in stream order on `stream`, contents overwritten).  The batch is packed
  * once into the workspace, then every CTA copies its bands of texels straight into shared memory
@@ -248,10 +261,12 @@ RADON_API radon_status radon_forward_ws(const radon_geometry* geometry, const vo
 
 /*
  * Device workspace, in bytes, that radon_backward_ws uses for `batch` sinograms of `dtype`: the
- * batch packed into FP32 quads of images, laid out [group][view][quad][detector][4], with 8 images
- * per group for batches of at most 8, 16 up to 16, and above that 32 where whole groups of 32 cost
- * less than groups of 16 (a 32-image CTA costs ~1.56x a 16-image one) and their staging fits one
- * CTA's shared memory, else 16.  Returns 0 for an invalid geometry, dtype or batch.
+ * batch packed into one row per (group, view, detector), laid out [group][view][detector][row], a row
+ * holding the group's images in the storage type (bg 16-bit values, or bg FP32 values and four
+ * padding words).  Groups of bg = 8 images for batches of at most 8, 16 up to 16; above that 16 for
+ * 16-bit storage when the geometry holds an adjoint weight table, else 32 where whole groups of 32
+ * cost less than groups of 16 (a 32-image CTA costs ~1.56x a 16-image one) and their staging fits
+ * one CTA's shared memory, else 16.  Returns 0 for an invalid geometry, dtype or batch.
  */
 RADON_API size_t radon_backward_workspace_size(const radon_geometry* geometry, radon_dtype dtype, int batch);
 
@@ -574,14 +589,18 @@ RADON_API void radon_batch_plan_destroy(radon_plan* plan);
 /*
  * Measures the achievable rate of the forward projection's inner loop on the current GPU: a kernel
  * that marches straight rays through a shared-memory-resident tile of batch-interleaved texels (four
- * 16-byte loads, one floor / weight evaluation and FP32 accumulation for every image of the texel per
- * sample, no geometry, no TMA) on every SM, with the forward's own accumulation code for `dtype`
- * storage and the `weights` setting of radon_launch_config (RADON_WEIGHTS_F16 for FP16 storage only).
- * *samples_per_second receives image-samples per second (one probe sample serves the 8 (16-bit) or
- * 4 (F32) images of a texel), the ceiling the forward's measured rate is compared with.
- * Synchronises the device; not capturable.  radon_probe_gather_ceiling(dtype, out) is
- * radon_probe_gather_ceiling_ex(dtype, RADON_WEIGHTS_DEFAULT, out).
+ * 16-byte loads per texel group, one floor / weight evaluation and FP32 accumulation for every image
+ * of the texels per sample, no geometry, no TMA) on every SM, with the forward's own accumulation
+ * code for `dtype` storage and the `weights` setting of radon_launch_config (RADON_WEIGHTS_F16 for
+ * FP16 storage only), over `groups` (1 or 2) texel groups per sample as the packed forward's CTAs
+ * take them (radon_forward_images_per_cta).  *samples_per_second receives image-samples per second
+ * (one probe sample serves the 8 (16-bit) or 4 (F32) images of each texel group), the ceiling the
+ * forward's measured rate is compared with.  Synchronises the device; not capturable.
+ * radon_probe_gather_ceiling_ex(dtype, weights, out) takes one group;
+ * radon_probe_gather_ceiling(dtype, out) is radon_probe_gather_ceiling_ex(dtype, RADON_WEIGHTS_DEFAULT, out).
  */
+RADON_API radon_status radon_probe_gather_ceiling_groups(radon_dtype dtype, int weights, int groups,
+                                                         double* samples_per_second);
 RADON_API radon_status radon_probe_gather_ceiling_ex(radon_dtype dtype, int weights, double* samples_per_second);
 RADON_API radon_status radon_probe_gather_ceiling(radon_dtype dtype, double* samples_per_second);
 

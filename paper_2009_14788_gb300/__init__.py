@@ -24,6 +24,7 @@ from .radon import (  # noqa: F401
     dot,
     filter_sinogram,
     forward_fused,
+    forward_images_per_cta,
     forward_raw,
     forward_workspace_bytes,
     launch_config,
@@ -35,5 +36,5 @@ __all__ = [
     "backward_raw", "launch_config", "forward_workspace_bytes", "backward_workspace_bytes", "forward_fused",
     "backward_fused", "dot", "axpby", "power_iteration", "Landweber", "LandweberFunction", "landweber", "BatchPlan",
     "filter_sinogram", "FilterSinogramFunction", "cg", "cgne",
-    "backproject_interpolating",
+    "backproject_interpolating", "forward_images_per_cta",
 ]

@@ -152,6 +152,8 @@ _SIGNATURES = [
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
       ctypes.POINTER(radon_launch_config), ctypes.c_void_p]),
     ("radon_forward_workspace_size", ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    ("radon_forward_images_per_cta", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(radon_launch_config), ctypes.POINTER(ctypes.c_int)]),
     ("radon_forward_ws", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
       ctypes.POINTER(radon_launch_config), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
@@ -190,6 +192,8 @@ _SIGNATURES = [
     ("radon_batch_plan_destroy", None, [ctypes.c_void_p]),
     ("radon_probe_gather_ceiling", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     ("radon_probe_gather_ceiling_ex", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    ("radon_probe_gather_ceiling_groups", ctypes.c_int,
+     [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     ("radon_filter_sinogram", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     ("radon_dot_batched_workspace_size", ctypes.c_size_t, [ctypes.c_int]),
@@ -322,6 +326,10 @@ def radon_forward_workspace_size(geom, dtype, batch):
     return _call("radon_forward_workspace_size", geom, dtype, batch)
 
 
+def radon_forward_images_per_cta(geom, dtype, batch, config_ptr, images_ptr):
+    return _call("radon_forward_images_per_cta", geom, dtype, batch, config_ptr, images_ptr)
+
+
 def radon_forward_ws(geom, img, sino, dtype, batch, config, workspace, workspace_bytes, stream):
     return _call("radon_forward_ws", geom, img, sino, dtype, batch, config, workspace, workspace_bytes, stream)
 
@@ -403,6 +411,10 @@ def radon_probe_gather_ceiling(dtype, out_ptr):
 
 def radon_probe_gather_ceiling_ex(dtype, weights, out_ptr):
     return _call("radon_probe_gather_ceiling_ex", dtype, weights, out_ptr)
+
+
+def radon_probe_gather_ceiling_groups(dtype, weights, groups, out_ptr):
+    return _call("radon_probe_gather_ceiling_groups", dtype, weights, groups, out_ptr)
 
 
 def radon_filter_sinogram(geom, sino, out, dtype, batch, filter_kind, stream):

@@ -82,8 +82,9 @@ constexpr int kFwdMaxStages = 4;
 
 __host__ __device__ inline size_t fwd_comp_bytes(int R, int wc) { return (size_t)(R + 2) * wc * 16; }
 
-__host__ __device__ inline size_t fwd_packed_smem_bytes(int R, int wbox, int stages) {
-    return 128 + 128 + (size_t)stages * ((fwd_comp_bytes(R, wbox) + 127) / 128 * 128);
+// Packed variant: each ring buffer holds NG image groups' bands, one plane of (R + 2) x wbox texels each.
+__host__ __device__ inline size_t fwd_packed_smem_bytes(int R, int wbox, int stages, int NG = 1) {
+    return 128 + 128 + (size_t)stages * ((NG * fwd_comp_bytes(R, wbox) + 127) / 128 * 128);
 }
 
 __host__ __device__ inline size_t fwd_smem_bytes(int stage_bytes, int R, int wc) {
@@ -342,11 +343,14 @@ __device__ void fwd_repack(const FwdTiledArgs& a, int cls, int yoff, const unsig
 }
 
 // Consumer warps: one ray per thread, marched slab by slab through the double-buffered compute
-// buffers (texels [row][col][image], row pitch wc), released through `empty` after each slab.
-template <typename T, int MODE>
+// buffers (texels [row][col][image], row pitch wc), released through `empty` after each slab.  With
+// NG = 2 a buffer holds two image groups' texel planes, `plane` bytes apart: one position, floor and
+// weight evaluation per sample serves both groups (2 BG images).
+template <typename T, int MODE, int NG = 1>
 __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int d0, int b0, uint64_t* full,
                             uint64_t* empty, const int* band_xc0, const int* band_bad, volatile int* abort_flag,
-                            const unsigned char* comp_base, size_t comp_stride, int wc, int* slab_rng) {
+                            const unsigned char* comp_base, size_t comp_stride, int wc, int* slab_rng,
+                            unsigned plane = 0u) {
     using TX = Texel<T, MODE>;
     constexpr int BG = TX::BG;
     const int tid = threadIdx.x;
@@ -402,8 +406,9 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
         s_hi = slab_rng[1];
     }
     int k = 0;
-    typename TX::Acc acc;
-    acc.zero();
+    typename TX::Acc acc[NG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) acc[g].zero();
 
     for (int s = s_lo; s <= s_hi; ++s) {
         const int j = s - s_lo;   // ring position
@@ -455,7 +460,7 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
                     // same column takes its upper row from the previous sample's lower row instead of
                     // loading it (same values: same bits; 2-5 % faster in FP32; the 16-bit paths, with
                     // twice the FMAs per load, measured 2-11 % slower and load every texel)
-                    constexpr bool kReuseRow = std::is_same<T, float>::value;
+                    constexpr bool kReuseRow = std::is_same<T, float>::value && NG == 1;
                     unsigned pa = 0x80000000u;   // no texel address of a band lies within a row of it
                     uint4 r10 = make_uint4(0u, 0u, 0u, 0u), r11 = r10;
                     for (; i < kleft; ++i, kk += 1.0f) {
@@ -464,26 +469,30 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
                         const float fxm = fmaf(kk, dX, sXm);
                         const float tx = fxm + M, ty = fym + M;
                         const unsigned ad = __float_as_uint(ty) * wc16 + __float_as_uint(tx) * 16u + base16;
-                        uint4 q00, q01;
-                        if (kReuseRow && ad == pa + wc16) {
-                            q00 = r10;
-                            q01 = r11;
-                        } else {
-                            q00 = lds4u(ad);
-                            q01 = lds4u(ad + 16u);
-                        }
-                        const uint4 q10 = lds4u(ad + wc16), q11 = lds4u(ad + wc16 + 16u);
-                        if (kReuseRow) {
-                            r10 = q10;
-                            r11 = q11;
-                            pa = ad;
-                        }
                         const float ax = fxm - (tx - M), ay = fym - (ty - M);   // in [-1/2, 1/2]
                         const float wx1 = 0.5f + ax, wx0 = 0.5f - ax, wy1 = 0.5f + ay, wy0 = 0.5f - ay;
-                        TX::fma(acc, TX::weight(wx0 * wy0), q00);
-                        TX::fma(acc, TX::weight(wx1 * wy0), q01);
-                        TX::fma(acc, TX::weight(wx0 * wy1), q10);
-                        TX::fma(acc, TX::weight(wx1 * wy1), q11);
+#pragma unroll
+                        for (int g = 0; g < NG; ++g) {
+                            const unsigned adg = ad + (unsigned)g * plane;
+                            uint4 q00, q01;
+                            if (kReuseRow && adg == pa + wc16) {
+                                q00 = r10;
+                                q01 = r11;
+                            } else {
+                                q00 = lds4u(adg);
+                                q01 = lds4u(adg + 16u);
+                            }
+                            const uint4 q10 = lds4u(adg + wc16), q11 = lds4u(adg + wc16 + 16u);
+                            if (kReuseRow) {
+                                r10 = q10;
+                                r11 = q11;
+                                pa = adg;
+                            }
+                            TX::fma(acc[g], TX::weight(wx0 * wy0), q00);
+                            TX::fma(acc[g], TX::weight(wx1 * wy0), q01);
+                            TX::fma(acc[g], TX::weight(wx0 * wy1), q10);
+                            TX::fma(acc[g], TX::weight(wx1 * wy1), q11);
+                        }
                     }
                     k += i;
                 }
@@ -501,10 +510,11 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
     const long long o = (long long)(v0 + vl) * a.D + d;
     const bool pairs = a.vec_store != 0 && __activemask() == 0xffffffffu;
 #pragma unroll
-    for (int b = 0; b < BG; ++b) {
+    for (int gb = 0; gb < NG * BG; ++gb) {
+        const int b = gb;   // image b0 + b: group b / BG, slot b % BG
         const bool mine = active && b0 + b < a.B;
         const long long idx = (long long)(b0 + b) * vd + o;
-        const float val = mine ? epilogue_value<T>(a.ep, a.h * acc.get(b), idx) : 0.0f;
+        const float val = mine ? epilogue_value<T>(a.ep, a.h * acc[gb / BG].get(gb % BG), idx) : 0.0f;
         if (pairs) {
             const float nval = __shfl_xor_sync(0xffffffffu, val, 1);
             const bool nmine = __shfl_xor_sync(0xffffffffu, mine ? 1 : 0, 1) != 0;
@@ -598,7 +608,7 @@ __global__ void __launch_bounds__(kFwdThreads, 3) forward_tiled_kernel(const __g
 // Packed variant: the image batch was packed once into 16-byte texels (rows / cols copies, see
 // pack.cu), so the producer warp only bounds each band and copies it with one 4-D TMA load straight
 // into the compute buffer it will become (row pitch = band width); no staging, no repack.
-template <typename T, int MODE>
+template <typename T, int MODE, int NG>
 __global__ void __launch_bounds__(kFwdThreads, 3) forward_packed_kernel(const __grid_constant__ CUtensorMap map_rows,
                                                                        const __grid_constant__ CUtensorMap map_cols,
                                                                        const FwdTiledArgs a) {
@@ -610,7 +620,8 @@ __global__ void __launch_bounds__(kFwdThreads, 3) forward_packed_kernel(const __
     int* band_bad = reinterpret_cast<int*>(smem + 80);          // [stages]
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 96);
     int* slab_rng = reinterpret_cast<int*>(smem + 104);         // [2]: first, last slab with samples
-    const size_t comp_stride = (fwd_comp_bytes(a.R, a.wbox) + 127) / 128 * 128;
+    const unsigned plane = (unsigned)fwd_comp_bytes(a.R, a.wbox);   // one image group's texels
+    const size_t comp_stride = ((size_t)NG * plane + 127) / 128 * 128;
     unsigned char* comp_base = smem + 128;
 
     const int tid = threadIdx.x;
@@ -623,7 +634,7 @@ __global__ void __launch_bounds__(kFwdThreads, 3) forward_packed_kernel(const __
     const Int2 grp = a.groups[grp_idx];
     const int v0 = grp.x, cnt = grp.y & 0xffff, cls = grp.y >> 16;
     const int d0 = dr * a.Dt;
-    const int b0 = blockIdx.y * Texel<T>::BG;
+    const int b0 = blockIdx.y * NG * Texel<T>::BG;
 
     if (tid < a.stages) {
         mbar_init(&full[tid], 1);
@@ -660,9 +671,10 @@ __global__ void __launch_bounds__(kFwdThreads, 3) forward_packed_kernel(const __
                     band_xc0[buf] = band.xc0;
                     band_bad[buf] = band.bad;
                     fence_proxy_async_shared();
-                    mbar_arrive_expect_tx(&full[buf], (uint32_t)(a.wbox * (a.R + 2) * 16));
+                    // NG groups' planes in one box (a group past the batch's last reads as zeros)
+                    mbar_arrive_expect_tx(&full[buf], (uint32_t)NG * plane);
                     tma_load_4d(comp_base + (size_t)buf * comp_stride, map, &full[buf], 0, band.xc0, -4 + s * a.R,
-                                blockIdx.y);
+                                (int)blockIdx.y * NG);
                 }
             }
             __syncwarp();
@@ -670,8 +682,12 @@ __global__ void __launch_bounds__(kFwdThreads, 3) forward_packed_kernel(const __
         }
         return;
     }
-    fwd_consume<T, MODE>(a, cls, v0, cnt, d0, b0, full, empty, band_xc0, band_bad, abort_flag, comp_base, comp_stride,
-                   a.wbox, slab_rng);
+    if (NG == 2 && b0 + Texel<T>::BG < a.B)
+        fwd_consume<T, MODE, NG>(a, cls, v0, cnt, d0, b0, full, empty, band_xc0, band_bad, abort_flag, comp_base,
+                                 comp_stride, a.wbox, slab_rng, plane);
+    else   // one group (or a pair whose second group lies past the batch: its plane is never read)
+        fwd_consume<T, MODE, 1>(a, cls, v0, cnt, d0, b0, full, empty, band_xc0, band_bad, abort_flag, comp_base,
+                                comp_stride, a.wbox, slab_rng);
 }
 
 }  // namespace radon

@@ -1,10 +1,11 @@
 // Gather-ceiling probe: the forward projection's inner loop with the geometry taken away.
 //
 // Every CTA fills a shared-memory tile of batch-interleaved texels (the packed forward's layout:
-// 16 bytes = 8 16-bit or 4 FP32 images per texel), then each thread marches a straight "ray" through
-// it -- per sample one position, one floor / weight evaluation, four 16-byte shared loads of the
-// 2 x 2 texels and the forward consumers' own accumulation code (Texel<T>) for every image of the
-// texel -- the work the forward kernel's consumers do per sample, minus ray tables, TMA and slabs.  Its sample rate is the
+// 16 bytes = 8 16-bit or 4 FP32 images per texel; NG planes of them for NG texel groups), then each
+// thread marches a straight "ray" through it -- per sample one position, one floor / weight
+// evaluation, and per group four 16-byte shared loads of the 2 x 2 texels and the forward consumers'
+// own accumulation code (Texel<T>) for every image of the texel -- the work the forward kernel's
+// consumers do per sample, minus ray tables, TMA and slabs.  Its sample rate is the
 // achievable ceiling of that inner loop on this GPU, the denominator the measured forward rate is
 // compared with beside the nominal load-pipe figure.
 #include <cmath>
@@ -23,10 +24,12 @@ constexpr int kProbeTile = 64;          // texels per row
 constexpr int kProbeRows = 40;          // rows (40 KB of texels)
 constexpr int kProbeSamples = 4096;     // samples per thread
 
-template <typename T, int MODE>
+template <typename T, int MODE, int NG>
 __global__ void __launch_bounds__(kProbeThreads) probe_kernel(float* sink) {
     using TX = Texel<T, MODE>;
     constexpr int BG = TX::BG;
+    // NG planes of kProbeRows / NG rows share the one tile (the same shared memory and occupancy)
+    constexpr int kPlane = kProbeTile * (kProbeRows / NG), kWrap = 56 / NG;
     __shared__ uint4 tile[kProbeTile * kProbeRows];
     for (int e = threadIdx.x; e < kProbeTile * kProbeRows; e += kProbeThreads) {
         const unsigned v = 0x3c003c00u ^ (unsigned)(e * 2654435761u & 0x03ff03ffu);   // finite 16-bit or FP32 bits
@@ -35,30 +38,39 @@ __global__ void __launch_bounds__(kProbeThreads) probe_kernel(float* sink) {
     __syncthreads();
     // a warp = 32 parallel rays one pixel apart, as the forward's warps hold neighbouring detectors of
     // one view: direction (sin a, cos a), a in [0, pi/4) per warp; lane l starts at (2 + l + 0.3, 2.2)
+    // and wraps after kWrap samples: x < 2.3 + 31 + 0.39 (kWrap - 1) + 1 < 64 and
+    // y < 2.2 + 0.55 (kWrap - 1) + 1 < 40 / NG for NG = 1 (56 samples) and 2 (28)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float ang = 0.7853982f * (float)((warp * 37 + blockIdx.x * 11) & 63) / 64.0f;
-    const float dx = sinf(ang) * 0.55f, dy = cosf(ang) * 0.55f;   // x < 2.3 + 31 + 21.4 + 1 < 64, y < 2.2 + 30.3 + 1 < 40
+    const float dx = sinf(ang) * 0.55f, dy = cosf(ang) * 0.55f;
     const float x0 = 2.3f + (float)lane, y0 = 2.2f;
-    typename TX::Acc acc;
-    acc.zero();
+    typename TX::Acc acc[NG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) acc[g].zero();
     for (int k = 0; k < kProbeSamples; ++k) {
-        // positions wrap inside the tile interior every 56 samples (no geometry, no bounds checks)
-        const float kk = (float)(k % 56);
+        // positions wrap inside the plane's interior every kWrap samples (no geometry, no bounds checks)
+        const float kk = (float)(k % kWrap);
         const float fx = fmaf(kk, dx, x0), fy = fmaf(kk, dy, y0);
         const float flx = floorf(fx), fly = floorf(fy);
         const float ax = fx - flx, ay = fy - fly;
-        const int idx = (int)fly * kProbeTile + (int)flx;
-        const uint4 q00 = tile[idx], q01 = tile[idx + 1], q10 = tile[idx + kProbeTile], q11 = tile[idx + kProbeTile + 1];
         const float wx1 = ax, wx0 = 1.0f - ax, wy1 = ay, wy0 = 1.0f - ay;
-        // the forward consumers' accumulation (Texel<T>, forward_tiled.cuh), weights rounded as there
-        TX::fma(acc, TX::weight(wx0 * wy0), q00);
-        TX::fma(acc, TX::weight(wx1 * wy0), q01);
-        TX::fma(acc, TX::weight(wx0 * wy1), q10);
-        TX::fma(acc, TX::weight(wx1 * wy1), q11);
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            const int idx = g * kPlane + (int)fly * kProbeTile + (int)flx;
+            const uint4 q00 = tile[idx], q01 = tile[idx + 1], q10 = tile[idx + kProbeTile],
+                        q11 = tile[idx + kProbeTile + 1];
+            // the forward consumers' accumulation (Texel<T>, forward_tiled.cuh), weights rounded as there
+            TX::fma(acc[g], TX::weight(wx0 * wy0), q00);
+            TX::fma(acc[g], TX::weight(wx1 * wy0), q01);
+            TX::fma(acc[g], TX::weight(wx0 * wy1), q10);
+            TX::fma(acc[g], TX::weight(wx1 * wy1), q11);
+        }
     }
     float s = 0.0f;
 #pragma unroll
-    for (int b = 0; b < BG; ++b) s += acc.get(b);
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+        for (int b = 0; b < BG; ++b) s += acc[g].get(b);
     if (s == 1234.5f) sink[0] = s;   // keeps the loop live; never true for these inputs in practice
 }
 
@@ -108,8 +120,20 @@ radon_status run_probe(ProbeKernel kern, double images_per_sample, double* sampl
 
 }  // namespace
 
-extern "C" RADON_API radon_status radon_probe_gather_ceiling_ex(radon_dtype dtype, int weights,
-                                                               double* samples_per_second) {
+template <int NG>
+radon_status probe_groups(radon_dtype dtype, int weights, double* samples_per_second) {
+    switch (dtype) {
+        case RADON_F16:
+            return weights == RADON_WEIGHTS_F16
+                       ? run_probe(probe_kernel<__half, kMathF16W, NG>, 8.0 * NG, samples_per_second)
+                       : run_probe(probe_kernel<__half, kMathScalar, NG>, 8.0 * NG, samples_per_second);
+        case RADON_BF16: return run_probe(probe_kernel<__nv_bfloat16, kMathScalar, NG>, 8.0 * NG, samples_per_second);
+        default: return run_probe(probe_kernel<float, kMathScalar, NG>, 4.0 * NG, samples_per_second);
+    }
+}
+
+extern "C" RADON_API radon_status radon_probe_gather_ceiling_groups(radon_dtype dtype, int weights, int groups,
+                                                                   double* samples_per_second) {
     if (samples_per_second == nullptr) return fail(RADON_ERR_INVALID_ARG, "samples_per_second is NULL");
     if (dtype != RADON_F32 && dtype != RADON_F16 && dtype != RADON_BF16)
         return fail(RADON_ERR_INVALID_ARG, "unknown dtype");
@@ -117,13 +141,14 @@ extern "C" RADON_API radon_status radon_probe_gather_ceiling_ex(radon_dtype dtyp
         return fail(RADON_ERR_INVALID_ARG, "weights must be 0, 1 or 2");
     if (weights == RADON_WEIGHTS_F16 && dtype != RADON_F16)
         return fail(RADON_ERR_INVALID_ARG, "FP16 weights apply to FP16 storage only");
-    switch (dtype) {
-        case RADON_F16:
-            return weights == RADON_WEIGHTS_F16 ? run_probe(probe_kernel<__half, kMathF16W>, 8.0, samples_per_second)
-                                                : run_probe(probe_kernel<__half, kMathScalar>, 8.0, samples_per_second);
-        case RADON_BF16: return run_probe(probe_kernel<__nv_bfloat16, kMathScalar>, 8.0, samples_per_second);
-        default: return run_probe(probe_kernel<float, kMathScalar>, 4.0, samples_per_second);
-    }
+    if (groups != 1 && groups != 2) return fail(RADON_ERR_INVALID_ARG, "groups must be 1 or 2");
+    return groups == 2 ? probe_groups<2>(dtype, weights, samples_per_second)
+                       : probe_groups<1>(dtype, weights, samples_per_second);
+}
+
+extern "C" RADON_API radon_status radon_probe_gather_ceiling_ex(radon_dtype dtype, int weights,
+                                                               double* samples_per_second) {
+    return radon_probe_gather_ceiling_groups(dtype, weights, 1, samples_per_second);
 }
 
 extern "C" RADON_API radon_status radon_probe_gather_ceiling(radon_dtype dtype, double* samples_per_second) {

@@ -199,6 +199,26 @@ radon_status validate_epilogue(const radon_epilogue* e, radon_dtype dt) {
 
 }  // namespace
 
+// The packed forward's config for shape candidate i (views per CTA 8, 4, 2, 1 in order unless the caller
+// fixed them); images per CTA: one texel group or two (a value meant for the adjoint leaves the default).
+radon_launch_config packed_forward_config(const radon_launch_config* cfg, radon_dtype dt, int i) {
+    static const int kViewsPacked[4] = {8, 4, 2, 1};
+    const bool fixed = cfg != nullptr && cfg->views_per_cta != 0;
+    const int bg = dt == RADON_F32 ? 4 : 8;
+    const int ipc = cfg != nullptr && (cfg->images_per_cta == bg || cfg->images_per_cta == 2 * bg)
+                        ? cfg->images_per_cta : 0;
+    return radon_launch_config{RADON_ALGO_TILED, fixed ? cfg->views_per_cta : kViewsPacked[i],
+                               cfg ? cfg->rows_per_slab : 0, ipc, 0, 0, cfg ? cfg->weights : 0};
+}
+
+// One image under AUTO with no tile parameters runs the single-image kernels.
+bool single_image_call(const radon_launch_config* cfg, int batch) {
+    const int algo = cfg ? cfg->algo : RADON_ALGO_AUTO;
+    return algo == RADON_ALGO_AUTO && batch == 1 &&
+           (cfg == nullptr || (cfg->views_per_cta == 0 && cfg->rows_per_slab == 0 && cfg->images_per_cta == 0 &&
+                               cfg->tile == 0 && cfg->threads == 0));
+}
+
 radon_status project(const radon_geometry* g, const void* in, void* out, radon_dtype dt, int batch,
                      const radon_launch_config* cfg, void* stream, bool forward, void* ws, size_t ws_bytes,
                      const radon_epilogue* epi) {
@@ -227,9 +247,7 @@ radon_status project(const radon_geometry* g, const void* in, void* out, radon_d
     // One image under AUTO with no tile parameters: the single-image kernels (a batch-interleaved
     // group would carry the image in one of its 4 / 8 / 16 slots).  The forward needs its quad
     // texels in the workspace; without one it continues below.
-    const bool single = algo == RADON_ALGO_AUTO && batch == 1 &&
-                        (cfg == nullptr || (cfg->views_per_cta == 0 && cfg->rows_per_slab == 0 &&
-                                            cfg->images_per_cta == 0 && cfg->tile == 0 && cfg->threads == 0));
+    const bool single = single_image_call(cfg, batch);
     if (single && !forward) {
         std::string why;
         st = launch_backward_single(g, in, out, dt, ep, s, &why);
@@ -270,13 +288,11 @@ radon_status project(const radon_geometry* g, const void* in, void* out, radon_d
     }
     if (forward && algo != RADON_ALGO_PLAIN && ws != nullptr && ws_bytes >= packed_image_bytes(g->n, batch, dt)) {
         // Packed path: pack the batch once, then copy bands of texels straight into shared memory.
-        static const int kViewsPacked[4] = {8, 4, 2, 1};
         const bool fixed = cfg != nullptr && cfg->views_per_cta != 0;
         std::string why;
         bool packed_done = false;
         for (int i = 0; i < (fixed ? 1 : 4); ++i) {
-            radon_launch_config c = {RADON_ALGO_TILED, fixed ? cfg->views_per_cta : kViewsPacked[i],
-                                     cfg ? cfg->rows_per_slab : 0, 0, 0, 0, cfg ? cfg->weights : 0};
+            const radon_launch_config c = packed_forward_config(cfg, dt, i);
             if (!packed_done) {
                 cudaError_t e = launch_pack_images(in, ws, g->n, batch, dt, s);
                 if (e != cudaSuccess) return cuda_fail(e, "pack launch");
@@ -458,6 +474,30 @@ size_t radon_forward_workspace_size(const radon_geometry* g, radon_dtype dtype, 
     // a single image runs the single-image forward, whose quad texels carry a one-pixel border
     if (batch == 1) return std::max(packed_image_bytes(g->n, batch, dtype), single_forward_workspace_bytes(g, dtype));
     return packed_image_bytes(g->n, batch, dtype);
+}
+
+radon_status radon_forward_images_per_cta(const radon_geometry* g, radon_dtype dtype, int batch,
+                                          const radon_launch_config* config, int* images) {
+    if (images == nullptr) return fail(RADON_ERR_INVALID_ARG, "images is NULL");
+    *images = 0;
+    radon_status st = validate_geometry(g);
+    if (st != RADON_OK) return st;
+    if (dtype != RADON_F32 && dtype != RADON_F16 && dtype != RADON_BF16) return fail(RADON_ERR_INVALID_ARG, "unknown dtype");
+    if (batch < 0) return fail(RADON_ERR_INVALID_ARG, "batch must be >= 0");
+    const int algo = config ? config->algo : RADON_ALGO_AUTO;
+    if (batch == 0 || algo == RADON_ALGO_PLAIN || single_image_call(config, batch)) return RADON_OK;
+    const bool f16w = dtype == RADON_F16 && config != nullptr && config->weights == RADON_WEIGHTS_F16;
+    const bool fixed = config != nullptr && config->views_per_cta != 0;
+    for (int i = 0; i < (fixed ? 1 : 4); ++i) {
+        const radon_launch_config c = packed_forward_config(config, dtype, i);
+        PackedFwdShape sh;
+        std::string why;
+        if (packed_forward_shape(const_cast<radon_geometry*>(g), dtype, batch, &c, f16w, &sh, &why) == RADON_OK) {
+            *images = sh.NG * (dtype == RADON_F32 ? 4 : 8);
+            return RADON_OK;
+        }
+    }
+    return RADON_OK;
 }
 
 radon_status radon_forward_ws(const radon_geometry* g, const void* img, void* sino, radon_dtype dtype, int batch,

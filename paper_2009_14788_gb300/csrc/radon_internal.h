@@ -133,6 +133,16 @@ radon_status launch_forward_tiled(radon_geometry* g, const void* img, void* sino
                                   const radon_launch_config* cfg, const Epilogue& ep, cudaStream_t s,
                                   std::string* why);
 
+// forward_tiled.cu: the packed forward's launch shape for a call (views per CTA from cfg or 8, image
+// groups per CTA, rows per slab, band width, ring stages, shared memory); RADON_ERR_UNSUPPORTED with
+// the reason if the geometry does not fit it.  `fp16_weights`: the FP16-weight mode will run.
+struct PackedFwdShape {
+    int G, Dt, NG, R, wbox, stages;
+    size_t smem;
+};
+radon_status packed_forward_shape(radon_geometry* g, radon_dtype dt, int batch, const radon_launch_config* cfg,
+                                  bool fp16_weights, PackedFwdShape* out, std::string* why);
+
 // forward_tiled.cu: the packed-input forward (the workspace already holds pack_images' output)
 radon_status launch_forward_packed(radon_geometry* g, const void* packed, void* sino, radon_dtype dt, int batch,
                                    const radon_launch_config* cfg, const Epilogue& ep, cudaStream_t s,

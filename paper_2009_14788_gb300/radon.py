@@ -158,6 +158,16 @@ def forward_workspace_bytes(geom: Geometry, dtype: torch.dtype, batch: int) -> i
     return int(L.radon_forward_workspace_size(geom.handle, _DTYPES[dtype], int(batch)))
 
 
+def forward_images_per_cta(geom: Geometry, dtype: torch.dtype, batch: int, config=None) -> int:
+    """Images per CTA of the packed forward for this call (``radon_forward_images_per_cta``): one texel
+    group (8 for 16-bit storage, 4 for FP32) or two; 0 when another kernel serves it."""
+    n = ctypes.c_int(0)
+    L.check(L.radon_forward_images_per_cta(geom.handle, _DTYPES[dtype], int(batch),
+                                           ctypes.byref(config) if config is not None else None, ctypes.byref(n)),
+            "radon_forward_images_per_cta")
+    return int(n.value)
+
+
 def forward_raw(geom: Geometry, x: torch.Tensor, config=None, out=None, workspace="auto") -> torch.Tensor:
     """y = A x through the C ABI (no autograd).
 

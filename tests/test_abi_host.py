@@ -337,6 +337,35 @@ def test_forward_workspace_covers_the_single_image_texels():
             assert two > 0 and int(L.radon_forward_workspace_size(g.handle, dt, 0)) == 0
 
 
+def test_forward_images_per_cta_on_the_host():
+    """The packed forward's images per CTA, asked without a launch: 16-bit batches of more than one
+    texel group (8 images) pair their groups, FP32 and single groups take one; images_per_cta picks one
+    or two groups where it names one of those values (else the default); one image under AUTO and the
+    PLAIN algorithm run other kernels (0)."""
+    from paper_2009_14788_gb300 import forward_images_per_cta, launch_config
+    import torch
+    a = workload_geometry_args(WORKLOADS["fan_b16_n512_v720_d1024"])
+    kind = a.pop("kind")
+    g = Geometry(kind, host_only=True, **a)
+    f16, bf16, f32 = torch.float16, torch.bfloat16, torch.float32
+    assert forward_images_per_cta(g, f16, 16) == 16
+    assert forward_images_per_cta(g, bf16, 9) == 16
+    assert forward_images_per_cta(g, f16, 8) == 8
+    assert forward_images_per_cta(g, f16, 2) == 8
+    assert forward_images_per_cta(g, f32, 16) == 4
+    assert forward_images_per_cta(g, f16, 16, launch_config(images_per_cta=8)) == 8
+    assert forward_images_per_cta(g, f16, 3, launch_config(images_per_cta=16)) == 16
+    assert forward_images_per_cta(g, f32, 16, launch_config(images_per_cta=8)) == 8
+    assert forward_images_per_cta(g, f16, 16, launch_config(images_per_cta=32)) == 16   # an adjoint value
+    assert forward_images_per_cta(g, f16, 1) == 0
+    assert forward_images_per_cta(g, f16, 1, launch_config("tiled")) == 8
+    assert forward_images_per_cta(g, f16, 16, launch_config("plain")) == 0
+    assert forward_images_per_cta(g, f16, 0) == 0
+    n = ctypes.c_int(-1)
+    assert L.radon_forward_images_per_cta(g.handle, L.RADON_F16, -1, None, ctypes.byref(n)) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_forward_images_per_cta(g.handle, L.RADON_F16, 4, None, None) == L.RADON_ERR_INVALID_ARG
+
+
 def test_adjoint_table_size_and_refusals_on_the_host():
     """The weight table's size is a closed form of the geometry (tiles x views x (128 pairs x 44 + 4)
     bytes); a host-only geometry can be asked for it but cannot build one, and without a table the

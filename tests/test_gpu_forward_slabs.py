@@ -84,8 +84,9 @@ def test_fp16_weight_mode_equals_the_full_slab_stream():
 
 def test_full_size_headline_geometry_equals_the_full_slab_stream():
     """The 16 x 512^2 fan batch (720 views x 1024 detectors; about a quarter of its CTAs see no
-    pixel, and about half of the slabs in all hold no sample): the library's default packed launch
-    equals the repacking kernel that streams every slab at the same shape, bit for bit."""
+    pixel, and about half of the slabs in all hold no sample): the library's default packed launch (8
+    views per CTA, two image groups per CTA, 12 rows per slab) equals the repacking kernel that
+    streams every slab at the same shape, bit for bit."""
     from paper_2009_14788_gb300 import Geometry
     from synth import WORKLOADS, workload_geometry_args
     a = workload_geometry_args(WORKLOADS["fan_b16_n512_v720_d1024"])
@@ -93,9 +94,43 @@ def test_full_size_headline_geometry_equals_the_full_slab_stream():
     g = Geometry(kind, **a)
     x = to_dev(np.random.default_rng(43).uniform(0.0, 1.0, (16, g.n, g.n)), torch.float16)
     default = forward_raw(g, x)
-    packed, tiled = _both(g, x, launch_config("tiled", views_per_cta=8, rows_per_slab=16))
+    packed, tiled = _both(g, x, launch_config("tiled", views_per_cta=8, rows_per_slab=12))
     assert packed is not None and tiled is not None
     assert torch.equal(default, packed)
     assert torch.equal(packed, tiled)
     _clean()
     g.close()
+
+
+@pytest.mark.parametrize("dtype", DTYPES, ids=["f32", "f16", "bf16"])
+@pytest.mark.parametrize("batch", [3, 16, 20])
+def test_two_image_groups_per_cta_give_the_same_bits(dtype, batch):
+    """images_per_cta = two texel groups: each sample's position, floor and weights serve both groups'
+    planes, every image keeps its own sum in the same order, so the projection equals the one-group
+    launch bit for bit -- including a last CTA whose second group lies past the batch (read as zeros,
+    never stored)."""
+    g, og = make("fan_n512_block")
+    bg = 4 if dtype == torch.float32 else 8
+    x = to_dev(np.random.default_rng(44).uniform(0.0, 1.0, (batch, g.n, g.n)), dtype)
+    compared = 0
+    for views, rows in [(8, 8), (4, 16), (8, 12)]:
+        one, l1 = _forward(g, x, launch_config("tiled", views_per_cta=views, rows_per_slab=rows, images_per_cta=bg))
+        two, l2 = _forward(g, x, launch_config("tiled", views_per_cta=views, rows_per_slab=rows,
+                                               images_per_cta=2 * bg))
+        if one is None or two is None or l1 != 2 or l2 != 2:
+            continue
+        assert torch.equal(one, two), (views, rows)
+        compared += 1
+    _clean()
+    assert compared > 0
+    if dtype == torch.float16:
+        one_w, _ = _forward(g, x, launch_config("tiled", views_per_cta=8, rows_per_slab=8, images_per_cta=8,
+                                                weights=2))
+        two_w, _ = _forward(g, x, launch_config("tiled", views_per_cta=8, rows_per_slab=8, images_per_cta=16,
+                                                weights=2))
+        assert one_w is not None and torch.equal(one_w, two_w)
+    ref = O.forward(og, to_np(x[:3]))
+    if dtype == torch.float32:
+        assert rel_l2(to_np(two[:3]), ref) <= TOL_F32
+    else:
+        assert within_16(to_np(two[:3]), ref, dtype)
