@@ -187,12 +187,12 @@ radon_status packed_forward_shape(radon_geometry* g, radon_dtype dt, int batch, 
     }
     // Default: 16-bit batches of more than one group pair their groups (one sample's index and weight
     // work then serves 16 images; measured 7-9 % faster on the fan and parallel workloads); FP32
-    // texels (4 images each) measured slower paired.  Rows per slab: 16 for one group; 12 for two
+    // texels (4 images each) measured slower paired.  Rows per slab: 16 for one group; 14 for two
     // (2 CTAs/SM), 8 with FP16 weights (3 CTAs/SM), the fastest of 8-16 rows measured.  A default pair
     // whose buffers would not fit falls back to one group.
     int NG = ipc != 0 ? (ipc == 2 * BG ? 2 : 1) : (esz == 2 && batch > BG ? 2 : 1);
     for (;;) {
-        const int R = cfg && cfg->rows_per_slab ? cfg->rows_per_slab : (NG == 2 ? (f16w ? 8 : 12) : 16);
+        const int R = cfg && cfg->rows_per_slab ? cfg->rows_per_slab : (NG == 2 ? (f16w ? 8 : 14) : 16);
         if (R < 2 || R > 64 || (R & 1)) {
             *why = "rows_per_slab must be even and in [2, 64]";
             return RADON_ERR_UNSUPPORTED;
