@@ -25,6 +25,7 @@
 #include "backward_tiled.cuh"
 #include "dtype.cuh"
 #include "epilogue.cuh"
+#include "f32x2.cuh"
 #include "radon_internal.h"
 #include "tensor_map.h"
 #include "tma.cuh"
@@ -485,19 +486,27 @@ __global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasP
                                     yw[2 * o + 1] = f[1];
                                 }
                             }
+                            // paired FMAs (two images per fma.rn.f32x2, each lane an IEEE fma: the same
+                            // bits as scalar FMAs, half the FMA instructions)
+                            const f32x2 wwa = f2_pack(wa[cr], wa[cr]), wwb = f2_pack(wb[cr], wb[cr]);
 #pragma unroll
                             for (int q = 0; q < NQ; ++q) {
                                 float4 y4;
                                 if constexpr (L::kConv) y4 = yw[q];
                                 else y4 = lds4(ya + 16 * q);
-                                acc[0][4 * q + 0] = fmaf(wa[cr], y4.x, acc[0][4 * q + 0]);
-                                acc[0][4 * q + 1] = fmaf(wa[cr], y4.y, acc[0][4 * q + 1]);
-                                acc[0][4 * q + 2] = fmaf(wa[cr], y4.z, acc[0][4 * q + 2]);
-                                acc[0][4 * q + 3] = fmaf(wa[cr], y4.w, acc[0][4 * q + 3]);
-                                acc[PX - 1][4 * q + 0] = fmaf(wb[cr], y4.x, acc[PX - 1][4 * q + 0]);
-                                acc[PX - 1][4 * q + 1] = fmaf(wb[cr], y4.y, acc[PX - 1][4 * q + 1]);
-                                acc[PX - 1][4 * q + 2] = fmaf(wb[cr], y4.z, acc[PX - 1][4 * q + 2]);
-                                acc[PX - 1][4 * q + 3] = fmaf(wb[cr], y4.w, acc[PX - 1][4 * q + 3]);
+                                const f32x2 y01 = f2_pack(y4.x, y4.y), y23 = f2_pack(y4.z, y4.w);
+                                f32x2 a0 = f2_pack(acc[0][4 * q + 0], acc[0][4 * q + 1]);
+                                f32x2 a1 = f2_pack(acc[0][4 * q + 2], acc[0][4 * q + 3]);
+                                f32x2 b0 = f2_pack(acc[PX - 1][4 * q + 0], acc[PX - 1][4 * q + 1]);
+                                f32x2 b1 = f2_pack(acc[PX - 1][4 * q + 2], acc[PX - 1][4 * q + 3]);
+                                a0 = f2_fma(wwa, y01, a0);
+                                a1 = f2_fma(wwa, y23, a1);
+                                b0 = f2_fma(wwb, y01, b0);
+                                b1 = f2_fma(wwb, y23, b1);
+                                f2_unpack(a0, &acc[0][4 * q + 0], &acc[0][4 * q + 1]);
+                                f2_unpack(a1, &acc[0][4 * q + 2], &acc[0][4 * q + 3]);
+                                f2_unpack(b0, &acc[PX - 1][4 * q + 0], &acc[PX - 1][4 * q + 1]);
+                                f2_unpack(b1, &acc[PX - 1][4 * q + 2], &acc[PX - 1][4 * q + 3]);
                             }
                         }
                     }
