@@ -539,12 +539,28 @@ __global__ void __launch_bounds__(BwdPShape<BG>::kThreads, BwdPShape<BG>::kCtasP
 #pragma unroll
                         for (int q = 0; q < NQ; ++q) {
                             const float4 y4 = lds4(ya + 16 * q);
+                            if constexpr (PX == 2) {
+                                // pixel pairs: paired FMAs (the same bits as scalar ones; measured 2-3 %
+                                // faster here, while the 32-image groups' single pixels ran slower paired)
+                                const f32x2 y01 = f2_pack(y4.x, y4.y), y23 = f2_pack(y4.z, y4.w);
 #pragma unroll
-                            for (int x = 0; x < PX; ++x) {
-                                acc[x][4 * q + 0] = fmaf(w[x], y4.x, acc[x][4 * q + 0]);
-                                acc[x][4 * q + 1] = fmaf(w[x], y4.y, acc[x][4 * q + 1]);
-                                acc[x][4 * q + 2] = fmaf(w[x], y4.z, acc[x][4 * q + 2]);
-                                acc[x][4 * q + 3] = fmaf(w[x], y4.w, acc[x][4 * q + 3]);
+                                for (int x = 0; x < PX; ++x) {
+                                    const f32x2 ww = f2_pack(w[x], w[x]);
+                                    f32x2 a0 = f2_pack(acc[x][4 * q + 0], acc[x][4 * q + 1]);
+                                    f32x2 a1 = f2_pack(acc[x][4 * q + 2], acc[x][4 * q + 3]);
+                                    a0 = f2_fma(ww, y01, a0);
+                                    a1 = f2_fma(ww, y23, a1);
+                                    f2_unpack(a0, &acc[x][4 * q + 0], &acc[x][4 * q + 1]);
+                                    f2_unpack(a1, &acc[x][4 * q + 2], &acc[x][4 * q + 3]);
+                                }
+                            } else {
+#pragma unroll
+                                for (int x = 0; x < PX; ++x) {
+                                    acc[x][4 * q + 0] = fmaf(w[x], y4.x, acc[x][4 * q + 0]);
+                                    acc[x][4 * q + 1] = fmaf(w[x], y4.y, acc[x][4 * q + 1]);
+                                    acc[x][4 * q + 2] = fmaf(w[x], y4.z, acc[x][4 * q + 2]);
+                                    acc[x][4 * q + 3] = fmaf(w[x], y4.w, acc[x][4 * q + 3]);
+                                }
                             }
                         }
                     }
