@@ -361,6 +361,14 @@ def test_forward_images_per_cta_on_the_host():
     assert forward_images_per_cta(g, f16, 1, launch_config("tiled")) == 8
     assert forward_images_per_cta(g, f16, 16, launch_config("plain")) == 0
     assert forward_images_per_cta(g, f16, 0) == 0
+    # sparse views widen the bands: at 8 views per CTA two groups' buffers (14 rows) exceed shared
+    # memory and the default falls back to one group; asked for explicitly, two groups are refused;
+    # at 2 views per CTA, or 8 rows per slab, two groups fit
+    sparse = Geometry("parallel", 256, uniform_angles(8, math.pi), det_count=363, host_only=True)
+    assert forward_images_per_cta(sparse, f16, 16, launch_config("tiled", views_per_cta=8)) == 8
+    assert forward_images_per_cta(sparse, f16, 16, launch_config("tiled", views_per_cta=8, images_per_cta=16)) == 0
+    assert forward_images_per_cta(sparse, f16, 16, launch_config("tiled", views_per_cta=2)) == 16
+    assert forward_images_per_cta(sparse, f16, 16, launch_config("tiled", views_per_cta=8, rows_per_slab=8)) == 16
     n = ctypes.c_int(-1)
     assert L.radon_forward_images_per_cta(g.handle, L.RADON_F16, -1, None, ctypes.byref(n)) == L.RADON_ERR_INVALID_ARG
     assert L.radon_forward_images_per_cta(g.handle, L.RADON_F16, 4, None, None) == L.RADON_ERR_INVALID_ARG
