@@ -386,3 +386,18 @@ def test_adjoint_table_size_and_refusals_on_the_host():
         st = L.radon_geometry_build_adjoint_table(g.handle)
         assert st == L.RADON_ERR_INVALID_ARG
         assert L.radon_geometry_free_adjoint_table(g.handle) == L.RADON_OK
+
+
+def test_probe_arguments_are_checked_on_the_host():
+    """The gather-ceiling probe refuses bad arguments before touching a GPU: a NULL result, an unknown
+    storage type, a weights setting outside 0..2, FP16 weights for other storage, and texel groups other
+    than 1 or 2."""
+    out = ctypes.c_double(0.0)
+    assert L.radon_probe_gather_ceiling_groups(L.RADON_F16, 0, 1, None) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_probe_gather_ceiling_groups(7, 0, 1, ctypes.byref(out)) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_probe_gather_ceiling_groups(L.RADON_F16, 3, 1, ctypes.byref(out)) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_probe_gather_ceiling_groups(L.RADON_BF16, 2, 1, ctypes.byref(out)) == L.RADON_ERR_INVALID_ARG
+    for groups in (0, 3, -1):
+        assert L.radon_probe_gather_ceiling_groups(L.RADON_F16, 0, groups, ctypes.byref(out)) == L.RADON_ERR_INVALID_ARG
+    assert L.radon_probe_gather_ceiling_ex(L.RADON_F32, 2, ctypes.byref(out)) == L.RADON_ERR_INVALID_ARG
+    assert out.value == 0.0
