@@ -16,11 +16,14 @@
 //     loads fetch the 2x2 texels of every image -- and release the buffer.
 // Each ray re-bases its next sample on the band origin from the split-precision table at every
 // slab.  All waits are bounded; on expiry the kernel records RADON_ERR_TIMEOUT and unwinds.
-// The packed variant streams only the slabs between the first and the last in which one of the CTA's
-// rays has a sample (about half of all slabs on a fan whose detector is wider than the image; a CTA
-// whose rays all miss the image streams none), and hands its CTAs out centre-out along the detector.
-// Shared memory: header (mbarriers, band origins, abort flag), staging buffer, two compute
-// buffers of (R+2) x wc texels.
+// The packed variant (the image batch already packed into texels) copies each band with one 4-D TMA
+// box straight into its compute buffer, streams only the slabs between the first and the last in
+// which one of the CTA's rays has a sample (about half of all slabs on a fan whose detector is wider
+// than the image; a CTA whose rays all miss the image streams none), hands its CTAs out centre-out
+// along the detector, and may take two texel groups (2 BG images) per CTA: the box then lands both
+// groups' bands as planes of one buffer, and each sample's position and weights serve both.
+// Shared memory: header (mbarriers, band origins, abort flag, slab range), staging buffer (repacking
+// variant only), compute buffers of (R+2) x wc texels (x NG planes).
 #pragma once
 
 #include <type_traits>
