@@ -242,8 +242,11 @@ RADON_API size_t radon_forward_workspace_size(const radon_geometry* geometry, ra
  * this call: one texel group (8 for 16-bit storage, 4 for FP32) or two groups whose images share each
  * sample's position, floor and weight evaluation (16 / 8).  By default 16-bit batches of more than 8
  * images take two groups and FP32 one; `config`'s images_per_cta chooses where it holds one of those
- * values.  *images = 0 when another kernel serves the call (one image under AUTO, the PLAIN algorithm,
- * a geometry no packed shape takes).  Host only (host-only geometries are answered too); no launch.
+ * values.  Where no shape with one thread per ray fits a TMA box (sparse views with a detector wider
+ * than the image) and `config` fixes no views per CTA, two threads share each ray (half the detectors
+ * per CTA, one texel group).  *images = 0 when another kernel serves the call (one image under AUTO,
+ * the PLAIN algorithm, a geometry no packed shape takes).  Host only (host-only geometries are
+ * answered too); no launch.
  */
 RADON_API radon_status radon_forward_images_per_cta(const radon_geometry* geometry, radon_dtype dtype, int batch,
                                                     const radon_launch_config* config, int* images);

@@ -145,10 +145,10 @@ namespace radon {
 
 namespace {
 
-template <typename T, int MODE, int NG>
+template <typename T, int MODE, int NG, int LN>
 cudaError_t launch_packed_ng(const CUtensorMap& mr, const CUtensorMap& mc, const FwdTiledArgs& a, dim3 grid,
                              size_t smem, cudaStream_t s) {
-    auto kern = forward_packed_kernel<T, MODE, NG>;
+    auto kern = forward_packed_kernel<T, MODE, NG, LN>;
     static size_t attr_bytes = 0;
     if (smem > attr_bytes) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -161,15 +161,16 @@ cudaError_t launch_packed_ng(const CUtensorMap& mr, const CUtensorMap& mc, const
 
 template <typename T, int MODE>
 cudaError_t launch_packed_t(const CUtensorMap& mr, const CUtensorMap& mc, const FwdTiledArgs& a, dim3 grid,
-                            size_t smem, int NG, cudaStream_t s) {
-    return NG == 2 ? launch_packed_ng<T, MODE, 2>(mr, mc, a, grid, smem, s)
-                   : launch_packed_ng<T, MODE, 1>(mr, mc, a, grid, smem, s);
+                            size_t smem, int NG, int LN, cudaStream_t s) {
+    if (LN == 2) return launch_packed_ng<T, MODE, 1, 2>(mr, mc, a, grid, smem, s);
+    return NG == 2 ? launch_packed_ng<T, MODE, 2, 1>(mr, mc, a, grid, smem, s)
+                   : launch_packed_ng<T, MODE, 1, 1>(mr, mc, a, grid, smem, s);
 }
 
 }  // namespace
 
 radon_status packed_forward_shape(radon_geometry* g, radon_dtype dt, int batch, const radon_launch_config* cfg,
-                                  bool f16w, PackedFwdShape* out, std::string* why) {
+                                  bool f16w, int lanes, PackedFwdShape* out, std::string* why) {
     const int esz = dt == RADON_F32 ? 4 : 2;
     const int BG = 16 / esz;
     const int G = cfg && cfg->views_per_cta ? cfg->views_per_cta : 8;
@@ -177,7 +178,11 @@ radon_status packed_forward_shape(radon_geometry* g, radon_dtype dt, int batch, 
         *why = "views_per_cta must be 1, 2, 4 or 8 for the tiled forward";
         return RADON_ERR_UNSUPPORTED;
     }
-    const int Dt = kFwdRays / G;
+    if (lanes != 1 && lanes != 2) {
+        *why = "lanes per ray must be 1 or 2";
+        return RADON_ERR_UNSUPPORTED;
+    }
+    const int Dt = kFwdRays / (G * lanes);
     // images per CTA: one texel group (BG images) or two groups sharing each sample's index work
     const int ipc = cfg ? cfg->images_per_cta : 0;
     if (ipc != 0 && ipc != BG && ipc != 2 * BG) {
@@ -185,12 +190,16 @@ radon_status packed_forward_shape(radon_geometry* g, radon_dtype dt, int batch, 
                " for the packed forward";
         return RADON_ERR_UNSUPPORTED;
     }
+    if (lanes == 2 && ipc == 2 * BG) {
+        *why = "two lanes per ray take one texel group";
+        return RADON_ERR_UNSUPPORTED;
+    }
     // Default: 16-bit batches of more than one group pair their groups (one sample's index and weight
     // work then serves 16 images; measured 7-9 % faster on the fan and parallel workloads); FP32
     // texels (4 images each) measured slower paired.  Rows per slab: 16 for one group; 14 for two
     // (2 CTAs/SM), 8 with FP16 weights (3 CTAs/SM), the fastest of 8-16 rows measured.  A default pair
     // whose buffers would not fit falls back to one group.
-    int NG = ipc != 0 ? (ipc == 2 * BG ? 2 : 1) : (esz == 2 && batch > BG ? 2 : 1);
+    int NG = lanes == 2 ? 1 : ipc != 0 ? (ipc == 2 * BG ? 2 : 1) : (esz == 2 && batch > BG ? 2 : 1);
     for (;;) {
         const int R = cfg && cfg->rows_per_slab ? cfg->rows_per_slab : (NG == 2 ? (f16w ? 8 : 14) : 16);
         if (R < 2 || R > 64 || (R & 1)) {
@@ -208,7 +217,7 @@ radon_status packed_forward_shape(radon_geometry* g, radon_dtype dt, int batch, 
         while (stages < kFwdMaxStages && fwd_packed_smem_bytes(R, wbox, stages + 1, NG) <= 75 * 1024) ++stages;
         const size_t smem = fwd_packed_smem_bytes(R, wbox, stages, NG);
         if (smem <= 227 * 1024) {
-            *out = PackedFwdShape{G, Dt, NG, R, wbox, stages, smem};
+            *out = PackedFwdShape{G, Dt, NG, lanes, R, wbox, stages, smem};
             return RADON_OK;
         }
         if (ipc == 0 && NG == 2) {
@@ -222,7 +231,7 @@ radon_status packed_forward_shape(radon_geometry* g, radon_dtype dt, int batch, 
 
 radon_status launch_forward_packed(radon_geometry* g, const void* packed, void* sino, radon_dtype dt, int batch,
                                    const radon_launch_config* cfg, const Epilogue& ep, cudaStream_t s,
-                                   std::string* why) {
+                                   std::string* why, int lanes) {
     const int esz = dt == RADON_F32 ? 4 : 2;
     const int BG = 16 / esz;
     if (((uintptr_t)packed & 15) != 0) {
@@ -230,9 +239,10 @@ radon_status launch_forward_packed(radon_geometry* g, const void* packed, void* 
         return RADON_ERR_UNSUPPORTED;
     }
     PackedFwdShape sh;
-    const radon_status st = packed_forward_shape(g, dt, batch, cfg, dt == RADON_F16 && fp16_weights(cfg, ep), &sh, why);
+    const radon_status st =
+        packed_forward_shape(g, dt, batch, cfg, dt == RADON_F16 && fp16_weights(cfg, ep), lanes, &sh, why);
     if (st != RADON_OK) return st;
-    const int G = sh.G, Dt = sh.Dt, NG = sh.NG, R = sh.R, wbox = sh.wbox, stages = sh.stages;
+    const int G = sh.G, Dt = sh.Dt, NG = sh.NG, LN = sh.LN, R = sh.R, wbox = sh.wbox, stages = sh.stages;
     const size_t smem = sh.smem;
     int gi = 0;
     while ((1 << gi) < G) ++gi;
@@ -266,7 +276,7 @@ radon_status launch_forward_packed(radon_geometry* g, const void* packed, void* 
     a.ep = ep;
     a.G = G;
     a.Dt = Dt;
-    a.pair_views = G >= 2 && g->fwd_pair_views ? 1 : 0;
+    a.pair_views = LN == 1 && G >= 2 && g->fwd_pair_views ? 1 : 0;
     a.n_dr = (g->D + Dt - 1) / Dt;
     a.R = R;
     a.n_slabs = (g->n + 4 + R - 1) / R;
@@ -288,11 +298,11 @@ radon_status launch_forward_packed(radon_geometry* g, const void* packed, void* 
     cudaError_t e;
     switch (dt) {
         case RADON_F16:
-            e = fp16_weights(cfg, ep) ? launch_packed_t<__half, kMathF16W>(mr, mc, a, grid, smem, NG, s)
-                                      : launch_packed_t<__half, kMathScalar>(mr, mc, a, grid, smem, NG, s);
+            e = fp16_weights(cfg, ep) ? launch_packed_t<__half, kMathF16W>(mr, mc, a, grid, smem, NG, LN, s)
+                                      : launch_packed_t<__half, kMathScalar>(mr, mc, a, grid, smem, NG, LN, s);
             break;
-        case RADON_BF16: e = launch_packed_t<__nv_bfloat16, kMathScalar>(mr, mc, a, grid, smem, NG, s); break;
-        default: e = launch_packed_t<float, kMathScalar>(mr, mc, a, grid, smem, NG, s); break;
+        case RADON_BF16: e = launch_packed_t<__nv_bfloat16, kMathScalar>(mr, mc, a, grid, smem, NG, LN, s); break;
+        default: e = launch_packed_t<float, kMathScalar>(mr, mc, a, grid, smem, NG, LN, s); break;
     }
     if (e != cudaSuccess) {
         *why = std::string("packed forward launch: ") + cudaGetErrorString(e);

@@ -47,7 +47,7 @@ struct FwdTiledArgs {
     void* sino;
     int n, V, D, B;
     float h;
-    int G, Dt;            // views and detectors per CTA (G * Dt == kFwdRays)
+    int G, Dt;            // views and detectors per CTA (G * Dt * lanes per ray == kFwdRays)
     int pair_views;       // 1: each 8-lane load phase holds two views x four detectors
     int n_dr;             // detector ranges
     int R;                // slab rows (even)
@@ -348,8 +348,11 @@ __device__ void fwd_repack(const FwdTiledArgs& a, int cls, int yoff, const unsig
 // Consumer warps: one ray per thread, marched slab by slab through the double-buffered compute
 // buffers (texels [row][col][image], row pitch wc), released through `empty` after each slab.  With
 // NG = 2 a buffer holds two image groups' texel planes, `plane` bytes apart: one position, floor and
-// weight evaluation per sample serves both groups (2 BG images).
-template <typename T, int MODE, int NG = 1>
+// weight evaluation per sample serves both groups (2 BG images).  With LN = 2 two lanes share each
+// ray (rays where bands of 256 detectors per view would not fit a TMA box): lane `sub` takes the
+// ray's samples sub, sub + 2, ... of every slab, the two lanes agree on where the slab's samples end,
+// and their partial sums meet in one shuffle before the store.
+template <typename T, int MODE, int NG = 1, int LN = 1>
 __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int d0, int b0, uint64_t* full,
                             uint64_t* empty, const int* band_xc0, const int* band_bad, volatile int* abort_flag,
                             const unsigned char* comp_base, size_t comp_stride, int wc, int* slab_rng,
@@ -361,7 +364,12 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
     // of one view; with pair_views each 8-lane phase of a 16-byte shared load takes views 2m, 2m + 1 x
     // four consecutive detectors (lanes 2j, 2j + 1 still hold neighbouring detectors of one view).
     int vl, dl;
-    if (a.pair_views) {
+    const int sub = LN == 2 ? (tid & 1) : 0;
+    if (LN == 2) {
+        const int r = tid >> 1;
+        vl = r / a.Dt;
+        dl = r - vl * a.Dt;
+    } else if (a.pair_views) {
         const int per = a.Dt >> 2, P = tid >> 3;
         vl = (P / per) * 2 + ((tid >> 2) & 1);
         dl = (P - (P / per) * per) * 4 + (tid & 3);
@@ -416,7 +424,10 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
     for (int s = s_lo; s <= s_hi; ++s) {
         const int j = s - s_lo;   // ring position
         const int buf = j % a.stages;
-        if (!mbar_wait_bounded(&full[buf], (uint32_t)((j / a.stages) & 1), a.spin_limit)) {
+        bool ok = mbar_wait_bounded(&full[buf], (uint32_t)((j / a.stages) & 1), a.spin_limit);
+        // two lanes per ray: the warp gives up together, so no lane is left waiting in a shuffle
+        if (LN == 2) ok = __all_sync(0xffffffffu, ok);
+        if (!ok) {
             record_device_error(a.err, RADON_ERR_TIMEOUT);
             return;
         }
@@ -457,16 +468,16 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
                     const unsigned wc16 = 16u * (unsigned)wc;
                     const unsigned base16 = comp_a + 16u * ((unsigned)(IB * wc + JB) - magic * (unsigned)(wc + 1));
                     const int kleft = nk - k;
-                    int i = 0;
-                    float kk = 0.0f;
+                    int i = sub;
+                    float kk = (float)sub;
                     // FP32 texels (4 images per load): a sample one row below the previous one in the
                     // same column takes its upper row from the previous sample's lower row instead of
                     // loading it (same values: same bits; 2-5 % faster in FP32; the 16-bit paths, with
                     // twice the FMAs per load, measured 2-11 % slower and load every texel)
-                    constexpr bool kReuseRow = std::is_same<T, float>::value && NG == 1;
+                    constexpr bool kReuseRow = std::is_same<T, float>::value && NG == 1 && LN == 1;
                     unsigned pa = 0x80000000u;   // no texel address of a band lies within a row of it
                     uint4 r10 = make_uint4(0u, 0u, 0u, 0u), r11 = r10;
-                    for (; i < kleft; ++i, kk += 1.0f) {
+                    for (; i < kleft; i += LN, kk += (float)LN) {
                         const float fym = fmaf(kk, dY, sYm);
                         if (fym >= ylim_m) break;
                         const float fxm = fmaf(kk, dX, sXm);
@@ -497,6 +508,12 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
                             TX::fma(acc[g], TX::weight(wx1 * wy1), q11);
                         }
                     }
+                    if (LN == 2) {
+                        // the slab's samples end where the first lane stopped (samples advance
+                        // monotonically, so the other lane stopped one sample later)
+                        const unsigned pair_mask = 3u << (threadIdx.x & 30);
+                        i = min(min(i, __shfl_xor_sync(pair_mask, i, 1)), kleft);
+                    }
                     k += i;
                 }
             }
@@ -511,11 +528,17 @@ __device__ void fwd_consume(const FwdTiledArgs& a, int cls, int v0, int cnt, int
     T* out = reinterpret_cast<T*>(a.sino);
     const long long vd = (long long)a.V * a.D;
     const long long o = (long long)(v0 + vl) * a.D + d;
-    const bool pairs = a.vec_store != 0 && __activemask() == 0xffffffffu;
+    if (LN == 2) {   // the two lanes' partial sums (every consumer thread is here)
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+#pragma unroll
+            for (int b = 0; b < BG; ++b) acc[g].v[b] += __shfl_xor_sync(0xffffffffu, acc[g].v[b], 1);
+    }
+    const bool pairs = LN == 1 && a.vec_store != 0 && __activemask() == 0xffffffffu;
 #pragma unroll
     for (int gb = 0; gb < NG * BG; ++gb) {
         const int b = gb;   // image b0 + b: group b / BG, slot b % BG
-        const bool mine = active && b0 + b < a.B;
+        const bool mine = active && sub == 0 && b0 + b < a.B;
         const long long idx = (long long)(b0 + b) * vd + o;
         const float val = mine ? epilogue_value<T>(a.ep, a.h * acc[gb / BG].get(gb % BG), idx) : 0.0f;
         if (pairs) {
@@ -611,7 +634,7 @@ __global__ void __launch_bounds__(kFwdThreads, 3) forward_tiled_kernel(const __g
 // Packed variant: the image batch was packed once into 16-byte texels (rows / cols copies, see
 // pack.cu), so the producer warp only bounds each band and copies it with one 4-D TMA load straight
 // into the compute buffer it will become (row pitch = band width); no staging, no repack.
-template <typename T, int MODE, int NG>
+template <typename T, int MODE, int NG, int LN>
 __global__ void __launch_bounds__(kFwdThreads, 3) forward_packed_kernel(const __grid_constant__ CUtensorMap map_rows,
                                                                        const __grid_constant__ CUtensorMap map_cols,
                                                                        const FwdTiledArgs a) {
@@ -686,11 +709,11 @@ __global__ void __launch_bounds__(kFwdThreads, 3) forward_packed_kernel(const __
         return;
     }
     if (NG == 2 && b0 + Texel<T>::BG < a.B)
-        fwd_consume<T, MODE, NG>(a, cls, v0, cnt, d0, b0, full, empty, band_xc0, band_bad, abort_flag, comp_base,
-                                 comp_stride, a.wbox, slab_rng, plane);
+        fwd_consume<T, MODE, NG, LN>(a, cls, v0, cnt, d0, b0, full, empty, band_xc0, band_bad, abort_flag,
+                                     comp_base, comp_stride, a.wbox, slab_rng, plane);
     else   // one group (or a pair whose second group lies past the batch: its plane is never read)
-        fwd_consume<T, MODE, 1>(a, cls, v0, cnt, d0, b0, full, empty, band_xc0, band_bad, abort_flag, comp_base,
-                                comp_stride, a.wbox, slab_rng);
+        fwd_consume<T, MODE, 1, LN>(a, cls, v0, cnt, d0, b0, full, empty, band_xc0, band_bad, abort_flag,
+                                    comp_base, comp_stride, a.wbox, slab_rng);
 }
 
 }  // namespace radon

@@ -288,23 +288,29 @@ radon_status project(const radon_geometry* g, const void* in, void* out, radon_d
     }
     if (forward && algo != RADON_ALGO_PLAIN && ws != nullptr && ws_bytes >= packed_image_bytes(g->n, batch, dt)) {
         // Packed path: pack the batch once, then copy bands of texels straight into shared memory.
+        // one lane per ray first; where no one-lane shape fits and the caller left the shape to the
+        // library, two lanes (half the detectors per CTA: narrower bands).  An explicit views per
+        // CTA keeps one lane per ray.
         const bool fixed = cfg != nullptr && cfg->views_per_cta != 0;
         std::string why;
         bool packed_done = false;
-        for (int i = 0; i < (fixed ? 1 : 4); ++i) {
-            const radon_launch_config c = packed_forward_config(cfg, dt, i);
-            if (!packed_done) {
-                cudaError_t e = launch_pack_images(in, ws, g->n, batch, dt, s);
-                if (e != cudaSuccess) return cuda_fail(e, "pack launch");
-                count_launches(1);
-                packed_done = true;
+        for (int lanes = 1; lanes <= (fixed ? 1 : 2); ++lanes) {
+            for (int i = 0; i < (fixed ? 1 : 4); ++i) {
+                const radon_launch_config c = packed_forward_config(cfg, dt, i);
+                if (!packed_done) {
+                    cudaError_t e = launch_pack_images(in, ws, g->n, batch, dt, s);
+                    if (e != cudaSuccess) return cuda_fail(e, "pack launch");
+                    count_launches(1);
+                    packed_done = true;
+                }
+                st = launch_forward_packed(const_cast<radon_geometry*>(g), ws, out, dt, batch, &c, ep, s, &why,
+                                           lanes);
+                if (st == RADON_OK) {
+                    count_launches(1);
+                    return RADON_OK;
+                }
+                if (st != RADON_ERR_UNSUPPORTED) return fail(st, why);
             }
-            st = launch_forward_packed(const_cast<radon_geometry*>(g), ws, out, dt, batch, &c, ep, s, &why);
-            if (st == RADON_OK) {
-                count_launches(1);
-                return RADON_OK;
-            }
-            if (st != RADON_ERR_UNSUPPORTED) return fail(st, why);
         }
         // no packed shape fits: continue with the paths that need no workspace
     }
@@ -488,13 +494,16 @@ radon_status radon_forward_images_per_cta(const radon_geometry* g, radon_dtype d
     if (batch == 0 || algo == RADON_ALGO_PLAIN || single_image_call(config, batch)) return RADON_OK;
     const bool f16w = dtype == RADON_F16 && config != nullptr && config->weights == RADON_WEIGHTS_F16;
     const bool fixed = config != nullptr && config->views_per_cta != 0;
-    for (int i = 0; i < (fixed ? 1 : 4); ++i) {
-        const radon_launch_config c = packed_forward_config(config, dtype, i);
-        PackedFwdShape sh;
-        std::string why;
-        if (packed_forward_shape(const_cast<radon_geometry*>(g), dtype, batch, &c, f16w, &sh, &why) == RADON_OK) {
-            *images = sh.NG * (dtype == RADON_F32 ? 4 : 8);
-            return RADON_OK;
+    for (int lanes = 1; lanes <= (fixed ? 1 : 2); ++lanes) {
+        for (int i = 0; i < (fixed ? 1 : 4); ++i) {
+            const radon_launch_config c = packed_forward_config(config, dtype, i);
+            PackedFwdShape sh;
+            std::string why;
+            if (packed_forward_shape(const_cast<radon_geometry*>(g), dtype, batch, &c, f16w, lanes, &sh, &why) ==
+                RADON_OK) {
+                *images = sh.NG * (dtype == RADON_F32 ? 4 : 8);
+                return RADON_OK;
+            }
         }
     }
     return RADON_OK;

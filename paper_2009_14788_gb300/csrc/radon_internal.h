@@ -134,19 +134,21 @@ radon_status launch_forward_tiled(radon_geometry* g, const void* img, void* sino
                                   std::string* why);
 
 // forward_tiled.cu: the packed forward's launch shape for a call (views per CTA from cfg or 8, image
-// groups per CTA, rows per slab, band width, ring stages, shared memory); RADON_ERR_UNSUPPORTED with
-// the reason if the geometry does not fit it.  `fp16_weights`: the FP16-weight mode will run.
+// groups per CTA, rows per slab, band width, ring stages, shared memory) with `lanes` (1 or 2) threads
+// per ray; RADON_ERR_UNSUPPORTED with the reason if the geometry does not fit it.  `fp16_weights`: the
+// FP16-weight mode will run.  Two lanes per ray halve the detectors of a CTA (narrower bands, for views
+// too sparse or detectors too wide for one lane) and take one texel group.
 struct PackedFwdShape {
-    int G, Dt, NG, R, wbox, stages;
+    int G, Dt, NG, LN, R, wbox, stages;
     size_t smem;
 };
 radon_status packed_forward_shape(radon_geometry* g, radon_dtype dt, int batch, const radon_launch_config* cfg,
-                                  bool fp16_weights, PackedFwdShape* out, std::string* why);
+                                  bool fp16_weights, int lanes, PackedFwdShape* out, std::string* why);
 
 // forward_tiled.cu: the packed-input forward (the workspace already holds pack_images' output)
 radon_status launch_forward_packed(radon_geometry* g, const void* packed, void* sino, radon_dtype dt, int batch,
                                    const radon_launch_config* cfg, const Epilogue& ep, cudaStream_t s,
-                                   std::string* why);
+                                   std::string* why, int lanes = 1);
 
 // batch_plan.cu: one image (a batch-1 call) through the uneven-batch plan's kernels -- one texel load
 // per forward sample, one weight per adjoint candidate -- instead of a batch-interleaved group that

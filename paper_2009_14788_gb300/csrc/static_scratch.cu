@@ -83,15 +83,17 @@ extern "C" RADON_API radon_status radon_forward_static_scratch(const radon_geome
     count_launches(1);
     static const int kViews[4] = {8, 4, 2, 1};
     std::string why;
-    for (int i = 0; i < 4; ++i) {
-        radon_launch_config c = {RADON_ALGO_TILED, kViews[i], 0, 0, 0, 0, 0};
-        st = launch_forward_packed(const_cast<radon_geometry*>(geometry), scratch, sino, dtype, batch, &c,
-                                   identity_epilogue(), s, &why);
-        if (st == RADON_OK) {
-            count_launches(1);
-            return RADON_OK;
+    for (int lanes = 1; lanes <= 2; ++lanes) {
+        for (int i = 0; i < 4; ++i) {
+            radon_launch_config c = {RADON_ALGO_TILED, kViews[i], 0, 0, 0, 0, 0};
+            st = launch_forward_packed(const_cast<radon_geometry*>(geometry), scratch, sino, dtype, batch, &c,
+                                       identity_epilogue(), s, &why, lanes);
+            if (st == RADON_OK) {
+                count_launches(1);
+                return RADON_OK;
+            }
+            if (st != RADON_ERR_UNSUPPORTED) return fail(st, why);
         }
-        if (st != RADON_ERR_UNSUPPORTED) return fail(st, why);
     }
     // No packed shape fits this geometry: the paths that need no scratch at all serve it.
     return radon_forward(geometry, img, sino, dtype, batch, stream);

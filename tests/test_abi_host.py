@@ -369,6 +369,16 @@ def test_forward_images_per_cta_on_the_host():
     assert forward_images_per_cta(sparse, f16, 16, launch_config("tiled", views_per_cta=8, images_per_cta=16)) == 0
     assert forward_images_per_cta(sparse, f16, 16, launch_config("tiled", views_per_cta=2)) == 16
     assert forward_images_per_cta(sparse, f16, 16, launch_config("tiled", views_per_cta=8, rows_per_slab=8)) == 16
+    # every 30th view of the fan (15 degrees apart): no one-lane shape fits a TMA box; two lanes per ray
+    # (half the detectors per CTA) take one texel group at two views per CTA or one
+    sub = workload_geometry_args(WORKLOADS["fan_b16_n512_v720_d1024"])
+    sub["angles"] = np.asarray(sub["angles"])[::30]
+    kind = sub.pop("kind")
+    gs = Geometry(kind, host_only=True, **sub)
+    assert forward_images_per_cta(gs, f16, 16) == 8
+    assert forward_images_per_cta(gs, f32, 3) == 4
+    assert forward_images_per_cta(gs, f16, 16, launch_config("tiled", views_per_cta=8)) == 0
+    assert forward_images_per_cta(gs, f16, 16, launch_config(images_per_cta=16)) == 0
     n = ctypes.c_int(-1)
     assert L.radon_forward_images_per_cta(g.handle, L.RADON_F16, -1, None, ctypes.byref(n)) == L.RADON_ERR_INVALID_ARG
     assert L.radon_forward_images_per_cta(g.handle, L.RADON_F16, 4, None, None) == L.RADON_ERR_INVALID_ARG

@@ -13,7 +13,7 @@ import torch
 
 import oracle as O
 from gpu_cases import TOL_F32, make, rel_l2, to_dev, to_np, within_16
-from paper_2009_14788_gb300 import _lib as L, forward_raw, launch_config
+from paper_2009_14788_gb300 import _lib as L, forward_images_per_cta, forward_raw, launch_config
 
 pytestmark = pytest.mark.gpu
 
@@ -134,3 +134,23 @@ def test_two_image_groups_per_cta_give_the_same_bits(dtype, batch):
         assert rel_l2(to_np(two[:3]), ref) <= TOL_F32
     else:
         assert within_16(to_np(two[:3]), ref, dtype)
+
+
+@pytest.mark.parametrize("dtype", DTYPES, ids=["f32", "f16", "bf16"])
+@pytest.mark.parametrize("batch", [3, 16])
+def test_sparse_views_take_two_lanes_per_ray(dtype, batch):
+    """Every 30th view of the fan (15 degrees apart, 1024 detectors over a 512^2 image): no CTA of 256
+    detector rays has a band that fits one TMA box, so two lanes share each ray (128 rays per CTA:
+    narrower bands), each summing every other sample of every slab, and the packed path still serves
+    the call (a packing pass and the projection) within the oracle's gates."""
+    g, og = make("fan_n512_sub")
+    assert forward_images_per_cta(g, dtype, batch) == (4 if dtype == torch.float32 else 8)
+    x = to_dev(np.random.default_rng(45).uniform(0.0, 1.0, (batch, g.n, g.n)), dtype)
+    y, launches = _forward(g, x, launch_config())
+    assert launches == 2
+    ref = O.forward(og, to_np(x))
+    if dtype == torch.float32:
+        assert rel_l2(to_np(y), ref) <= TOL_F32
+    else:
+        assert within_16(to_np(y), ref, dtype)
+    _clean()

@@ -369,14 +369,17 @@ def test_forward_paired_view_phases_give_the_same_bits(case, dtype, ws):
         assert rel_l2(got, ref) <= TOL_16
 
 
-def test_forward_tiled_refuses_sparse_wide_views_auto_serves():
-    """Every 30th view of the 512^2 fan set (15 degrees apart): no CTA shape keeps the working band
-    inside one TMA box, so TILED refuses and AUTO serves the request with the plain kernel."""
+def test_forward_sparse_wide_views_take_two_lanes_per_ray():
+    """Every 30th view of the 512^2 fan set (15 degrees apart): no CTA of one thread per ray keeps the
+    working band inside one TMA box.  An explicit views per CTA (one thread per ray) is refused; left
+    to the library, two threads share each ray (half the detectors per CTA) and the packed kernel
+    serves the request, TILED and AUTO alike."""
     g, og = make("fan_n512_sub")
     x = _rand_images(g.n, 2, 91)
     with pytest.raises(L.RadonError, match="TMA box"):
-        forward_raw(g, to_dev(x), launch_config("tiled"))
-    assert rel_l2(to_np(forward_raw(g, to_dev(x))), O.forward(og, x)) <= TOL_F32
+        forward_raw(g, to_dev(x), launch_config("tiled", views_per_cta=8))
+    for cfg in (launch_config("tiled"), None):
+        assert rel_l2(to_np(forward_raw(g, to_dev(x), cfg)), O.forward(og, x)) <= TOL_F32
 
 
 @pytest.mark.parametrize("case", ["parallel_ragged", "fan_ragged", "one_pixel"])
