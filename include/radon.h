@@ -212,7 +212,8 @@ enum { RADON_WEIGHTS_DEFAULT = 0, RADON_WEIGHTS_F32 = 1, RADON_WEIGHTS_F16 = 2 }
 
 typedef struct {
     int algo;            /* radon_algo */
-    int views_per_cta;   /* TILED forward: views per CTA (0 = default) */
+    int views_per_cta;   /* TILED forward: views per CTA (0 = default: 8, 4, 2, 1 tried in turn, then with two
+                            threads per ray where no one-thread shape fits; a fixed value keeps one) */
     int rows_per_slab;   /* TILED forward: image rows staged per step (0 = default) */
     int images_per_cta;  /* TILED: images sharing the geometry work in one CTA (0 = default; the packed
                             adjoint takes 8, 16 or 32, the staged one 4, 8 or 16; the packed forward one
